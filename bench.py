@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Throughput of the randomized Tikhonov solver on one GB300 (or N replicas).
+
+Workload (default): ridge_over_262144x2048_f64 -- A = U diag(sigma) V^T with
+m = 2^18, n = 2048 (4 GiB float64), sigma log-spaced 1..1e-8, b = A x + 1e-3
+noise, N = 32 lambda log-spaced 1e-8..1, SRHT sketch s = 4n.  One step = one
+full pass of the path for all 32 lambda (sketch, Gram, 32 Cholesky factors,
+batched preconditioned LSQR; the mixed form adds the float64 refinement).
+
+Timed: the batched mixed-precision solve (float32 LSQR + float64 refinement),
+inputs resident in HBM.  Reported beside it, on the same inputs: the plain
+float64 batched solve and the plain float64 one-lambda-at-a-time solve, and
+the oracle's CPU cost on a bounded sample.
+
+Prints one JSON line.  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lambda-solves/s to 1e-10 rel. error (batched mixed vs plain FP64); A-stream HBM GB/s"
+UNIT = "lambda-solves/s"
+WORKLOAD = "ridge_over_262144x2048_f64"
+
+# FP64 and FP32 SIMT peaks derived from unit counts and the maximum SM clock:
+# 152 SMs x 2 DFMA/clk (FP64) or 128 FFMA/clk (FP32) x 2 flop x 2.07 GHz.
+PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------ oracle arm ---
+def oracle_iteration_sample(A_np, b_np, lam, iters, threads):
+    """Seconds per LSQR iteration of the oracle on the full workload (one lambda).
+
+    The preconditioned operator costs the same for any upper triangular R, so
+    the sample uses R = sqrt(1 + lambda) I built on the CPU."""
+    import oracle
+    n = A_np.shape[1]
+    R = np.eye(n) * math.sqrt(1.0 + lam)
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    t0 = time.perf_counter()
+    oracle.lsqr_over_chol(A_np, b_np, lam, R, 1e-300, iters)
+    return (time.perf_counter() - t0) / iters
+
+
+def oracle_iters_per_solve():
+    """The oracle's own LSQR iteration count at the smallest lambda on a reduced
+    problem of the same family (SRHT s = 4n, sigma 1..1e-8, lambda 1e-8)."""
+    import oracle
+    from paper_2203_07329_gb300 import datagen
+    p = datagen.make_ridge_problem(4096, 64, datagen.spectrum("log", 64, hi=1.0, lo=1e-8),
+                                   datagen.log_lambdas(1, 1e-8, 1e-8), seed=5)
+    _, it, _, _ = oracle.alg1(p.A.numpy(), p.b.numpy(), np.array([1e-8]), 0, 256, 1, 1e-14, 500)
+    return int(it[0])
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle as it stands, bounded samples of the workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    import oracle
+    from paper_2203_07329_gb300 import datagen
+    oracle.build()
+    threads = 1
+    m, n = (args.m, args.n)
+    prob, w = datagen.workload_problem(WORKLOAD, device="cpu", m=m, n=n)
+    A_np = prob.A.numpy()
+    b_np = prob.b.numpy()
+    lam = float(prob.lambdas[0])
+    ips = oracle_iters_per_solve()
+    for _ in range(args.warmup):
+        oracle_iteration_sample(A_np, b_np, lam, 1, threads)
+    times = [oracle_iteration_sample(A_np, b_np, lam, 1, threads) for _ in range(args.steps)]
+    t_iter = float(np.mean(times))
+    value = 1.0 / (t_iter * ips)
+    sample = (f"oracle LSQR iterations (one lambda, full {m}x{n} float64 A, plain C loops, {threads} thread), "
+              f"{args.steps} timed; lambda-solve = {ips} iterations (oracle's own count on the same family); "
+              "sketch, Gram and Cholesky setup excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": m, "n": n, "N": w["N"], "sketch": "srht", "s": w["s"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm ---
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tikhonov", choices=["tikhonov", "reference"])
+    ap.add_argument("--m", type=int, default=262144)
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 comparison solves")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    from paper_2203_07329_gb300 import build, datagen
+    build.build()
+    from paper_2203_07329_gb300 import tikhonov as tk
+
+    m, n = args.m, args.n
+    prob, w = datagen.workload_problem(WORKLOAD, device="cuda", m=m, n=n)
+    A, b = prob.A, prob.b
+    lams = prob.lambdas.numpy()
+    N = len(lams)
+    s = w["s"]
+    o_mixed = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, precision=tk.TK_PREC_MIXED)
+    o_fp64 = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, tol=1e-14)
+    o_fp64_one = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, tol=1e-14,
+                                 schedule=tk.TK_SCHED_ONE_AT_A_TIME)
+    stream = torch.cuda.current_stream()
+    work = torch.empty(max(tk.workspace_size(tk.make_problem(A, b), N, o) for o in (o_mixed, o_fp64, o_fp64_one)),
+                       dtype=torch.uint8, device="cuda")
+    X = torch.empty((N, n), dtype=torch.float64, device="cuda")
+
+    def step(o, Xo=X):
+        return tk.tk_solve(A, b, lams, o, work=work, X=Xo, stream=stream)
+
+    for _ in range(args.warmup):
+        res = step(o_mixed)
+    barrier()
+    # ---- timed region: K batched mixed steps, inputs resident in HBM
+    clocks = ClockSampler(local)
+    clocks.start()
+    tk.tk_profile_enable(True)
+    tk.tk_profile_collect()
+    launches0 = tk.tk_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        res = step(o_mixed)
+    ev1.record(stream)
+    barrier()
+    launches = tk.tk_launch_count() - launches0
+    prof = tk.tk_profile_collect()
+    tk.tk_profile_enable(False)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * N / (ms / 1e3)
+    X_mixed = X.clone()
+    info_mixed = res.info
+
+    # ---- e2e: the same call with host buffers, copies inside the timed region
+    A_host = A.cpu().pin_memory()
+    b_host = b.cpu().pin_memory()
+    X_host = torch.empty((N, n), dtype=torch.float64).pin_memory()
+    A_dev = torch.empty_like(A)
+    b_dev = torch.empty_like(b)
+    barrier()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        A_dev.copy_(A_host, non_blocking=True)
+        b_dev.copy_(b_host, non_blocking=True)
+        tk.tk_solve(A_dev, b_dev, lams, o_mixed, work=work, X=X, stream=stream)
+        X_host.copy_(X, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    del A_dev, A_host
+
+    # ---- plain float64 comparisons on the same inputs (one step each)
+    extra = {}
+    if not args.no_fp64:
+        for key, o in (("fp64_batched", o_fp64), ("fp64_one_at_a_time", o_fp64_one)):
+            X64 = torch.empty((N, n), dtype=torch.float64, device="cuda")
+            barrier()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            r64 = step(o, X64)
+            a1.record(stream)
+            barrier()
+            t64 = a0.elapsed_time(a1)
+            extra[key] = {"value": N / (t64 / 1e3), "ms_per_step": t64,
+                          "iters_mean": float(np.mean([q["iters"] for q in r64.info]))}
+            if key == "fp64_batched":
+                d = (X_mixed - X64).norm(dim=1) / X64.norm(dim=1)
+                extra["max_rel_diff_mixed_vs_fp64"] = float(d.max())
+        extra["speedup_mixed_vs_fp64_one_at_a_time"] = value / ws / extra["fp64_one_at_a_time"]["value"]
+        extra["speedup_mixed_vs_fp64_batched"] = value / ws / extra["fp64_batched"]["value"]
+
+    # ---- roofline of the dominant phase (live events over the timed region)
+    peaks, peak_src = load_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, st = dom
+    fp64_phases = {"gram", "cholesky", "svd", "refine_residual64", "refine_normal64", "sketch"}
+    per_launch_ms = st["ms"] / max(st["launches"], 1)
+    achieved = st["flops"] / (st["ms"] / 1e3) / 1e12 if st["ms"] > 0 else 0.0
+    peak = PEAK_FP64_TFLOPS if name in fp64_phases else PEAK_FP32_TFLOPS
+    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "per_launch_ms": per_launch_ms, "launches": st["launches"],
+                "peak_source": "derived from unit counts and max clock (FP64 2 DFMA/clk/SM, FP32 128 FFMA/clk/SM)"}
+    a_stream_gbs = None
+    lsqr_bytes = prof["A_times_W"]["bytes"] + prof["At_times_U"]["bytes"] + prof["refine_residual64"]["bytes"] + \
+        prof["refine_normal64"]["bytes"]
+    lsqr_ms = prof["A_times_W"]["ms"] + prof["At_times_U"]["ms"] + prof["refine_residual64"]["ms"] + \
+        prof["refine_normal64"]["ms"]
+    if lsqr_ms > 0:
+        a_stream_gbs = lsqr_bytes / (lsqr_ms / 1e3) / 1e9
+    phases = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                  "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0}
+              for k, v in prof.items() if v["launches"]}
+
+    # ---- CPU oracle sample (rank 0 only, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        try:
+            import oracle
+            oracle.build()
+            A_np = A.cpu().numpy()
+            b_np = b.cpu().numpy()
+            ips = oracle_iters_per_solve()
+            t_it = np.mean([oracle_iteration_sample(A_np, b_np, float(lams[0]), 1, 1) for _ in range(2)])
+            cpu = {"value": 1.0 / (t_it * ips), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"2 oracle LSQR iterations on the full {m}x{n} float64 A (one lambda, 1 thread); "
+                             f"lambda-solve = {ips} iterations; setup excluded"}
+        except Exception as ex:  # the baseline is reported, never the target
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "m": m, "n": n, "N": N, "sketch": "srht", "s": s,
+                           "precision": "mixed (float32 LSQR, float64 refinement, Gram and Cholesky)",
+                           "schedule": "batched", "l2": "inputs larger than L2 (A is 4 GiB)",
+                           "parallelism": f"{ws} independent replicas" if ws > 1 else "1 GPU"},
+                "roofline": roofline, "a_stream_gbs": a_stream_gbs, "phases": phases,
+                "cpu_baseline": cpu,
+                "e2e": {"value": ws * N / (e2e_ms / 1e3), "unit": UNIT,
+                        "h2d_bytes_per_step": int(A.numel() * A.element_size() + b.numel() * 8),
+                        "d2h_bytes_per_step": int(N * n * 8)},
+                "gpu_launches": int(launches), "clocks": clk,
+                "iters_mean": float(np.mean([q["iters"] for q in info_mixed])),
+                "refine_steps_max": int(max(q["refine_steps"] for q in info_mixed)),
+                "peaks_source": peak_src}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

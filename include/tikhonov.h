@@ -1,0 +1,226 @@
+/*
+ * tikhonov.h -- C ABI of the GB300 (sm_103a) library for randomized Tikhonov
+ * regularization: min ||A x - b||^2 + lambda ||x||^2 for a list of
+ * regularization parameters lambda_1..lambda_N (Meier & Nakatsukasa,
+ * "Randomized algorithms for Tikhonov regularization in Linear Least Squares").
+ *
+ * The calls follow the paper's problem statement (Section 1, problems (1.2)-(1.4)):
+ * A, b, the lambda_i and a tolerance in; x_{lambda_i} and iteration counts out.
+ * A is sketched once (Section 2.1.1: SRHT or Gaussian embedding), a
+ * preconditioner is formed per lambda_i from the partly exact sketch
+ * (Algorithm 1 / 2: Cholesky of C + lambda_i I; Algorithm 3: the low-rank
+ * Woodbury form of Section 3.1), and preconditioned LSQR runs for every lambda_i.
+ *
+ * Conventions shared by every call:
+ *  - Matrices are row-major.  A is m x n with row stride lda >= n (elements).
+ *  - "device" pointers are CUDA device memory of the current device; "host"
+ *    pointers are ordinary host memory.  The caller owns all memory passed in.
+ *    The library never allocates device memory: every call that needs scratch
+ *    takes a caller-provided device workspace whose size tk_workspace_size()
+ *    (or the call's own size query) returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Kernels are issued on it in order.  Calls that return host results
+ *    synchronize the stream before returning.
+ *  - The return value is a tk_status.  Argument errors are detected on the
+ *    host before any launch (TK_EINVAL, nothing written).  TK_ECUDA reports a
+ *    CUDA error; tk_last_error() returns its text.
+ *  - m >= n selects the overdetermined algorithms (1 and 3); m < n selects the
+ *    underdetermined Algorithm 2.
+ */
+#ifndef TIKHONOV_H
+#define TIKHONOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define TK_API __attribute__((visibility("default")))
+#else
+#define TK_API
+#endif
+
+typedef enum {
+  TK_OK = 0,
+  TK_EINVAL = 1,    /* invalid argument (checked on the host, nothing launched) */
+  TK_ENOMEM = 2,    /* workspace smaller than the size query returned */
+  TK_ENOTSPD = 3,   /* Cholesky breakdown: C + lambda I not numerically positive definite */
+  TK_ENOCONV = 4,   /* LSQR reached maxiter (or refinement reached max_refine) */
+  TK_ENUMERIC = 5,  /* NaN/Inf met in the recurrences */
+  TK_ETIMEOUT = 6,  /* a bounded device-side wait gave up */
+  TK_ECUDA = 7      /* CUDA runtime error, see tk_last_error() */
+} tk_status;
+
+typedef enum { TK_F64 = 0, TK_F32 = 1 } tk_dtype;
+typedef enum { TK_SKETCH_SRHT = 0, TK_SKETCH_GAUSS = 1 } tk_sketch;
+typedef enum { TK_PRECOND_CHOL = 0, TK_PRECOND_LOWRANK = 1 } tk_precond;
+typedef enum { TK_PREC_FP64 = 0, TK_PREC_MIXED = 1 } tk_precision;
+typedef enum { TK_SCHED_BATCHED = 0, TK_SCHED_ONE_AT_A_TIME = 1 } tk_schedule;
+
+/* Problem (1.2): device A (m x n, row stride lda, dtype) and device b (m, float64). */
+typedef struct {
+  int64_t m, n, lda;
+  tk_dtype dtype;
+  const void* A;
+  const double* b;
+} tk_problem;
+
+/* Options.  tk_opts_default() fills the defaults given in brackets. */
+typedef struct {
+  tk_sketch sketch;       /* [SRHT] embedding of Section 2.1.1 */
+  int64_t s;              /* sketch size; 0 = 4 * min(m, n) for Cholesky, see alpha for low rank [0] */
+  tk_precond precond;     /* [CHOL] Algorithm 1/2, or LOWRANK = Algorithm 3 */
+  double alpha;           /* [2] oversampling of Algorithm 3: s_i = alpha * ceil(sd_i) */
+  tk_precision precision; /* [FP64] or MIXED (FP32 LSQR + FP64 refinement) */
+  double tol;             /* [1e-14] LSQR stopping tolerance (Paige-Saunders atol = btol) */
+  int maxiter;            /* [500] LSQR iteration cap per lambda */
+  int max_refine;         /* [6] refinement steps of the MIXED form */
+  double inner_tol;       /* [1e-6] FP32 LSQR tolerance inside the MIXED refinement */
+  double refine_tol;      /* [1e-11] MIXED stops when ||d|| <= refine_tol ||x|| */
+  uint64_t seed;          /* [1] Philox key of every draw */
+  tk_schedule schedule;   /* [BATCHED]: all lambda advance together; ONE_AT_A_TIME: one lambda per LSQR run */
+} tk_opts;
+
+/* Per-lambda report. */
+typedef struct {
+  int iters;          /* LSQR iterations (summed over refinement steps for MIXED) */
+  int refine_steps;   /* MIXED: corrections applied; FP64: 0 */
+  int istop;          /* Paige-Saunders stop reason of the last LSQR run: 1 test 1, 2 test 2, 7 maxiter */
+  int64_t rank;       /* LOWRANK: truncation s_i of Algorithm 3 step 5; else 0 */
+  double rnorm;       /* LSQR estimate of ||B x - b_hat|| (last run) */
+  double arnorm;      /* LSQR estimate of ||M^T r|| (last run) */
+  double ne_norm;     /* MIXED: ||A^T (A x - b) + lambda x|| in float64 at the last refinement check; else 0 */
+  tk_status status;
+} tk_info;
+
+TK_API tk_status tk_opts_default(tk_opts* o);
+TK_API const char* tk_status_str(tk_status s);
+TK_API const char* tk_last_error(void);
+
+/* Bytes of device workspace tk_solve needs for this problem, N and options. */
+TK_API tk_status tk_workspace_size(const tk_problem* p, int N, const tk_opts* o, size_t* bytes);
+
+/*
+ * tk_solve -- x_{lambda_i} for i = 0..N-1 (problem (1.2); Algorithms 1, 2, 3).
+ *   lambdas: host, N values > 0 (any order; results are returned in input order).
+ *   X:       device, N x n float64 row-major: row i = x_{lambda_i}.
+ *   info:    host, N entries (may be NULL).
+ *   work:    device workspace of at least tk_workspace_size() bytes.
+ * Synchronizes `stream` before returning.  Returns the worst per-lambda status
+ * (TK_OK < TK_ENOCONV < TK_ENUMERIC < TK_ENOTSPD); results of the other lambdas
+ * are still written.
+ */
+TK_API tk_status tk_solve(const tk_problem* p, const double* lambdas, int N, const tk_opts* o, void* work,
+                          size_t work_bytes, void* stream, double* X, tk_info* info);
+
+/*
+ * tk_solve_batched -- P independent problems (uneven m, n) with N lambdas each
+ * (Section 2.1.1: "the for loop can trivially be parallelized", extended
+ * across problems).  lambdas: host P x N.  X[p]: device N x n_p float64.
+ * info: host P x N (may be NULL).  The workspace size is
+ * tk_workspace_size_batched().
+ */
+TK_API tk_status tk_workspace_size_batched(const tk_problem* ps, int P, int N, const tk_opts* o, size_t* bytes);
+TK_API tk_status tk_solve_batched(const tk_problem* ps, int P, const double* lambdas, int N, const tk_opts* o,
+                                  void* work, size_t work_bytes, void* stream, double* const* X, tk_info* info);
+
+/* ---- introspection calls for parity tests (each step of the path on its own) ---- */
+
+/*
+ * tk_sketch_draw -- the integer draws of the SRHT (Section 2.1.1): signs d
+ * (mp values in {-1, +1}, Philox stream 0) and the s sampled rows of S
+ * (ascending; the s smallest (64-bit key, row) pairs of Philox stream 1).
+ *   signs: device int8[mp] (may be NULL); rows: device int64[s] (may be NULL).
+ *   work:  device, at least tk_sketch_draw_workspace(mp) bytes.
+ */
+TK_API size_t tk_sketch_draw_workspace(int64_t mp);
+TK_API tk_status tk_sketch_draw(uint64_t seed, int64_t mp, int64_t s, int8_t* signs, int64_t* rows, void* work,
+                                size_t work_bytes, void* stream);
+
+/*
+ * tk_sketch_apply -- Y = X A (m >= n: Y is s x n, Algorithm 1 step 2) or
+ * Y = A X (m < n: Y is m x s, Algorithm 2 step 2), float64 device output.
+ * SRHT: X = sqrt(mp/s) S (H/sqrt(mp)) D with mp the next power of two of the
+ * long dimension.  Gaussian: X has N(0, 1/s) entries from Philox stream 2.
+ * work: device, at least tk_sketch_apply_workspace() bytes.
+ */
+TK_API tk_status tk_sketch_apply_workspace(const tk_problem* p, const tk_opts* o, size_t* bytes);
+TK_API tk_status tk_sketch_apply(const tk_problem* p, const tk_opts* o, double* Y, void* work, size_t work_bytes,
+                                 void* stream);
+
+/*
+ * tk_gram -- C = Y^T Y (Y r x c, C c x c; Algorithm 1 step 3) when
+ * transpose_first != 0, else C = Y Y^T (C r x r; Algorithm 2 step 3).
+ * All device float64, row-major.
+ */
+TK_API tk_status tk_gram(const double* Y, int64_t r, int64_t c, int transpose_first, double* C, void* stream);
+
+/*
+ * tk_cholesky_shifted -- R_i = chol(C + lambda_i I) for i = 0..N-1
+ * (Algorithm 1 step 4), upper triangular, float64.
+ *   C: device n x n (symmetric, only the upper triangle is read).
+ *   lambdas: host N.   R: device N x n x n (zeros below the diagonal).
+ *   breakdown: host N (may be NULL): 0, or j+1 if the pivot of row j was not positive.
+ *   work: device, tk_cholesky_workspace(n, N) bytes.
+ */
+TK_API size_t tk_cholesky_workspace(int64_t n, int N);
+TK_API tk_status tk_cholesky_shifted(const double* C, int64_t n, const double* lambdas, int N, double* R,
+                                     int* breakdown, void* work, size_t work_bytes, void* stream);
+
+/*
+ * tk_sketch_svd -- [~, Sigma, V] = svd(Y, 'econ') of Algorithm 3 step 4 by
+ * one-sided Jacobi on Y^T (no Gram matrix is formed).  Y: device s x n
+ * float64 with s <= n.  sigma: device s (descending).  V: device n x s.
+ * work: device, tk_sketch_svd_workspace(s, n) bytes.  sweeps: host (may be NULL).
+ */
+TK_API size_t tk_sketch_svd_workspace(int64_t s, int64_t n);
+TK_API tk_status tk_sketch_svd(const double* Y, int64_t s, int64_t n, double* sigma, double* V, int* sweeps,
+                               void* work, size_t work_bytes, void* stream);
+
+/*
+ * tk_lowrank_ranks -- Section 3.1.2 and Algorithm 3 step 5: sd_i =
+ * sum_j 1/(1 + lambda_i/sigma_j^2) (float64, ascending j, no contraction) and
+ * s_i = min(s, ceil(alpha * ceil(sd_i))).  sigma: device s.  lambdas: host N.
+ * sd, ranks: host N.  work: device, tk_lowrank_ranks_workspace(N) bytes.
+ */
+TK_API size_t tk_lowrank_ranks_workspace(int N);
+TK_API tk_status tk_lowrank_ranks(const double* sigma, int64_t s, const double* lambdas, int N, double alpha,
+                                  double* sd, int64_t* ranks, void* work, size_t work_bytes, void* stream);
+
+/* ---- phase profiler (tracing) ----
+ * When enabled, each instrumented launch is bracketed by CUDA events on its
+ * stream and tagged with its algorithmic flops and bytes (the counts of the
+ * operation itself, not of the implementation).  tk_profile_collect() waits
+ * for the recorded events, fills out[TK_PHASE_COUNT] with per-phase totals
+ * and clears the records.  Not for use inside CUDA graph capture. */
+enum {
+  TK_PHASE_SKETCH = 0,        /* Y = XA (draws, FWHT passes / Gaussian GEMM) */
+  TK_PHASE_GRAM = 1,          /* C = Y^T Y */
+  TK_PHASE_CHOLESKY = 2,      /* R_i = chol(C + lambda_i I), all lambda */
+  TK_PHASE_SVD = 3,           /* one-sided Jacobi SVD of Y */
+  TK_PHASE_PRECOND = 4,       /* R^-1 / R^-T (or low-rank) applies inside LSQR */
+  TK_PHASE_AW = 5,            /* the product with A of every LSQR step (A R^-1 v for all lambda) */
+  TK_PHASE_ATU = 6,           /* the product with A^T of every LSQR step */
+  TK_PHASE_RES64 = 7,         /* MIXED: float64 residual b - A x */
+  TK_PHASE_NE64 = 8,          /* MIXED: float64 A^T (b - A x) */
+  TK_PHASE_COUNT = 9
+};
+typedef struct {
+  double ms;      /* summed event time */
+  double flops;   /* summed algorithmic flops */
+  double bytes;   /* summed algorithmic bytes (one read of each operand, one write of each result) */
+  int launches;
+} tk_phase_stats;
+TK_API const char* tk_phase_name(int phase);
+/* Number of kernel launches the library has issued in this process so far. */
+TK_API unsigned long long tk_launch_count(void);
+TK_API tk_status tk_profile_enable(int on);
+TK_API tk_status tk_profile_collect(tk_phase_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TIKHONOV_H */

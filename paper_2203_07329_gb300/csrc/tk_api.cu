@@ -1,0 +1,773 @@
+// C ABI of libtikhonov: argument checks, workspace planning and the order of
+// the steps of Algorithms 1, 2 and 3 (and the mixed-precision refinement
+// around Algorithm 1).  Every numerical step runs in the kernels of the other
+// translation units; this file only sequences them.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "tk_lsqr.cuh"
+
+namespace tk {
+
+thread_local char g_err[512] = "";
+
+void set_error(cudaError_t e, const char* file, int line) {
+  snprintf(g_err, sizeof g_err, "%s (%s:%d)", cudaGetErrorString(e), file, line);
+}
+void set_error_msg(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
+namespace {
+
+tk_status einval(const char* msg) {
+  set_error_msg(msg);
+  return TK_EINVAL;
+}
+
+int severity(tk_status s) {
+  switch (s) {
+    case TK_OK: return 0;
+    case TK_ENOCONV: return 1;
+    case TK_ENUMERIC: return 2;
+    case TK_ENOTSPD: return 3;
+    default: return 4;
+  }
+}
+tk_status worse(tk_status a, tk_status b) { return severity(b) > severity(a) ? b : a; }
+
+// ---------------------------------------------------------------- plan -----
+struct Plan {
+  int64_t m = 0, n = 0, lda = 0;
+  tk_dtype dt = TK_F64;
+  bool under = false;
+  int64_t L = 0, c = 0;  // long and short dimension
+  int64_t s = 0;
+  int64_t np = 0;        // Cholesky order padded to the 64 tile
+  int N = 0, N_cap = 0;
+  tk_opts o{};
+  bool mixed = false, lowrank = false;
+};
+
+constexpr int64_t kMaxShort = 8192;
+constexpr int64_t kMaxLong = (int64_t(1) << 30);
+
+tk_status check_opts(const tk_opts* o) {
+  if (!o) return einval("options pointer is NULL");
+  if (o->sketch != TK_SKETCH_SRHT && o->sketch != TK_SKETCH_GAUSS) return einval("unknown sketch kind");
+  if (o->precond != TK_PRECOND_CHOL && o->precond != TK_PRECOND_LOWRANK) return einval("unknown preconditioner");
+  if (o->precision != TK_PREC_FP64 && o->precision != TK_PREC_MIXED) return einval("unknown precision");
+  if (o->schedule != TK_SCHED_BATCHED && o->schedule != TK_SCHED_ONE_AT_A_TIME) return einval("unknown schedule");
+  if (!(o->tol > 0.0) || !std::isfinite(o->tol)) return einval("tol must be a positive finite number");
+  if (o->maxiter < 1) return einval("maxiter must be >= 1");
+  if (o->s < 0) return einval("sketch size s must be >= 0");
+  if (o->precond == TK_PRECOND_LOWRANK && !(o->alpha >= 1.0 && std::isfinite(o->alpha)))
+    return einval("alpha must be >= 1");
+  if (o->precision == TK_PREC_MIXED) {
+    if (o->max_refine < 1) return einval("max_refine must be >= 1");
+    if (!(o->inner_tol > 0.0) || !(o->refine_tol > 0.0)) return einval("inner_tol and refine_tol must be > 0");
+  }
+  return TK_OK;
+}
+
+tk_status make_plan(const tk_problem* p, int N, const tk_opts* o, Plan& P) {
+  if (!p) return einval("problem pointer is NULL");
+  TK_TRY(check_opts(o));
+  if (p->m < 1 || p->n < 1) return einval("m and n must be >= 1");
+  if (p->lda < p->n) return einval("lda must be >= n");
+  if (p->dtype != TK_F64 && p->dtype != TK_F32) return einval("unknown dtype");
+  if (N < 0) return einval("N must be >= 0");
+  P.m = p->m;
+  P.n = p->n;
+  P.lda = p->lda;
+  P.dt = p->dtype;
+  P.under = p->m < p->n;
+  P.L = std::max(p->m, p->n);
+  P.c = std::min(p->m, p->n);
+  if (P.c > kMaxShort) return einval("min(m, n) above 8192 is not supported");
+  if (P.L > kMaxLong) return einval("max(m, n) above 2^30 is not supported");
+  P.o = *o;
+  P.N = N;
+  P.mixed = o->precision == TK_PREC_MIXED;
+  P.lowrank = o->precond == TK_PRECOND_LOWRANK;
+  if (P.under && P.lowrank) return einval("the low-rank preconditioner is built for m >= n (Algorithm 3)");
+  if (P.under && P.mixed) return einval("the mixed-precision form is built for m >= n");
+  int64_t s = o->s;
+  if (s == 0) s = P.lowrank ? P.c : std::min<int64_t>(4 * P.c, P.L);
+  if (o->sketch == TK_SKETCH_SRHT && s > next_pow2(P.L)) return einval("SRHT sketch size exceeds the padded length");
+  if (P.lowrank && s > P.c) s = P.c;  // alpha * sd <= n (Algorithm 3); a full-size sketch is still exact
+  P.s = s;
+  P.np = cdiv(P.c, 64) * 64;
+  P.N_cap = (o->schedule == TK_SCHED_ONE_AT_A_TIME) ? 1 : std::max(N, 1);
+  return TK_OK;
+}
+
+// Device buffers of one solve, carved from the caller's workspace.
+struct Bufs {
+  double* lam = nullptr;
+  int* ids = nullptr;
+  int* info = nullptr;
+  double* ones = nullptr;
+  double* Y = nullptr;
+  void* AT = nullptr;
+  float* A32 = nullptr;
+  double* A64 = nullptr;
+  double* C = nullptr;
+  double* R = nullptr;
+  float* R32 = nullptr;
+  double* sig = nullptr;
+  double* lrV = nullptr;
+  double* lrS = nullptr;
+  float* lrV32 = nullptr;
+  float* lrS32 = nullptr;
+  int64_t* ranks = nullptr;
+  double* sd = nullptr;
+  double* D = nullptr;
+  double* Xa = nullptr;
+  double* G = nullptr;
+  double* Rres = nullptr;
+  double* part = nullptr;
+  double* nrm = nullptr;
+  char* scratch = nullptr;  // sketch / SVD scratch
+  size_t scratch_bytes = 0;
+  Lsqr<double> e64;
+  Lsqr<float> e32;
+  int splits = 1;
+};
+
+size_t sketch_scratch(const Plan& P) {
+  tk_dtype dt = P.mixed ? TK_F32 : P.dt;
+  if (P.o.sketch == TK_SKETCH_SRHT) return srht_rows_workspace(P.L, P.c, dt, P.s);
+  return gauss_rows_workspace(P.L, P.c, dt, P.s);
+}
+
+void carve(const Plan& P, Arena& a, Bufs& B) {
+  const int N = std::max(P.N, 1);
+  B.lam = a.take<double>(N);
+  B.ids = a.take<int>(N);
+  B.info = a.take<int>(N);
+  B.ones = a.take<double>(N);
+  B.Y = a.take<double>((size_t)P.s * P.c);
+  if (P.under) B.AT = a.take<char>((size_t)P.m * P.n * (P.dt == TK_F64 ? 8 : 4));
+  if (P.mixed && P.dt == TK_F64) B.A32 = a.take<float>((size_t)P.m * P.n);
+  if (!P.mixed && P.dt == TK_F32) B.A64 = a.take<double>((size_t)P.m * P.n);
+  if (!P.lowrank) {
+    B.C = a.take<double>((size_t)P.c * P.c);
+    B.R = a.take<double>((size_t)N * P.np * P.np);
+    if (P.mixed) B.R32 = a.take<float>((size_t)N * P.np * P.np);
+  } else {
+    B.sig = a.take<double>((size_t)P.s);
+    B.lrV = a.take<double>((size_t)P.c * P.s);
+    B.lrS = a.take<double>((size_t)N * P.s);
+    B.ranks = a.take<int64_t>(N);
+    B.sd = a.take<double>(N);
+    if (P.mixed) {
+      B.lrV32 = a.take<float>((size_t)P.c * P.s);
+      B.lrS32 = a.take<float>((size_t)N * P.s);
+    }
+  }
+  if (P.mixed) {
+    B.splits = splitk_count(N, P.n, P.m);
+    B.D = a.take<double>((size_t)N * P.n);
+    B.Xa = a.take<double>((size_t)N * P.n);
+    B.G = a.take<double>((size_t)N * P.n);
+    B.Rres = a.take<double>((size_t)N * P.m);
+    B.part = a.take<double>((size_t)B.splits * N * P.n);
+    B.nrm = a.take<double>((size_t)3 * N);
+  }
+  size_t sc = sketch_scratch(P);
+  if (P.lowrank) sc = std::max(sc, svd_workspace(P.s, P.c));
+  B.scratch_bytes = sc;
+  B.scratch = a.take<char>(sc);
+  const int64_t lr_s = P.lowrank ? P.s : 0;
+  if (P.mixed) {
+    B.e32.m = P.m; B.e32.n = P.n; B.e32.N_cap = P.N_cap; B.e32.under = false; B.e32.lr_s = lr_s;
+    B.e32.carve(a);
+  } else {
+    B.e64.m = P.m; B.e64.n = P.n; B.e64.N_cap = P.N_cap; B.e64.under = P.under; B.e64.lr_s = lr_s;
+    B.e64.carve(a);
+  }
+}
+
+size_t plan_bytes(const Plan& P) {
+  Arena a;
+  Bufs B;
+  carve(P, a, B);
+  return a.used + 4096;
+}
+
+// ------------------------------------------------------- small kernels ----
+__global__ void k_fill(double* x, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+__global__ void k_bcast(const double* __restrict__ b, int64_t m, double* __restrict__ out, int rows) {
+  const int r = blockIdx.y;
+  if (r >= rows) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    out[(int64_t)r * m + i] = b[i];
+}
+__global__ void k_gather_x(const double* __restrict__ X, int64_t n, const int* __restrict__ ids, double* __restrict__ Xa) {
+  const int k = blockIdx.y;
+  const int l = ids[k];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    Xa[(int64_t)k * n + j] = X[(int64_t)l * n + j];
+}
+// g_k = sum_z partial - lambda_l x_l  (float64 normal-equation residual
+// A^T (b - A x) - lambda x of the k-th listed lambda); nrm[3k] = ||g_k||
+__global__ void k_ne_finish(const double* __restrict__ part, int splits, int count, int64_t n,
+                            const int* __restrict__ ids, const double* __restrict__ lam, const double* __restrict__ Xa,
+                            double* __restrict__ G, double* __restrict__ nrm) {
+  __shared__ double sh[32];
+  const int k = blockIdx.x;
+  const double lv = lam[ids[k]];
+  const int64_t plane = (int64_t)count * n;
+  double acc = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    double g = 0.0;
+    for (int z = 0; z < splits; ++z) g += part[z * plane + (int64_t)k * n + j];
+    g = fma(-lv, Xa[(int64_t)k * n + j], g);
+    G[(int64_t)k * n + j] = g;
+    acc = fma(g, g, acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) nrm[3 * k] = sqrt(acc);
+}
+// X_l += D_l ; nrm[3k+1] = ||D_l||, nrm[3k+2] = ||X_l|| (after the update)
+__global__ void k_refine_update(double* __restrict__ X, const double* __restrict__ D, int64_t n,
+                                const int* __restrict__ ids, double* __restrict__ nrm) {
+  __shared__ double sh[32];
+  const int k = blockIdx.x;
+  const int l = ids[k];
+  double dd = 0.0, xx = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    double d = D[(int64_t)l * n + j];
+    double x = X[(int64_t)l * n + j] + d;
+    X[(int64_t)l * n + j] = x;
+    dd = fma(d, d, dd);
+    xx = fma(x, x, xx);
+  }
+  dd = block_sum(dd, sh);
+  xx = block_sum(xx, sh);
+  if (threadIdx.x == 0) {
+    nrm[3 * k + 1] = sqrt(dd);
+    nrm[3 * k + 2] = sqrt(xx);
+  }
+}
+__global__ void k_f64_to_f32_flat(const double* __restrict__ s, float* __restrict__ d, int64_t total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = (float)s[i];
+}
+__global__ void k_widen(const float* __restrict__ s, int64_t rows, int64_t cols, int64_t lds, double* __restrict__ d) {
+  const int64_t total = rows * cols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = i / cols, c = i - r * cols;
+    d[i] = (double)s[r * lds + c];
+  }
+}
+inline int gsz(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 152 * 32)); }
+inline dim3 rgrid(int64_t len, int rows) {
+  return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(len, 256), 64)), (unsigned)rows);
+}
+
+// ----------------------------------------------------------- sketch -------
+// Y (s x c): the sketch along the long axis (A for m >= n, A^T for m < n).
+tk_status do_sketch(const Plan& P, const void* A_sk, tk_dtype dt_sk, int64_t ld_sk, Bufs& B, cudaStream_t st) {
+  const void* src = A_sk;
+  int64_t ld = ld_sk;
+  if (P.under) {
+    TK_TRY(transpose(A_sk, dt_sk, P.m, P.n, ld_sk, B.AT, st));
+    src = B.AT;
+    ld = P.m;
+  }
+  Arena sa;
+  sa.base = B.scratch;
+  sa.cap = B.scratch_bytes;
+  if (P.o.sketch == TK_SKETCH_SRHT) return srht_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
+  return gauss_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
+}
+
+// ------------------------------------------------------------ solve -------
+tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk_opts* o, void* work,
+                     size_t work_bytes, cudaStream_t st, double* X, tk_info* info) {
+  Plan P;
+  TK_TRY(make_plan(p, N, o, P));
+  if (N == 0) return TK_OK;
+  if (!lambdas) return einval("lambdas pointer is NULL");
+  for (int i = 0; i < N; ++i)
+    if (!(lambdas[i] > 0.0) || !std::isfinite(lambdas[i])) return einval("every lambda must be a positive finite number");
+  if (!p->A || !p->b || !X) return einval("A, b and X must be non-NULL");
+  const size_t need = plan_bytes(P);
+  if (!work || work_bytes < need) {
+    set_error_msg("workspace smaller than tk_workspace_size()");
+    return TK_ENOMEM;
+  }
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  Bufs B;
+  carve(P, a, B);
+  if (!a.ok()) return TK_ENOMEM;
+
+  std::vector<tk_info> inf(N);
+  for (auto& x : inf) {
+    memset(&x, 0, sizeof(x));
+    x.status = TK_OK;
+  }
+  TK_CUDA(cudaMemcpyAsync(B.lam, lambdas, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+  k_fill<<<1, 256, 0, st>>>(B.ones, N, 1.0);
+  TK_LAUNCH_CHECK();
+
+  // compute-precision copies of A
+  const void* A_sk = p->A;
+  tk_dtype dt_sk = P.dt;
+  int64_t ld_sk = P.lda;
+  const double* A64 = (P.dt == TK_F64) ? (const double*)p->A : nullptr;
+  const float* A32 = (P.dt == TK_F32) ? (const float*)p->A : nullptr;
+  int64_t lda64 = P.lda, lda32 = P.lda;
+  if (P.mixed && P.dt == TK_F64) {
+    TK_TRY(convert_f64_to_f32((const double*)p->A, B.A32, P.m, P.n, P.lda, P.n, st));
+    A32 = B.A32;
+    lda32 = P.n;
+  }
+  if (!P.mixed && P.dt == TK_F32) {
+    // the plain float64 path on float32 data: widen A once (exact)
+    k_widen<<<gsz(P.m * P.n), 256, 0, st>>>((const float*)p->A, P.m, P.n, P.lda, B.A64);
+    TK_LAUNCH_CHECK();
+    A64 = B.A64;
+    lda64 = P.n;
+    A_sk = B.A64;
+    dt_sk = TK_F64;
+    ld_sk = P.n;
+  }
+  if (P.mixed) {
+    A_sk = A32;
+    dt_sk = TK_F32;
+    ld_sk = lda32;
+  }
+
+  // ---- step 1-2: draw X and sketch Y = XA (or A X)
+  {
+    const double es = dt_sk == TK_F64 ? 8.0 : 4.0;
+    const double Lp = (double)next_pow2(P.L);
+    const double fl = P.o.sketch == TK_SKETCH_SRHT ? Lp * std::log2(Lp) * P.c : 2.0 * P.s * P.L * P.c;
+    int tok = prof_begin(TK_PHASE_SKETCH, st);
+    TK_TRY(do_sketch(P, A_sk, dt_sk, ld_sk, B, st));
+    prof_end(tok, st, fl, es * P.L * P.c + 8.0 * P.s * P.c);
+  }
+
+  // ---- steps 3-4 (Cholesky) or 4-7 (low rank)
+  std::vector<int> ok_ids;
+  if (!P.lowrank) {
+    int tok = prof_begin(TK_PHASE_GRAM, st);
+    TK_TRY((gemm<double, double, double>(true, false, P.c, P.c, P.s, B.Y, P.c, B.Y, P.c, B.C, P.c, 1.0, nullptr,
+                                         nullptr, 0, st)));
+    prof_end(tok, st, 2.0 * P.s * P.c * P.c, 8.0 * (P.s * P.c + P.c * P.c));
+    Arena none;
+    tok = prof_begin(TK_PHASE_CHOLESKY, st);
+    TK_TRY(chol_shifted(B.C, P.c, B.lam, N, B.R, P.np, P.np * P.np, B.info, none, st));
+    prof_end(tok, st, (double)N * P.c * P.c * P.c / 3.0, 8.0 * N * P.c * P.c);
+    std::vector<int> hinfo(N);
+    TK_CUDA(cudaMemcpyAsync(hinfo.data(), B.info, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    TK_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < N; ++i) {
+      if (hinfo[i] != 0) inf[i].status = TK_ENOTSPD;
+      else ok_ids.push_back(i);
+    }
+    if (P.mixed) {
+      k_f64_to_f32_flat<<<gsz((int64_t)N * P.np * P.np), 256, 0, st>>>(B.R, B.R32, (int64_t)N * P.np * P.np);
+      TK_LAUNCH_CHECK();
+    }
+  } else {
+    Arena sa;
+    sa.base = B.scratch;
+    sa.cap = B.scratch_bytes;
+    int sweeps = 0;
+    int tok = prof_begin(TK_PHASE_SVD, st);
+    TK_TRY(jacobi_svd(B.Y, P.s, P.c, B.sig, B.lrV, &sweeps, sa, st));
+    prof_end(tok, st, 3.5 * sweeps * (double)P.s * P.s * P.c, 8.0 * P.s * P.c);
+    TK_TRY(lowrank_ranks_dev(B.sig, P.s, B.lam, N, P.o.alpha, B.sd, B.ranks, st));
+    TK_TRY(lowrank_diag_dev<double>(B.sig, P.s, B.lam, B.ranks, N, B.lrS, st));
+    std::vector<int64_t> hr(N);
+    TK_CUDA(cudaMemcpyAsync(hr.data(), B.ranks, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, st));
+    TK_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < N; ++i) {
+      inf[i].rank = hr[i];
+      ok_ids.push_back(i);
+    }
+    if (P.mixed) {
+      k_f64_to_f32_flat<<<gsz(P.c * P.s), 256, 0, st>>>(B.lrV, B.lrV32, P.c * P.s);
+      k_f64_to_f32_flat<<<gsz((int64_t)N * P.s), 256, 0, st>>>(B.lrS, B.lrS32, (int64_t)N * P.s);
+      TK_LAUNCH_CHECK();
+    }
+  }
+  TK_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)N * P.n, st));
+  const int nok = (int)ok_ids.size();
+  if (nok > 0) TK_CUDA(cudaMemcpyAsync(B.ids, ok_ids.data(), sizeof(int) * nok, cudaMemcpyHostToDevice, st));
+
+  // ---- LSQR for every lambda (step 5-6 / 8-9)
+  std::vector<LsqrResult> res;
+  if (!P.mixed) {
+    Lsqr<double>& e = B.e64;
+    e.A = A64; e.lda = lda64; e.st = st; e.atol = e.btol = P.o.tol; e.maxiter = P.o.maxiter;
+    if (!P.lowrank) {
+      e.prec_kind = TK_PRECOND_CHOL; e.R = B.R; e.ldr = P.np; e.rstride = P.np * P.np;
+    } else {
+      e.prec_kind = TK_PRECOND_LOWRANK; e.lrV = B.lrV; e.lrS = B.lrS;
+    }
+    if (P.o.schedule == TK_SCHED_BATCHED) {
+      TK_TRY(e.run(p->b, 0, nullptr, 0, B.ids, B.lam, nok, X, P.n, false, res));
+    } else {
+      for (int k = 0; k < nok; ++k) TK_TRY(e.run(p->b, 0, nullptr, 0, B.ids + k, B.lam, 1, X, P.n, false, res));
+    }
+    for (const auto& r : res) {
+      tk_info& q = inf[r.lam_idx];
+      q.iters += r.iters;
+      q.istop = r.istop;
+      q.rnorm = r.rnorm;
+      q.arnorm = r.arnorm;
+      if (r.istop == 7) q.status = worse(q.status, TK_ENOCONV);
+      if (r.istop == 5) q.status = worse(q.status, TK_ENUMERIC);
+    }
+  } else {
+    // ---- mixed: FP32 LSQR on corrections; the float64 pass forms r = b - A x
+    //      and g = A^T r - lambda x (the normal-equation check), and the
+    //      correction d solves min ||B d - [0; g/sqrt(l)]||, x <- x + d.
+    Lsqr<float>& e = B.e32;
+    e.A = A32; e.lda = lda32; e.st = st; e.atol = e.btol = P.o.inner_tol; e.maxiter = P.o.maxiter;
+    if (!P.lowrank) {
+      e.prec_kind = TK_PRECOND_CHOL; e.R = B.R32; e.ldr = P.np; e.rstride = P.np * P.np;
+    } else {
+      e.prec_kind = TK_PRECOND_LOWRANK; e.lrV = B.lrV32; e.lrS = B.lrS32;
+    }
+    std::vector<int> act = ok_ids;
+    std::vector<double> hn(3 * std::max(N, 1));
+    for (int round = 0; round < P.o.max_refine && !act.empty(); ++round) {
+      const int cnt = (int)act.size();
+      TK_CUDA(cudaMemcpyAsync(B.ids, act.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, st));
+      res.clear();
+      if (round == 0) {
+        if (P.o.schedule == TK_SCHED_BATCHED) TK_TRY(e.run(p->b, 0, nullptr, 0, B.ids, B.lam, cnt, B.D, P.n, false, res));
+        else
+          for (int k = 0; k < cnt; ++k) TK_TRY(e.run(p->b, 0, nullptr, 0, B.ids + k, B.lam, 1, B.D, P.n, false, res));
+      } else {
+        // FP64 pass: Rres = b - Xa A^T, G = Rres A - lambda Xa
+        k_gather_x<<<rgrid(P.n, cnt), 256, 0, st>>>(X, P.n, B.ids, B.Xa);
+        k_bcast<<<rgrid(P.m, cnt), 256, 0, st>>>(p->b, P.m, B.Rres, cnt);
+        TK_LAUNCH_CHECK();
+        const double ea = P.dt == TK_F64 ? 8.0 : 4.0;
+        const double fl = 2.0 * cnt * P.m * P.n;
+        int tok = prof_begin(TK_PHASE_RES64, st);
+        if (P.dt == TK_F64)
+          TK_TRY((gemm<double, double, double>(false, true, cnt, P.m, P.n, B.Xa, P.n, A64, lda64, B.Rres, P.m, -1.0,
+                                               B.ones, B.Rres, P.m, st)));
+        else
+          TK_TRY((gemm<double, float, double>(false, true, cnt, P.m, P.n, B.Xa, P.n, A32, lda32, B.Rres, P.m, -1.0,
+                                              B.ones, B.Rres, P.m, st)));
+        prof_end(tok, st, fl, ea * P.m * P.n + 8.0 * (2.0 * cnt * P.m + cnt * P.n));
+        tok = prof_begin(TK_PHASE_NE64, st);
+        if (P.dt == TK_F64)
+          TK_TRY((gemm_splitk<double, double>(false, false, cnt, P.n, P.m, B.Rres, P.m, A64, lda64, B.part, B.splits,
+                                              st)));
+        else
+          TK_TRY((gemm_splitk<double, float>(false, false, cnt, P.n, P.m, B.Rres, P.m, A32, lda32, B.part, B.splits,
+                                             st)));
+        prof_end(tok, st, fl, ea * P.m * P.n + 8.0 * (cnt * P.m + (double)B.splits * cnt * P.n));
+        k_ne_finish<<<cnt, 256, 0, st>>>(B.part, B.splits, cnt, P.n, B.ids, B.lam, B.Xa, B.G, B.nrm);
+        TK_LAUNCH_CHECK();
+        // correction: min ||B d - [0; g/sqrt(l)]||, whose normal equations are
+        // (A^T A + l I) d = g; the right-hand side shrinks with the error of x.
+        if (P.o.schedule == TK_SCHED_BATCHED) {
+          TK_TRY(e.run(nullptr, 0, B.G, P.n, B.ids, B.lam, cnt, B.D, P.n, false, res));
+        } else {
+          for (int k = 0; k < cnt; ++k)
+            TK_TRY(e.run(nullptr, 0, B.G + (int64_t)k * P.n, P.n, B.ids + k, B.lam, 1, B.D, P.n, false, res));
+        }
+      }
+      k_refine_update<<<cnt, 256, 0, st>>>(X, B.D, P.n, B.ids, B.nrm);
+      TK_LAUNCH_CHECK();
+      TK_CUDA(cudaMemcpyAsync(hn.data(), B.nrm, sizeof(double) * 3 * cnt, cudaMemcpyDeviceToHost, st));
+      TK_CUDA(cudaStreamSynchronize(st));
+      for (const auto& r : res) {
+        tk_info& q = inf[r.lam_idx];
+        q.iters += r.iters;
+        q.istop = r.istop;
+        q.rnorm = r.rnorm;
+        q.arnorm = r.arnorm;
+        if (r.istop == 5) q.status = worse(q.status, TK_ENUMERIC);
+      }
+      std::vector<int> next;
+      for (int k = 0; k < cnt; ++k) {
+        tk_info& q = inf[act[k]];
+        q.refine_steps += 1;
+        if (round > 0) q.ne_norm = hn[3 * k];
+        const double dn = hn[3 * k + 1], xn = hn[3 * k + 2];
+        const bool done = (dn <= P.o.refine_tol * xn) || !std::isfinite(dn);
+        if (!done) next.push_back(act[k]);
+      }
+      act.swap(next);
+    }
+    for (int l : act) inf[l].status = worse(inf[l].status, TK_ENOCONV);
+  }
+  tk_status worst = TK_OK;
+  for (int i = 0; i < N; ++i) worst = worse(worst, inf[i].status);
+  if (info)
+    for (int i = 0; i < N; ++i) info[i] = inf[i];
+  TK_CUDA(cudaStreamSynchronize(st));
+  return worst;
+}
+
+}  // namespace
+}  // namespace tk
+
+using namespace tk;
+
+extern "C" {
+
+TK_API tk_status tk_opts_default(tk_opts* o) {
+  if (!o) return TK_EINVAL;
+  memset(o, 0, sizeof(*o));
+  o->sketch = TK_SKETCH_SRHT;
+  o->s = 0;
+  o->precond = TK_PRECOND_CHOL;
+  o->alpha = 2.0;
+  o->precision = TK_PREC_FP64;
+  o->tol = 1e-14;
+  o->maxiter = 500;
+  o->max_refine = 6;
+  o->inner_tol = 1e-6;
+  o->refine_tol = 1e-11;
+  o->seed = 1;
+  o->schedule = TK_SCHED_BATCHED;
+  return TK_OK;
+}
+
+TK_API const char* tk_status_str(tk_status s) {
+  switch (s) {
+    case TK_OK: return "ok";
+    case TK_EINVAL: return "invalid argument";
+    case TK_ENOMEM: return "workspace too small";
+    case TK_ENOTSPD: return "Cholesky breakdown (C + lambda I not positive definite)";
+    case TK_ENOCONV: return "no convergence within the iteration cap";
+    case TK_ENUMERIC: return "NaN or Inf in the recurrences";
+    case TK_ETIMEOUT: return "device-side wait timed out";
+    case TK_ECUDA: return "CUDA error";
+  }
+  return "unknown status";
+}
+
+TK_API const char* tk_last_error(void) { return tk::g_err; }
+
+TK_API tk_status tk_workspace_size(const tk_problem* p, int N, const tk_opts* o, size_t* bytes) {
+  if (!bytes) return einval("bytes pointer is NULL");
+  Plan P;
+  TK_TRY(make_plan(p, N, o, P));
+  *bytes = plan_bytes(P);
+  return TK_OK;
+}
+
+TK_API tk_status tk_solve(const tk_problem* p, const double* lambdas, int N, const tk_opts* o, void* work,
+                          size_t work_bytes, void* stream, double* X, tk_info* info) {
+  return solve_impl(p, lambdas, N, o, work, work_bytes, (cudaStream_t)stream, X, info);
+}
+
+TK_API tk_status tk_workspace_size_batched(const tk_problem* ps, int P, int N, const tk_opts* o, size_t* bytes) {
+  if (!bytes || (P > 0 && !ps) || P < 0) return einval("bad batched arguments");
+  size_t mx = 0;
+  for (int i = 0; i < P; ++i) {
+    size_t b = 0;
+    TK_TRY(tk_workspace_size(&ps[i], N, o, &b));
+    mx = std::max(mx, b);
+  }
+  *bytes = mx;
+  return TK_OK;
+}
+
+TK_API tk_status tk_solve_batched(const tk_problem* ps, int P, const double* lambdas, int N, const tk_opts* o,
+                                  void* work, size_t work_bytes, void* stream, double* const* X, tk_info* info) {
+  if (P < 0 || (P > 0 && (!ps || !lambdas || !X))) return einval("bad batched arguments");
+  for (int i = 0; i < P; ++i) {
+    Plan pl;
+    TK_TRY(make_plan(&ps[i], N, o, pl));
+  }
+  tk_status worst = TK_OK;
+  for (int i = 0; i < P; ++i) {
+    tk_status s = solve_impl(&ps[i], lambdas + (size_t)i * N, N, o, work, work_bytes, (cudaStream_t)stream, X[i],
+                             info ? info + (size_t)i * N : nullptr);
+    if (s == TK_EINVAL || s == TK_ENOMEM || s == TK_ECUDA) return s;
+    worst = worse(worst, s);
+  }
+  return worst;
+}
+
+TK_API size_t tk_sketch_draw_workspace(int64_t mp) { return draw_workspace(mp > 0 ? mp : 1) + 1024; }
+
+TK_API tk_status tk_sketch_draw(uint64_t seed, int64_t mp, int64_t s, int8_t* signs, int64_t* rows, void* work,
+                                size_t work_bytes, void* stream) {
+  if (mp < 1 || mp > kMaxLong) return einval("mp out of range");
+  if (s < 0 || s > mp) return einval("s out of range");
+  if (rows && s > 0 && (!work || work_bytes < tk_sketch_draw_workspace(mp))) {
+    set_error_msg("workspace smaller than tk_sketch_draw_workspace()");
+    return TK_ENOMEM;
+  }
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  cudaStream_t st = (cudaStream_t)stream;
+  TK_TRY(draw_signs_rows(seed, mp, s, signs, rows, nullptr, a, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  return TK_OK;
+}
+
+TK_API tk_status tk_sketch_apply_workspace(const tk_problem* p, const tk_opts* o, size_t* bytes) {
+  if (!bytes) return einval("bytes pointer is NULL");
+  Plan P;
+  TK_TRY(make_plan(p, 1, o, P));
+  Arena a;
+  if (P.under) {
+    a.take<char>((size_t)P.m * P.n * (P.dt == TK_F64 ? 8 : 4));
+    a.take<double>((size_t)P.s * P.c);
+  }
+  a.take<char>(sketch_scratch(P));
+  *bytes = a.used + 4096;
+  return TK_OK;
+}
+
+TK_API tk_status tk_sketch_apply(const tk_problem* p, const tk_opts* o, double* Y, void* work, size_t work_bytes,
+                                 void* stream) {
+  Plan P;
+  TK_TRY(make_plan(p, 1, o, P));
+  if (P.mixed) return einval("tk_sketch_apply sketches in the dtype of A; use precision FP64");
+  if (!p->A || !Y) return einval("A and Y must be non-NULL");
+  size_t need = 0;
+  TK_TRY(tk_sketch_apply_workspace(p, o, &need));
+  if (!work || work_bytes < need) {
+    set_error_msg("workspace smaller than tk_sketch_apply_workspace()");
+    return TK_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  Bufs B;
+  if (P.under) {
+    B.AT = a.take<char>((size_t)P.m * P.n * (P.dt == TK_F64 ? 8 : 4));
+    B.Y = a.take<double>((size_t)P.s * P.c);
+  } else {
+    B.Y = Y;
+  }
+  B.scratch_bytes = sketch_scratch(P);
+  B.scratch = a.take<char>(B.scratch_bytes);
+  if (!a.ok()) return TK_ENOMEM;
+  TK_TRY(do_sketch(P, p->A, P.dt, P.lda, B, st));
+  if (P.under) TK_TRY(transpose(B.Y, TK_F64, P.s, P.m, P.m, Y, st));  // (s x m) -> (m x s)
+  TK_CUDA(cudaStreamSynchronize(st));
+  return TK_OK;
+}
+
+TK_API tk_status tk_gram(const double* Y, int64_t r, int64_t c, int transpose_first, double* C, void* stream) {
+  if (!Y || !C || r < 1 || c < 1) return einval("bad Gram arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (transpose_first)
+    TK_TRY((gemm<double, double, double>(true, false, c, c, r, Y, c, Y, c, C, c, 1.0, nullptr, nullptr, 0, st)));
+  else
+    TK_TRY((gemm<double, double, double>(false, true, r, r, c, Y, c, Y, c, C, r, 1.0, nullptr, nullptr, 0, st)));
+  TK_CUDA(cudaStreamSynchronize(st));
+  return TK_OK;
+}
+
+TK_API size_t tk_cholesky_workspace(int64_t n, int N) {
+  if (n < 1 || N < 1) return 0;
+  const int64_t np = cdiv(n, 64) * 64;
+  Arena a;
+  a.take<double>(N);
+  a.take<int>(N);
+  a.take<double>((size_t)N * np * np);
+  return a.used + 1024;
+}
+
+TK_API tk_status tk_cholesky_shifted(const double* C, int64_t n, const double* lambdas, int N, double* R,
+                                     int* breakdown, void* work, size_t work_bytes, void* stream) {
+  if (!C || !R || !lambdas || n < 1 || n > kMaxShort || N < 1) return einval("bad Cholesky arguments");
+  for (int i = 0; i < N; ++i)
+    if (!std::isfinite(lambdas[i])) return einval("lambda must be finite");
+  if (!work || work_bytes < tk_cholesky_workspace(n, N)) {
+    set_error_msg("workspace smaller than tk_cholesky_workspace()");
+    return TK_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t np = cdiv(n, 64) * 64;
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  double* lam = a.take<double>(N);
+  int* info = a.take<int>(N);
+  double* Rp = a.take<double>((size_t)N * np * np);
+  TK_CUDA(cudaMemcpyAsync(lam, lambdas, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+  Arena none;
+  TK_TRY(chol_shifted(C, n, lam, N, Rp, np, np * np, info, none, st));
+  for (int i = 0; i < N; ++i)
+    TK_CUDA(cudaMemcpy2DAsync(R + (size_t)i * n * n, sizeof(double) * n, Rp + (size_t)i * np * np,
+                              sizeof(double) * np, sizeof(double) * n, n, cudaMemcpyDeviceToDevice, st));
+  std::vector<int> h(N);
+  TK_CUDA(cudaMemcpyAsync(h.data(), info, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  tk_status worst = TK_OK;
+  for (int i = 0; i < N; ++i) {
+    if (breakdown) breakdown[i] = h[i];
+    if (h[i]) worst = TK_ENOTSPD;
+  }
+  return worst;
+}
+
+TK_API size_t tk_sketch_svd_workspace(int64_t s, int64_t n) { return svd_workspace(s, n) + 1024; }
+
+TK_API tk_status tk_sketch_svd(const double* Y, int64_t s, int64_t n, double* sigma, double* V, int* sweeps,
+                               void* work, size_t work_bytes, void* stream) {
+  if (!Y || !sigma || !V || s < 1 || n < 1 || s > n) return einval("bad SVD arguments (need 1 <= s <= n)");
+  if (!work || work_bytes < tk_sketch_svd_workspace(s, n)) {
+    set_error_msg("workspace smaller than tk_sketch_svd_workspace()");
+    return TK_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  int sw = 0;
+  TK_TRY(jacobi_svd(Y, s, n, sigma, V, &sw, a, st));
+  if (sweeps) *sweeps = sw;
+  TK_CUDA(cudaStreamSynchronize(st));
+  return TK_OK;
+}
+
+TK_API size_t tk_lowrank_ranks_workspace(int N) {
+  Arena a;
+  a.take<double>(N > 0 ? N : 1);
+  a.take<double>(N > 0 ? N : 1);
+  a.take<int64_t>(N > 0 ? N : 1);
+  return a.used + 1024;
+}
+
+TK_API tk_status tk_lowrank_ranks(const double* sigma, int64_t s, const double* lambdas, int N, double alpha,
+                                  double* sd, int64_t* ranks, void* work, size_t work_bytes, void* stream) {
+  if (!sigma || !lambdas || !ranks || s < 1 || N < 1 || !(alpha >= 1.0)) return einval("bad rank arguments");
+  if (!work || work_bytes < tk_lowrank_ranks_workspace(N)) {
+    set_error_msg("workspace smaller than tk_lowrank_ranks_workspace()");
+    return TK_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  double* lam = a.take<double>(N);
+  double* sdd = a.take<double>(N);
+  int64_t* rk = a.take<int64_t>(N);
+  TK_CUDA(cudaMemcpyAsync(lam, lambdas, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+  TK_TRY(lowrank_ranks_dev(sigma, s, lam, N, alpha, sdd, rk, st));
+  if (sd) TK_CUDA(cudaMemcpyAsync(sd, sdd, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaMemcpyAsync(ranks, rk, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  return TK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,503 @@
+// Dense building blocks of the path, all hand-written SIMT CUDA:
+//   * GEMM / split-K GEMM   -- sketch products, Gram matrix (Algorithm 1 step 3)
+//                              and the two products with A in every LSQR step
+//   * batched Cholesky      -- R_i = chol(C + lambda_i I) for all lambda at once
+//                              (Algorithm 1 step 4), blocked right-looking
+//   * batched TRSV          -- R^-1 v and R^-T g (the preconditioner apply)
+//
+// FP64 on this part issues about two DFMA per clock per SM (58x below FP32),
+// so every FP64 kernel here is DFMA-bound: the design goal is to keep the FP64
+// pipe busy with enough resident warps, not to save bytes.
+#include <algorithm>
+#include <type_traits>
+
+#include "tk_internal.cuh"
+
+namespace tk {
+namespace {
+
+template <typename A, typename B>
+struct AccOf { using type = double; };
+template <>
+struct AccOf<float, float> { using type = float; };
+
+// C = alpha op(A) op(B) [+ beta_row[i] * Cin]     or, with `partial`, the raw
+// split-K partial sum of K-range blockIdx.z into partial + z * M * N.
+// op(A) is M x K: A[i*lda + k] (N) or A[k*lda + i] (T).  op(B) is K x N:
+// B[k*ldb + j] (N) or B[j*ldb + k] (T).
+template <typename TA, typename TB, typename TC, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    k_gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
+           const TB* __restrict__ B, int64_t ldb, TC* C, int64_t ldc, double alpha,
+           const double* __restrict__ beta_row, const TC* Cin, int64_t ldcin, int64_t k_per_split,
+           double* __restrict__ partial) {
+  using Acc = typename AccOf<TA, TB>::type;
+  constexpr int NT = (BM / TM) * (BN / TN);
+  __shared__ Acc As[BK][BM + 1];
+  __shared__ Acc Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t kbeg = (int64_t)blockIdx.z * k_per_split;
+  const int64_t kend = std::min(K, kbeg + k_per_split);
+  Acc acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = Acc(0);
+
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    // A tile: BM x BK; the fastest thread index walks the contiguous axis.
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      int i, k;
+      if (!transA) { k = idx % BK; i = idx / BK; } else { i = idx % BM; k = idx / BM; }
+      int64_t gi = m0 + i, gk = k0 + k;
+      Acc v = Acc(0);
+      if (gi < M && gk < kend) v = (Acc)(transA ? A[gk * lda + gi] : A[gi * lda + gk]);
+      As[k][i] = v;
+    }
+    for (int idx = tid; idx < BK * BN; idx += NT) {
+      int j, k;
+      if (!transB) { j = idx % BN; k = idx / BN; } else { k = idx % BK; j = idx / BK; }
+      int64_t gj = n0 + j, gk = k0 + k;
+      Acc v = Acc(0);
+      if (gj < N && gk < kend) v = (Acc)(transB ? B[gj * ldb + gk] : B[gk * ldb + gj]);
+      Bs[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      Acc a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int64_t r = m0 + ty * TM + i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int64_t c = n0 + tx * TN + j;
+      if (c >= N) continue;
+      if (partial) {
+        partial[(int64_t)blockIdx.z * M * N + r * N + c] = (double)acc[i][j];
+      } else {
+        double v = alpha * (double)acc[i][j];
+        if (beta_row) v += beta_row[r] * (double)Cin[r * ldcin + c];
+        C[r * ldc + c] = (TC)v;
+      }
+    }
+  }
+}
+
+template <typename TA, typename TB, typename TC, int BM, int BN, int BK, int TM, int TN>
+tk_status launch_gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda,
+                      const TB* B, int64_t ldb, TC* C, int64_t ldc, double alpha, const double* beta_col,
+                      const TC* Cin, int64_t ldcin, int splits, double* partial, cudaStream_t st) {
+  int64_t kps = cdiv(cdiv(K, splits), BK) * BK;
+  if (kps <= 0) kps = BK;
+  dim3 grid((unsigned)cdiv(M, BM), (unsigned)cdiv(N, BN), (unsigned)splits);
+  if (grid.y > 65535u || grid.z > 65535u) {
+    set_error_msg("gemm: grid too large");
+    return TK_EINVAL;
+  }
+  k_gemm<TA, TB, TC, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(
+      transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta_col, Cin, ldcin, kps, partial);
+  TK_LAUNCH_CHECK();
+  return TK_OK;
+}
+
+template <typename TA, typename TB, typename TC>
+tk_status gemm_dispatch(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda,
+                        const TB* B, int64_t ldb, TC* C, int64_t ldc, double alpha, const double* beta_row,
+                        const TC* Cin, int64_t ldcin, int splits, double* partial, cudaStream_t st) {
+  if (M == 0 || N == 0) return TK_OK;
+  constexpr bool f32 = std::is_same<TA, float>::value && std::is_same<TB, float>::value;
+#define TK_G(BM, BN, TM, TN)                                                                                    \
+  return launch_gemm<TA, TB, TC, BM, BN, 16, TM, TN>(transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, \
+                                                      beta_row, Cin, ldcin, splits, partial, st)
+  // Shapes: a few lambda rows against a long axis (M small), a long axis
+  // against a few lambda columns (N small), or square-ish.
+  if (f32) {
+    if (M <= 32) TK_G(32, 128, 4, 4);
+    if (M <= 64) TK_G(64, 128, 8, 4);
+    if (N <= 32) TK_G(128, 32, 8, 2);
+    TK_G(128, 64, 8, 4);
+  }
+  if (M <= 8) TK_G(8, 256, 1, 8);
+  if (M <= 32) TK_G(32, 128, 4, 4);
+  if (N <= 8) TK_G(256, 8, 8, 1);
+  if (N <= 32) TK_G(128, 32, 4, 4);
+  TK_G(64, 64, 4, 4);
+#undef TK_G
+}
+
+// ------------------------------------------------------------- Cholesky ---
+constexpr int CB = 64;  // Cholesky tile
+
+// R_l[i, j] = C[i, j] + lambda_l delta_ij on the n x n block (upper triangle),
+// identity on the padding, zero below the diagonal.
+__global__ void k_chol_init(const double* __restrict__ Cm, int64_t n, int64_t np, const double* __restrict__ lam,
+                            double* __restrict__ R, int64_t ldr, int64_t rstride, int* __restrict__ info) {
+  const int l = blockIdx.y;
+  double* Rl = R + (int64_t)l * rstride;
+  const double lv = lam[l];
+  if (blockIdx.x == 0 && threadIdx.x == 0) info[l] = 0;
+  int64_t total = np * np;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = k / np, j = k - i * np;
+    double v = 0.0;
+    if (j >= i) {
+      if (i < n && j < n) v = Cm[i * n + j] + (i == j ? lv : 0.0);
+      else v = (i == j) ? 1.0 : 0.0;
+    }
+    Rl[i * ldr + j] = v;
+  }
+}
+
+// Factor the diagonal tile (kb, kb) of every lambda in shared memory
+// (right-looking within the tile).  A non-positive pivot records the global
+// row + 1 in info[l] (first one only) and continues with pivot 1.
+__global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ R, int64_t ldr, int64_t rstride, int kb,
+                                                   int* __restrict__ info) {
+  __shared__ double T[CB][CB + 1];
+  const int l = blockIdx.x;
+  double* Rl = R + (int64_t)l * rstride + (int64_t)kb * CB * ldr + (int64_t)kb * CB;
+  for (int idx = threadIdx.x; idx < CB * CB; idx += blockDim.x) {
+    int i = idx / CB, j = idx % CB;
+    T[i][j] = Rl[(int64_t)i * ldr + j];
+  }
+  __syncthreads();
+  for (int j = 0; j < CB; ++j) {
+    if (threadIdx.x == 0) {
+      double d = T[j][j];
+      if (!(d > 0.0)) {
+        if (info[l] == 0) info[l] = kb * CB + j + 1;
+        d = 1.0;
+      }
+      T[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const double rjj = T[j][j];
+    for (int k = j + 1 + threadIdx.x; k < CB; k += blockDim.x) T[j][k] /= rjj;
+    __syncthreads();
+    // trailing update of the upper triangle: T[i][k] -= T[j][i] T[j][k], j < i <= k
+    const int rem = CB - j - 1;
+    for (int p = threadIdx.x; p < rem * rem; p += blockDim.x) {
+      int i = j + 1 + p / rem, k = j + 1 + p % rem;
+      if (k >= i) T[i][k] -= T[j][i] * T[j][k];
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < CB * CB; idx += blockDim.x) {
+    int i = idx / CB, j = idx % CB;
+    if (j >= i) Rl[(int64_t)i * ldr + j] = T[i][j];
+  }
+}
+
+// Row panel: tile (kb, jb), jb > kb, becomes R_kk^-T tile (forward
+// substitution; one column of the tile per thread, held in registers).
+__global__ void __launch_bounds__(CB) k_chol_trsm(double* __restrict__ R, int64_t ldr, int64_t rstride, int kb) {
+  __shared__ double D[CB][CB + 1];
+  const int l = blockIdx.y;
+  const int jb = kb + 1 + blockIdx.x;
+  double* Rl = R + (int64_t)l * rstride;
+  const double* Dg = Rl + (int64_t)kb * CB * ldr + (int64_t)kb * CB;
+  double* Xg = Rl + (int64_t)kb * CB * ldr + (int64_t)jb * CB;
+  const int c = threadIdx.x;
+  double xr[CB];
+#pragma unroll
+  for (int i = 0; i < CB; ++i) {
+    D[i][c] = Dg[(int64_t)i * ldr + c];
+    xr[i] = Xg[(int64_t)i * ldr + c];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < CB; ++r) {
+    xr[r] = xr[r] / D[r][r];
+#pragma unroll
+    for (int q = r + 1; q < CB; ++q) xr[q] = fma(-D[r][q], xr[r], xr[q]);
+  }
+#pragma unroll
+  for (int i = 0; i < CB; ++i) Xg[(int64_t)i * ldr + c] = xr[i];
+}
+
+// Trailing update of tiles (ib, jb), kb < ib <= jb:
+// T[ib, jb] -= R[kb, ib]^T R[kb, jb].  One CTA per (tile pair, lambda).
+__global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ R, int64_t ldr, int64_t rstride, int kb,
+                                                     int nt) {
+  constexpr int KC = 16;
+  __shared__ double P[KC][CB + 1];  // rows of R[kb, ib]
+  __shared__ double Q[KC][CB + 1];  // rows of R[kb, jb]
+  const int l = blockIdx.y;
+  // decode the linear tile-pair index into (ib, jb) with ib <= jb
+  const int r = nt - kb - 1;
+  int t = blockIdx.x, ib = 0;
+  {
+    int row_len = r;
+    while (t >= row_len) {
+      t -= row_len;
+      --row_len;
+      ++ib;
+    }
+  }
+  int jb = ib + t;
+  ib += kb + 1;
+  jb += kb + 1;
+  double* Rl = R + (int64_t)l * rstride;
+  const double* Pg = Rl + (int64_t)kb * CB * ldr + (int64_t)ib * CB;
+  const double* Qg = Rl + (int64_t)kb * CB * ldr + (int64_t)jb * CB;
+  double* Tg = Rl + (int64_t)ib * CB * ldr + (int64_t)jb * CB;
+  // thread owns a 4 x 4 block of the 64 x 64 output
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int kc = 0; kc < CB; kc += KC) {
+    for (int idx = threadIdx.x; idx < KC * CB; idx += blockDim.x) {
+      int k = idx / CB, j = idx % CB;
+      P[k][j] = Pg[(int64_t)(kc + k) * ldr + j];
+      Q[k][j] = Qg[(int64_t)(kc + k) * ldr + j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      double pa[4], qb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) pa[a] = P[k][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) qb[b] = Q[k][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(pa[a], qb[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  const bool diag = (ib == jb);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int i = ty + 16 * a, j = tx + 16 * b;
+      if (diag && j < i) continue;
+      Tg[(int64_t)i * ldr + j] -= acc[a][b];
+    }
+}
+
+// ------------------------------------------------------------------ TRSV --
+constexpr int kTrsvThreads = 256;
+
+// x <- R^-1 x (back substitution) for each slot, R upper triangular.
+// Blocks of 32 rows from the bottom: the 8 warps first subtract the solved
+// part (row i of R against the solved tail, one warp per row), then warp 0
+// solves the 32 x 32 diagonal block with shuffles.
+template <typename TR, typename TX>
+__global__ void __launch_bounds__(kTrsvThreads)
+    k_trsv_upper(int64_t n, const TR* __restrict__ R, int64_t ldr, int64_t rstride, const int* __restrict__ idx,
+                 const TX* Xin, TX* X, int64_t ldx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* x = reinterpret_cast<double*>(smem_raw);
+  const int slot = blockIdx.x;
+  const TR* Rs = R + (int64_t)(idx ? idx[slot] : slot) * rstride;
+  TX* xg = X + (int64_t)slot * ldx;
+  const TX* xin = Xin + (int64_t)slot * ldx;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = (double)xin[i];
+  __syncthreads();
+  const int64_t nb = cdiv(n, 32);
+  for (int64_t b = nb - 1; b >= 0; --b) {
+    const int64_t r0 = b * 32, r1 = std::min<int64_t>(n, r0 + 32);
+    for (int64_t i = r0 + wid; i < r1; i += nw) {
+      double acc = 0.0;
+      for (int64_t k = r1 + lane; k < n; k += 32) acc = fma((double)Rs[i * ldr + k], x[k], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) x[i] -= acc;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      int64_t i = r0 + lane;
+      bool live = i < r1;
+      double xi = live ? x[i] : 0.0;
+      for (int q = (int)(r1 - r0) - 1; q >= 0; --q) {
+        double rq = live ? (double)Rs[i * ldr + r0 + q] : 0.0;  // R[i, r0+q]
+        double xq = __shfl_sync(0xffffffffu, xi, q);
+        if (lane == q) {
+          xq = xq / rq;
+          xi = xq;
+        }
+        xq = __shfl_sync(0xffffffffu, xi, q);
+        if (lane < q) xi = fma(-rq, xq, xi);
+      }
+      if (live) x[i] = xi;
+    }
+    __syncthreads();
+  }
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xg[i] = (TX)x[i];
+}
+
+// x <- R^-T x (forward substitution with the lower triangular R^T).
+// Block b of 32 unknowns first receives -sum_{k < r0} R[k, i] x_k: warps take
+// rows k, lanes take the 32 columns i (coalesced), partials meet in shared
+// memory; then warp 0 solves the diagonal block.
+template <typename TR, typename TX>
+__global__ void __launch_bounds__(kTrsvThreads)
+    k_trsv_upper_t(int64_t n, const TR* __restrict__ R, int64_t ldr, int64_t rstride, const int* __restrict__ idx,
+                   const TX* Xin, TX* X, int64_t ldx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* x = reinterpret_cast<double*>(smem_raw);
+  __shared__ double part[kTrsvThreads / 32][32];
+  const int slot = blockIdx.x;
+  const TR* Rs = R + (int64_t)(idx ? idx[slot] : slot) * rstride;
+  TX* xg = X + (int64_t)slot * ldx;
+  const TX* xin = Xin + (int64_t)slot * ldx;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = (double)xin[i];
+  __syncthreads();
+  const int64_t nb = cdiv(n, 32);
+  for (int64_t b = 0; b < nb; ++b) {
+    const int64_t r0 = b * 32, r1 = std::min<int64_t>(n, r0 + 32);
+    const int64_t i = r0 + lane;
+    const bool live = i < r1;
+    double acc = 0.0;
+    for (int64_t k = wid; k < r0; k += nw)
+      if (live) acc = fma((double)Rs[k * ldr + i], x[k], acc);
+    part[wid][lane] = acc;
+    __syncthreads();
+    if (wid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += part[w][lane];
+      double xi = live ? x[i] - s : 0.0;
+      for (int q = 0; q < (int)(r1 - r0); ++q) {
+        double rq = live ? (double)Rs[(r0 + q) * ldr + i] : 0.0;  // R[r0+q, i]
+        double xq = __shfl_sync(0xffffffffu, xi, q);
+        if (lane == q) {
+          xq = xq / rq;
+          xi = xq;
+        }
+        xq = __shfl_sync(0xffffffffu, xi, q);
+        if (lane > q) xi = fma(-rq, xq, xi);
+      }
+      if (live) x[i] = xi;
+    }
+    __syncthreads();
+  }
+  for (int64_t i2 = threadIdx.x; i2 < n; i2 += blockDim.x) xg[i2] = (TX)x[i2];
+}
+
+}  // namespace
+
+// ----------------------------------------------------------- host side ----
+template <typename TA, typename TB, typename TC>
+tk_status gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
+               int64_t ldb, TC* C, int64_t ldc, double alpha, const double* beta_col, const TC* Cin, int64_t ldcin,
+               cudaStream_t st) {
+  return gemm_dispatch<TA, TB, TC>(transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta_col, Cin, ldcin, 1,
+                                   nullptr, st);
+}
+
+int splitk_count(int64_t M, int64_t N, int64_t K) {
+  int64_t tiles = cdiv(M, 32) * cdiv(N, 128);
+  int64_t want = cdiv(152 * 4, std::max<int64_t>(tiles, 1));
+  int64_t maxs = std::max<int64_t>(1, K / 512);
+  return (int)std::max<int64_t>(1, std::min<int64_t>({want, maxs, 4096}));
+}
+
+template <typename TA, typename TB>
+tk_status gemm_splitk(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda,
+                      const TB* B, int64_t ldb, double* partial, int splits, cudaStream_t st) {
+  return gemm_dispatch<TA, TB, double>(transA, transB, M, N, K, A, lda, B, ldb, nullptr, 0, 1.0, nullptr, nullptr,
+                                       0, splits, partial, st);
+}
+
+#define TK_INST_GEMM(TA, TB, TC)                                                                            \
+  template tk_status gemm<TA, TB, TC>(bool, bool, int64_t, int64_t, int64_t, const TA*, int64_t, const TB*, \
+                                      int64_t, TC*, int64_t, double, const double*, const TC*, int64_t,      \
+                                      cudaStream_t);
+TK_INST_GEMM(double, double, double)
+TK_INST_GEMM(float, float, float)
+TK_INST_GEMM(float, float, double)
+TK_INST_GEMM(float, double, double)
+TK_INST_GEMM(double, float, float)
+TK_INST_GEMM(double, float, double)
+#undef TK_INST_GEMM
+template tk_status gemm_splitk<double, double>(bool, bool, int64_t, int64_t, int64_t, const double*, int64_t,
+                                               const double*, int64_t, double*, int, cudaStream_t);
+template tk_status gemm_splitk<float, float>(bool, bool, int64_t, int64_t, int64_t, const float*, int64_t,
+                                             const float*, int64_t, double*, int, cudaStream_t);
+template tk_status gemm_splitk<float, double>(bool, bool, int64_t, int64_t, int64_t, const float*, int64_t,
+                                              const double*, int64_t, double*, int, cudaStream_t);
+template tk_status gemm_splitk<double, float>(bool, bool, int64_t, int64_t, int64_t, const double*, int64_t,
+                                              const float*, int64_t, double*, int, cudaStream_t);
+
+size_t chol_workspace(int64_t n, int N) {
+  Arena a;
+  a.take<double>((size_t)N);
+  a.take<int>((size_t)N);
+  return a.used + 512;
+}
+
+// R: N matrices of padded order np = ceil(n/64)*64, row stride ldr >= np,
+// matrix stride rstride.  lambdas_dev: device N.  info_dev: device N.
+tk_status chol_shifted(const double* Cm, int64_t n, const double* lambdas_dev, int N, double* R, int64_t ldr,
+                       int64_t rstride, int* info_dev, Arena& ar, cudaStream_t st) {
+  (void)ar;
+  if (N == 0 || n == 0) return TK_OK;
+  const int64_t np = cdiv(n, CB) * CB;
+  const int nt = (int)(np / CB);
+  dim3 gi((unsigned)std::min<int64_t>(cdiv(np * np, 256), 4096), (unsigned)N);
+  k_chol_init<<<gi, 256, 0, st>>>(Cm, n, np, lambdas_dev, R, ldr, rstride, info_dev);
+  TK_LAUNCH_CHECK();
+  for (int kb = 0; kb < nt; ++kb) {
+    k_chol_diag<<<N, 256, 0, st>>>(R, ldr, rstride, kb, info_dev);
+    TK_LAUNCH_CHECK();
+    const int r = nt - kb - 1;
+    if (r == 0) break;
+    k_chol_trsm<<<dim3((unsigned)r, (unsigned)N), CB, 0, st>>>(R, ldr, rstride, kb);
+    TK_LAUNCH_CHECK();
+    k_chol_update<<<dim3((unsigned)(r * (r + 1) / 2), (unsigned)N), 256, 0, st>>>(R, ldr, rstride, kb, nt);
+    TK_LAUNCH_CHECK();
+  }
+  return TK_OK;
+}
+
+template <typename TR, typename TX>
+tk_status trsv_batched(bool transposed, int64_t n, const TR* R, int64_t ldr, int64_t rstride, const int* idx,
+                       const TX* Xin, TX* X, int64_t ldx, int count, cudaStream_t st) {
+  if (count <= 0 || n <= 0) return TK_OK;
+  const size_t smem = sizeof(double) * (size_t)n;
+  if (smem > 200 * 1024) {
+    set_error_msg("trsv: order too large for the shared-memory solve");
+    return TK_EINVAL;
+  }
+  if (transposed) {
+    auto kern = k_trsv_upper_t<TR, TX>;
+    TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<count, kTrsvThreads, smem, st>>>(n, R, ldr, rstride, idx, Xin, X, ldx);
+  } else {
+    auto kern = k_trsv_upper<TR, TX>;
+    TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<count, kTrsvThreads, smem, st>>>(n, R, ldr, rstride, idx, Xin, X, ldx);
+  }
+  TK_LAUNCH_CHECK();
+  return TK_OK;
+}
+
+template tk_status trsv_batched<double, double>(bool, int64_t, const double*, int64_t, int64_t, const int*,
+                                                const double*, double*, int64_t, int, cudaStream_t);
+template tk_status trsv_batched<float, float>(bool, int64_t, const float*, int64_t, int64_t, const int*, const float*,
+                                              float*, int64_t, int, cudaStream_t);
+template tk_status trsv_batched<double, float>(bool, int64_t, const double*, int64_t, int64_t, const int*,
+                                               const float*, float*, int64_t, int, cudaStream_t);
+
+}  // namespace tk

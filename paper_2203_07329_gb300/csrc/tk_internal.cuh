@@ -1,0 +1,183 @@
+// Internal declarations shared by the CUDA translation units of libtikhonov.
+// Nothing here is part of the C ABI (include/tikhonov.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <algorithm>
+
+#include "tikhonov.h"
+
+namespace tk {
+
+// ---------------------------------------------------------------- errors --
+void set_error(cudaError_t e, const char* file, int line);
+void set_error_msg(const char* msg);
+
+#define TK_CUDA(x)                                 \
+  do {                                             \
+    cudaError_t e__ = (x);                         \
+    if (e__ != cudaSuccess) {                      \
+      ::tk::set_error(e__, __FILE__, __LINE__);    \
+      return TK_ECUDA;                             \
+    }                                              \
+  } while (0)
+
+// Every kernel launch of the library is followed by TK_LAUNCH_CHECK(), which
+// also counts it (tk_launch_count()).
+void count_launch();
+#define TK_LAUNCH_CHECK()   \
+  do {                      \
+    ::tk::count_launch();   \
+    TK_CUDA(cudaGetLastError()); \
+  } while (0)
+
+#define TK_TRY(x)                  \
+  do {                             \
+    tk_status s__ = (x);           \
+    if (s__ != TK_OK) return s__;  \
+  } while (0)
+
+// ------------------------------------------------------------ workspace --
+// Bump allocator over a caller-provided device buffer (256-byte aligned
+// slices).  With base == nullptr it only measures.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  template <typename T>
+  T* take(size_t count) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + count * sizeof(T);
+    if (!base) return nullptr;
+    return reinterpret_cast<T*>(base + off);
+  }
+  bool ok() const { return base == nullptr || used <= cap; }
+};
+
+inline int64_t next_pow2(int64_t m) {
+  int64_t p = 1;
+  while (p < m) p <<= 1;
+  return p;
+}
+inline int ilog2(int64_t p) {
+  int a = 0;
+  while ((int64_t(1) << a) < p) ++a;
+  return a;
+}
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// --------------------------------------------------- Philox4x32-10 (GPU) --
+// Counter-based generator of Salmon, Moraes, Dror and Shaw (SC'11): ten
+// rounds of two 32x32 multiplies; the key advances by the Weyl constants
+// after each round.  Counter = (index lo, index hi, stream, 0), key = seed.
+__device__ __forceinline__ uint4 philox(uint64_t index, uint32_t stream, uint64_t seed) {
+  uint32_t x0 = (uint32_t)index, x1 = (uint32_t)(index >> 32), x2 = stream, x3 = 0u;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t h0 = __umulhi(0xD2511F53u, x0), l0 = 0xD2511F53u * x0;
+    uint32_t h1 = __umulhi(0xCD9E8D57u, x2), l1 = 0xCD9E8D57u * x2;
+    uint32_t y0 = h1 ^ x1 ^ k0, y2 = h0 ^ x3 ^ k1;
+    x0 = y0; x1 = l1; x2 = y2; x3 = l0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(x0, x1, x2, x3);
+}
+
+enum : uint32_t { STREAM_SIGNS = 0, STREAM_KEYS = 1, STREAM_GAUSS = 2 };
+
+// Gaussian entry k of an embedding with N(0, 1/s) entries: Philox call k/4 of
+// stream 2, Box-Muller on word pairs (w0, w1) and (w2, w3).
+__device__ __forceinline__ double gauss_entry(uint64_t seed, uint64_t k, double inv_sqrt_s) {
+  uint4 w = philox(k >> 2, STREAM_GAUSS, seed);
+  int lane = (int)(k & 3u);
+  uint32_t a = (lane < 2) ? w.x : w.z;
+  uint32_t b = (lane < 2) ? w.y : w.w;
+  double u1 = ((double)a + 1.0) * 2.3283064365386962890625e-10;
+  double u2 = (double)b * 2.3283064365386962890625e-10;
+  double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  return ((lane & 1) ? r * sn : r * cs) * inv_sqrt_s;
+}
+
+// -------------------------------------------------------------- reduce --
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread gets the result.  `sh` needs 32 entries.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  T t = (threadIdx.x < (unsigned)nw) ? sh[threadIdx.x] : T(0);
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------ profiler --
+int prof_begin(int phase, cudaStream_t st);
+void prof_end(int tok, cudaStream_t st, double flops, double bytes);
+
+// --------------------------------------------------------- launchers -----
+// Draws (tk_draw.cu)
+size_t draw_workspace(int64_t mp);
+tk_status draw_signs_rows(uint64_t seed, int64_t mp, int64_t s, int8_t* signs, int64_t* rows, int32_t* rowmap,
+                          Arena& ar, cudaStream_t st);
+
+// Sketches (tk_sketch.cu).  Y = X A (s x cols) of the "long axis first"
+// layout: the transform runs along the rows of a (L x cols) matrix with
+// row stride ld.  Output Y is s x cols float64.
+tk_status srht_rows(const void* A, tk_dtype dt, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s,
+                    double* Y, Arena& ar, cudaStream_t st);
+size_t srht_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s);
+tk_status gauss_rows(const void* A, tk_dtype dt, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s,
+                     double* Y, Arena& ar, cudaStream_t st);
+size_t gauss_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s);
+tk_status transpose(const void* A, tk_dtype dt, int64_t rows, int64_t cols, int64_t lda, void* AT,
+                    cudaStream_t st);
+tk_status convert_f64_to_f32(const double* src, float* dst, int64_t rows, int64_t cols, int64_t lds, int64_t ldd,
+                             cudaStream_t st);
+
+// Dense kernels (tk_dense.cu)
+template <typename TA, typename TB, typename TC>
+tk_status gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
+               int64_t ldb, TC* C, int64_t ldc, double alpha, const double* beta_row, const TC* Cin,
+               int64_t ldcin, cudaStream_t st);
+template <typename TA, typename TB>
+tk_status gemm_splitk(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda,
+                      const TB* B, int64_t ldb, double* partial, int splits, cudaStream_t st);
+int splitk_count(int64_t M, int64_t N, int64_t K);
+
+size_t chol_workspace(int64_t n, int N);
+tk_status chol_shifted(const double* C, int64_t n, const double* lambdas_dev, int N, double* R, int64_t ldr,
+                       int64_t rstride, int* info_dev, Arena& ar, cudaStream_t st);
+
+// Batched triangular solves on slots: vector of slot j is X + j*ldx (length
+// n); its factor is R + idx[j]*rstride (row stride ldr, upper triangular).
+template <typename TR, typename TX>
+tk_status trsv_batched(bool transposed, int64_t n, const TR* R, int64_t ldr, int64_t rstride, const int* idx,
+                       const TX* Xin, TX* X, int64_t ldx, int count, cudaStream_t st);
+
+// Low rank (tk_lowrank.cu)
+size_t svd_workspace(int64_t s, int64_t n);
+tk_status jacobi_svd(const double* Y, int64_t s, int64_t n, double* sigma, double* V, int* sweeps_host, Arena& ar,
+                     cudaStream_t st);
+
+}  // namespace tk

@@ -1,0 +1,79 @@
+// Batched preconditioned LSQR engine (internal).
+#pragma once
+
+#include <vector>
+
+#include "tk_internal.cuh"
+
+namespace tk {
+
+// Per-slot LSQR scalars (device resident).
+struct Scal {
+  double alpha, beta, rhobar, phibar, anorm2, bnorm, lam, sqrtl, coef, rnorm, arnorm, ynorm;
+  int iters, istop, lam_idx, pad;
+};
+
+struct LsqrResult {
+  int lam_idx, iters, istop;
+  double rnorm, arnorm;
+};
+
+// Low-rank preconditioner apply (Section 3.1, eq. for R^-1):
+// out_k = l^{-1/2} (in_k - V diag(S_l) V^T in_k) for each listed row k, with
+// l = lam_idx[k]; V is n x s (row-major), S is N_lam x s (zero past s_l).
+template <typename T>
+tk_status lr_apply(int count, int64_t n, int64_t s, const T* V, const T* S, const int* lam_idx,
+                   const double* lam_dev, const T* in, T* out, T* tmp, double* invs, cudaStream_t st);
+
+// sd_i, s_i of Algorithm 3 step 5 (device in/out) and the S_i rows (step 7).
+tk_status lowrank_ranks_dev(const double* sigma, int64_t s, const double* lam_dev, int N, double alpha,
+                            double* sd_dev, int64_t* rank_dev, cudaStream_t st);
+template <typename T>
+tk_status lowrank_diag_dev(const double* sigma, int64_t s, const double* lam_dev, const int64_t* rank_dev, int N,
+                           T* S, cudaStream_t st);
+
+template <typename T>
+struct Lsqr {
+  // problem: A (m x n, row stride lda) in the compute type
+  const T* A = nullptr;
+  int64_t m = 0, n = 0, lda = 0;
+  bool under = false;
+  // preconditioner: per-lambda Cholesky factors R + l*rstride, or low rank
+  tk_precond prec_kind = TK_PRECOND_CHOL;
+  const T* R = nullptr;
+  int64_t ldr = 0, rstride = 0;
+  int64_t lr_s = 0;
+  const T* lrV = nullptr;
+  const T* lrS = nullptr;
+  // parameters
+  int N_cap = 0;
+  double atol = 1e-14, btol = 1e-14;
+  int maxiter = 500;
+  cudaStream_t st = nullptr;
+  // workspace
+  int64_t nv = 0;
+  int splits = 1;
+  T *V = nullptr, *W = nullptr, *Y = nullptr, *Vraw = nullptr, *Ut = nullptr, *Tt = nullptr, *Ub = nullptr,
+    *xtmp = nullptr, *lr_tmp = nullptr;
+  double *part_u = nullptr, *part_g = nullptr, *coef_buf = nullptr, *lr_inv = nullptr;
+  Scal* sc = nullptr;
+  int* slot_lam = nullptr;
+  int* idx_buf = nullptr;
+  const double* lam_all = nullptr;
+
+  static size_t workspace(int64_t m, int64_t n, int N_cap, bool under, int64_t lr_s);
+  void carve(Arena& a);
+  // Solve for `count` lambdas (indices lam_ids_dev[k] into lam_dev).  The
+  // right-hand side of the k-th listed lambda is [b + k*ldbt; (bbot + k*ldbb) / sqrt(l)]
+  // (overdetermined; ldbt = 0 shares b; b or bbot null = zero block) or b
+  // (underdetermined).  Writes (or adds) x_l into Xout + l*ldo.
+  tk_status run(const double* b, int64_t ldbt, const double* bbot, int64_t ldbb, const int* lam_ids_dev,
+                const double* lam_dev, int count, double* Xout, int64_t ldo, bool accumulate,
+                std::vector<LsqrResult>& results);
+  tk_status apply_prec(bool transposed, const T* in, T* out, int count, int64_t len);
+  tk_status prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, int count);
+  tk_status prod_atu(const T* Uin, int count);
+  tk_status gather_coef(int count);
+};
+
+}  // namespace tk

@@ -1,0 +1,246 @@
+// Sketch of A (Section 2.1.1; Algorithm 1 step 2 / Algorithm 2 step 2).
+//
+// Every sketch here acts along the long axis of an L x cols row-major matrix
+// (the overdetermined A directly; the underdetermined A after a transpose, so
+// that Y = A X becomes Y^T = X^T A^T with the same kernels).
+//
+// SRHT: Y = sqrt(Lp/s) S (H/sqrt(Lp)) D [A; 0] = (1/sqrt(s)) S H D [A; 0].
+//   H_Lp (Sylvester) factors as a product of butterfly levels over the bits
+//   of the row index.  Each pass loads a tile of 2^t rows (rows that differ
+//   only in t consecutive index bits) x CB columns into shared memory, runs
+//   the t butterfly levels there, and writes it back: log2(Lp)/9 passes over
+//   the data instead of log2(Lp).  The first pass applies D while loading
+//   (rows >= L read as zero); the last pass writes only the sampled rows.
+// Gaussian: Y = G A with G (s x L) of N(0, 1/s) entries from Philox stream 2,
+//   generated into the workspace, then a plain GEMM.
+#include <algorithm>
+#include <type_traits>
+
+#include "tk_internal.cuh"
+
+namespace tk {
+namespace {
+
+constexpr int kFwhtThreads = 256;
+constexpr int kFwhtMaxBits = 9;
+
+template <typename TIn, typename TC, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(kFwhtThreads)
+    k_fwht_pass(const TIn* src, int64_t ld_src, TC* dst, double* __restrict__ Y,
+                const int8_t* __restrict__ signs, const int32_t* __restrict__ rowmap, int64_t L, int64_t cols,
+                int b0, int t, int CB, int64_t ncb, double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* tile = reinterpret_cast<TC*>(smem_raw);
+  const int64_t g = blockIdx.x / ncb;
+  const int64_t cb = blockIdx.x % ncb;
+  const int64_t lo = g & ((int64_t(1) << b0) - 1);
+  const int64_t hi = g >> b0;
+  const int rows_t = 1 << t;
+  const int64_t c0 = cb * CB;
+  const int tile_elems = rows_t * CB;
+  for (int idx = threadIdx.x; idx < tile_elems; idx += blockDim.x) {
+    int mid = idx / CB, c = idx - mid * CB;
+    int64_t r = (hi << (b0 + t)) | ((int64_t)mid << b0) | lo;
+    int64_t col = c0 + c;
+    TC v = TC(0);
+    if (col < cols) {
+      if (FIRST) {
+        if (r < L) v = (TC)src[r * ld_src + col] * (TC)signs[r];
+      } else {
+        v = (TC)src[r * ld_src + col];
+      }
+    }
+    tile[idx] = v;
+  }
+  __syncthreads();
+  const int pairs = (rows_t >> 1) * CB;
+  for (int h = 1; h < rows_t; h <<= 1) {
+    for (int p = threadIdx.x; p < pairs; p += blockDim.x) {
+      int q = p / CB, c = p - q * CB;
+      int i = (q / h) * 2 * h + (q % h);
+      int j = i + h;
+      TC a = tile[i * CB + c], b = tile[j * CB + c];
+      tile[i * CB + c] = a + b;
+      tile[j * CB + c] = a - b;
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < tile_elems; idx += blockDim.x) {
+    int mid = idx / CB, c = idx - mid * CB;
+    int64_t r = (hi << (b0 + t)) | ((int64_t)mid << b0) | lo;
+    int64_t col = c0 + c;
+    if (col >= cols) continue;
+    if (LAST) {
+      int32_t k = rowmap[r];
+      if (k >= 0) Y[(int64_t)k * cols + col] = scale * (double)tile[idx];
+    } else {
+      dst[r * cols + col] = tile[idx];
+    }
+  }
+}
+
+template <typename TIn, typename TC>
+tk_status run_fwht_pass(bool first, bool last, const TIn* srcA, const TC* srcZ, int64_t ld_src, TC* Z, double* Y,
+                        const int8_t* signs, const int32_t* rowmap, int64_t L, int64_t Lp, int64_t cols, int b0,
+                        int t, double scale, cudaStream_t st) {
+  const int CB = (int)(64 * 16 / sizeof(TC) / 8);  // 16 doubles or 32 floats = 128 bytes per row
+  const int64_t ncb = cdiv(cols, CB);
+  const int64_t groups = Lp >> t;
+  const int64_t blocks = groups * ncb;
+  const size_t smem = sizeof(TC) * (size_t)(1 << t) * CB;
+#define TK_FWHT_LAUNCH(F, LST, SRC)                                                                       \
+  do {                                                                                                    \
+    auto kern = k_fwht_pass<TIn, TC, F, LST>;                                                             \
+    TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));          \
+    kern<<<(unsigned)blocks, kFwhtThreads, smem, st>>>(SRC, ld_src, Z, Y, signs, rowmap, L, cols, b0, t, \
+                                                       CB, ncb, scale);                                   \
+  } while (0)
+  if (first && last) TK_FWHT_LAUNCH(true, true, srcA);
+  else if (first) TK_FWHT_LAUNCH(true, false, srcA);
+  else if (last) TK_FWHT_LAUNCH(false, true, reinterpret_cast<const TIn*>(srcZ));
+  else TK_FWHT_LAUNCH(false, false, reinterpret_cast<const TIn*>(srcZ));
+#undef TK_FWHT_LAUNCH
+  TK_LAUNCH_CHECK();
+  return TK_OK;
+}
+
+template <typename TC>
+__global__ void k_gauss_fill(uint64_t seed, int64_t s, int64_t L, double inv_sqrt_s, TC* __restrict__ G) {
+  int64_t total = s * L;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += stride)
+    G[k] = (TC)gauss_entry(seed, (uint64_t)k, inv_sqrt_s);
+}
+
+template <typename T>
+__global__ void k_transpose(const T* __restrict__ A, int64_t rows, int64_t cols, int64_t lda, T* __restrict__ AT) {
+  __shared__ T tileT[32][33];
+  int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int64_t r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tileT[k][threadIdx.x] = A[r * lda + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int64_t c = c0 + k, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) AT[c * rows + r] = tileT[threadIdx.x][k];
+  }
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ s, float* __restrict__ d, int64_t rows, int64_t cols,
+                             int64_t lds, int64_t ldd) {
+  int64_t total = rows * cols;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += stride) {
+    int64_t r = k / cols, c = k - r * cols;
+    d[r * ldd + c] = (float)s[r * lds + c];
+  }
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ s, double* __restrict__ d, int64_t total) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += stride) d[k] = (double)s[k];
+}
+
+int grid_for(int64_t total, int threads) { return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, threads), 152 * 32)); }
+
+template <typename TIn, typename TC>
+tk_status srht_impl(const TIn* A, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s, double* Y,
+                    Arena& ar, cudaStream_t st) {
+  const int64_t Lp = next_pow2(L);
+  const int a = ilog2(Lp);
+  int8_t* signs = ar.take<int8_t>((size_t)Lp);
+  int32_t* rowmap = ar.take<int32_t>((size_t)Lp);
+  TC* Z = (a > kFwhtMaxBits) ? ar.take<TC>((size_t)Lp * (size_t)cols) : nullptr;
+  if (!ar.ok()) return TK_ENOMEM;
+  TK_TRY(draw_signs_rows(seed, Lp, s, signs, nullptr, rowmap, ar, st));
+  if (s == 0 || cols == 0) return TK_OK;
+  const double scale = 1.0 / sqrt((double)s);
+  int npass = (a + kFwhtMaxBits - 1) / kFwhtMaxBits;
+  if (npass == 0) npass = 1;
+  int b0 = 0;
+  for (int p = 0; p < npass; ++p) {
+    int t = std::min(kFwhtMaxBits, a - b0);
+    if (t < 0) t = 0;
+    bool first = (p == 0), last = (p == npass - 1);
+    TK_TRY((run_fwht_pass<TIn, TC>(first, last, A, Z, first ? ld : cols, Z, Y, signs, rowmap, L, Lp, cols, b0, t,
+                                   scale, st)));
+    b0 += t;
+  }
+  return TK_OK;
+}
+
+template <typename TIn, typename TC>
+tk_status gauss_impl(const TIn* A, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s, double* Y,
+                     Arena& ar, cudaStream_t st) {
+  TC* G = ar.take<TC>((size_t)s * (size_t)L);
+  TC* Yc = std::is_same<TC, double>::value ? nullptr : ar.take<TC>((size_t)s * (size_t)cols);
+  if (!ar.ok()) return TK_ENOMEM;
+  if (s == 0 || cols == 0) return TK_OK;
+  k_gauss_fill<TC><<<grid_for(s * L, 256), 256, 0, st>>>(seed, s, L, 1.0 / sqrt((double)s), G);
+  TK_LAUNCH_CHECK();
+  if (std::is_same<TC, double>::value) {
+    TK_TRY((gemm<TC, TIn, double>(false, false, s, cols, L, G, L, A, ld, Y, cols, 1.0, nullptr, nullptr, 0, st)));
+  } else {
+    TK_TRY((gemm<TC, TIn, TC>(false, false, s, cols, L, G, L, A, ld, Yc, cols, 1.0, nullptr, nullptr, 0, st)));
+    k_f32_to_f64<<<grid_for(s * cols, 256), 256, 0, st>>>(reinterpret_cast<const float*>(Yc), Y, s * cols);
+    TK_LAUNCH_CHECK();
+  }
+  return TK_OK;
+}
+
+}  // namespace
+
+size_t srht_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s) {
+  (void)s;
+  const int64_t Lp = next_pow2(L);
+  Arena a;
+  a.take<int8_t>((size_t)Lp);
+  a.take<int32_t>((size_t)Lp);
+  if (ilog2(Lp) > kFwhtMaxBits) a.take<char>((size_t)Lp * (size_t)cols * (dt == TK_F64 ? 8 : 4));
+  return a.used + draw_workspace(Lp) + 512;
+}
+
+size_t gauss_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s) {
+  Arena a;
+  size_t es = dt == TK_F64 ? 8 : 4;
+  a.take<char>((size_t)s * (size_t)L * es);
+  if (dt != TK_F64) a.take<char>((size_t)s * (size_t)cols * es);
+  return a.used + 512;
+}
+
+tk_status srht_rows(const void* A, tk_dtype dt, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s,
+                    double* Y, Arena& ar, cudaStream_t st) {
+  if (dt == TK_F64) return srht_impl<double, double>((const double*)A, L, cols, ld, seed, s, Y, ar, st);
+  return srht_impl<float, float>((const float*)A, L, cols, ld, seed, s, Y, ar, st);
+}
+
+tk_status gauss_rows(const void* A, tk_dtype dt, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s,
+                     double* Y, Arena& ar, cudaStream_t st) {
+  if (dt == TK_F64) return gauss_impl<double, double>((const double*)A, L, cols, ld, seed, s, Y, ar, st);
+  return gauss_impl<float, float>((const float*)A, L, cols, ld, seed, s, Y, ar, st);
+}
+
+tk_status transpose(const void* A, tk_dtype dt, int64_t rows, int64_t cols, int64_t lda, void* AT, cudaStream_t st) {
+  if (rows == 0 || cols == 0) return TK_OK;
+  dim3 grid((unsigned)cdiv(cols, 32), (unsigned)cdiv(rows, 32));
+  dim3 block(32, 8);
+  if (grid.y > 65535u) {
+    set_error_msg("transpose: too many rows for one launch");
+    return TK_EINVAL;
+  }
+  if (dt == TK_F64) k_transpose<double><<<grid, block, 0, st>>>((const double*)A, rows, cols, lda, (double*)AT);
+  else k_transpose<float><<<grid, block, 0, st>>>((const float*)A, rows, cols, lda, (float*)AT);
+  TK_LAUNCH_CHECK();
+  return TK_OK;
+}
+
+tk_status convert_f64_to_f32(const double* src, float* dst, int64_t rows, int64_t cols, int64_t lds, int64_t ldd,
+                             cudaStream_t st) {
+  if (rows * cols == 0) return TK_OK;
+  k_f64_to_f32<<<grid_for(rows * cols, 256), 256, 0, st>>>(src, dst, rows, cols, lds, ldd);
+  TK_LAUNCH_CHECK();
+  return TK_OK;
+}
+
+}  // namespace tk

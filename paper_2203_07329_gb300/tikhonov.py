@@ -1,0 +1,299 @@
+"""ctypes binding of libtikhonov (include/tikhonov.h).  Argument marshalling only.
+
+Every function here forwards to the C ABI of the same name; torch is used for
+device buffers (inputs, outputs, the workspace) and streams.  There is no CPU
+fallback: if the shared library is missing this module raises on load.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtikhonov.so")
+
+TK_OK, TK_EINVAL, TK_ENOMEM, TK_ENOTSPD, TK_ENOCONV, TK_ENUMERIC, TK_ETIMEOUT, TK_ECUDA = range(8)
+TK_F64, TK_F32 = 0, 1
+TK_SKETCH_SRHT, TK_SKETCH_GAUSS = 0, 1
+TK_PRECOND_CHOL, TK_PRECOND_LOWRANK = 0, 1
+TK_PREC_FP64, TK_PREC_MIXED = 0, 1
+TK_SCHED_BATCHED, TK_SCHED_ONE_AT_A_TIME = 0, 1
+
+STATUS_NAMES = {0: "TK_OK", 1: "TK_EINVAL", 2: "TK_ENOMEM", 3: "TK_ENOTSPD", 4: "TK_ENOCONV", 5: "TK_ENUMERIC",
+                6: "TK_ETIMEOUT", 7: "TK_ECUDA"}
+
+
+class tk_problem(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("lda", C.c_int64), ("dtype", C.c_int),
+                ("A", C.c_void_p), ("b", C.c_void_p)]
+
+
+class tk_opts(C.Structure):
+    _fields_ = [("sketch", C.c_int), ("s", C.c_int64), ("precond", C.c_int), ("alpha", C.c_double),
+                ("precision", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int), ("max_refine", C.c_int),
+                ("inner_tol", C.c_double), ("refine_tol", C.c_double), ("seed", C.c_uint64),
+                ("schedule", C.c_int)]
+
+
+class tk_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("refine_steps", C.c_int), ("istop", C.c_int), ("rank", C.c_int64),
+                ("rnorm", C.c_double), ("arnorm", C.c_double), ("ne_norm", C.c_double), ("status", C.c_int)]
+
+
+TK_PHASE_COUNT = 9
+
+
+class tk_phase_stats(C.Structure):
+    _fields_ = [("ms", C.c_double), ("flops", C.c_double), ("bytes", C.c_double), ("launches", C.c_int)]
+
+
+class TikhonovError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libtikhonov.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+        L = C.CDLL(LIB_PATH)
+        P, I64, D, INT, SZ, U64 = C.c_void_p, C.c_int64, C.c_double, C.c_int, C.c_size_t, C.c_uint64
+        sigs = {
+            "tk_opts_default": (INT, [P]),
+            "tk_status_str": (C.c_char_p, [INT]),
+            "tk_last_error": (C.c_char_p, []),
+            "tk_workspace_size": (INT, [P, INT, P, P]),
+            "tk_solve": (INT, [P, P, INT, P, P, SZ, P, P, P]),
+            "tk_workspace_size_batched": (INT, [P, INT, INT, P, P]),
+            "tk_solve_batched": (INT, [P, INT, P, INT, P, P, SZ, P, P, P]),
+            "tk_sketch_draw_workspace": (SZ, [I64]),
+            "tk_sketch_draw": (INT, [U64, I64, I64, P, P, P, SZ, P]),
+            "tk_sketch_apply_workspace": (INT, [P, P, P]),
+            "tk_sketch_apply": (INT, [P, P, P, P, SZ, P]),
+            "tk_gram": (INT, [P, I64, I64, INT, P, P]),
+            "tk_cholesky_workspace": (SZ, [I64, INT]),
+            "tk_cholesky_shifted": (INT, [P, I64, P, INT, P, P, P, SZ, P]),
+            "tk_sketch_svd_workspace": (SZ, [I64, I64]),
+            "tk_sketch_svd": (INT, [P, I64, I64, P, P, P, P, SZ, P]),
+            "tk_lowrank_ranks_workspace": (SZ, [INT]),
+            "tk_lowrank_ranks": (INT, [P, I64, P, INT, D, P, P, P, SZ, P]),
+            "tk_phase_name": (C.c_char_p, [INT]),
+            "tk_launch_count": (C.c_ulonglong, []),
+            "tk_profile_enable": (INT, [INT]),
+            "tk_profile_collect": (INT, [P]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().tk_last_error().decode()
+
+
+def _check(status: int, ok=(TK_OK,)) -> int:
+    if status not in ok:
+        raise TikhonovError(status, last_error())
+    return status
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return TK_F64
+    if t.dtype == torch.float32:
+        return TK_F32
+    raise TypeError("A must be float64 or float32")
+
+
+def make_problem(A: torch.Tensor, b: torch.Tensor) -> tk_problem:
+    if not (A.is_cuda and b.is_cuda):
+        raise ValueError("A and b must be CUDA tensors")
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a row-major matrix (unit column stride)")
+    if b.dtype != torch.float64 or not b.is_contiguous() or b.numel() != A.shape[0]:
+        raise ValueError("b must be a contiguous float64 vector of length m")
+    return tk_problem(A.shape[0], A.shape[1], A.stride(0), _dtype_code(A), A.data_ptr(), b.data_ptr())
+
+
+def opts_default(**kw) -> tk_opts:
+    o = tk_opts()
+    lib().tk_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def workspace_size(prob: tk_problem, N: int, opts: tk_opts) -> int:
+    out = C.c_size_t(0)
+    _check(lib().tk_workspace_size(C.byref(prob), N, C.byref(opts), C.byref(out)))
+    return int(out.value)
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+@dataclass
+class SolveResult:
+    X: torch.Tensor          # N x n float64 on the device
+    info: list               # per-lambda dicts
+    status: int
+
+
+def _info_dicts(arr, N):
+    return [dict(iters=arr[i].iters, refine_steps=arr[i].refine_steps, istop=arr[i].istop, rank=arr[i].rank,
+                 rnorm=arr[i].rnorm, arnorm=arr[i].arnorm, ne_norm=arr[i].ne_norm, status=arr[i].status)
+            for i in range(N)]
+
+
+def tk_solve(A: torch.Tensor, b: torch.Tensor, lambdas, opts: tk_opts | None = None, *, work=None, stream=None,
+             X: torch.Tensor | None = None, allow=(TK_OK, TK_ENOCONV, TK_ENOTSPD)) -> SolveResult:
+    """x_{lambda_i} for all lambda_i (problem (1.2)); see tk_solve in include/tikhonov.h."""
+    opts = opts or opts_default()
+    prob = make_problem(A, b)
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+    N = int(lam.shape[0])
+    n = A.shape[1]
+    if X is None:
+        X = torch.empty((N, n), dtype=torch.float64, device=A.device)
+    nbytes = workspace_size(prob, N, opts)
+    if work is None or work.numel() < nbytes:
+        work = _workspace(nbytes, A.device)
+    info = (tk_info * max(N, 1))()
+    st = lib().tk_solve(C.byref(prob), lam.ctypes.data_as(C.c_void_p), N, C.byref(opts), _ptr(work),
+                        work.numel(), _stream(stream), _ptr(X), info)
+    _check(st, allow)
+    return SolveResult(X=X, info=_info_dicts(info, N), status=st)
+
+
+def tk_solve_batched(problems, lambdas, opts: tk_opts | None = None, *, work=None, stream=None,
+                     allow=(TK_OK, TK_ENOCONV, TK_ENOTSPD)):
+    """problems: list of (A, b) CUDA tensors; lambdas: P x N host array."""
+    opts = opts or opts_default()
+    P = len(problems)
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+    N = lam.shape[1]
+    probs = (tk_problem * P)(*[make_problem(A, b) for A, b in problems])
+    out = C.c_size_t(0)
+    _check(lib().tk_workspace_size_batched(probs, P, N, C.byref(opts), C.byref(out)))
+    dev = problems[0][0].device
+    if work is None or work.numel() < out.value:
+        work = _workspace(out.value, dev)
+    Xs = [torch.empty((N, A.shape[1]), dtype=torch.float64, device=dev) for A, _ in problems]
+    xp = (C.c_void_p * P)(*[x.data_ptr() for x in Xs])
+    info = (tk_info * (P * N))()
+    st = lib().tk_solve_batched(probs, P, lam.ctypes.data_as(C.c_void_p), N, C.byref(opts), _ptr(work),
+                                work.numel(), _stream(stream), xp, info)
+    _check(st, allow)
+    infos = _info_dicts(info, P * N)
+    return Xs, [infos[p * N:(p + 1) * N] for p in range(P)], st
+
+
+def tk_sketch_draw(seed: int, mp: int, s: int, device="cuda", stream=None):
+    """SRHT integer draws: (signs int8[mp], rows int64[s]) on the device."""
+    signs = torch.empty(mp, dtype=torch.int8, device=device)
+    rows = torch.empty(max(s, 1), dtype=torch.int64, device=device)
+    ws = int(lib().tk_sketch_draw_workspace(mp))
+    work = _workspace(ws, device)
+    _check(lib().tk_sketch_draw(seed, mp, s, _ptr(signs), _ptr(rows), _ptr(work), work.numel(), _stream(stream)))
+    return signs, rows[:s]
+
+
+def tk_sketch_apply(A: torch.Tensor, opts: tk_opts, stream=None) -> torch.Tensor:
+    """Y = X A (m >= n, s x n) or Y = A X (m < n, m x s), float64."""
+    b = torch.zeros(A.shape[0], dtype=torch.float64, device=A.device)
+    prob = make_problem(A, b)
+    out = C.c_size_t(0)
+    _check(lib().tk_sketch_apply_workspace(C.byref(prob), C.byref(opts), C.byref(out)))
+    m, n = A.shape
+    s = opts.s if opts.s > 0 else min(4 * min(m, n), max(m, n))
+    Y = torch.empty((s, n) if m >= n else (m, s), dtype=torch.float64, device=A.device)
+    work = _workspace(out.value, A.device)
+    _check(lib().tk_sketch_apply(C.byref(prob), C.byref(opts), _ptr(Y), _ptr(work), work.numel(), _stream(stream)))
+    return Y
+
+
+def tk_gram(Y: torch.Tensor, transpose_first: bool = True, stream=None) -> torch.Tensor:
+    r, c = Y.shape
+    Cm = torch.empty((c, c) if transpose_first else (r, r), dtype=torch.float64, device=Y.device)
+    _check(lib().tk_gram(_ptr(Y.contiguous()), r, c, 1 if transpose_first else 0, _ptr(Cm), _stream(stream)))
+    return Cm
+
+
+def tk_cholesky_shifted(Cm: torch.Tensor, lambdas, stream=None):
+    """R_i = chol(C + lambda_i I): returns (R N x n x n, breakdown list)."""
+    n = Cm.shape[0]
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+    N = lam.shape[0]
+    R = torch.empty((N, n, n), dtype=torch.float64, device=Cm.device)
+    brk = (C.c_int * N)()
+    work = _workspace(lib().tk_cholesky_workspace(n, N), Cm.device)
+    st = lib().tk_cholesky_shifted(_ptr(Cm.contiguous()), n, lam.ctypes.data_as(C.c_void_p), N, _ptr(R), brk,
+                                   _ptr(work), work.numel(), _stream(stream))
+    _check(st, (TK_OK, TK_ENOTSPD))
+    return R, list(brk)
+
+
+def tk_sketch_svd(Y: torch.Tensor, stream=None):
+    """[~, Sigma, V] = svd(Y, 'econ') by one-sided Jacobi: (sigma s, V n x s, sweeps)."""
+    s, n = Y.shape
+    sig = torch.empty(s, dtype=torch.float64, device=Y.device)
+    V = torch.empty((n, s), dtype=torch.float64, device=Y.device)
+    sw = C.c_int(0)
+    work = _workspace(lib().tk_sketch_svd_workspace(s, n), Y.device)
+    _check(lib().tk_sketch_svd(_ptr(Y.contiguous()), s, n, _ptr(sig), _ptr(V), C.byref(sw), _ptr(work),
+                               work.numel(), _stream(stream)))
+    return sig, V, sw.value
+
+
+def tk_lowrank_ranks(sigma: torch.Tensor, lambdas, alpha: float, stream=None):
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+    N = lam.shape[0]
+    sd = np.zeros(N)
+    rk = np.zeros(N, dtype=np.int64)
+    work = _workspace(lib().tk_lowrank_ranks_workspace(N), sigma.device)
+    _check(lib().tk_lowrank_ranks(_ptr(sigma.contiguous()), sigma.numel(), lam.ctypes.data_as(C.c_void_p), N,
+                                  alpha, sd.ctypes.data_as(C.c_void_p), rk.ctypes.data_as(C.c_void_p), _ptr(work),
+                                  work.numel(), _stream(stream)))
+    return sd, rk
+
+
+def tk_profile_enable(on: bool = True) -> None:
+    _check(lib().tk_profile_enable(1 if on else 0))
+
+
+def tk_profile_collect() -> dict:
+    """Per-phase totals since the last collect: {name: dict(ms, flops, bytes, launches)}."""
+    arr = (tk_phase_stats * TK_PHASE_COUNT)()
+    _check(lib().tk_profile_collect(arr))
+    return {lib().tk_phase_name(i).decode(): dict(ms=arr[i].ms, flops=arr[i].flops, bytes=arr[i].bytes,
+                                                   launches=arr[i].launches) for i in range(TK_PHASE_COUNT)}
+
+
+def tk_launch_count() -> int:
+    return int(lib().tk_launch_count())

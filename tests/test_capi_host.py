@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and loads,
+exports every symbol include/*.h declares, and rejects bad arguments on the
+host before any launch (no compute call is made)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tk():
+    from paper_2203_07329_gb300 import build
+    build.build()
+    from paper_2203_07329_gb300 import tikhonov
+    tikhonov.lib()
+    return tikhonov
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        names |= set(re.findall(r"TK_API\s+[\w\s\*]+?\b(tk_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(tk):
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    L = C.CDLL(tk.LIB_PATH)
+    for name in syms:
+        assert hasattr(L, name), name
+
+
+def test_status_strings_and_defaults(tk):
+    L = tk.lib()
+    for s in range(8):
+        assert len(L.tk_status_str(s)) > 0
+    o = tk.opts_default()
+    assert o.tol == 1e-14 and o.maxiter == 500 and o.sketch == tk.TK_SKETCH_SRHT and o.seed == 1
+
+
+def _prob(tk, m, n, lda=None):
+    # fake non-null device addresses: validation must reject before touching them
+    return tk.tk_problem(m, n, lda if lda is not None else n, tk.TK_F64, 0x1000, 0x2000)
+
+
+@pytest.mark.parametrize("lams,field", [([1.0, 0.0], "zero"), ([1.0, -2.0], "negative"),
+                                        ([float("nan")], "nan"), ([float("inf")], "inf")])
+def test_bad_lambda_rejected_on_host(tk, lams, field):
+    p = _prob(tk, 100, 10)
+    o = tk.opts_default()
+    lam = np.array(lams, dtype=np.float64)
+    st = tk.lib().tk_solve(C.byref(p), lam.ctypes.data_as(C.c_void_p), len(lams), C.byref(o), None, 0, None,
+                           C.c_void_p(0x3000), None)
+    assert st == tk.TK_EINVAL, field
+    assert "lambda" in tk.last_error()
+
+
+def test_bad_shapes_and_options_rejected(tk):
+    L = tk.lib()
+    o = tk.opts_default()
+    out = C.c_size_t(0)
+    assert L.tk_workspace_size(C.byref(_prob(tk, 100, 10, lda=5)), 2, C.byref(o), C.byref(out)) == tk.TK_EINVAL
+    assert L.tk_workspace_size(C.byref(_prob(tk, 0, 10)), 2, C.byref(o), C.byref(out)) == tk.TK_EINVAL
+    o2 = tk.opts_default(tol=-1.0)
+    assert L.tk_workspace_size(C.byref(_prob(tk, 100, 10)), 2, C.byref(o2), C.byref(out)) == tk.TK_EINVAL
+    o3 = tk.opts_default(s=1000)  # SRHT sketch larger than the padded length 128
+    assert L.tk_workspace_size(C.byref(_prob(tk, 100, 10)), 2, C.byref(o3), C.byref(out)) == tk.TK_EINVAL
+    o4 = tk.opts_default(precond=tk.TK_PRECOND_LOWRANK)
+    assert L.tk_workspace_size(C.byref(_prob(tk, 10, 100)), 2, C.byref(o4), C.byref(out)) == tk.TK_EINVAL
+    assert L.tk_workspace_size(C.byref(_prob(tk, 100, 10)), 2, C.byref(o), C.byref(out)) == tk.TK_OK
+    assert out.value > 100 * 10 * 8
+
+
+def test_workspace_too_small_is_enomem(tk):
+    p = _prob(tk, 100, 10)
+    o = tk.opts_default()
+    lam = np.array([1.0])
+    st = tk.lib().tk_solve(C.byref(p), lam.ctypes.data_as(C.c_void_p), 1, C.byref(o), C.c_void_p(0x4000), 16, None,
+                           C.c_void_p(0x3000), None)
+    assert st == tk.TK_ENOMEM
+
+
+def test_workspace_grows_with_lambda_count(tk):
+    o = tk.opts_default()
+    sizes = []
+    for N in (1, 8, 32):
+        out = C.c_size_t(0)
+        assert tk.lib().tk_workspace_size(C.byref(_prob(tk, 4096, 256)), N, C.byref(o), C.byref(out)) == 0
+        sizes.append(out.value)
+    assert sizes[0] < sizes[1] < sizes[2]

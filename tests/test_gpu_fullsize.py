@@ -1,0 +1,92 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py times.
+
+The oracle cannot run Algorithms 1-2 at these sizes in test time, so it
+computes the reference for sampled lambdas one by one: the closed form
+x = V diag(sigma/(sigma^2 + l)) U^T b from the generator's factors, refined
+against the stored A with double-double normal-equation residuals
+(oracle.ref_ridge_refine).  That reference is accurate far below 1e-10.
+
+Tolerance per lambda: 1e-10, or -- where float64 itself cannot reach it --
+8x the conditioning floor of any backward-stable float64 solve,
+u (kappa_B + kappa_B^2 ||r|| / (||B|| ||x||)) with kappa_B^2 = (s1^2 + l)/(sn^2 + l).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2203_07329_gb300 import datagen
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def tk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_07329_gb300 import build
+    build.build()
+    from paper_2203_07329_gb300 import tikhonov
+    tikhonov.lib()
+    return tikhonov
+
+
+def floor_tol(sig, lam, rnorm, xnorm):
+    kB = math.sqrt((sig.max() ** 2 + lam) / (sig.min() ** 2 + lam))
+    Bn = math.sqrt(sig.max() ** 2 + lam)
+    return U64 * (kB + kB * kB * rnorm / (Bn * xnorm))
+
+
+def reference(prob, lam, x0_dev=None):
+    """Closed form from the generator's factors, then double-double refinement."""
+    U, V = prob.U, prob.V
+    sig = prob.sigma.to(U.device)
+    c = (U.T @ prob.b) * (sig / (sig * sig + lam))
+    x0 = (V @ c).cpu().numpy()
+    A = prob.A.double().cpu().numpy() if prob.A.dtype != torch.float64 else prob.A.cpu().numpy()
+    return oracle.ref_ridge_refine(A, prob.b.cpu().numpy(), lam, V.cpu().numpy(), prob.sigma.numpy(), x0, steps=2), A
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_over_262144x2048_srht(tk, precision):
+    prob, w = datagen.workload_problem("ridge_over_262144x2048_f64", device="cuda", keep_factors=True)
+    lams = prob.lambdas.numpy()
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=w["s"], seed=1, tol=1e-14,
+                        precision=tk.TK_PREC_FP64 if precision == "fp64" else tk.TK_PREC_MIXED)
+    res = tk.tk_solve(prob.A, prob.b, lams, o)
+    X = res.X.cpu().numpy()
+    assert all(q["status"] == 0 for q in res.info), res.info
+    sig = prob.sigma.numpy()
+    for i in (0, len(lams) // 2, len(lams) - 1):
+        lam = float(lams[i])
+        xr, A = reference(prob, lam)
+        r = prob.b.cpu().numpy() - A @ xr
+        tol = max(1e-10, 8 * floor_tol(sig, lam, np.linalg.norm(r), np.linalg.norm(xr)))
+        err = np.linalg.norm(X[i] - xr) / np.linalg.norm(xr)
+        print(f"{precision} lambda={lam:.1e} rel.err={err:.2e} tol={tol:.2e} iters={res.info[i]['iters']}")
+        assert err < tol, (lam, err, tol)
+    # iterations flat in lambda (Lemma 2.1: kappa(B R^-1) <= kappa(X U_A) for every lambda)
+    its = [q["iters"] for q in res.info]
+    assert max(its) <= 2 * min(its) + 10, its
+
+
+def test_under_2048x262144_srht(tk):
+    prob, w = datagen.workload_problem("ridge_under_2048x262144_f64", device="cuda", keep_factors=True)
+    lams = prob.lambdas.numpy()
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=w["s"], seed=1, tol=1e-14)
+    res = tk.tk_solve(prob.A, prob.b, lams, o)
+    X = res.X.cpu().numpy()
+    assert all(q["status"] == 0 for q in res.info), res.info
+    sig = prob.sigma.numpy()
+    for i in (0, len(lams) - 1):
+        lam = float(lams[i])
+        xr, A = reference(prob, lam)
+        r = prob.b.cpu().numpy() - A @ xr
+        tol = max(1e-10, 8 * floor_tol(sig, lam, np.linalg.norm(r), np.linalg.norm(xr)))
+        err = np.linalg.norm(X[i] - xr) / np.linalg.norm(xr)
+        print(f"under lambda={lam:.1e} rel.err={err:.2e} tol={tol:.2e} iters={res.info[i]['iters']}")
+        assert err < tol, (lam, err, tol)

@@ -1,0 +1,291 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, against the
+CPU oracle on the same seeded inputs.
+
+Integer work (signs, sampled rows, truncation ranks) is compared bit for bit.
+Floating point: x_lambda within 1e-10 relative of the oracle's reference
+solution (dense QR + double-double refinement) for the float64 path and for the
+mixed form after refinement; intermediate floating-point steps within the
+rounding-level tolerances stated per test.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2203_07329_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+TOL_X = 1e-10  # relative error of x_lambda against the oracle (float64 and mixed)
+
+
+@pytest.fixture(scope="module")
+def tk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_07329_gb300 import build
+    build.build()
+    from paper_2203_07329_gb300 import tikhonov
+    tikhonov.lib()
+    return tikhonov
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def problem(m, n, lo=1e-4, kind="log", tau=50.0, N=4, lam=(1e-6, 1.0), seed=3, dtype=torch.float64):
+    k = min(m, n)
+    sig = datagen.spectrum("log", k, hi=1.0, lo=lo) if kind == "log" else datagen.spectrum("exp", k, tau=tau)
+    p = datagen.make_ridge_problem(m, n, sig, datagen.log_lambdas(N, *lam), seed=seed, dtype=dtype)
+    return p
+
+
+def to_dev(p):
+    return p.A.cuda(), p.b.cuda()
+
+
+# ------------------------------------------------------------- draws -------
+@pytest.mark.parametrize("mp,s", [(1, 1), (64, 0), (64, 16), (64, 64), (1000, 333), (1 << 14, 4096),
+                                  (1 << 18, 8192), (1 << 20, 5)])
+def test_draws_bit_exact(tk, mp, s):
+    signs, rows = tk.tk_sketch_draw(7, mp, s)
+    np.testing.assert_array_equal(signs.cpu().numpy(), oracle.draw_signs(7, mp))
+    np.testing.assert_array_equal(rows.cpu().numpy(), oracle.draw_rows(7, mp, s))
+
+
+# ---------------------------------------------------------- sketches -------
+@pytest.mark.parametrize("m,n,s", [(1000, 37, 300), (512, 16, 512), (3000, 130, 700), (700, 1, 50)])
+def test_srht_over_matches_oracle(tk, m, n, s):
+    A = torch.randn(m, n, dtype=torch.float64, generator=torch.Generator().manual_seed(m + n))
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=11)
+    Y = tk.tk_sketch_apply(A.cuda(), o).cpu().numpy()
+    Yo = oracle.srht_over(A.numpy(), 11, s)
+    # the same butterfly tree in the same order: rounding-identical up to FMA-free adds
+    np.testing.assert_allclose(Y, Yo, rtol=1e-13, atol=1e-13 * np.abs(Yo).max())
+
+
+def test_srht_over_two_pass_size(tk):
+    # 2^11 rows: the transform runs in two shared-memory passes (9 + 2 bits)
+    m, n, s = 2000, 20, 256
+    A = torch.randn(m, n, dtype=torch.float64, generator=torch.Generator().manual_seed(5))
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=2)
+    Y = tk.tk_sketch_apply(A.cuda(), o).cpu().numpy()
+    Yo = oracle.srht_over(A.numpy(), 2, s)
+    np.testing.assert_allclose(Y, Yo, rtol=1e-13, atol=1e-13 * np.abs(Yo).max())
+
+
+@pytest.mark.parametrize("m,n,s", [(20, 1000, 100), (3, 5000, 64)])
+def test_srht_under_matches_oracle(tk, m, n, s):
+    A = torch.randn(m, n, dtype=torch.float64, generator=torch.Generator().manual_seed(9))
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=4)
+    Y = tk.tk_sketch_apply(A.cuda(), o).cpu().numpy()
+    Yo = oracle.srht_under(A.numpy(), 4, s)
+    np.testing.assert_allclose(Y, Yo, rtol=1e-13, atol=1e-13 * np.abs(Yo).max())
+
+
+@pytest.mark.parametrize("m,n,s", [(500, 30, 120), (130, 65, 65)])
+def test_gauss_over_matches_oracle(tk, m, n, s):
+    A = torch.randn(m, n, dtype=torch.float64, generator=torch.Generator().manual_seed(1))
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=s, seed=8)
+    Y = tk.tk_sketch_apply(A.cuda(), o).cpu().numpy()
+    Yo = oracle.gauss_over(A.numpy(), 8, s)
+    # Gaussian entries agree to libm-vs-CUDA rounding (~1e-16); sums differ in order
+    np.testing.assert_allclose(Y, Yo, rtol=1e-12, atol=1e-12 * np.abs(Yo).max())
+
+
+def test_gauss_under_matches_oracle(tk):
+    A = torch.randn(12, 300, dtype=torch.float64, generator=torch.Generator().manual_seed(2))
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=40, seed=8)
+    Y = tk.tk_sketch_apply(A.cuda(), o).cpu().numpy()
+    Yo = oracle.gauss_under(A.numpy(), 8, 40)
+    np.testing.assert_allclose(Y, Yo, rtol=1e-12, atol=1e-12 * np.abs(Yo).max())
+
+
+# ------------------------------------------------------ Gram / Cholesky ----
+@pytest.mark.parametrize("r,c", [(300, 70), (64, 64), (1000, 129)])
+def test_gram_matches_oracle(tk, r, c):
+    Y = torch.randn(r, c, dtype=torch.float64, generator=torch.Generator().manual_seed(r))
+    G = tk.tk_gram(Y.cuda(), True).cpu().numpy()
+    np.testing.assert_allclose(G, oracle.gram_tn(Y.numpy()), rtol=1e-12, atol=1e-12 * r)
+    G2 = tk.tk_gram(Y.T.contiguous().cuda(), False).cpu().numpy()
+    np.testing.assert_allclose(G2, oracle.gram_nt(Y.T.contiguous().numpy()), rtol=1e-12, atol=1e-12 * r)
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 100, 200])
+def test_cholesky_matches_oracle(tk, n):
+    Y = torch.randn(3 * n + 5, n, dtype=torch.float64, generator=torch.Generator().manual_seed(n))
+    Cm = (Y.T @ Y).numpy()
+    lams = [1e-8, 1e-3, 1.0]
+    R, brk = tk.tk_cholesky_shifted(torch.from_numpy(Cm).cuda(), lams)
+    R = R.cpu().numpy()
+    assert brk == [0, 0, 0]
+    for i, lam in enumerate(lams):
+        Ro, info = oracle.cholesky_shifted(Cm, lam)
+        assert info == 0
+        np.testing.assert_allclose(R[i], Ro, rtol=1e-9, atol=1e-11 * np.abs(Ro).max())
+        np.testing.assert_allclose(R[i].T @ R[i], Cm + lam * np.eye(n), rtol=1e-12, atol=1e-12 * np.abs(Cm).max())
+
+
+def test_cholesky_reports_breakdown(tk):
+    n = 70
+    Cm = np.eye(n)
+    Cm[40, 40] = -3.0
+    R, brk = tk.tk_cholesky_shifted(torch.from_numpy(Cm).cuda(), [0.5, 5.0])
+    _, info = oracle.cholesky_shifted(Cm, 0.5)
+    assert brk[0] == info == 41
+    assert brk[1] == 0
+
+
+# ----------------------------------------------------- low-rank pieces -----
+def test_jacobi_svd_and_ranks_match_oracle(tk):
+    s, n = 30, 90
+    Y = torch.randn(s, n, dtype=torch.float64, generator=torch.Generator().manual_seed(4)) @ \
+        torch.diag(torch.logspace(0, -8, n, dtype=torch.float64))
+    sig, V, sweeps = tk.tk_sketch_svd(Y.cuda())
+    sig, V = sig.cpu().numpy(), V.cpu().numpy()
+    so, Vo, _ = oracle.jacobi_svd(Y.numpy())
+    np.testing.assert_allclose(sig, so, rtol=1e-11, atol=1e-15)
+    np.testing.assert_allclose(sig, np.linalg.svd(Y.numpy(), compute_uv=False), rtol=1e-11, atol=1e-15)
+    # same subspaces: |V^T Vo| = I (singular values are distinct here)
+    np.testing.assert_allclose(np.abs(V.T @ Vo), np.eye(s), atol=1e-8)
+    lams = [1e-12, 1e-8, 1e-4, 1.0, 10.0]
+    sd, rk = tk.tk_lowrank_ranks(torch.from_numpy(sig).cuda(), lams, 2.0)
+    for i, lam in enumerate(lams):
+        sdo = oracle.sd_estimate(sig, lam)
+        assert sd[i] == sdo  # same float64 operations in the same order
+        assert rk[i] == oracle.truncation(sdo, 2.0, s)
+
+
+# ------------------------------------------------------------ solves -------
+def ref_over(p, lams):
+    A, b = p.A.double().numpy(), p.b.numpy()
+    return np.stack([oracle.ref_ridge_qr(A, b, lam, refine=3) for lam in lams])
+
+
+@pytest.mark.parametrize("sketch", ["gauss", "srht"])
+def test_alg1_fp64_matches_oracle(tk, sketch):
+    p = problem(2000, 100, lo=1e-5, N=5, lam=(1e-8, 1.0))
+    lams = p.lambdas.numpy()
+    A, b = to_dev(p)
+    kind = tk.TK_SKETCH_GAUSS if sketch == "gauss" else tk.TK_SKETCH_SRHT
+    o = tk.opts_default(sketch=kind, s=400, seed=5, tol=1e-14)
+    res = tk.tk_solve(A, b, lams, o)
+    X = res.X.cpu().numpy()
+    Xr = ref_over(p, lams)
+    for i in range(len(lams)):
+        assert rel(X[i], Xr[i]) < TOL_X, (i, rel(X[i], Xr[i]))
+    # iteration counts agree with the oracle's Algorithm 1 on the same draws
+    _, it_o, _, _ = oracle.alg1(p.A.numpy(), p.b.numpy(), lams, 1 if sketch == "gauss" else 0, 400, 5, 1e-14, 500)
+    its = np.array([r["iters"] for r in res.info])
+    assert np.all(np.abs(its - it_o) <= 2), (its, it_o)
+
+
+def test_alg1_small_workload_4096x256(tk):
+    prob, w = datagen.workload_problem("ridge_over_4096x256_f64")
+    lams = prob.lambdas.numpy()
+    A, b = to_dev(prob)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=w["s"], seed=1, tol=1e-14)
+    res = tk.tk_solve(A, b, lams, o)
+    X = res.X.cpu().numpy()
+    Xr = ref_over(prob, lams)
+    errs = [rel(X[i], Xr[i]) for i in range(len(lams))]
+    assert max(errs) < TOL_X, errs
+    assert all(r["status"] == 0 for r in res.info)
+
+
+def test_one_at_a_time_equals_batched(tk):
+    p = problem(1500, 90, lo=1e-4, N=4)
+    lams = p.lambdas.numpy()
+    A, b = to_dev(p)
+    o1 = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=360, seed=2)
+    o2 = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=360, seed=2, schedule=tk.TK_SCHED_ONE_AT_A_TIME)
+    X1 = tk.tk_solve(A, b, lams, o1).X.cpu().numpy()
+    X2 = tk.tk_solve(A, b, lams, o2).X.cpu().numpy()
+    Xr = ref_over(p, lams)
+    for i in range(len(lams)):
+        assert rel(X1[i], Xr[i]) < TOL_X and rel(X2[i], Xr[i]) < TOL_X
+
+
+def test_alg2_underdetermined_matches_oracle(tk):
+    m, n = 40, 3000
+    p = problem(m, n, kind="exp", tau=10.0, N=4, lam=(1e-6, 1e-1))
+    lams = p.lambdas.numpy()
+    A, b = to_dev(p)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=160, seed=3, tol=1e-14)
+    res = tk.tk_solve(A, b, lams, o)
+    X = res.X.cpu().numpy()
+    for i, lam in enumerate(lams):
+        xr = oracle.ref_ridge_under(p.A.numpy(), p.b.numpy(), lam, refine=3)
+        assert rel(X[i], xr) < TOL_X, (lam, rel(X[i], xr))
+    Xo, it_o, _, _ = oracle.alg2(p.A.numpy(), p.b.numpy(), lams, 0, 160, 3, 1e-14, 500)
+    its = np.array([r["iters"] for r in res.info])
+    assert np.all(np.abs(its - it_o) <= 2), (its, it_o)
+
+
+def test_alg3_lowrank_matches_oracle(tk):
+    m, n = 3000, 120
+    p = problem(m, n, kind="exp", tau=8.0, N=5, lam=(1e-6, 1.0))
+    lams = p.lambdas.numpy()[::-1].copy()
+    A, b = to_dev(p)
+    s = 60
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=s, seed=6, precond=tk.TK_PRECOND_LOWRANK, alpha=2.0, tol=1e-14)
+    res = tk.tk_solve(A, b, lams, o)
+    X = res.X.cpu().numpy()
+    Xr = ref_over(p, lams)
+    for i in range(len(lams)):
+        assert rel(X[i], Xr[i]) < TOL_X, (lams[i], rel(X[i], Xr[i]))
+    Xo, it_o, st_o, si_o, sig_o = oracle.alg3(p.A.numpy(), p.b.numpy(), lams, 1, s, 2.0, 6, 1e-14, 500)
+    ranks = np.array([r["rank"] for r in res.info])
+    # ranks are integers decided in float64 from each side's own sigma(Y); equal unless an sd
+    # estimate lies within rounding of an integer
+    assert np.all(np.abs(ranks - si_o) <= 0), (ranks, si_o)
+
+
+def test_mixed_precision_reaches_fp64_accuracy(tk):
+    p = problem(4096, 256, lo=1e-5, N=6, lam=(1e-5, 1.0), dtype=torch.float32)
+    lams = p.lambdas.numpy()
+    A, b = to_dev(p)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=512, seed=9, precision=tk.TK_PREC_MIXED)
+    res = tk.tk_solve(A, b, lams, o)
+    X = res.X.cpu().numpy()
+    Xr = ref_over(p, lams)
+    for i in range(len(lams)):
+        assert rel(X[i], Xr[i]) < TOL_X, (lams[i], rel(X[i], Xr[i]), res.info[i])
+    assert all(r["refine_steps"] >= 2 for r in res.info)
+
+
+def test_mixed_on_float64_input(tk):
+    p = problem(3000, 128, lo=1e-4, N=3, lam=(1e-4, 1.0))
+    lams = p.lambdas.numpy()
+    A, b = to_dev(p)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=512, seed=9, precision=tk.TK_PREC_MIXED)
+    X = tk.tk_solve(A, b, lams, o).X.cpu().numpy()
+    Xr = ref_over(p, lams)
+    for i in range(len(lams)):
+        assert rel(X[i], Xr[i]) < TOL_X
+
+
+def test_batched_uneven_problems(tk):
+    probs = datagen.uneven_batch(5, m_range=(300, 2500), n_range=(8, 120), N=3, dtype=torch.float64)
+    pairs = [(p.A.cuda(), p.b.cuda()) for p in probs]
+    lams = np.stack([p.lambdas.numpy() for p in probs])
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=0, seed=4)
+    Xs, infos, st = tk.tk_solve_batched(pairs, lams, o)
+    for p, X, lam in zip(probs, Xs, lams):
+        Xr = ref_over(p, lam)
+        Xc = X.cpu().numpy()
+        for i in range(len(lam)):
+            assert rel(Xc[i], Xr[i]) < TOL_X
+
+
+def test_edge_single_column_and_single_lambda(tk):
+    p = problem(257, 1, N=1, lam=(0.5, 0.5))
+    A, b = to_dev(p)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=4, seed=1)
+    X = tk.tk_solve(A, b, [0.5], o).X.cpu().numpy()
+    a = p.A.numpy()[:, 0]
+    x_exact = a @ p.b.numpy() / (a @ a + 0.5)
+    assert abs(X[0, 0] - x_exact) <= 1e-12 * abs(x_exact)
