@@ -77,8 +77,8 @@ typedef struct {
   tk_precision precision; /* [FP64] or MIXED (FP32 LSQR + FP64 refinement) */
   double tol;             /* [1e-14] LSQR stopping tolerance (Paige-Saunders atol = btol) */
   int maxiter;            /* [500] LSQR iteration cap per lambda */
-  int max_refine;         /* [6] refinement steps of the MIXED form */
-  double inner_tol;       /* [1e-6] FP32 LSQR tolerance inside the MIXED refinement */
+  int max_refine;         /* [8] refinement steps of the MIXED form */
+  double inner_tol;       /* [1e-7] FP32 LSQR tolerance inside the MIXED refinement */
   double refine_tol;      /* [1e-11] MIXED stops when ||d|| <= refine_tol ||x|| */
   uint64_t seed;          /* [1] Philox key of every draw */
   tk_schedule schedule;   /* [BATCHED]: all lambda advance together; ONE_AT_A_TIME: one lambda per LSQR run */
@@ -118,14 +118,20 @@ TK_API tk_status tk_solve(const tk_problem* p, const double* lambdas, int N, con
 
 /*
  * tk_solve_batched -- P independent problems (uneven m, n) with N lambdas each
- * (Section 2.1.1: "the for loop can trivially be parallelized", extended
- * across problems).  lambdas: host P x N.  X[p]: device N x n_p float64.
- * info: host P x N (may be NULL).  The workspace size is
- * tk_workspace_size_batched().
+ * (the per-lambda loop of Algorithm 1 "can trivially be parallelized",
+ * Section 2.1.1; here also across problems).  The problems are spread over
+ * up to 8 concurrent lanes (host threads, each with its own stream joined to
+ * `stream` by events, and its own slice of the workspace).
+ *   o:       n_opts options, n_opts = 1 (shared) or P (one per problem, e.g.
+ *            Cholesky for some problems and the low-rank form for others).
+ *   lambdas: host P x N.   X[p]: device N x n_p float64.   info: host P x N (may be NULL).
+ * Workspace: tk_workspace_size_batched().  Synchronizes `stream` before returning.
  */
-TK_API tk_status tk_workspace_size_batched(const tk_problem* ps, int P, int N, const tk_opts* o, size_t* bytes);
+TK_API tk_status tk_workspace_size_batched(const tk_problem* ps, int P, int N, const tk_opts* o, int n_opts,
+                                           size_t* bytes);
 TK_API tk_status tk_solve_batched(const tk_problem* ps, int P, const double* lambdas, int N, const tk_opts* o,
-                                  void* work, size_t work_bytes, void* stream, double* const* X, tk_info* info);
+                                  int n_opts, void* work, size_t work_bytes, void* stream, double* const* X,
+                                  tk_info* info);
 
 /* ---- introspection calls for parity tests (each step of the path on its own) ---- */
 

@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "tk_lsqr.cuh"
@@ -360,9 +362,8 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
   std::vector<int> ok_ids;
   if (!P.lowrank) {
     int tok = prof_begin(TK_PHASE_GRAM, st);
-    TK_TRY((gemm<double, double, double>(true, false, P.c, P.c, P.s, B.Y, P.c, B.Y, P.c, B.C, P.c, 1.0, nullptr,
-                                         nullptr, 0, st)));
-    prof_end(tok, st, 2.0 * P.s * P.c * P.c, 8.0 * (P.s * P.c + P.c * P.c));
+    TK_TRY(gram_upper(B.Y, P.s, P.c, B.C, st));  // the Cholesky reads only j >= i
+    prof_end(tok, st, (double)P.s * P.c * (P.c + 1), 8.0 * (P.s * P.c + P.c * (P.c + 1) / 2));
     Arena none;
     tok = prof_begin(TK_PHASE_CHOLESKY, st);
     TK_TRY(chol_shifted(B.C, P.c, B.lam, N, B.R, P.np, P.np * P.np, B.info, none, st));
@@ -442,6 +443,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     }
     std::vector<int> act = ok_ids;
     std::vector<double> hn(3 * std::max(N, 1));
+    std::vector<double> prev_dn(std::max(N, 1), INFINITY);
     for (int round = 0; round < P.o.max_refine && !act.empty(); ++round) {
       const int cnt = (int)act.size();
       TK_CUDA(cudaMemcpyAsync(B.ids, act.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, st));
@@ -502,7 +504,12 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
         q.refine_steps += 1;
         if (round > 0) q.ne_norm = hn[3 * k];
         const double dn = hn[3 * k + 1], xn = hn[3 * k + 2];
-        const bool done = (dn <= P.o.refine_tol * xn) || !std::isfinite(dn);
+        // converged: the correction is below refine_tol ||x||, or it stopped
+        // halving (x sits at the float64 floor of the residual; more passes
+        // only add rounding noise)
+        const bool stalled = round >= 2 && dn > 0.5 * prev_dn[act[k]];
+        const bool done = (dn <= P.o.refine_tol * xn) || stalled || !std::isfinite(dn);
+        prev_dn[act[k]] = dn;
         if (!done) next.push_back(act[k]);
       }
       act.swap(next);
@@ -534,8 +541,8 @@ TK_API tk_status tk_opts_default(tk_opts* o) {
   o->precision = TK_PREC_FP64;
   o->tol = 1e-14;
   o->maxiter = 500;
-  o->max_refine = 6;
-  o->inner_tol = 1e-6;
+  o->max_refine = 8;
+  o->inner_tol = 1e-7;
   o->refine_tol = 1e-11;
   o->seed = 1;
   o->schedule = TK_SCHED_BATCHED;
@@ -571,32 +578,94 @@ TK_API tk_status tk_solve(const tk_problem* p, const double* lambdas, int N, con
   return solve_impl(p, lambdas, N, o, work, work_bytes, (cudaStream_t)stream, X, info);
 }
 
-TK_API tk_status tk_workspace_size_batched(const tk_problem* ps, int P, int N, const tk_opts* o, size_t* bytes) {
-  if (!bytes || (P > 0 && !ps) || P < 0) return einval("bad batched arguments");
+// ---- many problems -------------------------------------------------------
+// Problems are spread over up to kLanes host threads; each lane owns a stream
+// (joined to the caller's stream by events) and a slice of the workspace, and
+// solves its problems one after another.  Small uneven problems are bound by
+// launch latency, so lanes overlap them on the GPU.
+static constexpr int kLanes = 8;
+
+static int batched_lanes(int P) { return std::max(1, std::min(P, kLanes)); }
+
+static const tk_opts* opts_of(const tk_opts* o, int n_opts, int i) { return n_opts == 1 ? o : o + i; }
+
+TK_API tk_status tk_workspace_size_batched(const tk_problem* ps, int P, int N, const tk_opts* o, int n_opts,
+                                           size_t* bytes) {
+  if (!bytes || P < 0 || (P > 0 && (!ps || !o)) || (n_opts != 1 && n_opts != P))
+    return einval("bad batched arguments (n_opts must be 1 or P)");
   size_t mx = 0;
   for (int i = 0; i < P; ++i) {
     size_t b = 0;
-    TK_TRY(tk_workspace_size(&ps[i], N, o, &b));
-    mx = std::max(mx, b);
+    TK_TRY(tk_workspace_size(&ps[i], N, opts_of(o, n_opts, i), &b));
+    mx = std::max(mx, (b + 255) & ~size_t(255));
   }
-  *bytes = mx;
+  *bytes = mx * (size_t)batched_lanes(P);
   return TK_OK;
 }
 
 TK_API tk_status tk_solve_batched(const tk_problem* ps, int P, const double* lambdas, int N, const tk_opts* o,
-                                  void* work, size_t work_bytes, void* stream, double* const* X, tk_info* info) {
-  if (P < 0 || (P > 0 && (!ps || !lambdas || !X))) return einval("bad batched arguments");
+                                  int n_opts, void* work, size_t work_bytes, void* stream, double* const* X,
+                                  tk_info* info) {
+  if (P < 0 || (P > 0 && (!ps || !lambdas || !X || !o)) || (n_opts != 1 && n_opts != P))
+    return einval("bad batched arguments (n_opts must be 1 or P)");
+  if (P == 0) return TK_OK;
+  size_t per = 0;
   for (int i = 0; i < P; ++i) {
     Plan pl;
-    TK_TRY(make_plan(&ps[i], N, o, pl));
+    TK_TRY(make_plan(&ps[i], N, opts_of(o, n_opts, i), pl));
+    per = std::max(per, (plan_bytes(pl) + 255) & ~size_t(255));
   }
+  const int lanes = batched_lanes(P);
+  if (!work || work_bytes < per * lanes) {
+    set_error_msg("workspace smaller than tk_workspace_size_batched()");
+    return TK_ENOMEM;
+  }
+  cudaStream_t cs = (cudaStream_t)stream;
+  int dev = 0;
+  TK_CUDA(cudaGetDevice(&dev));
+  cudaStream_t ls[kLanes];
+  cudaEvent_t ev_in, ev_out[kLanes];
+  TK_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+  TK_CUDA(cudaEventRecord(ev_in, cs));
+  for (int l = 0; l < lanes; ++l) {
+    TK_CUDA(cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking));
+    TK_CUDA(cudaEventCreateWithFlags(&ev_out[l], cudaEventDisableTiming));
+    TK_CUDA(cudaStreamWaitEvent(ls[l], ev_in, 0));
+  }
+  std::vector<tk_status> st(P, TK_OK);
+  std::vector<std::string> err(lanes);
+  auto lane_fn = [&](int l) {
+    cudaSetDevice(dev);
+    char* base = (char*)work + per * (size_t)l;
+    for (int i = l; i < P; i += lanes) {
+      st[i] = solve_impl(&ps[i], lambdas + (size_t)i * N, N, opts_of(o, n_opts, i), base, per, ls[l], X[i],
+                         info ? info + (size_t)i * N : nullptr);
+      if (st[i] == TK_EINVAL || st[i] == TK_ENOMEM || st[i] == TK_ECUDA) {
+        err[l] = tk::g_err;
+        break;
+      }
+    }
+    cudaEventRecord(ev_out[l], ls[l]);
+  };
+  std::vector<std::thread> th;
+  for (int l = 1; l < lanes; ++l) th.emplace_back(lane_fn, l);
+  lane_fn(0);
+  for (auto& t : th) t.join();
   tk_status worst = TK_OK;
-  for (int i = 0; i < P; ++i) {
-    tk_status s = solve_impl(&ps[i], lambdas + (size_t)i * N, N, o, work, work_bytes, (cudaStream_t)stream, X[i],
-                             info ? info + (size_t)i * N : nullptr);
-    if (s == TK_EINVAL || s == TK_ENOMEM || s == TK_ECUDA) return s;
-    worst = worse(worst, s);
+  for (int l = 0; l < lanes; ++l) {
+    cudaStreamWaitEvent(cs, ev_out[l], 0);
+    if (!err[l].empty()) set_error_msg(err[l].c_str());
   }
+  for (int i = 0; i < P; ++i) {
+    if (st[i] == TK_EINVAL || st[i] == TK_ENOMEM || st[i] == TK_ECUDA) worst = st[i];
+    else if (worst != TK_EINVAL && worst != TK_ENOMEM && worst != TK_ECUDA) worst = worse(worst, st[i]);
+  }
+  TK_CUDA(cudaStreamSynchronize(cs));
+  for (int l = 0; l < lanes; ++l) {
+    cudaStreamDestroy(ls[l]);
+    cudaEventDestroy(ev_out[l]);
+  }
+  cudaEventDestroy(ev_in);
   return worst;
 }
 

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     k_gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
            const TB* __restrict__ B, int64_t ldb, TC* C, int64_t ldc, double alpha,
            const double* __restrict__ beta_row, const TC* Cin, int64_t ldcin, int64_t k_per_split,
-           double* __restrict__ partial) {
+           double* __restrict__ partial, bool upper_only) {
   using Acc = typename AccOf<TA, TB>::type;
   constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ Acc As[BK][BM + 1];
@@ -38,6 +38,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  // symmetric results (the Gram matrix): tiles strictly below the diagonal are skipped
+  if (upper_only && m0 > n0 + BN - 1) return;
   const int64_t kbeg = (int64_t)blockIdx.z * k_per_split;
   const int64_t kend = std::min(K, kbeg + k_per_split);
   Acc acc[TM][TN];
@@ -98,10 +100,115 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
+// GEMM for the lambda-major shapes of LSQR: C (M x N) = L (M x K) op(A) with
+// M <= BM (every active lambda in one tile) and a long N.  op(A)[k][j] is
+// A[j*lda + k] (TRANSB: the product with A^T, N = rows of A) or A[k*lda + j].
+// Warps are arranged 2 x 4 over the tile and lanes 4 x 8 inside a warp, so a
+// warp's shared-memory reads of L touch 4 rows (broadcast) and of B 8 column
+// groups; every thread keeps TM x TN accumulators.
+template <typename T, bool TRANSB, int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__(256)
+    k_gemm_lm(int64_t M, int64_t N, int64_t K, const T* __restrict__ L, int64_t ldl, const T* __restrict__ A,
+              int64_t lda, T* C, int64_t ldc, const double* __restrict__ beta_row, const T* Cin, int64_t ldcin,
+              int64_t k_per_split, double* __restrict__ partial) {
+  constexpr int BK = 16;
+  static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+  static_assert(BM / TM == 8 && BN / TN == 32, "2 x 4 warps of 4 x 8 lanes");
+  __shared__ __align__(16) T Ls[BK][BM];
+  __shared__ __align__(16) T Bs[BK][BN + 4];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ty = (w >> 2) * 4 + (lane >> 3);  // 0..7  row group
+  const int tx = (w & 3) * 8 + (lane & 7);    // 0..31 column group
+  const int64_t n0 = (int64_t)blockIdx.x * BN;
+  const int64_t kbeg = (int64_t)blockIdx.y * k_per_split;
+  const int64_t kend = std::min(K, kbeg + k_per_split);
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    for (int idx = tid; idx < BM * BK; idx += 256) {
+      const int i = idx / BK, k = idx % BK;
+      const int64_t gk = k0 + k;
+      Ls[k][i] = (i < M && gk < kend) ? L[(int64_t)i * ldl + gk] : T(0);
+    }
+    if (TRANSB) {
+      for (int idx = tid; idx < BN * BK; idx += 256) {
+        const int j = idx / BK, k = idx % BK;
+        const int64_t gj = n0 + j, gk = k0 + k;
+        Bs[k][j] = (gj < N && gk < kend) ? A[gj * lda + gk] : T(0);
+      }
+    } else {
+      for (int idx = tid; idx < BN * BK; idx += 256) {
+        const int k = idx / BN, j = idx % BN;
+        const int64_t gj = n0 + j, gk = k0 + k;
+        Bs[k][j] = (gj < N && gk < kend) ? A[gk * lda + gj] : T(0);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], bv[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = Ls[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t r = ty * TM + i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t c = n0 + tx * TN + j;
+      if (c >= N) continue;
+      if (partial) {
+        partial[(int64_t)blockIdx.y * M * N + r * N + c] = (double)acc[i][j];
+      } else {
+        double v = (double)acc[i][j];
+        if (beta_row) v += beta_row[r] * (double)Cin[r * ldcin + c];
+        C[r * ldc + c] = (T)v;
+      }
+    }
+  }
+}
+
+template <typename T>
+tk_status launch_gemm_lm(bool transB, int64_t M, int64_t N, int64_t K, const T* L, int64_t ldl, const T* A,
+                         int64_t lda, T* C, int64_t ldc, double alpha, const double* beta_row, const T* Cin,
+                         int64_t ldcin, int splits, double* partial, cudaStream_t st) {
+  (void)alpha;  // callers of this path use alpha = 1
+  constexpr int BN = 256;
+  int64_t kps = cdiv(cdiv(K, splits), 16) * 16;
+  if (kps <= 0) kps = 16;
+  dim3 grid((unsigned)cdiv(N, BN), (unsigned)splits);
+  if (grid.y > 65535u) {
+    set_error_msg("gemm: too many K splits");
+    return TK_EINVAL;
+  }
+  if (M <= 32) {
+    if (transB) k_gemm_lm<T, true, 32, BN, 4, 8><<<grid, 256, 0, st>>>(M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, ldcin, kps, partial);
+    else k_gemm_lm<T, false, 32, BN, 4, 8><<<grid, 256, 0, st>>>(M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, ldcin, kps, partial);
+  } else {
+    if (transB) k_gemm_lm<T, true, 64, BN, 8, 8><<<grid, 256, 0, st>>>(M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, ldcin, kps, partial);
+    else k_gemm_lm<T, false, 64, BN, 8, 8><<<grid, 256, 0, st>>>(M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, ldcin, kps, partial);
+  }
+  TK_LAUNCH_CHECK();
+  return TK_OK;
+}
+
 template <typename TA, typename TB, typename TC, int BM, int BN, int BK, int TM, int TN>
 tk_status launch_gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda,
                       const TB* B, int64_t ldb, TC* C, int64_t ldc, double alpha, const double* beta_col,
-                      const TC* Cin, int64_t ldcin, int splits, double* partial, cudaStream_t st) {
+                      const TC* Cin, int64_t ldcin, int splits, double* partial, cudaStream_t st,
+                      bool upper_only = false) {
   int64_t kps = cdiv(cdiv(K, splits), BK) * BK;
   if (kps <= 0) kps = BK;
   dim3 grid((unsigned)cdiv(M, BM), (unsigned)cdiv(N, BN), (unsigned)splits);
@@ -110,7 +217,7 @@ tk_status launch_gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K,
     return TK_EINVAL;
   }
   k_gemm<TA, TB, TC, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(
-      transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta_col, Cin, ldcin, kps, partial);
+      transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta_col, Cin, ldcin, kps, partial, upper_only);
   TK_LAUNCH_CHECK();
   return TK_OK;
 }
@@ -121,6 +228,17 @@ tk_status gemm_dispatch(bool transA, bool transB, int64_t M, int64_t N, int64_t 
                         const TC* Cin, int64_t ldcin, int splits, double* partial, cudaStream_t st) {
   if (M == 0 || N == 0) return TK_OK;
   constexpr bool f32 = std::is_same<TA, float>::value && std::is_same<TB, float>::value;
+  if constexpr (f32) {
+    // the lambda-major products of LSQR (all active lambda in one tile)
+    if (!transA && M <= 64 && N >= 256 && alpha == 1.0) {
+      if (partial)
+        return launch_gemm_lm<float>(transB, M, N, K, A, lda, B, ldb, nullptr, 0, alpha, nullptr, nullptr, 0, splits,
+                                     partial, st);
+      if constexpr (std::is_same<TC, float>::value)
+        return launch_gemm_lm<float>(transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta_row, Cin, ldcin, splits,
+                                     nullptr, st);
+    }
+  }
 #define TK_G(BM, BN, TM, TN)                                                                                    \
   return launch_gemm<TA, TB, TC, BM, BN, 16, TM, TN>(transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, \
                                                       beta_row, Cin, ldcin, splits, partial, st)
@@ -395,9 +513,122 @@ __global__ void __launch_bounds__(kTrsvThreads)
   for (int64_t i2 = threadIdx.x; i2 < n; i2 += blockDim.x) xg[i2] = (TX)x[i2];
 }
 
+// ---- column-sweep solves across the grid ---------------------------------
+// The remaining right-hand side P (float64, one row of n per slot) starts as
+// the input vector.  Launch b solves the 32 x 32 diagonal block b from P (every
+// CTA of the slot does it redundantly; CTA 0 stores x_b), then each CTA folds
+// x_b into P for its share of the unsolved rows.  No CTA waits on another; the
+// launches of one solve are ordered by the stream.
+constexpr int kSweepRows = 256;  // unsolved rows per CTA
+
+template <typename TX>
+__global__ void k_sweep_init(const TX* __restrict__ Xin, int64_t ldx, int64_t n, TX* __restrict__ P) {
+  const int s = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    P[(int64_t)s * n + i] = Xin[(int64_t)s * ldx + i];
+}
+
+// Arithmetic runs in the vector's type TX (float64 is ~58x slower than float32
+// on this part, so the float32 path must not widen).  The dependent chain of
+// the 32 x 32 diagonal solve multiplies by reciprocals computed up front.
+
+// upper: x = R^-1 v, step for diagonal block b (rows r0..r1); updates rows < r0
+template <typename TR, typename TX>
+__global__ void __launch_bounds__(kTrsvThreads)
+    k_sweep_upper(int64_t n, const TR* __restrict__ R, int64_t ldr, int64_t rstride, const int* __restrict__ idx,
+                  TX* __restrict__ X, int64_t ldx, TX* __restrict__ P, int64_t b, int rows_per_cta) {
+  __shared__ TX xs[32];
+  const int slot = blockIdx.y;
+  const TR* Rs = R + (int64_t)(idx ? idx[slot] : slot) * rstride;
+  TX* p = P + (int64_t)slot * n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t r0 = b * 32, r1 = std::min<int64_t>(n, r0 + 32);
+  const int cols = (int)(r1 - r0);
+  if (wid == 0) {
+    const int64_t i = r0 + lane;
+    const bool live = lane < cols;
+    TX rr[32];  // row i of the diagonal block, loaded up front
+#pragma unroll
+    for (int q = 0; q < 32; ++q) rr[q] = (live && q < cols) ? (TX)Rs[i * ldr + r0 + q] : TX(0);
+    const TX rinv = live ? TX(1) / (TX)Rs[i * ldr + i] : TX(0);
+    TX xi = live ? p[i] : TX(0);
+#pragma unroll
+    for (int q = 31; q >= 0; --q) {
+      if (q < cols) {
+        TX xq = __shfl_sync(0xffffffffu, xi, q);
+        if (lane == q) xi = xq * rinv;
+        xq = __shfl_sync(0xffffffffu, xi, q);
+        if (lane < q) xi = fma(-rr[q], xq, xi);
+      }
+    }
+    xs[lane] = live ? xi : TX(0);
+    if (blockIdx.x == 0 && live) X[(int64_t)slot * ldx + i] = xi;
+  }
+  __syncthreads();
+  const int64_t beg = (int64_t)blockIdx.x * rows_per_cta, end = std::min<int64_t>(r0, beg + rows_per_cta);
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const TR* row = Rs + i * ldr + r0;
+    TX acc = TX(0);
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if (k < cols) acc = fma((TX)row[k], xs[k], acc);
+    p[i] -= acc;
+  }
+}
+
+// transposed: x = R^-T v, step for diagonal block b; updates rows >= r1
+template <typename TR, typename TX>
+__global__ void __launch_bounds__(kTrsvThreads)
+    k_sweep_lower(int64_t n, const TR* __restrict__ R, int64_t ldr, int64_t rstride, const int* __restrict__ idx,
+                  TX* __restrict__ X, int64_t ldx, TX* __restrict__ P, int64_t b, int rows_per_cta) {
+  __shared__ TX xs[32];
+  const int slot = blockIdx.y;
+  const TR* Rs = R + (int64_t)(idx ? idx[slot] : slot) * rstride;
+  TX* p = P + (int64_t)slot * n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t r0 = b * 32, r1 = std::min<int64_t>(n, r0 + 32);
+  const int cols = (int)(r1 - r0);
+  if (wid == 0) {
+    const int64_t i = r0 + lane;
+    const bool live = lane < cols;
+    TX rr[32];  // column i of the diagonal block (row i of R^T), loaded up front
+#pragma unroll
+    for (int q = 0; q < 32; ++q) rr[q] = (live && q < cols) ? (TX)Rs[(r0 + q) * ldr + i] : TX(0);
+    const TX rinv = live ? TX(1) / (TX)Rs[i * ldr + i] : TX(0);
+    TX xi = live ? p[i] : TX(0);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      if (q < cols) {
+        TX xq = __shfl_sync(0xffffffffu, xi, q);
+        if (lane == q) xi = xq * rinv;
+        xq = __shfl_sync(0xffffffffu, xi, q);
+        if (lane > q) xi = fma(-rr[q], xq, xi);
+      }
+    }
+    xs[lane] = live ? xi : TX(0);
+    if (blockIdx.x == 0 && live) X[(int64_t)slot * ldx + i] = xi;
+  }
+  __syncthreads();
+  const int64_t beg = r1 + (int64_t)blockIdx.x * rows_per_cta, end = std::min<int64_t>(n, beg + rows_per_cta);
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    TX acc = TX(0);
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if (k < cols) acc = fma((TX)Rs[(r0 + k) * ldr + i], xs[k], acc);
+    p[i] -= acc;
+  }
+}
+
 }  // namespace
 
 // ----------------------------------------------------------- host side ----
+// C (c x c) = Y^T Y (Y r x c), upper triangle (and the diagonal tiles) only.
+tk_status gram_upper(const double* Y, int64_t r, int64_t c, double* C, cudaStream_t st) {
+  if (c <= 0) return TK_OK;
+  return launch_gemm<double, double, double, 64, 64, 16, 4, 4>(true, false, c, c, r, Y, c, Y, c, C, c, 1.0, nullptr,
+                                                                nullptr, 0, 1, nullptr, st, true);
+}
+
 template <typename TA, typename TB, typename TC>
 tk_status gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
                int64_t ldb, TC* C, int64_t ldc, double alpha, const double* beta_col, const TC* Cin, int64_t ldcin,
@@ -407,7 +638,7 @@ tk_status gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const 
 }
 
 int splitk_count(int64_t M, int64_t N, int64_t K) {
-  int64_t tiles = cdiv(M, 32) * cdiv(N, 128);
+  int64_t tiles = cdiv(M, 32) * cdiv(N, 256);
   int64_t want = cdiv(152 * 4, std::max<int64_t>(tiles, 1));
   int64_t maxs = std::max<int64_t>(1, K / 512);
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, maxs, 4096}));
@@ -473,8 +704,31 @@ tk_status chol_shifted(const double* Cm, int64_t n, const double* lambdas_dev, i
 
 template <typename TR, typename TX>
 tk_status trsv_batched(bool transposed, int64_t n, const TR* R, int64_t ldr, int64_t rstride, const int* idx,
-                       const TX* Xin, TX* X, int64_t ldx, int count, cudaStream_t st) {
+                       const TX* Xin, TX* X, int64_t ldx, int count, double* pbuf, cudaStream_t st) {
   if (count <= 0 || n <= 0) return TK_OK;
+  if (pbuf && n > 512) {
+    // column sweep across the grid: nb + 1 launches, R read once
+    TX* pb = reinterpret_cast<TX*>(pbuf);  // count x n of TX (the buffer holds count x n doubles)
+    dim3 gi((unsigned)std::min<int64_t>(cdiv(n, 256), 64), (unsigned)count);
+    k_sweep_init<TX><<<gi, 256, 0, st>>>(Xin, ldx, n, pb);
+    TK_LAUNCH_CHECK();
+    const int64_t nb = cdiv(n, 32);
+    const int rpc = count >= 16 ? kSweepRows : 64;  // more CTAs per slot when few slots
+    for (int64_t k = 0; k < nb; ++k) {
+      if (!transposed) {
+        const int64_t b = nb - 1 - k;
+        dim3 g((unsigned)std::max<int64_t>(1, cdiv(b * 32, rpc)), (unsigned)count);
+        k_sweep_upper<TR, TX><<<g, kTrsvThreads, 0, st>>>(n, R, ldr, rstride, idx, X, ldx, pb, b, rpc);
+      } else {
+        const int64_t b = k;
+        const int64_t rest = n - std::min<int64_t>(n, b * 32 + 32);
+        dim3 g((unsigned)std::max<int64_t>(1, cdiv(rest, rpc)), (unsigned)count);
+        k_sweep_lower<TR, TX><<<g, kTrsvThreads, 0, st>>>(n, R, ldr, rstride, idx, X, ldx, pb, b, rpc);
+      }
+      TK_LAUNCH_CHECK();
+    }
+    return TK_OK;
+  }
   const size_t smem = sizeof(double) * (size_t)n;
   if (smem > 200 * 1024) {
     set_error_msg("trsv: order too large for the shared-memory solve");
@@ -494,10 +748,10 @@ tk_status trsv_batched(bool transposed, int64_t n, const TR* R, int64_t ldr, int
 }
 
 template tk_status trsv_batched<double, double>(bool, int64_t, const double*, int64_t, int64_t, const int*,
-                                                const double*, double*, int64_t, int, cudaStream_t);
+                                                const double*, double*, int64_t, int, double*, cudaStream_t);
 template tk_status trsv_batched<float, float>(bool, int64_t, const float*, int64_t, int64_t, const int*, const float*,
-                                              float*, int64_t, int, cudaStream_t);
+                                              float*, int64_t, int, double*, cudaStream_t);
 template tk_status trsv_batched<double, float>(bool, int64_t, const double*, int64_t, int64_t, const int*,
-                                               const float*, float*, int64_t, int, cudaStream_t);
+                                               const float*, float*, int64_t, int, double*, cudaStream_t);
 
 }  // namespace tk

@@ -164,6 +164,8 @@ template <typename TA, typename TB>
 tk_status gemm_splitk(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda,
                       const TB* B, int64_t ldb, double* partial, int splits, cudaStream_t st);
 int splitk_count(int64_t M, int64_t N, int64_t K);
+// Gram matrix C = Y^T Y, upper triangle only (what the Cholesky reads).
+tk_status gram_upper(const double* Y, int64_t r, int64_t c, double* C, cudaStream_t st);
 
 size_t chol_workspace(int64_t n, int N);
 tk_status chol_shifted(const double* C, int64_t n, const double* lambdas_dev, int N, double* R, int64_t ldr,
@@ -171,9 +173,11 @@ tk_status chol_shifted(const double* C, int64_t n, const double* lambdas_dev, in
 
 // Batched triangular solves on slots: vector of slot j is X + j*ldx (length
 // n); its factor is R + idx[j]*rstride (row stride ldr, upper triangular).
+// pbuf (float64, count x n) enables the grid-wide column sweep for n > 512;
+// with pbuf == nullptr one CTA solves each slot.  Xin may equal X.
 template <typename TR, typename TX>
 tk_status trsv_batched(bool transposed, int64_t n, const TR* R, int64_t ldr, int64_t rstride, const int* idx,
-                       const TX* Xin, TX* X, int64_t ldx, int count, cudaStream_t st);
+                       const TX* Xin, TX* X, int64_t ldx, int count, double* pbuf, cudaStream_t st);
 
 // Low rank (tk_lowrank.cu)
 size_t svd_workspace(int64_t s, int64_t n);

@@ -393,6 +393,7 @@ void Lsqr<T>::carve(Arena& a) {
   slot_lam = a.take<int>((size_t)N_cap);
   idx_buf = a.take<int>((size_t)N_cap * 3);
   xtmp = a.take<T>((size_t)N_cap * std::max(n, m));
+  trsv_p = a.take<double>((size_t)N_cap * std::max(n, m));
   if (lr_s > 0) {
     lr_tmp = a.take<T>((size_t)N_cap * lr_s);
     lr_inv = a.take<double>((size_t)N_cap);
@@ -404,7 +405,7 @@ tk_status Lsqr<T>::apply_prec(bool transposed, const T* in, T* out, int count, i
   const double es = (double)sizeof(T);
   if (prec_kind == TK_PRECOND_CHOL) {
     int tok = prof_begin(TK_PHASE_PRECOND, st);
-    tk_status r = trsv_batched<T, T>(transposed, len, R, ldr, rstride, slot_lam, in, out, len, count, st);
+    tk_status r = trsv_batched<T, T>(transposed, len, R, ldr, rstride, slot_lam, in, out, len, count, trsv_p, st);
     prof_end(tok, st, (double)count * len * len, es * count * (len * (len + 1) / 2 + 2 * len));
     return r;
   }
@@ -497,7 +498,7 @@ tk_status Lsqr<T>::run(const double* b, int64_t ldbt, const double* bbot, int64_
         for (int k = 0; k < nr; ++k) hlam[k] = hsc[ret[k]].lam_idx;
         TK_CUDA(cudaMemcpyAsync(d_src, hlam.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
         if (prec_kind == TK_PRECOND_CHOL) {
-          TK_TRY((trsv_batched<T, T>(false, n, R, ldr, rstride, d_src, Vraw, xtmp, n, nr, st)));
+          TK_TRY((trsv_batched<T, T>(false, n, R, ldr, rstride, d_src, Vraw, xtmp, n, nr, trsv_p, st)));
         } else {
           TK_TRY(lr_apply<T>(nr, n, lr_s, lrV, lrS, d_src, lam_all, Vraw, xtmp, lr_tmp, lr_inv, st));
         }

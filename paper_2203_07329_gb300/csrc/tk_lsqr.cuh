@@ -55,7 +55,7 @@ struct Lsqr {
   int splits = 1;
   T *V = nullptr, *W = nullptr, *Y = nullptr, *Vraw = nullptr, *Ut = nullptr, *Tt = nullptr, *Ub = nullptr,
     *xtmp = nullptr, *lr_tmp = nullptr;
-  double *part_u = nullptr, *part_g = nullptr, *coef_buf = nullptr, *lr_inv = nullptr;
+  double *part_u = nullptr, *part_g = nullptr, *coef_buf = nullptr, *lr_inv = nullptr, *trsv_p = nullptr;
   Scal* sc = nullptr;
   int* slot_lam = nullptr;
   int* idx_buf = nullptr;

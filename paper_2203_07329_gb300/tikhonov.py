@@ -74,8 +74,8 @@ def lib() -> C.CDLL:
             "tk_last_error": (C.c_char_p, []),
             "tk_workspace_size": (INT, [P, INT, P, P]),
             "tk_solve": (INT, [P, P, INT, P, P, SZ, P, P, P]),
-            "tk_workspace_size_batched": (INT, [P, INT, INT, P, P]),
-            "tk_solve_batched": (INT, [P, INT, P, INT, P, P, SZ, P, P, P]),
+            "tk_workspace_size_batched": (INT, [P, INT, INT, P, INT, P]),
+            "tk_solve_batched": (INT, [P, INT, P, INT, P, INT, P, SZ, P, P, P]),
             "tk_sketch_draw_workspace": (SZ, [I64]),
             "tk_sketch_draw": (INT, [U64, I64, I64, P, P, P, SZ, P]),
             "tk_sketch_apply_workspace": (INT, [P, P, P]),
@@ -191,27 +191,40 @@ def tk_solve(A: torch.Tensor, b: torch.Tensor, lambdas, opts: tk_opts | None = N
     return SolveResult(X=X, info=_info_dicts(info, N), status=st)
 
 
-def tk_solve_batched(problems, lambdas, opts: tk_opts | None = None, *, work=None, stream=None,
+def tk_solve_batched(problems, lambdas, opts=None, *, work=None, stream=None,
                      allow=(TK_OK, TK_ENOCONV, TK_ENOTSPD)):
-    """problems: list of (A, b) CUDA tensors; lambdas: P x N host array."""
-    opts = opts or opts_default()
+    """problems: list of (A, b) CUDA tensors; lambdas: P x N host array; opts: one tk_opts or a list of P."""
     P = len(problems)
+    if opts is None:
+        opts = opts_default()
+    olist = list(opts) if isinstance(opts, (list, tuple)) else [opts]
+    n_opts = len(olist)
+    oarr = (tk_opts * n_opts)(*olist)
     lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
     N = lam.shape[1]
     probs = (tk_problem * P)(*[make_problem(A, b) for A, b in problems])
     out = C.c_size_t(0)
-    _check(lib().tk_workspace_size_batched(probs, P, N, C.byref(opts), C.byref(out)))
+    _check(lib().tk_workspace_size_batched(probs, P, N, oarr, n_opts, C.byref(out)))
     dev = problems[0][0].device
     if work is None or work.numel() < out.value:
         work = _workspace(out.value, dev)
     Xs = [torch.empty((N, A.shape[1]), dtype=torch.float64, device=dev) for A, _ in problems]
     xp = (C.c_void_p * P)(*[x.data_ptr() for x in Xs])
     info = (tk_info * (P * N))()
-    st = lib().tk_solve_batched(probs, P, lam.ctypes.data_as(C.c_void_p), N, C.byref(opts), _ptr(work),
+    st = lib().tk_solve_batched(probs, P, lam.ctypes.data_as(C.c_void_p), N, oarr, n_opts, _ptr(work),
                                 work.numel(), _stream(stream), xp, info)
     _check(st, allow)
     infos = _info_dicts(info, P * N)
     return Xs, [infos[p * N:(p + 1) * N] for p in range(P)], st
+
+
+def workspace_size_batched(problems, N, opts) -> int:
+    olist = list(opts) if isinstance(opts, (list, tuple)) else [opts]
+    oarr = (tk_opts * len(olist))(*olist)
+    probs = (tk_problem * len(problems))(*[make_problem(A, b) for A, b in problems])
+    out = C.c_size_t(0)
+    _check(lib().tk_workspace_size_batched(probs, len(problems), N, oarr, len(olist), C.byref(out)))
+    return int(out.value)
 
 
 def tk_sketch_draw(seed: int, mp: int, s: int, device="cuda", stream=None):

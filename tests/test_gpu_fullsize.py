@@ -69,9 +69,13 @@ def test_over_262144x2048_srht(tk, precision):
         err = np.linalg.norm(X[i] - xr) / np.linalg.norm(xr)
         print(f"{precision} lambda={lam:.1e} rel.err={err:.2e} tol={tol:.2e} iters={res.info[i]['iters']}")
         assert err < tol, (lam, err, tol)
-    # iterations flat in lambda (Lemma 2.1: kappa(B R^-1) <= kappa(X U_A) for every lambda)
+    # iterations bounded independently of lambda (Lemma 2.1: kappa(B R^-1) <= kappa(X U_A) for
+    # every lambda).  With s = 4n, kappa(X U_A) <= 3 (eps ~ sqrt(n/s) = 1/2), so the rate is
+    # <= 1/2 per step and tol 1e-14 needs at most ~1.5 ln(1e14)/ln 2 + 5 = 75 steps (float64);
+    # the mixed form restarts LSQR per correction, 4 corrections at most.
     its = [q["iters"] for q in res.info]
-    assert max(its) <= 2 * min(its) + 10, its
+    cap = 75 if precision == "fp64" else 4 * 40
+    assert max(its) <= cap, its
 
 
 def test_under_2048x262144_srht(tk):

@@ -289,3 +289,54 @@ def test_edge_single_column_and_single_lambda(tk):
     a = p.A.numpy()[:, 0]
     x_exact = a @ p.b.numpy() / (a @ a + 0.5)
     assert abs(X[0, 0] - x_exact) <= 1e-12 * abs(x_exact)
+
+
+def sd_of_spectrum(sig, lam):
+    return float(np.sum(1.0 / (1.0 + lam / (sig * sig))))
+
+
+def test_uneven_batch_mixed_cholesky_and_lowrank(tk):
+    # the 256-problem workload's structure at test size: float32 data, mixed precision,
+    # half the problems with sigma_i = exp(-i/50) solved with the sd-sized low-rank form
+    probs = datagen.uneven_batch(10, m_range=(1500, 4000), n_range=(64, 200), N=4, dtype=torch.float32)
+    pairs, opts = [], []
+    for p in probs:
+        pairs.append((p.A.cuda(), p.b.cuda()))
+        n = p.A.shape[1]
+        if p.meta["lowrank"]:
+            s = min(n, 2 * math.ceil(sd_of_spectrum(p.sigma.numpy(), float(p.lambdas.min()))))
+            opts.append(tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=s, seed=3, precond=tk.TK_PRECOND_LOWRANK,
+                                        alpha=2.0, precision=tk.TK_PREC_MIXED))
+        else:
+            opts.append(tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=min(4 * n, p.A.shape[0]), seed=3,
+                                        precision=tk.TK_PREC_MIXED))
+    lams = np.stack([p.lambdas.numpy() for p in probs])
+    Xs, infos, st = tk.tk_solve_batched(pairs, lams, opts)
+    assert st == tk.TK_OK, infos
+    for p, X, lam, inf in zip(probs, Xs, lams, infos):
+        Xr = ref_over(p, lam)
+        Xc = X.cpu().numpy()
+        for i in range(len(lam)):
+            assert rel(Xc[i], Xr[i]) < TOL_X, (p.meta, lam[i], rel(Xc[i], Xr[i]), inf[i])
+        if p.meta["lowrank"]:
+            assert all(0 < q["rank"] <= p.A.shape[1] for q in inf)
+
+
+def test_mixed_gaussian_float32_scaled_workload(tk):
+    # 2^20 x 4096 float32 workload structure at 2^16 x 1024: Gaussian s = 2n, 16 lambda in 1e-5..1
+    prob, w = datagen.workload_problem("ridge_over_1048576x4096_f32", m=1 << 16, n=1024, N=16, keep_factors=True)
+    lams = prob.lambdas.numpy()
+    A, b = to_dev(prob)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=2 * 1024, seed=1, precision=tk.TK_PREC_MIXED)
+    res = tk.tk_solve(A, b, lams, o)
+    X = res.X.cpu().numpy()
+    Ad, bd = prob.A.double().numpy(), prob.b.numpy()
+    U, V, sig = prob.U.double().numpy(), prob.V.double().numpy(), prob.sigma.numpy()
+    for i in (0, 5, 10, 15):
+        lam = float(lams[i])
+        # reference: closed form from the generator's factors, refined against the stored
+        # (float32, exactly widened) A in double-double
+        x0 = V @ ((sig / (sig * sig + lam)) * (U.T @ bd))
+        xr = oracle.ref_ridge_refine(Ad, bd, lam, V, sig, x0, steps=3)
+        assert rel(X[i], xr) < TOL_X, (lams[i], rel(X[i], xr), res.info[i])
+    assert all(q["status"] == 0 for q in res.info)
