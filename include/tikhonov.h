@@ -147,6 +147,30 @@ TK_API tk_status tk_sketch_draw(uint64_t seed, int64_t mp, int64_t s, int8_t* si
                                 size_t work_bytes, void* stream);
 
 /*
+ * tk_sketch_draw_static -- the same draws as tk_sketch_draw, for callers that
+ * cannot allocate device memory.  The paper has no counterpart to this call.
+ *
+ * Some callers cannot call cudaMalloc or hand over a workspace: code that runs
+ * after an "allocate once at start-up" phase has closed (real-time loops,
+ * services whose memory pool owns every byte of the device), plugins invoked
+ * by a host framework that gives them no allocator, or code between two
+ * kernels of someone else's stream where an allocation would synchronize the
+ * device.  This entry point allocates nothing: its scratch (the 64-bit
+ * sampling keys) is a fixed array inside the library, TK_DRAW_STATIC_MAX_MP + 2
+ * words = 8 MiB + 16 B, which every GPU that loads the library holds until
+ * the process exits.
+ *   mp:    1 <= mp <= TK_DRAW_STATIC_MAX_MP, else TK_EINVAL (nothing launched).
+ *   signs, rows: as tk_sketch_draw (device, caller-owned, may be NULL).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (other streams, other host threads) race;
+ * serialize them.  Synchronizes `stream` before returning.
+ */
+#define TK_DRAW_STATIC_MAX_MP ((int64_t)1 << 20)
+TK_API tk_status tk_sketch_draw_static(uint64_t seed, int64_t mp, int64_t s, int8_t* signs, int64_t* rows,
+                                       void* stream);
+
+/*
  * tk_sketch_apply -- Y = X A (m >= n: Y is s x n, Algorithm 1 step 2) or
  * Y = A X (m < n: Y is m x s, Algorithm 2 step 2), float64 device output.
  * SRHT: X = sqrt(mp/s) S (H/sqrt(mp)) D with mp the next power of two of the

@@ -5,9 +5,17 @@
 // the GPU that is a radix select of the s-th smallest key (eight 8-bit
 // digit passes) followed by an order-preserving compaction, so the selected
 // rows come out ascending with no sort.
+#include <mutex>
+
 #include "tk_internal.cuh"
 
 namespace tk {
+
+// Scratch of tk_sketch_draw_static: the 64-bit sampling keys plus the two
+// words of the radix select, for at most TK_DRAW_STATIC_MAX_MP rows.  Every
+// device that loads the library holds this array (8 MiB + 16 B) until exit.
+static __device__ __align__(256) uint64_t g_draw_scratch[TK_DRAW_STATIC_MAX_MP + 2];
+
 namespace {
 
 __global__ void k_signs_keys(uint64_t seed, int64_t mp, int8_t* __restrict__ signs, uint64_t* __restrict__ keys) {
@@ -161,4 +169,52 @@ tk_status draw_signs_rows(uint64_t seed, int64_t mp, int64_t s, int8_t* signs, i
   return TK_OK;
 }
 
+// Device address of g_draw_scratch on the current device, looked up once per
+// device (host code only sees a host-side stand-in under that name).
+static tk_status static_scratch(uint64_t** out) {
+  static std::mutex mu;
+  static uint64_t* addr[64] = {nullptr};
+  int dev = 0;
+  TK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error_msg("tk_sketch_draw_static: device index out of range");
+    return TK_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    TK_CUDA(cudaGetSymbolAddress(&p, g_draw_scratch));
+    addr[dev] = static_cast<uint64_t*>(p);
+  }
+  *out = addr[dev];
+  return TK_OK;
+}
+
 }  // namespace tk
+
+extern "C" TK_API tk_status tk_sketch_draw_static(uint64_t seed, int64_t mp, int64_t s, int8_t* signs, int64_t* rows,
+                                                  void* stream) {
+  using namespace tk;
+  if (mp < 1 || mp > TK_DRAW_STATIC_MAX_MP) {
+    set_error_msg("tk_sketch_draw_static: mp must be in [1, TK_DRAW_STATIC_MAX_MP]; use tk_sketch_draw with a "
+                  "caller workspace for longer draws");
+    return TK_EINVAL;
+  }
+  if (s < 0 || s > mp) {
+    set_error_msg("tk_sketch_draw_static: s out of range");
+    return TK_EINVAL;
+  }
+  uint64_t* scratch = nullptr;
+  TK_TRY(static_scratch(&scratch));
+  // Same kernels as tk_sketch_draw; the keys and select words live in the static
+  // array.  Every word read is written earlier in the same call (keys[0, mp) by
+  // the draw kernel, the select words by the radix select), so the contents a
+  // previous call left behind are never read and nothing needs clearing.
+  Arena a;
+  a.base = reinterpret_cast<char*>(scratch);
+  a.cap = sizeof(uint64_t) * (size_t)(TK_DRAW_STATIC_MAX_MP + 2);
+  cudaStream_t st = (cudaStream_t)stream;
+  TK_TRY(draw_signs_rows(seed, mp, s, signs, rows, nullptr, a, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  return TK_OK;
+}

@@ -87,6 +87,7 @@ def lib() -> C.CDLL:
             "tk_sketch_svd": (INT, [P, I64, I64, P, P, P, P, SZ, P]),
             "tk_lowrank_ranks_workspace": (SZ, [INT]),
             "tk_lowrank_ranks": (INT, [P, I64, P, INT, D, P, P, P, SZ, P]),
+            "tk_sketch_draw_static": (INT, [U64, I64, I64, P, P, P]),
             "tk_phase_name": (C.c_char_p, [INT]),
             "tk_launch_count": (C.c_ulonglong, []),
             "tk_profile_enable": (INT, [INT]),
@@ -234,6 +235,14 @@ def tk_sketch_draw(seed: int, mp: int, s: int, device="cuda", stream=None):
     ws = int(lib().tk_sketch_draw_workspace(mp))
     work = _workspace(ws, device)
     _check(lib().tk_sketch_draw(seed, mp, s, _ptr(signs), _ptr(rows), _ptr(work), work.numel(), _stream(stream)))
+    return signs, rows[:s]
+
+
+def tk_sketch_draw_static(seed: int, mp: int, s: int, device="cuda", stream=None):
+    """The same draws as tk_sketch_draw with no workspace (library-held scratch, mp <= 2^20)."""
+    signs = torch.empty(mp, dtype=torch.int8, device=device)
+    rows = torch.empty(max(s, 1), dtype=torch.int64, device=device)
+    _check(lib().tk_sketch_draw_static(seed, mp, s, _ptr(signs), _ptr(rows), _stream(stream)))
     return signs, rows[:s]
 
 
