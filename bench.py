@@ -179,6 +179,9 @@ def main():
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core LSQR comparison step")
+    ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
+                    help="where the synthetic problem is generated (cpu for profiler runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -200,8 +203,9 @@ def main():
     from paper_2203_07329_gb300 import tikhonov as tk
 
     m, n = args.m, args.n
-    prob, w = datagen.workload_problem(WORKLOAD, device="cuda", m=m, n=n)
-    A, b = prob.A, prob.b
+    prob, w = datagen.workload_problem(WORKLOAD, device=args.gen_device, m=m, n=n)
+    A, b = prob.A.cuda(), prob.b.cuda()
+    del prob.A
     lams = prob.lambdas.numpy()
     N = len(lams)
     s = w["s"]
@@ -266,8 +270,37 @@ def main():
     e2e_ms = e0.elapsed_time(e1) / args.steps
     del A_dev, A_host
 
-    # ---- plain float64 comparisons on the same inputs (one step each)
+    # ---- the mixed solve with the LSQR products on the tensor cores (one step)
     extra = {}
+    if not args.no_tc:
+        o_tc = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, precision=tk.TK_PREC_MIXED, lsqr_tc=1)
+        need = tk.workspace_size(tk.make_problem(A, b), N, o_tc)
+        work_tc = work if work.numel() >= need else torch.empty(need, dtype=torch.uint8, device="cuda")
+        Xtc = torch.empty((N, n), dtype=torch.float64, device="cuda")
+        tk.tk_solve(A, b, lams, o_tc, work=work_tc, X=Xtc, stream=stream)  # warm-up
+        barrier()
+        tk.tk_profile_enable(True)
+        tk.tk_profile_collect()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        rtc = tk.tk_solve(A, b, lams, o_tc, work=work_tc, X=Xtc, stream=stream)
+        c1.record(stream)
+        barrier()
+        prof_tc = tk.tk_profile_collect()
+        tk.tk_profile_enable(False)
+        ttc = c0.elapsed_time(c1)
+        dtc = (Xtc - X_mixed).norm(dim=1) / X_mixed.norm(dim=1)
+        extra["mixed_tensor_core_lsqr"] = {
+            "value": N / (ttc / 1e3), "ms_per_step": ttc,
+            "iters_mean": float(np.mean([q["iters"] for q in rtc.info])),
+            "refine_steps_max": int(max(q["refine_steps"] for q in rtc.info)),
+            "max_rel_diff_vs_simt_mixed": float(dtc.max()),
+            "phases": {k: {"ms": v["ms"], "launches": v["launches"],
+                           "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0}
+                       for k, v in prof_tc.items() if v["launches"]}}
+        del work_tc, Xtc
+
+    # ---- plain float64 comparisons on the same inputs (one step each)
     if not args.no_fp64:
         for key, o in (("fp64_batched", o_fp64), ("fp64_one_at_a_time", o_fp64_one)):
             X64 = torch.empty((N, n), dtype=torch.float64, device="cuda")

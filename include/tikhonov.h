@@ -82,6 +82,9 @@ typedef struct {
   double refine_tol;      /* [1e-11] MIXED stops when ||d|| <= refine_tol ||x|| */
   uint64_t seed;          /* [1] Philox key of every draw */
   tk_schedule schedule;   /* [BATCHED]: all lambda advance together; ONE_AT_A_TIME: one lambda per LSQR run */
+  int lsqr_tc;            /* [0] MIXED: the two products with A of each LSQR step on the tensor cores
+                             (tcgen05 kind::tf32, 3-term split = float32 accuracy; needs 16-byte aligned
+                             rows of A and keeps a float32 copy of A^T); 0 = SIMT float32 */
 } tk_opts;
 
 /* Per-lambda report. */
@@ -175,6 +178,9 @@ TK_API tk_status tk_sketch_draw_static(uint64_t seed, int64_t mp, int64_t s, int
  * Y = A X (m < n: Y is m x s, Algorithm 2 step 2), float64 device output.
  * SRHT: X = sqrt(mp/s) S (H/sqrt(mp)) D with mp the next power of two of the
  * long dimension.  Gaussian: X has N(0, 1/s) entries from Philox stream 2.
+ * With precision MIXED (Gaussian, m >= n only) the sketch is the one the
+ * mixed form uses: X and A rounded to BF16, products on the tensor cores
+ * with FP32 accumulation.
  * work: device, at least tk_sketch_apply_workspace() bytes.
  */
 TK_API tk_status tk_sketch_apply_workspace(const tk_problem* p, const tk_opts* o, size_t* bytes);

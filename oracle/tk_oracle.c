@@ -28,6 +28,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_API __attribute__((visibility("default")))
 
@@ -762,16 +765,22 @@ ORC_API void orc_ridge_residual_dd(const double* A, int64_t m, int64_t n, int64_
     rh[i] = hi;
     rl[i] = lo;
   }
-#pragma omp parallel for schedule(static)
-  for (int64_t j = 0; j < n; ++j) {
-    double hi = 0.0, lo = 0.0;
-    for (int64_t i = 0; i < m; ++i) {
-      dd_fma_acc(&hi, &lo, A[i * lda + j], rh[i]);
-      dd_fma_acc(&hi, &lo, A[i * lda + j], rl[i]);
-    }
-    dd_fma_acc(&hi, &lo, -lambda, x[j]);
-    gh[j] = hi;
-    gl[j] = lo;
+  /* g_j accumulates over i = 0..m-1 in ascending order; the loop nest walks
+   * rows (each thread owns a slice of columns) so A is read row by row. */
+#pragma omp parallel
+  {
+    int64_t nt = 1, t = 0;
+#ifdef _OPENMP
+    nt = omp_get_num_threads();
+    t = omp_get_thread_num();
+#endif
+    int64_t j0 = n * t / nt, j1 = n * (t + 1) / nt;
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t j = j0; j < j1; ++j) {
+        dd_fma_acc(&gh[j], &gl[j], A[i * lda + j], rh[i]);
+        dd_fma_acc(&gh[j], &gl[j], A[i * lda + j], rl[i]);
+      }
+    for (int64_t j = j0; j < j1; ++j) dd_fma_acc(&gh[j], &gl[j], -lambda, x[j]);
   }
   for (int64_t j = 0; j < n; ++j) g[j] = gh[j] + gl[j];
   if (r_out)

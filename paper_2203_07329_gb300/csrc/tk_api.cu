@@ -49,6 +49,7 @@ struct Plan {
   int N = 0, N_cap = 0;
   tk_opts o{};
   bool mixed = false, lowrank = false;
+  bool lsqr_tc = false;  // tensor-core float32 LSQR products
 };
 
 constexpr int64_t kMaxShort = 8192;
@@ -101,6 +102,10 @@ tk_status make_plan(const tk_problem* p, int N, const tk_opts* o, Plan& P) {
   P.s = s;
   P.np = cdiv(P.c, 64) * 64;
   P.N_cap = (o->schedule == TK_SCHED_ONE_AT_A_TIME) ? 1 : std::max(N, 1);
+  // the tensor-core products need 16-byte aligned float32 rows of A, A^T and
+  // the lambda-major vectors; other shapes keep the SIMT float32 products
+  P.lsqr_tc = P.mixed && o->lsqr_tc != 0 && P.N_cap <= 64 && !P.under && P.m % 4 == 0 && P.n % 4 == 0 &&
+              (P.dt == TK_F64 || P.lda % 4 == 0);
   return TK_OK;
 }
 
@@ -113,6 +118,7 @@ struct Bufs {
   double* Y = nullptr;
   void* AT = nullptr;
   float* A32 = nullptr;
+  float* AT32 = nullptr;
   double* A64 = nullptr;
   double* C = nullptr;
   double* R = nullptr;
@@ -137,8 +143,13 @@ struct Bufs {
   int splits = 1;
 };
 
+// The mixed form's Gaussian sketch of an overdetermined A runs on the tensor
+// cores (BF16 operands, FP32 accumulation); every other sketch is SIMT.
+bool tc_sketch(const Plan& P) { return P.mixed && P.o.sketch == TK_SKETCH_GAUSS && !P.under; }
+
 size_t sketch_scratch(const Plan& P) {
   tk_dtype dt = P.mixed ? TK_F32 : P.dt;
+  if (tc_sketch(P)) return tc_sketch_workspace(P.L, P.c, P.s);
   if (P.o.sketch == TK_SKETCH_SRHT) return srht_rows_workspace(P.L, P.c, dt, P.s);
   return gauss_rows_workspace(P.L, P.c, dt, P.s);
 }
@@ -152,6 +163,7 @@ void carve(const Plan& P, Arena& a, Bufs& B) {
   B.Y = a.take<double>((size_t)P.s * P.c);
   if (P.under) B.AT = a.take<char>((size_t)P.m * P.n * (P.dt == TK_F64 ? 8 : 4));
   if (P.mixed && P.dt == TK_F64) B.A32 = a.take<float>((size_t)P.m * P.n);
+  if (P.lsqr_tc) B.AT32 = a.take<float>((size_t)P.m * P.n);
   if (!P.mixed && P.dt == TK_F32) B.A64 = a.take<double>((size_t)P.m * P.n);
   if (!P.lowrank) {
     B.C = a.take<double>((size_t)P.c * P.c);
@@ -184,6 +196,7 @@ void carve(const Plan& P, Arena& a, Bufs& B) {
   const int64_t lr_s = P.lowrank ? P.s : 0;
   if (P.mixed) {
     B.e32.m = P.m; B.e32.n = P.n; B.e32.N_cap = P.N_cap; B.e32.under = false; B.e32.lr_s = lr_s;
+    B.e32.tc = P.lsqr_tc;
     B.e32.carve(a);
   } else {
     B.e64.m = P.m; B.e64.n = P.n; B.e64.N_cap = P.N_cap; B.e64.under = P.under; B.e64.lr_s = lr_s;
@@ -285,6 +298,7 @@ tk_status do_sketch(const Plan& P, const void* A_sk, tk_dtype dt_sk, int64_t ld_
   Arena sa;
   sa.base = B.scratch;
   sa.cap = B.scratch_bytes;
+  if (tc_sketch(P)) return tc_gauss_sketch(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
   if (P.o.sketch == TK_SKETCH_SRHT) return srht_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
   return gauss_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
 }
@@ -436,6 +450,12 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     //      correction d solves min ||B d - [0; g/sqrt(l)]||, x <- x + d.
     Lsqr<float>& e = B.e32;
     e.A = A32; e.lda = lda32; e.st = st; e.atol = e.btol = P.o.inner_tol; e.maxiter = P.o.maxiter;
+    if (P.lsqr_tc && ((uintptr_t)A32 % 16) == 0) {
+      TK_TRY(transpose(A32, TK_F32, P.m, P.n, lda32, B.AT32, st));  // float32 A^T for the A^T U product
+      e.AT = B.AT32;
+    } else {
+      e.tc = false;  // unaligned base address: SIMT float32 products
+    }
     if (!P.lowrank) {
       e.prec_kind = TK_PRECOND_CHOL; e.R = B.R32; e.ldr = P.np; e.rstride = P.np * P.np;
     } else {
@@ -546,6 +566,7 @@ TK_API tk_status tk_opts_default(tk_opts* o) {
   o->refine_tol = 1e-11;
   o->seed = 1;
   o->schedule = TK_SCHED_BATCHED;
+  o->lsqr_tc = 0;
   return TK_OK;
 }
 
@@ -706,7 +727,7 @@ TK_API tk_status tk_sketch_apply(const tk_problem* p, const tk_opts* o, double* 
                                  void* stream) {
   Plan P;
   TK_TRY(make_plan(p, 1, o, P));
-  if (P.mixed) return einval("tk_sketch_apply sketches in the dtype of A; use precision FP64");
+  if (P.mixed && !tc_sketch(P)) return einval("tk_sketch_apply: MIXED selects the tensor-core Gaussian sketch only");
   if (!p->A || !Y) return einval("A and Y must be non-NULL");
   size_t need = 0;
   TK_TRY(tk_sketch_apply_workspace(p, o, &need));

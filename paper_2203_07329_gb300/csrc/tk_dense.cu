@@ -105,17 +105,23 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 // A[j*lda + k] (TRANSB: the product with A^T, N = rows of A) or A[k*lda + j].
 // Warps are arranged 2 x 4 over the tile and lanes 4 x 8 inside a warp, so a
 // warp's shared-memory reads of L touch 4 rows (broadcast) and of B 8 column
-// groups; every thread keeps TM x TN accumulators.
-template <typename T, bool TRANSB, int BM, int BN, int TM, int TN>
+// groups; every thread keeps TM x TN accumulators.  The next K-slab is loaded
+// into registers (16-byte loads when VEC) while the current one is consumed
+// from shared memory (two buffers, one barrier per slab).
+template <typename T, bool TRANSB, bool VEC, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(256)
     k_gemm_lm(int64_t M, int64_t N, int64_t K, const T* __restrict__ L, int64_t ldl, const T* __restrict__ A,
               int64_t lda, T* C, int64_t ldc, const double* __restrict__ beta_row, const T* Cin, int64_t ldcin,
               int64_t k_per_split, double* __restrict__ partial) {
   constexpr int BK = 16;
+  constexpr int LV = (BM * BK) / (4 * 256) > 0 ? (BM * BK) / (4 * 256) : 1;  // float4 per thread for L
+  constexpr int BV = (BN * BK) / (4 * 256);                                 // float4 per thread for B
   static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
   static_assert(BM / TM == 8 && BN / TN == 32, "2 x 4 warps of 4 x 8 lanes");
-  __shared__ __align__(16) T Ls[BK][BM];
-  __shared__ __align__(16) T Bs[BK][BN + 4];
+  static_assert(sizeof(T) == 4, "float path");
+  static_assert(TN == 8 && BN == 256, "column pairs 64 j2 + 2 tx");
+  __shared__ __align__(16) T Ls[2][BK][BM];
+  __shared__ __align__(16) T Bs[2][BK][BN + 4];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int ty = (w >> 2) * 4 + (lane >> 3);  // 0..7  row group
   const int tx = (w & 3) * 8 + (lane & 7);    // 0..31 column group
@@ -127,39 +133,115 @@ __global__ void __launch_bounds__(256)
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+  float4 rl[LV], rb[BV];
+  // quad q of L: row i = q / (BK/4), k = 4 * (q % (BK/4)); of B (TRANSB): row j = q / 4, k = 4 * (q % 4);
+  // of B (not TRANSB): k = q / (BN/4), j = 4 * (q % (BN/4))
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int v = 0; v < LV; ++v) {
+      const int q = tid + v * 256;
+      const int i = q / (BK / 4), k = 4 * (q % (BK / 4));
+      float e[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) e[t] = 0.f;
+      if (q < BM * BK / 4 && i < M) {
+        const int64_t gk = k0 + k;
+        if (VEC && gk + 3 < kend) {
+          const float4 f = *reinterpret_cast<const float4*>(L + (int64_t)i * ldl + gk);
+          e[0] = f.x; e[1] = f.y; e[2] = f.z; e[3] = f.w;
+        } else {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) e[t] = (gk + t < kend) ? L[(int64_t)i * ldl + gk + t] : 0.f;
+        }
+      }
+      rl[v] = make_float4(e[0], e[1], e[2], e[3]);
+    }
+#pragma unroll
+    for (int v = 0; v < BV; ++v) {
+      const int q = tid + v * 256;
+      float e[4];
+      if (TRANSB) {
+        const int j = q / 4, k = 4 * (q % 4);
+        const int64_t gj = n0 + j, gk = k0 + k;
+        if (gj < N && VEC && gk + 3 < kend) {
+          const float4 f = *reinterpret_cast<const float4*>(A + gj * lda + gk);
+          e[0] = f.x; e[1] = f.y; e[2] = f.z; e[3] = f.w;
+        } else {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) e[t] = (gj < N && gk + t < kend) ? A[gj * lda + gk + t] : 0.f;
+        }
+      } else {
+        const int k = q / (BN / 4), j = 4 * (q % (BN / 4));
+        const int64_t gj = n0 + j, gk = k0 + k;
+        if (gk < kend && VEC && gj + 3 < N) {
+          const float4 f = *reinterpret_cast<const float4*>(A + gk * lda + gj);
+          e[0] = f.x; e[1] = f.y; e[2] = f.z; e[3] = f.w;
+        } else {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) e[t] = (gk < kend && gj + t < N) ? A[gk * lda + gj + t] : 0.f;
+        }
+      }
+      rb[v] = make_float4(e[0], e[1], e[2], e[3]);
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int v = 0; v < LV; ++v) {
+      const int q = tid + v * 256;
+      if (q < BM * BK / 4) {
+        const int i = q / (BK / 4), k = 4 * (q % (BK / 4));
+        Ls[buf][k + 0][i] = rl[v].x;
+        Ls[buf][k + 1][i] = rl[v].y;
+        Ls[buf][k + 2][i] = rl[v].z;
+        Ls[buf][k + 3][i] = rl[v].w;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < BV; ++v) {
+      const int q = tid + v * 256;
+      if (TRANSB) {
+        const int j = q / 4, k = 4 * (q % 4);
+        Bs[buf][k + 0][j] = rb[v].x;
+        Bs[buf][k + 1][j] = rb[v].y;
+        Bs[buf][k + 2][j] = rb[v].z;
+        Bs[buf][k + 3][j] = rb[v].w;
+      } else {
+        const int k = q / (BN / 4), j = 4 * (q % (BN / 4));
+        *reinterpret_cast<float4*>(&Bs[buf][k][j]) = rb[v];
+      }
+    }
+  };
+  int cur = 0;
+  if (kbeg < kend) {
+    load(kbeg);
+    store(0);
+  }
+  __syncthreads();
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-    for (int idx = tid; idx < BM * BK; idx += 256) {
-      const int i = idx / BK, k = idx % BK;
-      const int64_t gk = k0 + k;
-      Ls[k][i] = (i < M && gk < kend) ? L[(int64_t)i * ldl + gk] : T(0);
-    }
-    if (TRANSB) {
-      for (int idx = tid; idx < BN * BK; idx += 256) {
-        const int j = idx / BK, k = idx % BK;
-        const int64_t gj = n0 + j, gk = k0 + k;
-        Bs[k][j] = (gj < N && gk < kend) ? A[gj * lda + gk] : T(0);
-      }
-    } else {
-      for (int idx = tid; idx < BN * BK; idx += 256) {
-        const int k = idx / BN, j = idx % BN;
-        const int64_t gj = n0 + j, gk = k0 + k;
-        Bs[k][j] = (gj < N && gk < kend) ? A[gk * lda + gj] : T(0);
-      }
-    }
-    __syncthreads();
+    const bool more = k0 + BK < kend;
+    if (more) load(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       T a[TM], bv[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = Ls[kk][ty * TM + i];
+      for (int i = 0; i < TM; ++i) a[i] = Ls[cur][kk][ty * TM + i];
+      // column pairs 64 j2 + 2 tx + {0, 1}: a warp's 8 column groups read one
+      // contiguous 64-byte chunk per 8-byte load (no bank conflicts)
 #pragma unroll
-      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx * TN + j];
+      for (int j2 = 0; j2 < TN / 2; ++j2) {
+        const float2 f = *reinterpret_cast<const float2*>(&Bs[cur][kk][64 * j2 + 2 * tx]);
+        bv[2 * j2] = f.x;
+        bv[2 * j2 + 1] = f.y;
+      }
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
     }
+    if (more) store(cur ^ 1);
     __syncthreads();
+    cur ^= 1;
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
@@ -167,7 +249,7 @@ __global__ void __launch_bounds__(256)
     if (r >= M) continue;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      const int64_t c = n0 + tx * TN + j;
+      const int64_t c = n0 + 64 * (j >> 1) + 2 * tx + (j & 1);
       if (c >= N) continue;
       if (partial) {
         partial[(int64_t)blockIdx.y * M * N + r * N + c] = (double)acc[i][j];
@@ -193,13 +275,19 @@ tk_status launch_gemm_lm(bool transB, int64_t M, int64_t N, int64_t K, const T* 
     set_error_msg("gemm: too many K splits");
     return TK_EINVAL;
   }
+  // 16-byte loads need 16-byte aligned rows
+  const bool vec = ((uintptr_t)L % 16 == 0) && ((uintptr_t)A % 16 == 0) && (ldl % 4 == 0) && (lda % 4 == 0);
+#define TK_LM(TRB, V, BM_, TM_)                                                                                 \
+  k_gemm_lm<T, TRB, V, BM_, BN, TM_, 8><<<grid, 256, 0, st>>>(M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, \
+                                                              ldcin, kps, partial)
   if (M <= 32) {
-    if (transB) k_gemm_lm<T, true, 32, BN, 4, 8><<<grid, 256, 0, st>>>(M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, ldcin, kps, partial);
-    else k_gemm_lm<T, false, 32, BN, 4, 8><<<grid, 256, 0, st>>>(M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, ldcin, kps, partial);
+    if (transB) { if (vec) TK_LM(true, true, 32, 4); else TK_LM(true, false, 32, 4); }
+    else { if (vec) TK_LM(false, true, 32, 4); else TK_LM(false, false, 32, 4); }
   } else {
-    if (transB) k_gemm_lm<T, true, 64, BN, 8, 8><<<grid, 256, 0, st>>>(M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, ldcin, kps, partial);
-    else k_gemm_lm<T, false, 64, BN, 8, 8><<<grid, 256, 0, st>>>(M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, ldcin, kps, partial);
+    if (transB) { if (vec) TK_LM(true, true, 64, 8); else TK_LM(true, false, 64, 8); }
+    else { if (vec) TK_LM(false, true, 64, 8); else TK_LM(false, false, 64, 8); }
   }
+#undef TK_LM
   TK_LAUNCH_CHECK();
   return TK_OK;
 }
@@ -734,13 +822,16 @@ tk_status trsv_batched(bool transposed, int64_t n, const TR* R, int64_t ldr, int
     set_error_msg("trsv: order too large for the shared-memory solve");
     return TK_EINVAL;
   }
+  // The cap is set to the same constant by every caller: host threads of the
+  // batched solver launch concurrently, and a per-call value would race.
+  constexpr int kCap = 200 * 1024;
   if (transposed) {
     auto kern = k_trsv_upper_t<TR, TX>;
-    TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kCap));
     kern<<<count, kTrsvThreads, smem, st>>>(n, R, ldr, rstride, idx, Xin, X, ldx);
   } else {
     auto kern = k_trsv_upper<TR, TX>;
-    TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kCap));
     kern<<<count, kTrsvThreads, smem, st>>>(n, R, ldr, rstride, idx, Xin, X, ldx);
   }
   TK_LAUNCH_CHECK();

@@ -155,6 +155,18 @@ tk_status transpose(const void* A, tk_dtype dt, int64_t rows, int64_t cols, int6
 tk_status convert_f64_to_f32(const double* src, float* dst, int64_t rows, int64_t cols, int64_t lds, int64_t ldd,
                              cudaStream_t st);
 
+// Tensor-core BF16 Gaussian sketch (tk_tc.cu): Y (s x n) = G A, A m x n.
+size_t tc_sketch_workspace(int64_t m, int64_t n, int64_t s);
+tk_status tc_gauss_sketch(const void* A, tk_dtype dt, int64_t m, int64_t n, int64_t lda, uint64_t seed, int64_t s,
+                          double* Y, Arena& ar, cudaStream_t st);
+
+// Tensor-core LSQR products (tk_tc.cu), float32 operands, 3-term TF32 split.
+size_t tc_lmaj_workspace(int N_cap, int64_t K);
+tk_status tc_lmaj_product(bool update, const float* X, int64_t rows, int64_t K, int64_t ldx, const float* L,
+                          int64_t ldl, int N, float* U, int64_t ldu, const double* coef, double* partial, int splits,
+                          void* scratch, cudaStream_t st);
+tk_status tc_lmaj_check(void* scratch, int N, int64_t K, cudaStream_t st);
+
 // Dense kernels (tk_dense.cu)
 template <typename TA, typename TB, typename TC>
 tk_status gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,

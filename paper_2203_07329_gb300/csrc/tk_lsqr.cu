@@ -15,6 +15,7 @@
 // Underdetermined (R^-T D, D = [A sqrt(l) I], min-norm):
 //   P  = V1 A^T + sqrt(l) V2;  u = R^-T P - alpha u;  beta = ||u||
 //   T  = R^-1 u;  v = [T A; sqrt(l) T] - beta v;  alpha = ||v||;  Givens on z = [x; y]
+#include <type_traits>
 #include <vector>
 
 #include "tk_lsqr.cuh"
@@ -368,6 +369,7 @@ size_t Lsqr<T>::workspace(int64_t m, int64_t n, int N_cap, bool under, int64_t l
   e.N_cap = N_cap;
   e.under = under;
   e.lr_s = lr_s;
+  e.tc = false;
   Arena a;
   e.carve(a);
   return a.used + 4096;
@@ -398,6 +400,7 @@ void Lsqr<T>::carve(Arena& a) {
     lr_tmp = a.take<T>((size_t)N_cap * lr_s);
     lr_inv = a.take<double>((size_t)N_cap);
   }
+  if (tc) tc_scratch = a.take<char>(tc_lmaj_workspace(N_cap, std::max(n, m)));
 }
 
 template <typename T>
@@ -420,8 +423,15 @@ template <typename T>
 tk_status Lsqr<T>::prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, int count) {
   // C (count x m) = Win (count x n) A^T  [+ beta_row * C]
   int tok = prof_begin(TK_PHASE_AW, st);
-  tk_status r = gemm<T, T, T>(false, true, count, m, n, Win, ldw, A, lda, C, m, 1.0, beta, beta ? C : nullptr,
-                              m, st);
+  tk_status r;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc && beta) {
+      r = tc_lmaj_product(true, A, m, n, lda, Win, ldw, count, C, m, beta, nullptr, 1, tc_scratch, st);
+      prof_end(tok, st, 2.0 * count * m * n, (double)sizeof(T) * ((double)m * n + count * (double)n + 2.0 * count * m));
+      return r;
+    }
+  }
+  r = gemm<T, T, T>(false, true, count, m, n, Win, ldw, A, lda, C, m, 1.0, beta, beta ? C : nullptr, m, st);
   prof_end(tok, st, 2.0 * count * m * n, (double)sizeof(T) * ((double)m * n + count * (double)n + 2.0 * count * m));
   return r;
 }
@@ -430,7 +440,16 @@ template <typename T>
 tk_status Lsqr<T>::prod_atu(const T* Uin, int count) {
   // part_g (splits x count x n) = Uin (count x m) A
   int tok = prof_begin(TK_PHASE_ATU, st);
-  tk_status r = gemm_splitk<T, T>(false, false, count, n, m, Uin, m, A, lda, part_g, splits, st);
+  tk_status r;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc && AT) {
+      r = tc_lmaj_product(false, AT, n, m, m, Uin, m, count, nullptr, 0, nullptr, part_g, splits, tc_scratch, st);
+      prof_end(tok, st, 2.0 * count * m * n,
+               (double)sizeof(T) * ((double)m * n + count * (double)m) + 8.0 * splits * count * n);
+      return r;
+    }
+  }
+  r = gemm_splitk<T, T>(false, false, count, n, m, Uin, m, A, lda, part_g, splits, st);
   prof_end(tok, st, 2.0 * count * m * n,
            (double)sizeof(T) * ((double)m * n + count * (double)m) + 8.0 * splits * count * n);
   return r;
@@ -569,6 +588,7 @@ tk_status Lsqr<T>::run(const double* b, int64_t ldbt, const double* bbot, int64_
     k_vstep<T><<<nact, kVecThreads, 0, st>>>(Vraw, V, W, Y, nv, sc, atol, btol, maxiter, 0);
     TK_LAUNCH_CHECK();
   }
+  if (tc) TK_TRY(tc_lmaj_check(tc_scratch, N_cap, std::max(n, m), st));
   return TK_OK;
 }
 

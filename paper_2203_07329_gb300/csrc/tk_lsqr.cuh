@@ -60,6 +60,10 @@ struct Lsqr {
   int* slot_lam = nullptr;
   int* idx_buf = nullptr;
   const double* lam_all = nullptr;
+  // tensor-core products (float32 engine only): AT = float32 A^T (n x m)
+  bool tc = false;
+  const T* AT = nullptr;
+  void* tc_scratch = nullptr;
 
   static size_t workspace(int64_t m, int64_t n, int N_cap, bool under, int64_t lr_s);
   void carve(Arena& a);

@@ -91,7 +91,8 @@ tk_status run_fwht_pass(bool first, bool last, const TIn* srcA, const TC* srcZ, 
 #define TK_FWHT_LAUNCH(F, LST, SRC)                                                                       \
   do {                                                                                                    \
     auto kern = k_fwht_pass<TIn, TC, F, LST>;                                                             \
-    TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));          \
+    /* one constant cap for every caller (concurrent host threads must not race on it) */                 \
+    TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));          \
     kern<<<(unsigned)blocks, kFwhtThreads, smem, st>>>(SRC, ld_src, Z, Y, signs, rowmap, L, cols, b0, t, \
                                                        CB, ncb, scale);                                   \
   } while (0)

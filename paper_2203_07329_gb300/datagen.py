@@ -133,7 +133,8 @@ def workload_problem(name: str, *, device="cpu", m: int | None = None, n: int | 
 
 
 def uneven_batch(P: int = 256, *, seed: int = 20220320, m_range=(2000, 65536), n_range=(64, 1024), N: int = 16,
-                 lam=(1e-6, 1.0), device="cpu", dtype=torch.float32, max_total_bytes: int | None = None):
+                 lam=(1e-6, 1.0), device="cpu", dtype=torch.float32, max_total_bytes: int | None = None,
+                 keep_factors: bool = False):
     """Many independent problems of uneven size: m, n uniform in the given
     ranges (m >= n enforced), half with log-spaced spectra 1..1e-5, half with
     sigma_i = exp(-i/50) (small statistical dimension)."""
@@ -147,7 +148,7 @@ def uneven_batch(P: int = 256, *, seed: int = 20220320, m_range=(2000, 65536), n
         lowrank = (p % 2 == 1)
         sig = spectrum("exp", n, tau=50.0) if lowrank else spectrum("log", n, hi=1.0, lo=1e-5)
         pr = make_ridge_problem(m, n, sig, log_lambdas(N, lam[0], lam[1]), seed=seed * 1000 + p, dtype=dtype,
-                                device=device)
+                                device=device, keep_factors=keep_factors)
         pr.meta["lowrank"] = lowrank
         probs.append(pr)
         total += m * n * pr.A.element_size()

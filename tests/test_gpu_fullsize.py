@@ -94,3 +94,65 @@ def test_under_2048x262144_srht(tk):
         err = np.linalg.norm(X[i] - xr) / np.linalg.norm(xr)
         print(f"under lambda={lam:.1e} rel.err={err:.2e} tol={tol:.2e} iters={res.info[i]['iters']}")
         assert err < tol, (lam, err, tol)
+
+
+def refine_reference(A64, b, lam, U, V, sig, steps):
+    x0 = V @ ((sig / (sig * sig + lam)) * (U.T @ b))
+    return oracle.ref_ridge_refine(A64, b, lam, V, sig, x0, steps=steps)
+
+
+def test_over_1048576x4096_f32_mixed_tensor_core_sketch(tk):
+    prob, w = datagen.workload_problem("ridge_over_1048576x4096_f32", device="cuda", keep_factors=True)
+    lams = prob.lambdas.numpy()
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=w["s"], seed=1, precision=tk.TK_PREC_MIXED)
+    res = tk.tk_solve(prob.A, prob.b, lams, o)
+    X = res.X.cpu().numpy()
+    assert all(q["status"] == 0 for q in res.info), res.info
+    A64 = prob.A.cpu().double().numpy()
+    b = prob.b.cpu().numpy()
+    U, V = prob.U.cpu().double().numpy(), prob.V.cpu().double().numpy()
+    sig = prob.sigma.numpy()
+    del prob
+    for i in (0, len(lams) - 1):
+        lam = float(lams[i])
+        # float32 factors: the closed form is good to ~1e-7; each double-double
+        # step contracts by ~||A^T A - V S^2 V^T|| / lambda, so 4 steps reach far below 1e-10
+        xr = refine_reference(A64, b, lam, U, V, sig, steps=4)
+        err = np.linalg.norm(X[i] - xr) / np.linalg.norm(xr)
+        print(f"f32 mixed lambda={lam:.1e} rel.err={err:.2e} iters={res.info[i]['iters']} "
+              f"refine={res.info[i]['refine_steps']}")
+        assert err < 1e-10, (lam, err)
+
+
+def test_uneven_256_problems_full_size(tk):
+    import math
+    probs = datagen.uneven_batch(256, device="cuda", dtype=torch.float32, keep_factors=True)
+    pairs, opts = [], []
+    for p in probs:
+        n = p.A.shape[1]
+        lam_min = float(p.lambdas.min())
+        if p.meta["lowrank"]:
+            sd = float(np.sum(1.0 / (1.0 + lam_min / (p.sigma.numpy() ** 2))))
+            opts.append(tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=min(n, 2 * math.ceil(sd)), seed=1,
+                                        precond=tk.TK_PRECOND_LOWRANK, alpha=2.0, precision=tk.TK_PREC_MIXED))
+        else:
+            opts.append(tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=min(4 * n, p.A.shape[0]), seed=1,
+                                        precision=tk.TK_PREC_MIXED))
+        pairs.append((p.A, p.b))
+    lams = np.stack([p.lambdas.numpy() for p in probs])
+    Xs, infos, st = tk.tk_solve_batched(pairs, lams, opts)
+    assert st == tk.TK_OK
+    for k in range(0, 256, 37):
+        p = probs[k]
+        A64 = p.A.cpu().double().numpy()
+        b = p.b.cpu().numpy()
+        U, V = p.U.cpu().double().numpy(), p.V.cpu().double().numpy()
+        sig = p.sigma.numpy()
+        X = Xs[k].cpu().numpy()
+        for i in (0, lams.shape[1] - 1):
+            lam = float(lams[k, i])
+            xr = refine_reference(A64, b, lam, U, V, sig, steps=4)
+            err = np.linalg.norm(X[i] - xr) / np.linalg.norm(xr)
+            print(f"problem {k} m={A64.shape[0]} n={A64.shape[1]} lowrank={p.meta['lowrank']} "
+                  f"lambda={lam:.1e} rel.err={err:.2e}")
+            assert err < 1e-10, (k, lam, err)

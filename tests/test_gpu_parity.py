@@ -340,3 +340,41 @@ def test_mixed_gaussian_float32_scaled_workload(tk):
         xr = oracle.ref_ridge_refine(Ad, bd, lam, V, sig, x0, steps=3)
         assert rel(X[i], xr) < TOL_X, (lams[i], rel(X[i], xr), res.info[i])
     assert all(q["status"] == 0 for q in res.info)
+
+
+@pytest.mark.parametrize("m,n,s", [(1000, 300, 256), (4096, 256, 1024), (777, 513, 130), (64, 8, 16)])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_tensor_core_gauss_sketch(tk, m, n, s, dtype):
+    # the mixed form's sketch: G and A rounded to BF16, tcgen05 products with FP32
+    # accumulation.  Each term carries two BF16 roundings (relative 2^-8 each) with
+    # random signs, so ||Y - Y_oracle||_F / ||Y_oracle||_F is a few 1e-3.
+    A = torch.randn(m, n, dtype=torch.float64, generator=torch.Generator().manual_seed(m * 7 + n)).to(dtype)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=s, seed=8, precision=tk.TK_PREC_MIXED)
+    Y = tk.tk_sketch_apply(A.cuda(), o).cpu().numpy()
+    Yo = oracle.gauss_over(A.double().numpy(), 8, s)
+    err = np.linalg.norm(Y - Yo) / np.linalg.norm(Yo)
+    assert err < 2e-2, err
+    # the sketch is still an embedding: columns keep their norms to within sampling error
+    assert np.all(np.isfinite(Y))
+
+
+@pytest.mark.parametrize("m,n,N", [(4096, 256, 6), (3004, 164, 40), (12000, 384, 64)])
+def test_mixed_tensor_core_lsqr_products(tk, m, n, N):
+    # the two products with A of every LSQR step on tcgen05 (kind::tf32, 3-term split),
+    # then float64 refinement: x must reach the same 1e-10 as the SIMT float32 path
+    p = problem(m, n, lo=1e-5, N=N, lam=(1e-5, 1.0), dtype=torch.float32)
+    lams = p.lambdas.numpy()
+    A, b = to_dev(p)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=min(4 * n, m), seed=9, precision=tk.TK_PREC_MIXED, lsqr_tc=1)
+    res = tk.tk_solve(A, b, lams, o)
+    X = res.X.cpu().numpy()
+    o0 = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=min(4 * n, m), seed=9, precision=tk.TK_PREC_MIXED)
+    res0 = tk.tk_solve(A, b, lams, o0)
+    Ad, bd = p.A.double().numpy(), p.b.numpy()
+    for i in sorted({0, N // 2, N - 1}):
+        xr = oracle.ref_ridge_qr(Ad, bd, float(lams[i]), refine=3)
+        assert rel(X[i], xr) < TOL_X, (lams[i], rel(X[i], xr), res.info[i])
+    # same inner accuracy as the float32 SIMT products: comparable iteration counts
+    it_tc = sum(q["iters"] for q in res.info)
+    it_simt = sum(q["iters"] for q in res0.info)
+    assert it_tc <= 1.3 * it_simt + 5, (it_tc, it_simt)
