@@ -102,10 +102,8 @@ class ClockSampler:
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2203_07329_gb300 import replicas
+    return replicas.env()
 
 
 # ------------------------------------------------------------ oracle arm ---
@@ -193,10 +191,11 @@ def main():
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    from paper_2203_07329_gb300 import replicas
+    dev = torch.device("cuda", local)
+
     def barrier():
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+        replicas.barrier(dev)
 
     from paper_2203_07329_gb300 import build, datagen
     build.build()
@@ -241,12 +240,8 @@ def main():
     prof = tk.tk_profile_collect()
     tk.tk_profile_enable(False)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * N / (ms / 1e3)
+    ms = replicas.max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev)
+    value = replicas.job_throughput(N, ms, ws)
     X_mixed = X.clone()
     info_mixed = res.info
 
@@ -267,7 +262,7 @@ def main():
         X_host.copy_(X, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     del A_dev, A_host
 
     # ---- the mixed solve with the LSQR products on the tensor cores (one step)

@@ -151,7 +151,8 @@ def test_uneven_256_problems_full_size(tk):
         X = Xs[k].cpu().numpy()
         for i in (0, lams.shape[1] - 1):
             lam = float(lams[k, i])
-            xr = refine_reference(A64, b, lam, U, V, sig, steps=4)
+            # float32 factors: the double-double refinement contracts by ~1e-7/lambda per step
+            xr = refine_reference(A64, b, lam, U, V, sig, steps=10)
             err = np.linalg.norm(X[i] - xr) / np.linalg.norm(xr)
             print(f"problem {k} m={A64.shape[0]} n={A64.shape[1]} lowrank={p.meta['lowrank']} "
                   f"lambda={lam:.1e} rel.err={err:.2e}")
