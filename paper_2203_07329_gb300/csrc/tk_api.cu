@@ -122,7 +122,8 @@ struct Bufs {
   double* A64 = nullptr;
   double* C = nullptr;
   double* R = nullptr;
-  float* R32 = nullptr;
+  float* Minv = nullptr;   // mixed: R^-1 in float32 (N x np x np)
+  float* Mtinv = nullptr;  // mixed: R^-T in float32
   double* sig = nullptr;
   double* lrV = nullptr;
   double* lrS = nullptr;
@@ -168,7 +169,10 @@ void carve(const Plan& P, Arena& a, Bufs& B) {
   if (!P.lowrank) {
     B.C = a.take<double>((size_t)P.c * P.c);
     B.R = a.take<double>((size_t)N * P.np * P.np);
-    if (P.mixed) B.R32 = a.take<float>((size_t)N * P.np * P.np);
+    if (P.mixed) {
+      B.Minv = a.take<float>((size_t)N * P.np * P.np);
+      B.Mtinv = a.take<float>((size_t)N * P.np * P.np);
+    }
   } else {
     B.sig = a.take<double>((size_t)P.s);
     B.lrV = a.take<double>((size_t)P.c * P.s);
@@ -390,8 +394,10 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       else ok_ids.push_back(i);
     }
     if (P.mixed) {
-      k_f64_to_f32_flat<<<gsz((int64_t)N * P.np * P.np), 256, 0, st>>>(B.R, B.R32, (int64_t)N * P.np * P.np);
-      TK_LAUNCH_CHECK();
+      // the float32 LSQR applies R^-1 and R^-T as explicit float32 matrices
+      tok = prof_begin(TK_PHASE_TRINV, st);
+      TK_TRY(tri_inverse_f32(B.R, P.c, P.np, P.np * P.np, N, B.Minv, B.Mtinv, st));
+      prof_end(tok, st, (double)N * P.c * P.c * P.c / 3.0, 4.0 * N * P.np * P.np * 3.0);
     }
   } else {
     Arena sa;
@@ -457,7 +463,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       e.tc = false;  // unaligned base address: SIMT float32 products
     }
     if (!P.lowrank) {
-      e.prec_kind = TK_PRECOND_CHOL; e.R = B.R32; e.ldr = P.np; e.rstride = P.np * P.np;
+      e.prec_kind = TK_PRECOND_CHOL; e.Mi = B.Minv; e.Mti = B.Mtinv; e.ldm = P.np; e.mstride = P.np * P.np;
     } else {
       e.prec_kind = TK_PRECOND_LOWRANK; e.lrV = B.lrV32; e.lrS = B.lrS32;
     }

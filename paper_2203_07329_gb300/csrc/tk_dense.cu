@@ -501,6 +501,175 @@ __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ R, int
     }
 }
 
+// ------------------------------------------- triangular inverse (FP32) ---
+// M = R^-1 of the upper triangular factors, built in float32 as an explicit
+// preconditioner for the float32 LSQR of the mixed form: every application
+// of R^-1 or R^-T is then one batched triangular matrix-vector product
+// (HBM-bound, one launch) instead of a substitution (a chain of dependent
+// launches).  Blocks of 64 rows are finished from the bottom: R M = I gives
+// M_ii = R_ii^-1 (float64, in shared memory) and, for c > i,
+// M_ic = M_ii S_ic with S_ic = -sum_{i<k<=c} R_ik M_kc, accumulated
+// right-looking in the not yet finished blocks of M (zero on entry).  Mt
+// receives M^T (its blocks above the diagonal are left unwritten).
+
+// M_kk = R_kk^-1: thread c back-substitutes column c of the identity.
+__global__ void __launch_bounds__(CB) k_tinv_diag(const double* __restrict__ R, int64_t ldr, int64_t rstride,
+                                                  float* __restrict__ M, float* __restrict__ Mt, int64_t ldm,
+                                                  int64_t mstride) {
+  __shared__ double D[CB][CB + 1];
+  const int kb = blockIdx.x, l = blockIdx.y, c = threadIdx.x;
+  const double* Rg = R + (int64_t)l * rstride + (int64_t)kb * CB * ldr + (int64_t)kb * CB;
+  for (int i = 0; i < CB; ++i) D[i][c] = Rg[(int64_t)i * ldr + c];
+  __syncthreads();
+  double x[CB];
+#pragma unroll
+  for (int r = 0; r < CB; ++r) x[r] = (r == c) ? 1.0 : 0.0;
+#pragma unroll
+  for (int r = CB - 1; r >= 0; --r) {
+    x[r] = x[r] / D[r][r];
+#pragma unroll
+    for (int q = 0; q < r; ++q) x[q] = fma(-D[q][r], x[r], x[q]);
+  }
+  __syncthreads();
+  float* Mg = M + (int64_t)l * mstride + (int64_t)kb * CB * ldm + (int64_t)kb * CB;
+#pragma unroll
+  for (int r = 0; r < CB; ++r) {
+    Mg[(int64_t)r * ldm + c] = (float)x[r];
+    D[r][c] = x[r];
+  }
+  __syncthreads();
+  float* Mtg = Mt + (int64_t)l * mstride + (int64_t)kb * CB * ldm + (int64_t)kb * CB;
+  for (int i = 0; i < CB; ++i) Mtg[(int64_t)i * ldm + c] = (float)D[c][i];
+}
+
+// S_{rb,cb} -= R_{rb,k} M_{k,cb} for rb < k <= cb (float32; R read as float64).
+__global__ void __launch_bounds__(256) k_tinv_update(const double* __restrict__ R, int64_t ldr, int64_t rstride,
+                                                     float* __restrict__ M, int64_t ldm, int64_t mstride, int k,
+                                                     int nt) {
+  constexpr int KC = 32;
+  __shared__ float P[KC][CB + 4];  // P[kk][i] = R[rb*64 + i, k*64 + kc + kk]
+  __shared__ float Q[KC][CB];      // Q[kk][j] = M[k*64 + kc + kk, cb*64 + j]
+  const int l = blockIdx.y;
+  const int rb = blockIdx.x / (nt - k), cb = k + blockIdx.x % (nt - k);
+  const double* Pg = R + (int64_t)l * rstride + (int64_t)rb * CB * ldr + (int64_t)k * CB;
+  float* Ml = M + (int64_t)l * mstride;
+  const float* Qg = Ml + (int64_t)k * CB * ldm + (int64_t)cb * CB;
+  float* Sg = Ml + (int64_t)rb * CB * ldm + (int64_t)cb * CB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4] = {};
+  for (int kc = 0; kc < CB; kc += KC) {
+    for (int idx = threadIdx.x; idx < KC * CB; idx += blockDim.x) {
+      const int i = idx / KC, kk = idx % KC;
+      P[kk][i] = (float)Pg[(int64_t)i * ldr + kc + kk];
+      const int q = idx / CB, j = idx % CB;
+      Q[q][j] = Qg[(int64_t)(kc + q) * ldm + j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      float pa[4], qb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) pa[a] = P[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) qb[b] = Q[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], qb[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) Sg[(int64_t)(ty + 16 * a) * ldm + tx + 16 * b] -= acc[a][b];
+}
+
+// M_{i,cb} = M_{i,i} S_{i,cb} for cb > i, and Mt_{cb,i} = M_{i,cb}^T.
+__global__ void __launch_bounds__(256) k_tinv_final(float* __restrict__ M, float* __restrict__ Mt, int64_t ldm,
+                                                    int64_t mstride, int i) {
+  __shared__ float D[CB][CB + 1];
+  __shared__ float S[CB][CB + 1];
+  const int l = blockIdx.y, cb = i + 1 + blockIdx.x;
+  float* Ml = M + (int64_t)l * mstride;
+  const float* Dg = Ml + (int64_t)i * CB * ldm + (int64_t)i * CB;
+  float* Sg = Ml + (int64_t)i * CB * ldm + (int64_t)cb * CB;
+  for (int idx = threadIdx.x; idx < CB * CB; idx += blockDim.x) {
+    const int r = idx / CB, c = idx % CB;
+    D[r][c] = Dg[(int64_t)r * ldm + c];
+    S[r][c] = Sg[(int64_t)r * ldm + c];
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4] = {};
+#pragma unroll 8
+  for (int kk = 0; kk < CB; ++kk) {
+    float da[4], sb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) da[a] = D[ty + 16 * a][kk];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sb[b] = S[kk][tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(da[a], sb[b], acc[a][b]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      Sg[(int64_t)(ty + 16 * a) * ldm + tx + 16 * b] = acc[a][b];
+      S[ty + 16 * a][tx + 16 * b] = acc[a][b];
+    }
+  __syncthreads();
+  float* Mtg = Mt + (int64_t)l * mstride + (int64_t)cb * CB * ldm + (int64_t)i * CB;
+  for (int idx = threadIdx.x; idx < CB * CB; idx += blockDim.x) {
+    const int r = idx / CB, c = idx % CB;
+    Mtg[(int64_t)r * ldm + c] = S[c][r];
+  }
+}
+
+// ------------------------------------------------------------------ TRMV --
+constexpr int kTrmvRows = 64;  // rows per CTA (8 warps x 8 rows)
+
+// out_k = M_l in_k for slot k (l = idx[k]): UPPER reads row i over columns
+// i..n-1 of M, otherwise (M = Mt, lower) over columns 0..i.  The slot's vector
+// sits in shared memory, zero past n; the rows are read as float4 (ldm and
+// mstride are multiples of 64 and the bases 256-byte aligned), starting at the
+// float4 that holds column i (upper) or ending at it (lower): the extra
+// entries lie in the diagonal block, where that triangle is stored as zeros.
+template <bool UPPER>
+__global__ void __launch_bounds__(256) k_trmv(int64_t n, const float* __restrict__ M, int64_t ldm, int64_t mstride,
+                                              const int* __restrict__ idx, const float* in, float* out, int64_t ldx) {
+  extern __shared__ float4 v4[];
+  float* v = reinterpret_cast<float*>(v4);
+  const int slot = blockIdx.y;
+  const float* Ml = M + (int64_t)(idx ? idx[slot] : slot) * mstride;
+  const float* x = in + (int64_t)slot * ldx;
+  const int64_t n4 = cdiv(n, 4);
+  for (int64_t j = threadIdx.x; j < 4 * n4; j += blockDim.x) v[j] = j < n ? x[j] : 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int q = 0; q < kTrmvRows / 8; ++q) {
+    const int64_t i = (int64_t)blockIdx.x * kTrmvRows + w + 8 * q;
+    if (i >= n) break;
+    const float4* row = reinterpret_cast<const float4*>(Ml + i * ldm);
+    const int64_t j0 = UPPER ? (i >> 2) : 0, j1 = UPPER ? n4 : (i >> 2) + 1;
+    float acc = 0.f;
+#pragma unroll 4
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
+      const float4 a = __ldg(row + j), b = v4[j];
+      acc = fmaf(a.x, b.x, acc);
+      acc = fmaf(a.y, b.y, acc);
+      acc = fmaf(a.z, b.z, acc);
+      acc = fmaf(a.w, b.w, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[(int64_t)slot * ldx + i] = acc;
+  }
+}
+
 // ------------------------------------------------------------------ TRSV --
 constexpr int kTrsvThreads = 256;
 
@@ -758,6 +927,35 @@ template tk_status gemm_splitk<float, double>(bool, bool, int64_t, int64_t, int6
                                               const double*, int64_t, double*, int, cudaStream_t);
 template tk_status gemm_splitk<double, float>(bool, bool, int64_t, int64_t, int64_t, const double*, int64_t,
                                               const float*, int64_t, double*, int, cudaStream_t);
+
+tk_status tri_inverse_f32(const double* R, int64_t n, int64_t ldr, int64_t rstride, int N, float* M, float* Mt,
+                          cudaStream_t st) {
+  if (N == 0 || n == 0) return TK_OK;
+  const int64_t np = cdiv(n, CB) * CB;
+  const int nt = (int)(np / CB);
+  TK_CUDA(cudaMemsetAsync(M, 0, sizeof(float) * (size_t)N * np * np, st));
+  k_tinv_diag<<<dim3((unsigned)nt, (unsigned)N), CB, 0, st>>>(R, ldr, rstride, M, Mt, np, np * np);
+  TK_LAUNCH_CHECK();
+  for (int k = nt - 1; k >= 1; --k) {
+    k_tinv_update<<<dim3((unsigned)(k * (nt - k)), (unsigned)N), 256, 0, st>>>(R, ldr, rstride, M, np, np * np, k,
+                                                                              nt);
+    TK_LAUNCH_CHECK();
+    k_tinv_final<<<dim3((unsigned)(nt - k), (unsigned)N), 256, 0, st>>>(M, Mt, np, np * np, k - 1);
+    TK_LAUNCH_CHECK();
+  }
+  return TK_OK;
+}
+
+tk_status trmv_batched(bool transposed, int64_t n, const float* M, const float* Mt, int64_t ldm, int64_t mstride,
+                       const int* idx, const float* in, float* out, int64_t ldx, int count, cudaStream_t st) {
+  if (count == 0 || n == 0) return TK_OK;
+  const dim3 grid((unsigned)cdiv(n, kTrmvRows), (unsigned)count);
+  const size_t smem = sizeof(float) * 4 * (size_t)cdiv(n, 4);
+  if (!transposed) k_trmv<true><<<grid, 256, smem, st>>>(n, M, ldm, mstride, idx, in, out, ldx);
+  else k_trmv<false><<<grid, 256, smem, st>>>(n, Mt, ldm, mstride, idx, in, out, ldx);
+  TK_LAUNCH_CHECK();
+  return TK_OK;
+}
 
 size_t chol_workspace(int64_t n, int N) {
   Arena a;

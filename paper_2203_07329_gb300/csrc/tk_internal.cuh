@@ -183,6 +183,16 @@ size_t chol_workspace(int64_t n, int N);
 tk_status chol_shifted(const double* C, int64_t n, const double* lambdas_dev, int N, double* R, int64_t ldr,
                        int64_t rstride, int* info_dev, Arena& ar, cudaStream_t st);
 
+// M = R^-1 (upper) and Mt = M^T (lower) in float32 for N factors R (float64,
+// padded order np = ceil(n/64)*64, row stride ldr, matrix stride rstride);
+// M and Mt: N x np x np, row stride np.
+tk_status tri_inverse_f32(const double* R, int64_t n, int64_t ldr, int64_t rstride, int N, float* M, float* Mt,
+                          cudaStream_t st);
+// out_k = M_l in_k (or Mt_l in_k when transposed) for slots k < count,
+// l = idx[k] (idx null: l = k); in/out vectors of length n at stride ldx.
+tk_status trmv_batched(bool transposed, int64_t n, const float* M, const float* Mt, int64_t ldm, int64_t mstride,
+                       const int* idx, const float* in, float* out, int64_t ldx, int count, cudaStream_t st);
+
 // Batched triangular solves on slots: vector of slot j is X + j*ldx (length
 // n); its factor is R + idx[j]*rstride (row stride ldr, upper triangular).
 // pbuf (float64, count x n) enables the grid-wide column sweep for n > 512;
