@@ -167,6 +167,80 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------- GPU arm ---
+def small_workload_step(tk, datagen, stream, barrier, reps=20):
+    """The 4096 x 256 float64 workload (8 lambda, Gaussian sketch s = 1024): it
+    fits in L2, so the figure of merit is microseconds per lambda-solve."""
+    import torch
+    prob, w = datagen.workload_problem("ridge_over_4096x256_f64", device="cuda")
+    lams = prob.lambdas.numpy()
+    out = {}
+    for key, prec in (("fp64", tk.TK_PREC_FP64), ("mixed", tk.TK_PREC_MIXED)):
+        o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=w["s"], seed=1, precision=prec)
+        work = torch.empty(tk.workspace_size(tk.make_problem(prob.A, prob.b), len(lams), o), dtype=torch.uint8,
+                           device="cuda")
+        X = torch.empty((len(lams), prob.A.shape[1]), dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            tk.tk_solve(prob.A, prob.b, lams, o, work=work, X=X, stream=stream)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = tk.tk_launch_count()
+        e0.record(stream)
+        for _ in range(reps):
+            r = tk.tk_solve(prob.A, prob.b, lams, o, work=work, X=X, stream=stream)
+        e1.record(stream)
+        barrier()
+        t = e0.elapsed_time(e1) / reps
+        out[key] = {"us_per_lambda_solve": t * 1e3 / len(lams), "ms_per_solve_call": t,
+                    "launches_per_call": (tk.tk_launch_count() - l0) / reps,
+                    "iters_mean": float(np.mean([q["iters"] for q in r.info]))}
+    return out
+
+
+def uneven_batch_step(tk, datagen, stream, barrier):
+    """256 problems, m in [2000, 65536], n in [64, 1024], float32, 16 lambda each;
+    odd problems have a small statistical dimension and take the low-rank
+    preconditioner (sketch size 2 sd), the others the Cholesky one (s = 4n)."""
+    import math
+    import torch
+    probs = datagen.uneven_batch(256, device="cuda", dtype=torch.float32)
+    pairs, opts = [], []
+    for p in probs:
+        n = p.A.shape[1]
+        lam_min = float(p.lambdas.min())
+        if p.meta["lowrank"]:
+            sd = float(np.sum(1.0 / (1.0 + lam_min / (p.sigma.numpy() ** 2))))
+            opts.append(tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=min(n, 2 * math.ceil(sd)), seed=1,
+                                        precond=tk.TK_PRECOND_LOWRANK, alpha=2.0, precision=tk.TK_PREC_MIXED))
+        else:
+            opts.append(tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=min(4 * n, p.A.shape[0]), seed=1,
+                                        precision=tk.TK_PREC_MIXED))
+        pairs.append((p.A, p.b))
+    lams = np.stack([p.lambdas.numpy() for p in probs])
+    need = tk.workspace_size_batched(pairs, lams.shape[1], opts)
+    work = torch.empty(need, dtype=torch.uint8, device="cuda")
+    tk.tk_solve_batched(pairs, lams, opts, work=work, stream=stream)  # warm-up
+    barrier()
+    tk.tk_profile_enable(True)
+    tk.tk_profile_collect()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, infos, _ = tk.tk_solve_batched(pairs, lams, opts, work=work, stream=stream)
+    e1.record(stream)
+    barrier()
+    prof = tk.tk_profile_collect()
+    tk.tk_profile_enable(False)
+    t = e0.elapsed_time(e1)
+    solves = int(lams.size)
+    a_bytes = sum(A.numel() * A.element_size() for A, _ in pairs)
+    stream_ms = sum(prof[k]["ms"] for k in ("A_times_W", "At_times_U", "refine_residual64", "refine_normal64"))
+    stream_bytes = sum(prof[k]["bytes"] for k in ("A_times_W", "At_times_U", "refine_residual64", "refine_normal64"))
+    return {"value": solves / (t / 1e3), "unit": "lambda-solves/s", "ms_per_step": t, "problems": len(pairs),
+            "lambda_solves": solves, "a_bytes": a_bytes,
+            "a_stream_gbs_summed_phases": stream_bytes / (stream_ms / 1e3) / 1e9 if stream_ms > 0 else None,
+            "iters_mean": float(np.mean([q["iters"] for inf in infos for q in inf])),
+            "phase_ms_summed_over_lanes": {k: v["ms"] for k, v in prof.items() if v["launches"]}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -178,6 +252,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core LSQR comparison step")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the 256 uneven problems batch")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="where the synthetic problem is generated (cpu for profiler runs)")
     args = ap.parse_args()
@@ -313,6 +388,13 @@ def main():
                 extra["max_rel_diff_mixed_vs_fp64"] = float(d.max())
         extra["speedup_mixed_vs_fp64_one_at_a_time"] = value / ws / extra["fp64_one_at_a_time"]["value"]
         extra["speedup_mixed_vs_fp64_batched"] = value / ws / extra["fp64_batched"]["value"]
+
+    # ---- the small 4096 x 256 workload (fits in L2: launch/latency-bound)
+    extra["small_4096x256_f64"] = small_workload_step(tk, datagen, stream, barrier)
+
+    # ---- many independent problems of uneven size in one batched call (one step)
+    if not args.no_uneven:
+        extra["uneven_256_mixed"] = uneven_batch_step(tk, datagen, stream, barrier)
 
     # ---- roofline of the dominant phase (live events over the timed region)
     peaks, peak_src = load_peaks()

@@ -85,6 +85,10 @@ typedef struct {
   int lsqr_tc;            /* [0] MIXED: the two products with A of each LSQR step on the tensor cores
                              (tcgen05 kind::tf32, 3-term split = float32 accuracy; needs 16-byte aligned
                              rows of A and keeps a float32 copy of A^T); 0 = SIMT float32 */
+  int group;              /* [1] tk_solve_batched: when every problem is MIXED, m >= n, BATCHED, n <= 4096,
+                             N <= 64 and lsqr_tc = 0, the problems advance together in one grouped LSQR and
+                             refinement (one launch per phase for all problems); 0 in any problem's options =
+                             each problem solved on its own (host lanes) */
 } tk_opts;
 
 /* Per-lambda report. */

@@ -7,8 +7,10 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <utility>
 #include <vector>
 
+#include "tk_group.cuh"
 #include "tk_lsqr.cuh"
 
 namespace tk {
@@ -27,16 +29,6 @@ tk_status einval(const char* msg) {
   return TK_EINVAL;
 }
 
-int severity(tk_status s) {
-  switch (s) {
-    case TK_OK: return 0;
-    case TK_ENOCONV: return 1;
-    case TK_ENUMERIC: return 2;
-    case TK_ENOTSPD: return 3;
-    default: return 4;
-  }
-}
-tk_status worse(tk_status a, tk_status b) { return severity(b) > severity(a) ? b : a; }
 
 // ---------------------------------------------------------------- plan -----
 struct Plan {
@@ -50,6 +42,7 @@ struct Plan {
   tk_opts o{};
   bool mixed = false, lowrank = false;
   bool lsqr_tc = false;  // tensor-core float32 LSQR products
+  bool prep_only = false;  // grouped batch: build the preconditioner only
 };
 
 constexpr int64_t kMaxShort = 8192;
@@ -137,8 +130,10 @@ struct Bufs {
   double* Rres = nullptr;
   double* part = nullptr;
   double* nrm = nullptr;
-  char* scratch = nullptr;  // sketch / SVD scratch
+  char* scratch = nullptr;  // sketch scratch
   size_t scratch_bytes = 0;
+  char* svd = nullptr;      // SVD scratch (low rank)
+  size_t svd_bytes = 0;
   Lsqr<double> e64;
   Lsqr<float> e32;
   int splits = 1;
@@ -155,36 +150,46 @@ size_t sketch_scratch(const Plan& P) {
   return gauss_rows_workspace(P.L, P.c, dt, P.s);
 }
 
-void carve(const Plan& P, Arena& a, Bufs& B) {
+// `a` holds what the LSQR phase reads (lambda, A copies, the float32
+// preconditioner, the LSQR and refinement state), `t` what only the
+// preconditioner build needs (sketch, Gram, float64 factors, SVD); a single
+// solve passes the same arena twice.  prep_only (grouped batch) skips the
+// LSQR and refinement state, which the grouped engine owns.
+void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
   const int N = std::max(P.N, 1);
+  // grouped low-rank problems: the SVD runs later over all problems at once,
+  // so the sketch and the SVD buffers outlive the build
+  Arena& ty = (P.prep_only && P.lowrank) ? a : t;
   B.lam = a.take<double>(N);
   B.ids = a.take<int>(N);
   B.info = a.take<int>(N);
   B.ones = a.take<double>(N);
-  B.Y = a.take<double>((size_t)P.s * P.c);
-  if (P.under) B.AT = a.take<char>((size_t)P.m * P.n * (P.dt == TK_F64 ? 8 : 4));
+  B.Y = ty.take<double>((size_t)P.s * P.c);
+  if (P.under) B.AT = t.take<char>((size_t)P.m * P.n * (P.dt == TK_F64 ? 8 : 4));
   if (P.mixed && P.dt == TK_F64) B.A32 = a.take<float>((size_t)P.m * P.n);
   if (P.lsqr_tc) B.AT32 = a.take<float>((size_t)P.m * P.n);
   if (!P.mixed && P.dt == TK_F32) B.A64 = a.take<double>((size_t)P.m * P.n);
   if (!P.lowrank) {
-    B.C = a.take<double>((size_t)P.c * P.c);
-    B.R = a.take<double>((size_t)N * P.np * P.np);
+    B.C = t.take<double>((size_t)P.c * P.c);
+    B.R = (P.mixed ? t : a).take<double>((size_t)N * P.np * P.np);
     if (P.mixed) {
       B.Minv = a.take<float>((size_t)N * P.np * P.np);
       B.Mtinv = a.take<float>((size_t)N * P.np * P.np);
     }
   } else {
-    B.sig = a.take<double>((size_t)P.s);
-    B.lrV = a.take<double>((size_t)P.c * P.s);
-    B.lrS = a.take<double>((size_t)N * P.s);
-    B.ranks = a.take<int64_t>(N);
-    B.sd = a.take<double>(N);
+    B.sig = ty.take<double>((size_t)P.s);
+    B.lrV = (P.mixed ? ty : a).take<double>((size_t)P.c * P.s);
+    B.lrS = (P.mixed ? ty : a).take<double>((size_t)N * P.s);
+    B.ranks = ty.take<int64_t>(N);
+    B.sd = ty.take<double>(N);
+    B.svd_bytes = svd_workspace(P.s, P.c);
+    B.svd = ty.take<char>(B.svd_bytes);
     if (P.mixed) {
       B.lrV32 = a.take<float>((size_t)P.c * P.s);
       B.lrS32 = a.take<float>((size_t)N * P.s);
     }
   }
-  if (P.mixed) {
+  if (P.mixed && !P.prep_only) {
     B.splits = splitk_count(N, P.n, P.m);
     B.D = a.take<double>((size_t)N * P.n);
     B.Xa = a.take<double>((size_t)N * P.n);
@@ -193,10 +198,10 @@ void carve(const Plan& P, Arena& a, Bufs& B) {
     B.part = a.take<double>((size_t)B.splits * N * P.n);
     B.nrm = a.take<double>((size_t)3 * N);
   }
-  size_t sc = sketch_scratch(P);
-  if (P.lowrank) sc = std::max(sc, svd_workspace(P.s, P.c));
+  const size_t sc = sketch_scratch(P);
   B.scratch_bytes = sc;
-  B.scratch = a.take<char>(sc);
+  B.scratch = t.take<char>(sc);
+  if (P.prep_only) return;
   const int64_t lr_s = P.lowrank ? P.s : 0;
   if (P.mixed) {
     B.e32.m = P.m; B.e32.n = P.n; B.e32.N_cap = P.N_cap; B.e32.under = false; B.e32.lr_s = lr_s;
@@ -211,8 +216,15 @@ void carve(const Plan& P, Arena& a, Bufs& B) {
 size_t plan_bytes(const Plan& P) {
   Arena a;
   Bufs B;
-  carve(P, a, B);
+  carve(P, a, a, B);
   return a.used + 4096;
+}
+// the two parts of a prep_only plan: (kept for the LSQR phase, build scratch)
+std::pair<size_t, size_t> plan_bytes_split(const Plan& P) {
+  Arena a, t;
+  Bufs B;
+  carve(P, a, t, B);
+  return {a.used + 4096, t.used + 4096};
 }
 
 // ------------------------------------------------------- small kernels ----
@@ -307,27 +319,65 @@ tk_status do_sketch(const Plan& P, const void* A_sk, tk_dtype dt_sk, int64_t ld_
   return gauss_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
 }
 
+// ------------------------------------------------------ low rank ----------
+// Algorithm 3 steps 5 and 7 after the SVD of the sketch: sd_i and the ranks
+// s_i, the diagonals S_i, the float32 copies for the mixed form; every lambda
+// has a preconditioner.
+tk_status lowrank_finish(const LowRankParts& L, tk_info* inf, std::vector<int>& ok_ids, cudaStream_t st) {
+  TK_TRY(lowrank_ranks_dev(L.sig, L.s, L.lam, L.N, L.alpha, L.sd, L.ranks, st));
+  TK_TRY(lowrank_diag_dev<double>(L.sig, L.s, L.lam, L.ranks, L.N, L.lrS, st));
+  std::vector<int64_t> hr(L.N);
+  TK_CUDA(cudaMemcpyAsync(hr.data(), L.ranks, sizeof(int64_t) * L.N, cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  ok_ids.clear();
+  for (int i = 0; i < L.N; ++i) {
+    inf[i].rank = hr[i];
+    ok_ids.push_back(i);
+  }
+  if (L.lrV32) {
+    k_f64_to_f32_flat<<<gsz(L.c * L.s), 256, 0, st>>>(L.lrV, L.lrV32, L.c * L.s);
+    k_f64_to_f32_flat<<<gsz((int64_t)L.N * L.s), 256, 0, st>>>(L.lrS, L.lrS32, (int64_t)L.N * L.s);
+    TK_LAUNCH_CHECK();
+  }
+  return TK_OK;
+}
+
 // ------------------------------------------------------------ solve -------
+// With gp (grouped batch) only the preconditioner is built: `work` receives
+// what the grouped LSQR reads, `scratch` the build-only buffers, and gp the
+// pointers and the lambdas that have a preconditioner.
 tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk_opts* o, void* work,
-                     size_t work_bytes, cudaStream_t st, double* X, tk_info* info) {
+                     size_t work_bytes, cudaStream_t st, double* X, tk_info* info, GroupProblem* gp = nullptr,
+                     void* scratch = nullptr, size_t scratch_bytes = 0) {
   Plan P;
   TK_TRY(make_plan(p, N, o, P));
+  P.prep_only = gp != nullptr;
   if (N == 0) return TK_OK;
   if (!lambdas) return einval("lambdas pointer is NULL");
   for (int i = 0; i < N; ++i)
     if (!(lambdas[i] > 0.0) || !std::isfinite(lambdas[i])) return einval("every lambda must be a positive finite number");
   if (!p->A || !p->b || !X) return einval("A, b and X must be non-NULL");
-  const size_t need = plan_bytes(P);
-  if (!work || work_bytes < need) {
-    set_error_msg("workspace smaller than tk_workspace_size()");
-    return TK_ENOMEM;
-  }
   Arena a;
   a.base = (char*)work;
   a.cap = work_bytes;
+  Arena t;
+  t.base = (char*)scratch;
+  t.cap = scratch_bytes;
   Bufs B;
-  carve(P, a, B);
-  if (!a.ok()) return TK_ENOMEM;
+  if (!gp) {
+    const size_t need = plan_bytes(P);
+    if (!work || work_bytes < need) {
+      set_error_msg("workspace smaller than tk_workspace_size()");
+      return TK_ENOMEM;
+    }
+    carve(P, a, a, B);
+  } else {
+    carve(P, a, t, B);
+  }
+  if (!a.ok() || !t.ok()) {
+    set_error_msg("workspace smaller than the solve needs");
+    return TK_ENOMEM;
+  }
 
   std::vector<tk_info> inf(N);
   for (auto& x : inf) {
@@ -399,30 +449,53 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       TK_TRY(tri_inverse_f32(B.R, P.c, P.np, P.np * P.np, N, B.Minv, B.Mtinv, st));
       prof_end(tok, st, (double)N * P.c * P.c * P.c / 3.0, 4.0 * N * P.np * P.np * 3.0);
     }
-  } else {
+  } else if (!gp) {
     Arena sa;
-    sa.base = B.scratch;
-    sa.cap = B.scratch_bytes;
+    sa.base = B.svd;
+    sa.cap = B.svd_bytes;
     int sweeps = 0;
     int tok = prof_begin(TK_PHASE_SVD, st);
     TK_TRY(jacobi_svd(B.Y, P.s, P.c, B.sig, B.lrV, &sweeps, sa, st));
     prof_end(tok, st, 3.5 * sweeps * (double)P.s * P.s * P.c, 8.0 * P.s * P.c);
-    TK_TRY(lowrank_ranks_dev(B.sig, P.s, B.lam, N, P.o.alpha, B.sd, B.ranks, st));
-    TK_TRY(lowrank_diag_dev<double>(B.sig, P.s, B.lam, B.ranks, N, B.lrS, st));
-    std::vector<int64_t> hr(N);
-    TK_CUDA(cudaMemcpyAsync(hr.data(), B.ranks, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, st));
-    TK_CUDA(cudaStreamSynchronize(st));
-    for (int i = 0; i < N; ++i) {
-      inf[i].rank = hr[i];
-      ok_ids.push_back(i);
-    }
-    if (P.mixed) {
-      k_f64_to_f32_flat<<<gsz(P.c * P.s), 256, 0, st>>>(B.lrV, B.lrV32, P.c * P.s);
-      k_f64_to_f32_flat<<<gsz((int64_t)N * P.s), 256, 0, st>>>(B.lrS, B.lrS32, (int64_t)N * P.s);
-      TK_LAUNCH_CHECK();
-    }
+    LowRankParts L{P.s, P.c, N, P.o.alpha, B.lam, B.sig, B.sd, B.ranks, B.lrV, B.lrS,
+                   P.mixed ? B.lrV32 : nullptr, P.mixed ? B.lrS32 : nullptr};
+    TK_TRY(lowrank_finish(L, inf.data(), ok_ids, st));
   }
   TK_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)N * P.n, st));
+  if (gp) {
+    gp->m = P.m;
+    gp->n = P.n;
+    gp->A32 = A32;
+    gp->lda32 = lda32;
+    gp->Af = p->A;
+    gp->f64 = P.dt == TK_F64;
+    gp->ldaf = P.lda;
+    gp->b = p->b;
+    gp->lam = B.lam;
+    gp->X = X;
+    gp->lowrank = P.lowrank;
+    gp->Mi = B.Minv;
+    gp->Mti = B.Mtinv;
+    gp->np = P.np;
+    gp->lrV = B.lrV32;
+    gp->lrS = B.lrS32;
+    gp->lr_s = P.lowrank ? P.s : 0;
+    gp->inner_tol = P.o.inner_tol;
+    gp->maxiter = P.o.maxiter;
+    gp->max_refine = P.o.max_refine;
+    gp->refine_tol = P.o.refine_tol;
+    gp->ok_ids = ok_ids;
+    if (P.lowrank) {  // the SVD and the ranks follow over all problems at once
+      gp->lr_parts = LowRankParts{P.s, P.c, N, P.o.alpha, B.lam, B.sig, B.sd, B.ranks, B.lrV, B.lrS,
+                                  B.lrV32, B.lrS32};
+      gp->svd_Y = B.Y;
+      gp->svd_scratch = B.svd;
+      gp->svd_bytes = B.svd_bytes;
+    }
+    for (int i = 0; i < N; ++i) gp->inf[i] = inf[i];
+    TK_CUDA(cudaStreamSynchronize(st));  // the build scratch is reused by the lane's next problem
+    return TK_OK;
+  }
   const int nok = (int)ok_ids.size();
   if (nok > 0) TK_CUDA(cudaMemcpyAsync(B.ids, ok_ids.data(), sizeof(int) * nok, cudaMemcpyHostToDevice, st));
 
@@ -573,6 +646,7 @@ TK_API tk_status tk_opts_default(tk_opts* o) {
   o->seed = 1;
   o->schedule = TK_SCHED_BATCHED;
   o->lsqr_tc = 0;
+  o->group = 1;
   return TK_OK;
 }
 
@@ -606,27 +680,90 @@ TK_API tk_status tk_solve(const tk_problem* p, const double* lambdas, int N, con
 }
 
 // ---- many problems -------------------------------------------------------
-// Problems are spread over up to kLanes host threads; each lane owns a stream
-// (joined to the caller's stream by events) and a slice of the workspace, and
-// solves its problems one after another.  Small uneven problems are bound by
-// launch latency, so lanes overlap them on the GPU.
+// Two schedules.  Grouped (every problem mixed, overdetermined, batched,
+// n <= 4096, N <= 64, SIMT products, opts.group = 1): each problem's sketch
+// and preconditioner are built on host lanes (below), then ONE grouped LSQR
+// and refinement advances all problems together (tk_group.cu).  Otherwise
+// the problems are spread over up to kLanes host threads; each lane owns a
+// stream (joined to the caller's stream by events) and a slice of the
+// workspace, and solves its problems one after another.
 static constexpr int kLanes = 8;
 
 static int batched_lanes(int P) { return std::max(1, std::min(P, kLanes)); }
 
 static const tk_opts* opts_of(const tk_opts* o, int n_opts, int i) { return n_opts == 1 ? o : o + i; }
 
+namespace {
+struct BatchLayout {
+  bool grouped = false;
+  int lanes = 1;
+  size_t per = 0;                // lanes: slice per lane
+  std::vector<size_t> keep_off;  // grouped: what problem i keeps for the LSQR phase
+  std::vector<size_t> keep_len;
+  size_t scratch_off = 0, scratch_per = 0;  // grouped: build scratch per lane
+  size_t group_off = 0, group_len = 0;
+  size_t svd_off = 0, svd_len = 0;  // grouped SVD of the low-rank problems
+  size_t total = 0;
+};
+
+tk_status batch_layout(const tk_problem* ps, int P, int N, const tk_opts* o, int n_opts, BatchLayout& L) {
+  L = BatchLayout{};
+  L.lanes = batched_lanes(P);
+  std::vector<Plan> pl(P);
+  bool grouped = P >= 2 && N >= 1 && N <= kGroupMaxLambda && (int64_t)P * N <= 65535;  // slot lists index grid.y
+  for (int i = 0; i < P; ++i) {
+    TK_TRY(make_plan(&ps[i], N, opts_of(o, n_opts, i), pl[i]));
+    const Plan& q = pl[i];
+    grouped = grouped && q.mixed && !q.under && q.o.schedule == TK_SCHED_BATCHED && !q.lsqr_tc &&
+              q.n <= kGroupMaxN && q.o.group != 0;
+  }
+  L.grouped = grouped;
+  if (!grouped) {
+    for (int i = 0; i < P; ++i) L.per = std::max(L.per, (plan_bytes(pl[i]) + 255) & ~size_t(255));
+    L.total = L.per * (size_t)L.lanes;
+    return TK_OK;
+  }
+  size_t off = 0;
+  std::vector<GroupProblem> gp(P);
+  L.keep_off.resize(P);
+  L.keep_len.resize(P);
+  for (int i = 0; i < P; ++i) {
+    pl[i].prep_only = true;
+    const auto kb = plan_bytes_split(pl[i]);
+    L.keep_off[i] = off;
+    L.keep_len[i] = (kb.first + 255) & ~size_t(255);
+    off += L.keep_len[i];
+    L.scratch_per = std::max(L.scratch_per, (kb.second + 255) & ~size_t(255));
+    gp[i].m = pl[i].m;
+    gp[i].n = pl[i].n;
+  }
+  L.scratch_off = off;
+  off += L.scratch_per * (size_t)L.lanes;
+  L.group_off = off;
+  L.group_len = (group_workspace(gp, N) + 255) & ~size_t(255);
+  off += L.group_len;
+  std::vector<SvdJob> jobs;
+  for (int i = 0; i < P; ++i)
+    if (pl[i].lowrank) {
+      SvdJob j;
+      j.s = pl[i].s;
+      j.n = pl[i].c;
+      jobs.push_back(j);
+    }
+  L.svd_off = off;
+  L.svd_len = (svd_grouped_workspace(jobs) + 255) & ~size_t(255);
+  L.total = off + L.svd_len;
+  return TK_OK;
+}
+}  // namespace
+
 TK_API tk_status tk_workspace_size_batched(const tk_problem* ps, int P, int N, const tk_opts* o, int n_opts,
                                            size_t* bytes) {
   if (!bytes || P < 0 || (P > 0 && (!ps || !o)) || (n_opts != 1 && n_opts != P))
     return einval("bad batched arguments (n_opts must be 1 or P)");
-  size_t mx = 0;
-  for (int i = 0; i < P; ++i) {
-    size_t b = 0;
-    TK_TRY(tk_workspace_size(&ps[i], N, opts_of(o, n_opts, i), &b));
-    mx = std::max(mx, (b + 255) & ~size_t(255));
-  }
-  *bytes = mx * (size_t)batched_lanes(P);
+  BatchLayout L;
+  TK_TRY(batch_layout(ps, P, N, o, n_opts, L));
+  *bytes = L.total;
   return TK_OK;
 }
 
@@ -636,14 +773,10 @@ TK_API tk_status tk_solve_batched(const tk_problem* ps, int P, const double* lam
   if (P < 0 || (P > 0 && (!ps || !lambdas || !X || !o)) || (n_opts != 1 && n_opts != P))
     return einval("bad batched arguments (n_opts must be 1 or P)");
   if (P == 0) return TK_OK;
-  size_t per = 0;
-  for (int i = 0; i < P; ++i) {
-    Plan pl;
-    TK_TRY(make_plan(&ps[i], N, opts_of(o, n_opts, i), pl));
-    per = std::max(per, (plan_bytes(pl) + 255) & ~size_t(255));
-  }
-  const int lanes = batched_lanes(P);
-  if (!work || work_bytes < per * lanes) {
+  BatchLayout Ly;
+  TK_TRY(batch_layout(ps, P, N, o, n_opts, Ly));
+  const int lanes = Ly.lanes;
+  if (!work || work_bytes < Ly.total) {
     set_error_msg("workspace smaller than tk_workspace_size_batched()");
     return TK_ENOMEM;
   }
@@ -659,14 +792,23 @@ TK_API tk_status tk_solve_batched(const tk_problem* ps, int P, const double* lam
     TK_CUDA(cudaEventCreateWithFlags(&ev_out[l], cudaEventDisableTiming));
     TK_CUDA(cudaStreamWaitEvent(ls[l], ev_in, 0));
   }
+  std::vector<tk_info> own_info(info ? 0 : (size_t)P * N);
+  tk_info* infos = info ? info : own_info.data();
+  std::vector<GroupProblem> gps(Ly.grouped ? P : 0);
+  for (int i = 0; i < (int)gps.size(); ++i) gps[i].inf = infos + (size_t)i * N;
   std::vector<tk_status> st(P, TK_OK);
   std::vector<std::string> err(lanes);
   auto lane_fn = [&](int l) {
     cudaSetDevice(dev);
-    char* base = (char*)work + per * (size_t)l;
     for (int i = l; i < P; i += lanes) {
-      st[i] = solve_impl(&ps[i], lambdas + (size_t)i * N, N, opts_of(o, n_opts, i), base, per, ls[l], X[i],
-                         info ? info + (size_t)i * N : nullptr);
+      if (Ly.grouped) {
+        st[i] = solve_impl(&ps[i], lambdas + (size_t)i * N, N, opts_of(o, n_opts, i), (char*)work + Ly.keep_off[i],
+                           Ly.keep_len[i], ls[l], X[i], nullptr, &gps[i],
+                           (char*)work + Ly.scratch_off + Ly.scratch_per * (size_t)l, Ly.scratch_per);
+      } else {
+        st[i] = solve_impl(&ps[i], lambdas + (size_t)i * N, N, opts_of(o, n_opts, i),
+                           (char*)work + Ly.per * (size_t)l, Ly.per, ls[l], X[i], infos + (size_t)i * N);
+      }
       if (st[i] == TK_EINVAL || st[i] == TK_ENOMEM || st[i] == TK_ECUDA) {
         err[l] = tk::g_err;
         break;
@@ -679,20 +821,65 @@ TK_API tk_status tk_solve_batched(const tk_problem* ps, int P, const double* lam
   lane_fn(0);
   for (auto& t : th) t.join();
   tk_status worst = TK_OK;
+  bool hard = false;
   for (int l = 0; l < lanes; ++l) {
     cudaStreamWaitEvent(cs, ev_out[l], 0);
     if (!err[l].empty()) set_error_msg(err[l].c_str());
   }
   for (int i = 0; i < P; ++i) {
-    if (st[i] == TK_EINVAL || st[i] == TK_ENOMEM || st[i] == TK_ECUDA) worst = st[i];
-    else if (worst != TK_EINVAL && worst != TK_ENOMEM && worst != TK_ECUDA) worst = worse(worst, st[i]);
+    if (st[i] == TK_EINVAL || st[i] == TK_ENOMEM || st[i] == TK_ECUDA) {
+      worst = st[i];
+      hard = true;
+    } else if (!hard) {
+      worst = worse(worst, st[i]);
+    }
   }
-  TK_CUDA(cudaStreamSynchronize(cs));
+  if (Ly.grouped && !hard) {
+    // the low-rank problems' SVDs together (one launch per Jacobi round), then
+    // their ranks and diagonals
+    std::vector<SvdJob> jobs;
+    std::vector<int> jp;
+    for (int i = 0; i < P; ++i)
+      if (gps[i].lowrank) {
+        SvdJob j;
+        j.Y = gps[i].svd_Y;
+        j.s = gps[i].lr_parts.s;
+        j.n = gps[i].lr_parts.c;
+        j.sigma = gps[i].lr_parts.sig;
+        j.V = gps[i].lr_parts.lrV;
+        j.scratch = gps[i].svd_scratch;
+        j.scratch_bytes = gps[i].svd_bytes;
+        jobs.push_back(j);
+        jp.push_back(i);
+      }
+    tk_status g = TK_OK;
+    if (!jobs.empty()) {
+      const int tok = prof_begin(TK_PHASE_SVD, cs);
+      g = jacobi_svd_grouped(jobs, (char*)work + Ly.svd_off, Ly.svd_len, cs);
+      double fl = 0.0;
+      for (const auto& j : jobs) fl += 3.5 * j.sweeps * (double)j.s * j.s * j.n;
+      prof_end(tok, cs, fl, 0.0);
+      for (size_t k = 0; k < jp.size() && g == TK_OK; ++k)
+        g = lowrank_finish(gps[jp[k]].lr_parts, gps[jp[k]].inf, gps[jp[k]].ok_ids, cs);
+    }
+    // every problem's preconditioner is built: all of them iterate together
+    if (g == TK_OK) g = group_solve_mixed(gps, N, (char*)work + Ly.group_off, Ly.group_len, cs);
+    if (g != TK_OK) {
+      worst = g;
+    } else {
+      for (size_t k = 0; k < (size_t)P * N; ++k) worst = worse(worst, infos[k].status);
+    }
+  }
+  const cudaError_t sync = cudaStreamSynchronize(cs);
   for (int l = 0; l < lanes; ++l) {
     cudaStreamDestroy(ls[l]);
     cudaEventDestroy(ev_out[l]);
   }
   cudaEventDestroy(ev_in);
+  if (sync != cudaSuccess) {
+    tk::set_error(sync, __FILE__, __LINE__);
+    return TK_ECUDA;
+  }
   return worst;
 }
 

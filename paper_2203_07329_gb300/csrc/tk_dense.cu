@@ -11,255 +11,47 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "tk_gemm_tiles.cuh"
 #include "tk_internal.cuh"
 
 namespace tk {
 namespace {
 
-template <typename A, typename B>
-struct AccOf { using type = double; };
-template <>
-struct AccOf<float, float> { using type = float; };
+using tiles::AccOf;
 
 // C = alpha op(A) op(B) [+ beta_row[i] * Cin]     or, with `partial`, the raw
-// split-K partial sum of K-range blockIdx.z into partial + z * M * N.
-// op(A) is M x K: A[i*lda + k] (N) or A[k*lda + i] (T).  op(B) is K x N:
-// B[k*ldb + j] (N) or B[j*ldb + k] (T).
+// split-K partial sum of K-range blockIdx.z into partial + z * M * N
+// (tile body: tiles::gemm_tile).
 template <typename TA, typename TB, typename TC, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     k_gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* __restrict__ A, int64_t lda,
            const TB* __restrict__ B, int64_t ldb, TC* C, int64_t ldc, double alpha,
            const double* __restrict__ beta_row, const TC* Cin, int64_t ldcin, int64_t k_per_split,
            double* __restrict__ partial, bool upper_only) {
-  using Acc = typename AccOf<TA, TB>::type;
-  constexpr int NT = (BM / TM) * (BN / TN);
-  __shared__ Acc As[BK][BM + 1];
-  __shared__ Acc Bs[BK][BN + 1];
-  const int tid = threadIdx.x;
-  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  __shared__ tiles::GemmSmem<TA, TB, BM, BN, BK> sm;
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
   // symmetric results (the Gram matrix): tiles strictly below the diagonal are skipped
   if (upper_only && m0 > n0 + BN - 1) return;
   const int64_t kbeg = (int64_t)blockIdx.z * k_per_split;
   const int64_t kend = std::min(K, kbeg + k_per_split);
-  Acc acc[TM][TN];
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = Acc(0);
-
-  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-    // A tile: BM x BK; the fastest thread index walks the contiguous axis.
-    for (int idx = tid; idx < BM * BK; idx += NT) {
-      int i, k;
-      if (!transA) { k = idx % BK; i = idx / BK; } else { i = idx % BM; k = idx / BM; }
-      int64_t gi = m0 + i, gk = k0 + k;
-      Acc v = Acc(0);
-      if (gi < M && gk < kend) v = (Acc)(transA ? A[gk * lda + gi] : A[gi * lda + gk]);
-      As[k][i] = v;
-    }
-    for (int idx = tid; idx < BK * BN; idx += NT) {
-      int j, k;
-      if (!transB) { j = idx % BN; k = idx / BN; } else { k = idx % BK; j = idx / BK; }
-      int64_t gj = n0 + j, gk = k0 + k;
-      Acc v = Acc(0);
-      if (gj < N && gk < kend) v = (Acc)(transB ? B[gj * ldb + gk] : B[gk * ldb + gj]);
-      Bs[k][j] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      Acc a[TM], b[TN];
-#pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
-#pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < TM; ++i) {
-    int64_t r = m0 + ty * TM + i;
-    if (r >= M) continue;
-#pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      int64_t c = n0 + tx * TN + j;
-      if (c >= N) continue;
-      if (partial) {
-        partial[(int64_t)blockIdx.z * M * N + r * N + c] = (double)acc[i][j];
-      } else {
-        double v = alpha * (double)acc[i][j];
-        if (beta_row) v += beta_row[r] * (double)Cin[r * ldcin + c];
-        C[r * ldc + c] = (TC)v;
-      }
-    }
-  }
+  tiles::gemm_tile<TA, TB, TC, BM, BN, BK, TM, TN>(sm, transA, transB, M, N, A, lda, B, ldb, C, ldc, alpha, beta_row,
+                                                   Cin, ldcin, m0, n0, kbeg, kend,
+                                                   partial ? partial + (int64_t)blockIdx.z * M * N : nullptr);
 }
 
-// GEMM for the lambda-major shapes of LSQR: C (M x N) = L (M x K) op(A) with
-// M <= BM (every active lambda in one tile) and a long N.  op(A)[k][j] is
-// A[j*lda + k] (TRANSB: the product with A^T, N = rows of A) or A[k*lda + j].
-// Warps are arranged 2 x 4 over the tile and lanes 4 x 8 inside a warp, so a
-// warp's shared-memory reads of L touch 4 rows (broadcast) and of B 8 column
-// groups; every thread keeps TM x TN accumulators.  The next K-slab is loaded
-// into registers (16-byte loads when VEC) while the current one is consumed
-// from shared memory (two buffers, one barrier per slab).
-template <typename T, bool TRANSB, bool VEC, int BM, int BN, int TM, int TN>
+// Lambda-major float32 products of LSQR (tile body: tiles::gemm_lm_tile): one
+// column tile of 256 per blockIdx.x, K split blockIdx.y.
+template <bool TRANSB, int BM, int TM>
 __global__ void __launch_bounds__(256)
-    k_gemm_lm(int64_t M, int64_t N, int64_t K, const T* __restrict__ L, int64_t ldl, const T* __restrict__ A,
-              int64_t lda, T* C, int64_t ldc, const double* __restrict__ beta_row, const T* Cin, int64_t ldcin,
-              int64_t k_per_split, double* __restrict__ partial) {
-  constexpr int BK = 16;
-  constexpr int LV = (BM * BK) / (4 * 256) > 0 ? (BM * BK) / (4 * 256) : 1;  // float4 per thread for L
-  constexpr int BV = (BN * BK) / (4 * 256);                                 // float4 per thread for B
-  static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
-  static_assert(BM / TM == 8 && BN / TN == 32, "2 x 4 warps of 4 x 8 lanes");
-  static_assert(sizeof(T) == 4, "float path");
-  static_assert(TN == 8 && BN == 256, "column pairs 64 j2 + 2 tx");
-  __shared__ __align__(16) T Ls[2][BK][BM];
-  __shared__ __align__(16) T Bs[2][BK][BN + 4];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int ty = (w >> 2) * 4 + (lane >> 3);  // 0..7  row group
-  const int tx = (w & 3) * 8 + (lane & 7);    // 0..31 column group
-  const int64_t n0 = (int64_t)blockIdx.x * BN;
+    k_gemm_lm(bool vec, int64_t M, int64_t N, int64_t K, const float* __restrict__ L, int64_t ldl,
+              const float* __restrict__ A, int64_t lda, float* C, int64_t ldc, const double* __restrict__ beta_row,
+              const float* Cin, int64_t ldcin, int64_t k_per_split, double* __restrict__ partial) {
+  __shared__ __align__(16) tiles::LmSmem<BM> sm;
+  const int64_t n0 = (int64_t)blockIdx.x * tiles::LM_BN;
   const int64_t kbeg = (int64_t)blockIdx.y * k_per_split;
   const int64_t kend = std::min(K, kbeg + k_per_split);
-  T acc[TM][TN];
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
-
-  float4 rl[LV], rb[BV];
-  // quad q of L: row i = q / (BK/4), k = 4 * (q % (BK/4)); of B (TRANSB): row j = q / 4, k = 4 * (q % 4);
-  // of B (not TRANSB): k = q / (BN/4), j = 4 * (q % (BN/4))
-  auto load = [&](int64_t k0) {
-#pragma unroll
-    for (int v = 0; v < LV; ++v) {
-      const int q = tid + v * 256;
-      const int i = q / (BK / 4), k = 4 * (q % (BK / 4));
-      float e[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) e[t] = 0.f;
-      if (q < BM * BK / 4 && i < M) {
-        const int64_t gk = k0 + k;
-        if (VEC && gk + 3 < kend) {
-          const float4 f = *reinterpret_cast<const float4*>(L + (int64_t)i * ldl + gk);
-          e[0] = f.x; e[1] = f.y; e[2] = f.z; e[3] = f.w;
-        } else {
-#pragma unroll
-          for (int t = 0; t < 4; ++t) e[t] = (gk + t < kend) ? L[(int64_t)i * ldl + gk + t] : 0.f;
-        }
-      }
-      rl[v] = make_float4(e[0], e[1], e[2], e[3]);
-    }
-#pragma unroll
-    for (int v = 0; v < BV; ++v) {
-      const int q = tid + v * 256;
-      float e[4];
-      if (TRANSB) {
-        const int j = q / 4, k = 4 * (q % 4);
-        const int64_t gj = n0 + j, gk = k0 + k;
-        if (gj < N && VEC && gk + 3 < kend) {
-          const float4 f = *reinterpret_cast<const float4*>(A + gj * lda + gk);
-          e[0] = f.x; e[1] = f.y; e[2] = f.z; e[3] = f.w;
-        } else {
-#pragma unroll
-          for (int t = 0; t < 4; ++t) e[t] = (gj < N && gk + t < kend) ? A[gj * lda + gk + t] : 0.f;
-        }
-      } else {
-        const int k = q / (BN / 4), j = 4 * (q % (BN / 4));
-        const int64_t gj = n0 + j, gk = k0 + k;
-        if (gk < kend && VEC && gj + 3 < N) {
-          const float4 f = *reinterpret_cast<const float4*>(A + gk * lda + gj);
-          e[0] = f.x; e[1] = f.y; e[2] = f.z; e[3] = f.w;
-        } else {
-#pragma unroll
-          for (int t = 0; t < 4; ++t) e[t] = (gk < kend && gj + t < N) ? A[gk * lda + gj + t] : 0.f;
-        }
-      }
-      rb[v] = make_float4(e[0], e[1], e[2], e[3]);
-    }
-  };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int v = 0; v < LV; ++v) {
-      const int q = tid + v * 256;
-      if (q < BM * BK / 4) {
-        const int i = q / (BK / 4), k = 4 * (q % (BK / 4));
-        Ls[buf][k + 0][i] = rl[v].x;
-        Ls[buf][k + 1][i] = rl[v].y;
-        Ls[buf][k + 2][i] = rl[v].z;
-        Ls[buf][k + 3][i] = rl[v].w;
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < BV; ++v) {
-      const int q = tid + v * 256;
-      if (TRANSB) {
-        const int j = q / 4, k = 4 * (q % 4);
-        Bs[buf][k + 0][j] = rb[v].x;
-        Bs[buf][k + 1][j] = rb[v].y;
-        Bs[buf][k + 2][j] = rb[v].z;
-        Bs[buf][k + 3][j] = rb[v].w;
-      } else {
-        const int k = q / (BN / 4), j = 4 * (q % (BN / 4));
-        *reinterpret_cast<float4*>(&Bs[buf][k][j]) = rb[v];
-      }
-    }
-  };
-  int cur = 0;
-  if (kbeg < kend) {
-    load(kbeg);
-    store(0);
-  }
-  __syncthreads();
-  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-    const bool more = k0 + BK < kend;
-    if (more) load(k0 + BK);
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      T a[TM], bv[TN];
-#pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = Ls[cur][kk][ty * TM + i];
-      // column pairs 64 j2 + 2 tx + {0, 1}: a warp's 8 column groups read one
-      // contiguous 64-byte chunk per 8-byte load (no bank conflicts)
-#pragma unroll
-      for (int j2 = 0; j2 < TN / 2; ++j2) {
-        const float2 f = *reinterpret_cast<const float2*>(&Bs[cur][kk][64 * j2 + 2 * tx]);
-        bv[2 * j2] = f.x;
-        bv[2 * j2 + 1] = f.y;
-      }
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
-    }
-    if (more) store(cur ^ 1);
-    __syncthreads();
-    cur ^= 1;
-  }
-#pragma unroll
-  for (int i = 0; i < TM; ++i) {
-    const int64_t r = ty * TM + i;
-    if (r >= M) continue;
-#pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      const int64_t c = n0 + 64 * (j >> 1) + 2 * tx + (j & 1);
-      if (c >= N) continue;
-      if (partial) {
-        partial[(int64_t)blockIdx.y * M * N + r * N + c] = (double)acc[i][j];
-      } else {
-        double v = (double)acc[i][j];
-        if (beta_row) v += beta_row[r] * (double)Cin[r * ldcin + c];
-        C[r * ldc + c] = (T)v;
-      }
-    }
-  }
+  tiles::gemm_lm_tile<TRANSB, BM, TM>(sm, vec, M, N, L, ldl, A, lda, C, ldc, beta_row, Cin, ldcin, n0, kbeg, kend,
+                                      partial ? partial + (int64_t)blockIdx.y * M * N : nullptr);
 }
 
 template <typename T>
@@ -277,15 +69,15 @@ tk_status launch_gemm_lm(bool transB, int64_t M, int64_t N, int64_t K, const T* 
   }
   // 16-byte loads need 16-byte aligned rows
   const bool vec = ((uintptr_t)L % 16 == 0) && ((uintptr_t)A % 16 == 0) && (ldl % 4 == 0) && (lda % 4 == 0);
-#define TK_LM(TRB, V, BM_, TM_)                                                                                 \
-  k_gemm_lm<T, TRB, V, BM_, BN, TM_, 8><<<grid, 256, 0, st>>>(M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, \
-                                                              ldcin, kps, partial)
-  if (M <= 32) {
-    if (transB) { if (vec) TK_LM(true, true, 32, 4); else TK_LM(true, false, 32, 4); }
-    else { if (vec) TK_LM(false, true, 32, 4); else TK_LM(false, false, 32, 4); }
+#define TK_LM(TRB, BM_, TM_)                                                                                  \
+  k_gemm_lm<TRB, BM_, TM_><<<grid, 256, 0, st>>>(vec, M, N, K, L, ldl, A, lda, C, ldc, beta_row, Cin, ldcin, kps, \
+                                                 partial)
+  if (M <= 16) {
+    if (transB) TK_LM(true, 16, 2); else TK_LM(false, 16, 2);
+  } else if (M <= 32) {
+    if (transB) TK_LM(true, 32, 4); else TK_LM(false, 32, 4);
   } else {
-    if (transB) { if (vec) TK_LM(true, true, 64, 8); else TK_LM(true, false, 64, 8); }
-    else { if (vec) TK_LM(false, true, 64, 8); else TK_LM(false, false, 64, 8); }
+    if (transB) TK_LM(true, 64, 8); else TK_LM(false, 64, 8);
   }
 #undef TK_LM
   TK_LAUNCH_CHECK();
@@ -631,7 +423,6 @@ __global__ void __launch_bounds__(256) k_tinv_final(float* __restrict__ M, float
 }
 
 // ------------------------------------------------------------------ TRMV --
-constexpr int kTrmvRows = 64;  // rows per CTA (8 warps x 8 rows)
 
 // out_k = M_l in_k for slot k (l = idx[k]): UPPER reads row i over columns
 // i..n-1 of M, otherwise (M = Mt, lower) over columns 0..i.  The slot's vector
@@ -642,32 +433,10 @@ constexpr int kTrmvRows = 64;  // rows per CTA (8 warps x 8 rows)
 template <bool UPPER>
 __global__ void __launch_bounds__(256) k_trmv(int64_t n, const float* __restrict__ M, int64_t ldm, int64_t mstride,
                                               const int* __restrict__ idx, const float* in, float* out, int64_t ldx) {
-  extern __shared__ float4 v4[];
-  float* v = reinterpret_cast<float*>(v4);
+  extern __shared__ float4 trmv_v4[];
   const int slot = blockIdx.y;
-  const float* Ml = M + (int64_t)(idx ? idx[slot] : slot) * mstride;
-  const float* x = in + (int64_t)slot * ldx;
-  const int64_t n4 = cdiv(n, 4);
-  for (int64_t j = threadIdx.x; j < 4 * n4; j += blockDim.x) v[j] = j < n ? x[j] : 0.f;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int q = 0; q < kTrmvRows / 8; ++q) {
-    const int64_t i = (int64_t)blockIdx.x * kTrmvRows + w + 8 * q;
-    if (i >= n) break;
-    const float4* row = reinterpret_cast<const float4*>(Ml + i * ldm);
-    const int64_t j0 = UPPER ? (i >> 2) : 0, j1 = UPPER ? n4 : (i >> 2) + 1;
-    float acc = 0.f;
-#pragma unroll 4
-    for (int64_t j = j0 + lane; j < j1; j += 32) {
-      const float4 a = __ldg(row + j), b = v4[j];
-      acc = fmaf(a.x, b.x, acc);
-      acc = fmaf(a.y, b.y, acc);
-      acc = fmaf(a.z, b.z, acc);
-      acc = fmaf(a.w, b.w, acc);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) out[(int64_t)slot * ldx + i] = acc;
-  }
+  tiles::trmv_rows<UPPER>(n, M + (int64_t)(idx ? idx[slot] : slot) * mstride, ldm, in + (int64_t)slot * ldx,
+                          out + (int64_t)slot * ldx, (int64_t)blockIdx.x * tiles::kTrmvRows, trmv_v4);
 }
 
 // ------------------------------------------------------------------ TRSV --
@@ -949,7 +718,7 @@ tk_status tri_inverse_f32(const double* R, int64_t n, int64_t ldr, int64_t rstri
 tk_status trmv_batched(bool transposed, int64_t n, const float* M, const float* Mt, int64_t ldm, int64_t mstride,
                        const int* idx, const float* in, float* out, int64_t ldx, int count, cudaStream_t st) {
   if (count == 0 || n == 0) return TK_OK;
-  const dim3 grid((unsigned)cdiv(n, kTrmvRows), (unsigned)count);
+  const dim3 grid((unsigned)cdiv(n, tiles::kTrmvRows), (unsigned)count);
   const size_t smem = sizeof(float) * 4 * (size_t)cdiv(n, 4);
   if (!transposed) k_trmv<true><<<grid, 256, smem, st>>>(n, M, ldm, mstride, idx, in, out, ldx);
   else k_trmv<false><<<grid, 256, smem, st>>>(n, Mt, ldm, mstride, idx, in, out, ldx);

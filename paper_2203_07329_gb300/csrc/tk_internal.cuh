@@ -7,6 +7,7 @@
 #include <stddef.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "tikhonov.h"
 
@@ -39,6 +40,18 @@ void count_launch();
     tk_status s__ = (x);           \
     if (s__ != TK_OK) return s__;  \
   } while (0)
+
+// Per-lambda status order: the worse of two statuses is kept.
+inline int severity(tk_status s) {
+  switch (s) {
+    case TK_OK: return 0;
+    case TK_ENOCONV: return 1;
+    case TK_ENUMERIC: return 2;
+    case TK_ENOTSPD: return 3;
+    default: return 4;
+  }
+}
+inline tk_status worse(tk_status a, tk_status b) { return severity(b) > severity(a) ? b : a; }
 
 // ------------------------------------------------------------ workspace --
 // Bump allocator over a caller-provided device buffer (256-byte aligned
@@ -203,6 +216,22 @@ tk_status trsv_batched(bool transposed, int64_t n, const TR* R, int64_t ldr, int
 
 // Low rank (tk_lowrank.cu)
 size_t svd_workspace(int64_t s, int64_t n);
+// Many one-sided Jacobi SVDs at once (grouped batch): every round of the
+// circle schedule is one launch over the pairs of all matrices still rotating.
+struct SvdJob {
+  const double* Y = nullptr;  // s x n (read only)
+  int64_t s = 0, n = 0;
+  double* sigma = nullptr;    // s, descending
+  double* V = nullptr;        // n x s
+  void* scratch = nullptr;    // svd_workspace(s, n) bytes
+  size_t scratch_bytes = 0;
+  int sweeps = 0;             // out
+  double* W = nullptr;        // carved from scratch
+  double* nrm = nullptr;
+  int* perm = nullptr;
+};
+size_t svd_grouped_workspace(const std::vector<SvdJob>& jobs);
+tk_status jacobi_svd_grouped(std::vector<SvdJob>& jobs, void* work, size_t work_bytes, cudaStream_t st);
 tk_status jacobi_svd(const double* Y, int64_t s, int64_t n, double* sigma, double* V, int* sweeps_host, Arena& ar,
                      cudaStream_t st);
 

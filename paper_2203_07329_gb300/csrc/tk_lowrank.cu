@@ -27,13 +27,12 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// One round of the circle schedule over sp (even) players; player sp-1 is a
-// dummy when s is odd.
-__global__ void __launch_bounds__(kJacThreads)
-    k_jacobi_round(double* __restrict__ W, int64_t s, int64_t n, int64_t sp, int64_t round, double tol,
-                   double* __restrict__ off_max, int* __restrict__ rotated) {
-  __shared__ double sh[32];
-  const int64_t k = blockIdx.x;
+// Pair k of round `round` of the circle schedule over sp (even) players
+// (player sp-1 is a dummy when s is odd): rows p < q of W are rotated so that
+// they become orthogonal, unless already orthogonal to tol.  One CTA.
+__device__ __forceinline__ void jacobi_pair(double* __restrict__ W, int64_t s, int64_t n, int64_t sp, int64_t round,
+                                            int64_t k, double tol, double* __restrict__ off_max,
+                                            int* __restrict__ rotated, double* sh) {
   int64_t p, q;
   if (k == 0) {
     p = sp - 1;
@@ -75,6 +74,42 @@ __global__ void __launch_bounds__(kJacThreads)
     double x = wp[i], y = wq[i];
     wp[i] = c * x - sn * y;
     wq[i] = sn * x + c * y;
+  }
+}
+
+// One round for one matrix: sp/2 disjoint pairs, one CTA each.
+__global__ void __launch_bounds__(kJacThreads)
+    k_jacobi_round(double* __restrict__ W, int64_t s, int64_t n, int64_t sp, int64_t round, double tol,
+                   double* __restrict__ off_max, int* __restrict__ rotated) {
+  __shared__ double sh[32];
+  jacobi_pair(W, s, n, sp, round, blockIdx.x, tol, off_max, rotated, sh);
+}
+
+// One round for many matrices (grouped batch): CTA = (matrix, pair).
+struct SvdDesc {
+  double* W;
+  int64_t s, n, sp;
+  double* off_max;
+  int* rotated;
+  int done;
+};
+struct SvdTile {
+  int job, k;
+};
+__global__ void __launch_bounds__(kJacThreads)
+    k_jacobi_round_grouped(const SvdDesc* __restrict__ D, const SvdTile* __restrict__ tl, int64_t round, double tol) {
+  __shared__ double sh[32];
+  const SvdTile t = tl[blockIdx.x];
+  const SvdDesc& d = D[t.job];
+  if (d.done || round >= d.sp - 1) return;
+  jacobi_pair(d.W, d.s, d.n, d.sp, round, t.k, tol, d.off_max, d.rotated, sh);
+}
+
+__global__ void k_svd_reset(SvdDesc* __restrict__ D, int J) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < J && !D[j].done) {
+    *D[j].rotated = 0;
+    *D[j].off_max = 0.0;
   }
 }
 
@@ -154,6 +189,26 @@ size_t svd_workspace(int64_t s, int64_t n) {
   return a.used + 512;
 }
 
+// The sorted singular values and right singular vectors from the rotated
+// rows: sigma_j = ||W_perm[j]||, V[:, j] = W_perm[j] / sigma_j.
+static tk_status svd_finish(const double* W, int64_t s, int64_t n, double* nrm, int* perm, double* sigma, double* V,
+                            cudaStream_t st) {
+  k_row_norms<<<(unsigned)s, 256, 0, st>>>(W, n, nrm);
+  TK_LAUNCH_CHECK();
+  std::vector<double> h(s);
+  TK_CUDA(cudaMemcpyAsync(h.data(), nrm, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  std::vector<int> order(s);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h[a] > h[b]; });
+  TK_CUDA(cudaMemcpyAsync(perm, order.data(), sizeof(int) * s, cudaMemcpyHostToDevice, st));
+  dim3 g((unsigned)std::min<int64_t>(cdiv(n, 256), 64), (unsigned)s);
+  k_write_v<<<g, 256, 0, st>>>(W, nrm, perm, s, n, V, sigma);
+  TK_LAUNCH_CHECK();
+  TK_CUDA(cudaStreamSynchronize(st));  // `order` is a host temporary
+  return TK_OK;
+}
+
 tk_status jacobi_svd(const double* Y, int64_t s, int64_t n, double* sigma, double* V, int* sweeps_host, Arena& ar,
                      cudaStream_t st) {
   double* W = ar.take<double>((size_t)s * n);
@@ -181,20 +236,83 @@ tk_status jacobi_svd(const double* Y, int64_t s, int64_t n, double* sigma, doubl
     if (hrot == 0) break;
   }
   if (sweeps_host) *sweeps_host = sweep + 1;
-  k_row_norms<<<(unsigned)s, 256, 0, st>>>(W, n, nrm);
-  TK_LAUNCH_CHECK();
-  std::vector<double> h(s);
-  TK_CUDA(cudaMemcpyAsync(h.data(), nrm, sizeof(double) * s, cudaMemcpyDeviceToHost, st));
-  TK_CUDA(cudaStreamSynchronize(st));
-  std::vector<int> order(s);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h[a] > h[b]; });
-  TK_CUDA(cudaMemcpyAsync(perm, order.data(), sizeof(int) * s, cudaMemcpyHostToDevice, st));
-  dim3 g((unsigned)std::min<int64_t>(cdiv(n, 256), 64), (unsigned)s);
-  k_write_v<<<g, 256, 0, st>>>(W, nrm, perm, s, n, V, sigma);
-  TK_LAUNCH_CHECK();
-  TK_CUDA(cudaStreamSynchronize(st));  // `order` is a host temporary
+  return svd_finish(W, s, n, nrm, perm, sigma, V, st);
+}
+
+tk_status jacobi_svd_grouped(std::vector<SvdJob>& jobs, void* work, size_t work_bytes, cudaStream_t st) {
+  const int J = (int)jobs.size();
+  if (J == 0) return TK_OK;
+  std::vector<SvdDesc> hd(J);
+  std::vector<SvdTile> tiles;
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  SvdDesc* dd = a.take<SvdDesc>(J);
+  double* offs = a.take<double>(J);
+  int* rots = a.take<int>(J);
+  size_t ntiles = 0;
+  for (const auto& j : jobs) ntiles += (size_t)((j.s % 2 == 0) ? j.s : j.s + 1) / 2;
+  SvdTile* dt = a.take<SvdTile>(std::max<size_t>(ntiles, 1));
+  if (!a.ok()) {
+    set_error_msg("grouped SVD: workspace too small");
+    return TK_ENOMEM;
+  }
+  int64_t max_rounds = 0;
+  for (int j = 0; j < J; ++j) {
+    SvdJob& q = jobs[j];
+    Arena sa;
+    sa.base = (char*)q.scratch;
+    sa.cap = q.scratch_bytes;
+    q.W = sa.take<double>((size_t)q.s * q.n);
+    q.nrm = sa.take<double>((size_t)q.s);
+    q.perm = sa.take<int>((size_t)q.s);
+    if (!sa.ok()) return TK_ENOMEM;
+    if (q.s > 0) TK_CUDA(cudaMemcpyAsync(q.W, q.Y, sizeof(double) * (size_t)q.s * q.n, cudaMemcpyDeviceToDevice, st));
+    const int64_t sp = (q.s % 2 == 0) ? q.s : q.s + 1;
+    hd[j] = SvdDesc{q.W, q.s, q.n, sp, offs + j, rots + j, q.s <= 1 ? 1 : 0};
+    for (int64_t k = 0; k < sp / 2; ++k) tiles.push_back(SvdTile{j, (int)k});
+    if (q.s > 1) max_rounds = std::max(max_rounds, sp - 1);
+    q.sweeps = 0;
+  }
+  TK_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(SvdDesc) * J, cudaMemcpyHostToDevice, st));
+  TK_CUDA(cudaMemcpyAsync(dt, tiles.data(), sizeof(SvdTile) * tiles.size(), cudaMemcpyHostToDevice, st));
+  const double tol = 1e-15;  // the single-matrix SVD's threshold
+  const int max_sweeps = 80;
+  std::vector<int> hrot(J);
+  for (int sweep = 0; sweep < max_sweeps && max_rounds > 0; ++sweep) {
+    k_svd_reset<<<cdiv(J, 128), 128, 0, st>>>(dd, J);
+    TK_LAUNCH_CHECK();
+    for (int64_t r = 0; r < max_rounds; ++r) {
+      k_jacobi_round_grouped<<<(unsigned)tiles.size(), kJacThreads, 0, st>>>(dd, dt, r, tol);
+      TK_LAUNCH_CHECK();
+    }
+    TK_CUDA(cudaMemcpyAsync(hrot.data(), rots, sizeof(int) * J, cudaMemcpyDeviceToHost, st));
+    TK_CUDA(cudaStreamSynchronize(st));
+    max_rounds = 0;
+    for (int j = 0; j < J; ++j) {
+      if (hd[j].done) continue;
+      jobs[j].sweeps = sweep + 1;
+      if (hrot[j] == 0) hd[j].done = 1;
+      else max_rounds = std::max(max_rounds, hd[j].sp - 1);
+    }
+    if (max_rounds == 0) break;
+    TK_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(SvdDesc) * J, cudaMemcpyHostToDevice, st));
+  }
+  for (auto& q : jobs)
+    if (q.s > 0) TK_TRY(svd_finish(q.W, q.s, q.n, q.nrm, q.perm, q.sigma, q.V, st));
+  TK_CUDA(cudaStreamSynchronize(st));  // hd, tiles are host temporaries
   return TK_OK;
+}
+
+size_t svd_grouped_workspace(const std::vector<SvdJob>& jobs) {
+  Arena a;
+  size_t ntiles = 0;
+  for (const auto& j : jobs) ntiles += (size_t)((j.s % 2 == 0) ? j.s : j.s + 1) / 2;
+  a.take<SvdDesc>(std::max<size_t>(jobs.size(), 1));
+  a.take<double>(std::max<size_t>(jobs.size(), 1));
+  a.take<int>(std::max<size_t>(jobs.size(), 1));
+  a.take<SvdTile>(std::max<size_t>(ntiles, 1));
+  return a.used + 1024;
 }
 
 tk_status lowrank_ranks_dev(const double* sigma, int64_t s, const double* lam_dev, int N, double alpha,

@@ -26,8 +26,6 @@ namespace {
 constexpr int kVecThreads = 256;
 constexpr int kSumChunks = 64;
 
-__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
-
 // partial[s * chunks + c] = sum of squares of row s over chunk c
 template <typename T>
 __global__ void k_sumsq_rows(const T* __restrict__ X, int64_t ld, int64_t len, int chunks,
@@ -137,90 +135,15 @@ __global__ void k_over_g(const double* __restrict__ part, int splits, int count,
   }
 }
 
-// ---- shared Golub-Kahan v-step + Givens + tests ----------------------
-// Vraw holds M^T u for each slot (length nv).  On return V = normalized v,
-// W, Y updated and the scalars advanced.
+// ---- shared Golub-Kahan v-step + Givens + tests (body: vstep_block) ---
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
     k_vstep(const T* __restrict__ Vraw, T* __restrict__ V, T* __restrict__ W, T* __restrict__ Y, int64_t nv,
             Scal* __restrict__ sc, double atol, double btol, int maxiter, int init) {
   __shared__ double sh[32];
   const int s = blockIdx.x;
-  Scal q = sc[s];
   const int64_t off = (int64_t)s * nv;
-  const double beta = q.beta;
-  // v' = Vraw - beta v  (init: v' = Vraw)
-  double acc = 0.0;
-  for (int64_t j = threadIdx.x; j < nv; j += blockDim.x) {
-    double v = (double)Vraw[off + j];
-    if (!init) v = fma(-beta, (double)V[off + j], v);
-    V[off + j] = (T)v;
-    acc = fma(v, v, acc);
-  }
-  const double alpha = sqrt(block_sum(acc, sh));
-  const double ainv = alpha > 0.0 ? 1.0 / alpha : 0.0;
-  if (init) {
-    double yn = 0.0;
-    for (int64_t j = threadIdx.x; j < nv; j += blockDim.x) {
-      T v = (T)((double)V[off + j] * ainv);
-      V[off + j] = v;
-      W[off + j] = v;
-      Y[off + j] = T(0);
-    }
-    (void)yn;
-    if (threadIdx.x == 0) {
-      q.alpha = alpha;
-      q.rhobar = alpha;
-      q.coef = (q.beta > 0.0) ? -alpha / q.beta : 0.0;
-      q.arnorm = alpha * q.beta;
-      if (alpha == 0.0 && q.istop == 0) q.istop = 1;  // b orthogonal to range(M): y = 0 is exact
-      if (!finite_d(alpha)) q.istop = 5;
-      sc[s] = q;
-    }
-    return;
-  }
-  const double rho = sqrt(q.rhobar * q.rhobar + beta * beta);
-  const double c = rho > 0.0 ? q.rhobar / rho : 1.0;
-  const double sn = rho > 0.0 ? beta / rho : 0.0;
-  const double theta = sn * alpha;
-  const double rhobar = -c * alpha;
-  const double phi = c * q.phibar;
-  const double phibar = sn * q.phibar;
-  const double t1 = rho > 0.0 ? phi / rho : 0.0;
-  const double t2 = rho > 0.0 ? theta / rho : 0.0;
-  double yy = 0.0;
-  for (int64_t j = threadIdx.x; j < nv; j += blockDim.x) {
-    double v = (double)V[off + j] * ainv;
-    double w = (double)W[off + j];
-    double y = fma(t1, w, (double)Y[off + j]);
-    w = fma(-t2, w, v);
-    V[off + j] = (T)v;
-    W[off + j] = (T)w;
-    Y[off + j] = (T)y;
-    yy = fma(y, y, yy);
-  }
-  const double ynorm = sqrt(block_sum(yy, sh));
-  if (threadIdx.x == 0) {
-    q.alpha = alpha;
-    q.rhobar = rhobar;
-    q.phibar = phibar;
-    q.iters += 1;
-    q.coef = beta > 0.0 ? -alpha / beta : 0.0;
-    const double rnorm = phibar;
-    const double arnorm = phibar * alpha * fabs(c);
-    const double anorm = sqrt(q.anorm2);
-    q.rnorm = rnorm;
-    q.arnorm = arnorm;
-    q.ynorm = ynorm;
-    int istop = 0;
-    if (!finite_d(alpha) || !finite_d(beta) || !finite_d(ynorm)) istop = 5;
-    else if (rnorm == 0.0) istop = 1;
-    else if (arnorm / (anorm * rnorm) <= atol) istop = 2;
-    else if (rnorm <= btol * q.bnorm + atol * anorm * ynorm) istop = 1;
-    else if (q.iters >= maxiter) istop = 7;
-    q.istop = istop;
-    sc[s] = q;
-  }
+  vstep_block<T>(Vraw + off, V + off, W + off, Y + off, nv, sc + s, atol, btol, maxiter, init, sh);
 }
 
 // ---- underdetermined ----------------------------------------------------

@@ -32,6 +32,93 @@ template <typename T>
 tk_status lowrank_diag_dev(const double* sigma, int64_t s, const double* lam_dev, const int64_t* rank_dev, int N,
                            T* S, cudaStream_t st);
 
+// One block's Golub-Kahan v-step for one slot (Paige & Saunders' LSQR):
+// Vraw holds M^T u (length nv).  v' = Vraw - beta v, alpha = ||v'||, then the
+// Givens rotation, the y and w updates and the stopping tests (istop 1: the
+// residual test, 2: the normal-equation test, 5: non-finite, 7: iteration
+// cap).  init: the first v (alpha_1 v_1 = M^T u_1), w = v, y = 0.  sh: 32
+// doubles of shared memory.
+template <typename T>
+__device__ __forceinline__ void vstep_block(const T* __restrict__ Vraw, T* __restrict__ V, T* __restrict__ W,
+                                            T* __restrict__ Y, int64_t nv, Scal* __restrict__ sq, double atol,
+                                            double btol, int maxiter, int init, double* sh) {
+  Scal q = *sq;
+  const int64_t off = 0;
+  const double beta = q.beta;
+  // v' = Vraw - beta v  (init: v' = Vraw)
+  double acc = 0.0;
+  for (int64_t j = threadIdx.x; j < nv; j += blockDim.x) {
+    double v = (double)Vraw[off + j];
+    if (!init) v = fma(-beta, (double)V[off + j], v);
+    V[off + j] = (T)v;
+    acc = fma(v, v, acc);
+  }
+  const double alpha = sqrt(block_sum(acc, sh));
+  const double ainv = alpha > 0.0 ? 1.0 / alpha : 0.0;
+  if (init) {
+    double yn = 0.0;
+    for (int64_t j = threadIdx.x; j < nv; j += blockDim.x) {
+      T v = (T)((double)V[off + j] * ainv);
+      V[off + j] = v;
+      W[off + j] = v;
+      Y[off + j] = T(0);
+    }
+    (void)yn;
+    if (threadIdx.x == 0) {
+      q.alpha = alpha;
+      q.rhobar = alpha;
+      q.coef = (q.beta > 0.0) ? -alpha / q.beta : 0.0;
+      q.arnorm = alpha * q.beta;
+      if (alpha == 0.0 && q.istop == 0) q.istop = 1;  // b orthogonal to range(M): y = 0 is exact
+      if (!isfinite(alpha)) q.istop = 5;
+      *sq = q;
+    }
+    return;
+  }
+  const double rho = sqrt(q.rhobar * q.rhobar + beta * beta);
+  const double c = rho > 0.0 ? q.rhobar / rho : 1.0;
+  const double sn = rho > 0.0 ? beta / rho : 0.0;
+  const double theta = sn * alpha;
+  const double rhobar = -c * alpha;
+  const double phi = c * q.phibar;
+  const double phibar = sn * q.phibar;
+  const double t1 = rho > 0.0 ? phi / rho : 0.0;
+  const double t2 = rho > 0.0 ? theta / rho : 0.0;
+  double yy = 0.0;
+  for (int64_t j = threadIdx.x; j < nv; j += blockDim.x) {
+    double v = (double)V[off + j] * ainv;
+    double w = (double)W[off + j];
+    double y = fma(t1, w, (double)Y[off + j]);
+    w = fma(-t2, w, v);
+    V[off + j] = (T)v;
+    W[off + j] = (T)w;
+    Y[off + j] = (T)y;
+    yy = fma(y, y, yy);
+  }
+  const double ynorm = sqrt(block_sum(yy, sh));
+  if (threadIdx.x == 0) {
+    q.alpha = alpha;
+    q.rhobar = rhobar;
+    q.phibar = phibar;
+    q.iters += 1;
+    q.coef = beta > 0.0 ? -alpha / beta : 0.0;
+    const double rnorm = phibar;
+    const double arnorm = phibar * alpha * fabs(c);
+    const double anorm = sqrt(q.anorm2);
+    q.rnorm = rnorm;
+    q.arnorm = arnorm;
+    q.ynorm = ynorm;
+    int istop = 0;
+    if (!isfinite(alpha) || !isfinite(beta) || !isfinite(ynorm)) istop = 5;
+    else if (rnorm == 0.0) istop = 1;
+    else if (arnorm / (anorm * rnorm) <= atol) istop = 2;
+    else if (rnorm <= btol * q.bnorm + atol * anorm * ynorm) istop = 1;
+    else if (q.iters >= maxiter) istop = 7;
+    q.istop = istop;
+    *sq = q;
+  }
+}
+
 template <typename T>
 struct Lsqr {
   // problem: A (m x n, row stride lda) in the compute type

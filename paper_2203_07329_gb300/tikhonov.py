@@ -36,7 +36,7 @@ class tk_opts(C.Structure):
     _fields_ = [("sketch", C.c_int), ("s", C.c_int64), ("precond", C.c_int), ("alpha", C.c_double),
                 ("precision", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int), ("max_refine", C.c_int),
                 ("inner_tol", C.c_double), ("refine_tol", C.c_double), ("seed", C.c_uint64),
-                ("schedule", C.c_int), ("lsqr_tc", C.c_int)]
+                ("schedule", C.c_int), ("lsqr_tc", C.c_int), ("group", C.c_int)]
 
 
 class tk_info(C.Structure):

@@ -295,9 +295,11 @@ def sd_of_spectrum(sig, lam):
     return float(np.sum(1.0 / (1.0 + lam / (sig * sig))))
 
 
-def test_uneven_batch_mixed_cholesky_and_lowrank(tk):
+@pytest.mark.parametrize("group", [1, 0])
+def test_uneven_batch_mixed_cholesky_and_lowrank(tk, group):
     # the 256-problem workload's structure at test size: float32 data, mixed precision,
-    # half the problems with sigma_i = exp(-i/50) solved with the sd-sized low-rank form
+    # half the problems with sigma_i = exp(-i/50) solved with the sd-sized low-rank form;
+    # group = 1: all problems advance in one grouped LSQR, 0: each problem on its own
     probs = datagen.uneven_batch(10, m_range=(1500, 4000), n_range=(64, 200), N=4, dtype=torch.float32)
     pairs, opts = [], []
     for p in probs:
@@ -306,10 +308,10 @@ def test_uneven_batch_mixed_cholesky_and_lowrank(tk):
         if p.meta["lowrank"]:
             s = min(n, 2 * math.ceil(sd_of_spectrum(p.sigma.numpy(), float(p.lambdas.min()))))
             opts.append(tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=s, seed=3, precond=tk.TK_PRECOND_LOWRANK,
-                                        alpha=2.0, precision=tk.TK_PREC_MIXED))
+                                        alpha=2.0, precision=tk.TK_PREC_MIXED, group=group))
         else:
             opts.append(tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=min(4 * n, p.A.shape[0]), seed=3,
-                                        precision=tk.TK_PREC_MIXED))
+                                        precision=tk.TK_PREC_MIXED, group=group))
     lams = np.stack([p.lambdas.numpy() for p in probs])
     Xs, infos, st = tk.tk_solve_batched(pairs, lams, opts)
     assert st == tk.TK_OK, infos
@@ -318,8 +320,33 @@ def test_uneven_batch_mixed_cholesky_and_lowrank(tk):
         Xc = X.cpu().numpy()
         for i in range(len(lam)):
             assert rel(Xc[i], Xr[i]) < TOL_X, (p.meta, lam[i], rel(Xc[i], Xr[i]), inf[i])
+            assert 1 <= inf[i]["refine_steps"] <= 8 and inf[i]["iters"] > 0
         if p.meta["lowrank"]:
             assert all(0 < q["rank"] <= p.A.shape[1] for q in inf)
+
+
+def test_grouped_batch_float64_and_float32_inputs(tk):
+    # grouped mixed solve over problems whose A is float64 (float32 copy for the LSQR,
+    # float64 residual passes) and float32, Cholesky preconditioner, SRHT and Gaussian
+    # sketches, ragged m and n (no 16-byte multiple), 12 lambda each
+    shapes = [(3001, 131), (2048, 256), (5003, 77), (1777, 300), (4096, 64), (2500, 199)]
+    pairs, opts, refs, lam_rows = [], [], [], []
+    for i, (m, n) in enumerate(shapes):
+        dt = torch.float64 if i % 2 == 0 else torch.float32
+        p = datagen.make_ridge_problem(m, n, datagen.spectrum("log", n, hi=1.0, lo=1e-5),
+                                       datagen.log_lambdas(12, 1e-6, 1.0), seed=900 + i, dtype=dt)
+        pairs.append((p.A.cuda(), p.b.cuda()))
+        sk = tk.TK_SKETCH_SRHT if i % 3 == 0 else tk.TK_SKETCH_GAUSS
+        opts.append(tk.opts_default(sketch=sk, s=min(4 * n, m), seed=5, precision=tk.TK_PREC_MIXED))
+        lam_rows.append(p.lambdas.numpy())
+        refs.append(ref_over(p, p.lambdas.numpy()))
+    lams = np.stack(lam_rows)
+    Xs, infos, st = tk.tk_solve_batched(pairs, lams, opts)
+    assert st == tk.TK_OK, infos
+    for k in range(len(shapes)):
+        Xc = Xs[k].cpu().numpy()
+        for i in range(lams.shape[1]):
+            assert rel(Xc[i], refs[k][i]) < TOL_X, (shapes[k], lams[k, i], rel(Xc[i], refs[k][i]), infos[k][i])
 
 
 def test_mixed_gaussian_float32_scaled_workload(tk):
