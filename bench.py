@@ -190,9 +190,18 @@ def small_workload_step(tk, datagen, stream, barrier, reps=20):
         e1.record(stream)
         barrier()
         t = e0.elapsed_time(e1) / reps
+        launches = (tk.tk_launch_count() - l0) / reps
+        tk.tk_profile_enable(True)  # one more call, profiled, for the phase split
+        tk.tk_profile_collect()
+        tk.tk_solve(prob.A, prob.b, lams, o, work=work, X=X, stream=stream)
+        barrier()
+        prof = tk.tk_profile_collect()
+        tk.tk_profile_enable(False)
         out[key] = {"us_per_lambda_solve": t * 1e3 / len(lams), "ms_per_solve_call": t,
-                    "launches_per_call": (tk.tk_launch_count() - l0) / reps,
-                    "iters_mean": float(np.mean([q["iters"] for q in r.info]))}
+                    "launches_per_call": launches,
+                    "iters_mean": float(np.mean([q["iters"] for q in r.info])),
+                    "phase_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["launches"]},
+                    "phase_launches": {k: v["launches"] for k, v in prof.items() if v["launches"]}}
     return out
 
 

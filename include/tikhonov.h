@@ -246,7 +246,7 @@ enum {
   TK_PHASE_ATU = 6,           /* the product with A^T of every LSQR step */
   TK_PHASE_RES64 = 7,         /* MIXED: float64 residual b - A x */
   TK_PHASE_NE64 = 8,          /* MIXED: float64 A^T (b - A x) */
-  TK_PHASE_TRINV = 9,         /* MIXED: float32 R^-1 and R^-T built from the float64 factors */
+  TK_PHASE_TRINV = 9,         /* explicit R^-1 and R^-T from the float64 factors (MIXED: float32; FP64: n <= 512) */
   TK_PHASE_COUNT = 10
 };
 typedef struct {

@@ -43,6 +43,7 @@ struct Plan {
   bool mixed = false, lowrank = false;
   bool lsqr_tc = false;  // tensor-core float32 LSQR products
   bool prep_only = false;  // grouped batch: build the preconditioner only
+  bool inv64 = false;      // float64 form: explicit float64 R^-1 (small factors)
 };
 
 constexpr int64_t kMaxShort = 8192;
@@ -97,6 +98,10 @@ tk_status make_plan(const tk_problem* p, int N, const tk_opts* o, Plan& P) {
   P.N_cap = (o->schedule == TK_SCHED_ONE_AT_A_TIME) ? 1 : std::max(N, 1);
   // the tensor-core products need 16-byte aligned float32 rows of A, A^T and
   // the lambda-major vectors; other shapes keep the SIMT float32 products
+  // small float64 factors: an explicit inverse costs N n^3/3 flops once and
+  // turns each preconditioner apply into one launch (substitution on a
+  // factor of order <= 512 runs in a single CTA per lambda)
+  P.inv64 = !P.mixed && !P.lowrank && !P.under && P.c <= 512;
   P.lsqr_tc = P.mixed && o->lsqr_tc != 0 && P.N_cap <= 64 && !P.under && P.m % 4 == 0 && P.n % 4 == 0 &&
               (P.dt == TK_F64 || P.lda % 4 == 0);
   return TK_OK;
@@ -117,6 +122,8 @@ struct Bufs {
   double* R = nullptr;
   float* Minv = nullptr;   // mixed: R^-1 in float32 (N x np x np)
   float* Mtinv = nullptr;  // mixed: R^-T in float32
+  double* Minv64 = nullptr;   // float64 form, small factors: R^-1
+  double* Mtinv64 = nullptr;  // and R^-T
   double* sig = nullptr;
   double* lrV = nullptr;
   double* lrS = nullptr;
@@ -176,6 +183,10 @@ void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
       B.Minv = a.take<float>((size_t)N * P.np * P.np);
       B.Mtinv = a.take<float>((size_t)N * P.np * P.np);
     }
+    if (P.inv64) {
+      B.Minv64 = a.take<double>((size_t)N * P.np * P.np);
+      B.Mtinv64 = a.take<double>((size_t)N * P.np * P.np);
+    }
   } else {
     B.sig = ty.take<double>((size_t)P.s);
     B.lrV = (P.mixed ? ty : a).take<double>((size_t)P.c * P.s);
@@ -198,7 +209,8 @@ void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
     B.part = a.take<double>((size_t)B.splits * N * P.n);
     B.nrm = a.take<double>((size_t)3 * N);
   }
-  const size_t sc = sketch_scratch(P);
+  // the sketch's scratch is free again when the Gram matrix is formed
+  const size_t sc = std::max(sketch_scratch(P), P.lowrank ? size_t(0) : gram_scratch_bytes(P.s, P.c));
   B.scratch_bytes = sc;
   B.scratch = t.take<char>(sc);
   if (P.prep_only) return;
@@ -430,7 +442,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
   std::vector<int> ok_ids;
   if (!P.lowrank) {
     int tok = prof_begin(TK_PHASE_GRAM, st);
-    TK_TRY(gram_upper(B.Y, P.s, P.c, B.C, st));  // the Cholesky reads only j >= i
+    TK_TRY(gram_upper(B.Y, P.s, P.c, B.C, B.scratch, B.scratch_bytes, st));  // the Cholesky reads only j >= i
     prof_end(tok, st, (double)P.s * P.c * (P.c + 1), 8.0 * (P.s * P.c + P.c * (P.c + 1) / 2));
     Arena none;
     tok = prof_begin(TK_PHASE_CHOLESKY, st);
@@ -446,8 +458,13 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     if (P.mixed) {
       // the float32 LSQR applies R^-1 and R^-T as explicit float32 matrices
       tok = prof_begin(TK_PHASE_TRINV, st);
-      TK_TRY(tri_inverse_f32(B.R, P.c, P.np, P.np * P.np, N, B.Minv, B.Mtinv, st));
+      TK_TRY(tri_inverse<float>(B.R, P.c, P.np, P.np * P.np, N, B.Minv, B.Mtinv, st));
       prof_end(tok, st, (double)N * P.c * P.c * P.c / 3.0, 4.0 * N * P.np * P.np * 3.0);
+    }
+    if (P.inv64) {
+      tok = prof_begin(TK_PHASE_TRINV, st);
+      TK_TRY(tri_inverse<double>(B.R, P.c, P.np, P.np * P.np, N, B.Minv64, B.Mtinv64, st));
+      prof_end(tok, st, (double)N * P.c * P.c * P.c / 3.0, 8.0 * N * P.np * P.np * 3.0);
     }
   } else if (!gp) {
     Arena sa;
@@ -506,6 +523,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     e.A = A64; e.lda = lda64; e.st = st; e.atol = e.btol = P.o.tol; e.maxiter = P.o.maxiter;
     if (!P.lowrank) {
       e.prec_kind = TK_PRECOND_CHOL; e.R = B.R; e.ldr = P.np; e.rstride = P.np * P.np;
+      if (P.inv64) { e.Mi = B.Minv64; e.Mti = B.Mtinv64; e.ldm = P.np; e.mstride = P.np * P.np; }
     } else {
       e.prec_kind = TK_PRECOND_LOWRANK; e.lrV = B.lrV; e.lrS = B.lrS;
     }

@@ -123,7 +123,13 @@ tk_status gemm_dispatch(bool transA, bool transB, int64_t M, int64_t N, int64_t 
   return launch_gemm<TA, TB, TC, BM, BN, 16, TM, TN>(transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, \
                                                       beta_row, Cin, ldcin, splits, partial, st)
   // Shapes: a few lambda rows against a long axis (M small), a long axis
-  // against a few lambda columns (N small), or square-ish.
+  // against a few lambda columns (N small), or square-ish.  Few CTAs (a
+  // small problem: fewer than one per SM) take the narrower column tile.
+  const bool few = cdiv(N, 128) * (int64_t)splits < 152;
+  if (!f32 && few) {
+    if (M <= 8) TK_G(8, 64, 1, 2);
+    if (M <= 32) TK_G(32, 32, 4, 1);
+  }
   if (f32) {
     if (M <= 32) TK_G(32, 128, 4, 4);
     if (M <= 64) TK_G(64, 128, 8, 4);
@@ -293,20 +299,21 @@ __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ R, int
     }
 }
 
-// ------------------------------------------- triangular inverse (FP32) ---
-// M = R^-1 of the upper triangular factors, built in float32 as an explicit
-// preconditioner for the float32 LSQR of the mixed form: every application
-// of R^-1 or R^-T is then one batched triangular matrix-vector product
-// (HBM-bound, one launch) instead of a substitution (a chain of dependent
-// launches).  Blocks of 64 rows are finished from the bottom: R M = I gives
+// --------------------------------------------------- triangular inverse ---
+// M = R^-1 of the upper triangular factors as an explicit preconditioner (in
+// float32 for the float32 LSQR of the mixed form, in float64 for small
+// factors of the float64 form): every application of R^-1 or R^-T is then
+// one batched triangular matrix-vector product (HBM-bound, one launch)
+// instead of a substitution (a chain of dependent launches).  Blocks of 64 rows are finished from the bottom: R M = I gives
 // M_ii = R_ii^-1 (float64, in shared memory) and, for c > i,
 // M_ic = M_ii S_ic with S_ic = -sum_{i<k<=c} R_ik M_kc, accumulated
 // right-looking in the not yet finished blocks of M (zero on entry).  Mt
 // receives M^T (its blocks above the diagonal are left unwritten).
 
 // M_kk = R_kk^-1: thread c back-substitutes column c of the identity.
+template <typename T>
 __global__ void __launch_bounds__(CB) k_tinv_diag(const double* __restrict__ R, int64_t ldr, int64_t rstride,
-                                                  float* __restrict__ M, float* __restrict__ Mt, int64_t ldm,
+                                                  T* __restrict__ M, T* __restrict__ Mt, int64_t ldm,
                                                   int64_t mstride) {
   __shared__ double D[CB][CB + 1];
   const int kb = blockIdx.x, l = blockIdx.y, c = threadIdx.x;
@@ -323,43 +330,44 @@ __global__ void __launch_bounds__(CB) k_tinv_diag(const double* __restrict__ R, 
     for (int q = 0; q < r; ++q) x[q] = fma(-D[q][r], x[r], x[q]);
   }
   __syncthreads();
-  float* Mg = M + (int64_t)l * mstride + (int64_t)kb * CB * ldm + (int64_t)kb * CB;
+  T* Mg = M + (int64_t)l * mstride + (int64_t)kb * CB * ldm + (int64_t)kb * CB;
 #pragma unroll
   for (int r = 0; r < CB; ++r) {
-    Mg[(int64_t)r * ldm + c] = (float)x[r];
+    Mg[(int64_t)r * ldm + c] = (T)x[r];
     D[r][c] = x[r];
   }
   __syncthreads();
-  float* Mtg = Mt + (int64_t)l * mstride + (int64_t)kb * CB * ldm + (int64_t)kb * CB;
-  for (int i = 0; i < CB; ++i) Mtg[(int64_t)i * ldm + c] = (float)D[c][i];
+  T* Mtg = Mt + (int64_t)l * mstride + (int64_t)kb * CB * ldm + (int64_t)kb * CB;
+  for (int i = 0; i < CB; ++i) Mtg[(int64_t)i * ldm + c] = (T)D[c][i];
 }
 
-// S_{rb,cb} -= R_{rb,k} M_{k,cb} for rb < k <= cb (float32; R read as float64).
+// S_{rb,cb} -= R_{rb,k} M_{k,cb} for rb < k <= cb (arithmetic in T; R read as float64).
+template <typename T>
 __global__ void __launch_bounds__(256) k_tinv_update(const double* __restrict__ R, int64_t ldr, int64_t rstride,
-                                                     float* __restrict__ M, int64_t ldm, int64_t mstride, int k,
+                                                     T* __restrict__ M, int64_t ldm, int64_t mstride, int k,
                                                      int nt) {
   constexpr int KC = 32;
-  __shared__ float P[KC][CB + 4];  // P[kk][i] = R[rb*64 + i, k*64 + kc + kk]
-  __shared__ float Q[KC][CB];      // Q[kk][j] = M[k*64 + kc + kk, cb*64 + j]
+  __shared__ T P[KC][CB + 4];  // P[kk][i] = R[rb*64 + i, k*64 + kc + kk]
+  __shared__ T Q[KC][CB];      // Q[kk][j] = M[k*64 + kc + kk, cb*64 + j]
   const int l = blockIdx.y;
   const int rb = blockIdx.x / (nt - k), cb = k + blockIdx.x % (nt - k);
   const double* Pg = R + (int64_t)l * rstride + (int64_t)rb * CB * ldr + (int64_t)k * CB;
-  float* Ml = M + (int64_t)l * mstride;
-  const float* Qg = Ml + (int64_t)k * CB * ldm + (int64_t)cb * CB;
-  float* Sg = Ml + (int64_t)rb * CB * ldm + (int64_t)cb * CB;
+  T* Ml = M + (int64_t)l * mstride;
+  const T* Qg = Ml + (int64_t)k * CB * ldm + (int64_t)cb * CB;
+  T* Sg = Ml + (int64_t)rb * CB * ldm + (int64_t)cb * CB;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float acc[4][4] = {};
+  T acc[4][4] = {};
   for (int kc = 0; kc < CB; kc += KC) {
     for (int idx = threadIdx.x; idx < KC * CB; idx += blockDim.x) {
       const int i = idx / KC, kk = idx % KC;
-      P[kk][i] = (float)Pg[(int64_t)i * ldr + kc + kk];
+      P[kk][i] = (T)Pg[(int64_t)i * ldr + kc + kk];
       const int q = idx / CB, j = idx % CB;
       Q[q][j] = Qg[(int64_t)(kc + q) * ldm + j];
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
-      float pa[4], qb[4];
+      T pa[4], qb[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) pa[a] = P[kk][ty + 16 * a];
 #pragma unroll
@@ -367,7 +375,7 @@ __global__ void __launch_bounds__(256) k_tinv_update(const double* __restrict__ 
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], qb[b], acc[a][b]);
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(pa[a], qb[b], acc[a][b]);
     }
     __syncthreads();
   }
@@ -377,34 +385,34 @@ __global__ void __launch_bounds__(256) k_tinv_update(const double* __restrict__ 
     for (int b = 0; b < 4; ++b) Sg[(int64_t)(ty + 16 * a) * ldm + tx + 16 * b] -= acc[a][b];
 }
 
-// M_{i,cb} = M_{i,i} S_{i,cb} for cb > i, and Mt_{cb,i} = M_{i,cb}^T.
-__global__ void __launch_bounds__(256) k_tinv_final(float* __restrict__ M, float* __restrict__ Mt, int64_t ldm,
+// M_{i,cb} = M_{i,i} S_{i,cb} for cb > i (in place: every read of the tile
+// precedes the barrier, every write follows it), and Mt_{cb,i} = M_{i,cb}^T.
+template <typename T>
+__global__ void __launch_bounds__(256) k_tinv_final(T* __restrict__ M, T* __restrict__ Mt, int64_t ldm,
                                                     int64_t mstride, int i) {
-  __shared__ float D[CB][CB + 1];
-  __shared__ float S[CB][CB + 1];
+  __shared__ T D[CB][CB + 1];
   const int l = blockIdx.y, cb = i + 1 + blockIdx.x;
-  float* Ml = M + (int64_t)l * mstride;
-  const float* Dg = Ml + (int64_t)i * CB * ldm + (int64_t)i * CB;
-  float* Sg = Ml + (int64_t)i * CB * ldm + (int64_t)cb * CB;
+  T* Ml = M + (int64_t)l * mstride;
+  const T* Dg = Ml + (int64_t)i * CB * ldm + (int64_t)i * CB;
+  T* Sg = Ml + (int64_t)i * CB * ldm + (int64_t)cb * CB;
   for (int idx = threadIdx.x; idx < CB * CB; idx += blockDim.x) {
     const int r = idx / CB, c = idx % CB;
     D[r][c] = Dg[(int64_t)r * ldm + c];
-    S[r][c] = Sg[(int64_t)r * ldm + c];
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float acc[4][4] = {};
+  T acc[4][4] = {};
 #pragma unroll 8
   for (int kk = 0; kk < CB; ++kk) {
-    float da[4], sb[4];
+    T da[4], sb[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) da[a] = D[ty + 16 * a][kk];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) sb[b] = S[kk][tx + 16 * b];
+    for (int b = 0; b < 4; ++b) sb[b] = Sg[(int64_t)kk * ldm + tx + 16 * b];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(da[a], sb[b], acc[a][b]);
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(da[a], sb[b], acc[a][b]);
   }
   __syncthreads();
 #pragma unroll
@@ -412,31 +420,24 @@ __global__ void __launch_bounds__(256) k_tinv_final(float* __restrict__ M, float
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       Sg[(int64_t)(ty + 16 * a) * ldm + tx + 16 * b] = acc[a][b];
-      S[ty + 16 * a][tx + 16 * b] = acc[a][b];
+      D[ty + 16 * a][tx + 16 * b] = acc[a][b];
     }
   __syncthreads();
-  float* Mtg = Mt + (int64_t)l * mstride + (int64_t)cb * CB * ldm + (int64_t)i * CB;
+  T* Mtg = Mt + (int64_t)l * mstride + (int64_t)cb * CB * ldm + (int64_t)i * CB;
   for (int idx = threadIdx.x; idx < CB * CB; idx += blockDim.x) {
     const int r = idx / CB, c = idx % CB;
-    Mtg[(int64_t)r * ldm + c] = S[c][r];
+    Mtg[(int64_t)r * ldm + c] = D[c][r];
   }
 }
 
 // ------------------------------------------------------------------ TRMV --
-
-// out_k = M_l in_k for slot k (l = idx[k]): UPPER reads row i over columns
-// i..n-1 of M, otherwise (M = Mt, lower) over columns 0..i.  The slot's vector
-// sits in shared memory, zero past n; the rows are read as float4 (ldm and
-// mstride are multiples of 64 and the bases 256-byte aligned), starting at the
-// float4 that holds column i (upper) or ending at it (lower): the extra
-// entries lie in the diagonal block, where that triangle is stored as zeros.
-template <bool UPPER>
-__global__ void __launch_bounds__(256) k_trmv(int64_t n, const float* __restrict__ M, int64_t ldm, int64_t mstride,
-                                              const int* __restrict__ idx, const float* in, float* out, int64_t ldx) {
+template <typename T, bool UPPER>
+__global__ void __launch_bounds__(256) k_trmv(int64_t n, const T* __restrict__ M, int64_t ldm, int64_t mstride,
+                                              const int* __restrict__ idx, const T* in, T* out, int64_t ldx) {
   extern __shared__ float4 trmv_v4[];
   const int slot = blockIdx.y;
-  tiles::trmv_rows<UPPER>(n, M + (int64_t)(idx ? idx[slot] : slot) * mstride, ldm, in + (int64_t)slot * ldx,
-                          out + (int64_t)slot * ldx, (int64_t)blockIdx.x * tiles::kTrmvRows, trmv_v4);
+  tiles::trmv_rows<T, UPPER>(n, M + (int64_t)(idx ? idx[slot] : slot) * mstride, ldm, in + (int64_t)slot * ldx,
+                             out + (int64_t)slot * ldx, (int64_t)blockIdx.x * tiles::kTrmvRows, trmv_v4);
 }
 
 // ------------------------------------------------------------------ TRSV --
@@ -649,10 +650,42 @@ __global__ void __launch_bounds__(kTrsvThreads)
 
 // ----------------------------------------------------------- host side ----
 // C (c x c) = Y^T Y (Y r x c), upper triangle (and the diagonal tiles) only.
-tk_status gram_upper(const double* Y, int64_t r, int64_t c, double* C, cudaStream_t st) {
+// C[i][j] = sum_z partial[z][i][j] on the upper triangle (j >= i)
+__global__ void k_gram_reduce(const double* __restrict__ part, int splits, int64_t c, double* __restrict__ C) {
+  const int64_t total = c * c;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = k / c, j = k - i * c;
+    if (j < i) continue;
+    double acc = 0.0;
+    for (int z = 0; z < splits; ++z) acc += part[(int64_t)z * total + k];
+    C[k] = acc;
+  }
+}
+
+size_t gram_scratch_bytes(int64_t r, int64_t c) {
+  const int64_t nt = cdiv(c, 64), upper = nt * (nt + 1) / 2;
+  if (upper >= 152) return 0;
+  const int64_t splits = std::max<int64_t>(1, std::min<int64_t>(cdiv(2 * 152, upper), r / 64));
+  return splits > 1 ? sizeof(double) * (size_t)splits * c * c : 0;
+}
+
+tk_status gram_upper(const double* Y, int64_t r, int64_t c, double* C, void* scratch, size_t scratch_bytes,
+                     cudaStream_t st) {
   if (c <= 0) return TK_OK;
-  return launch_gemm<double, double, double, 64, 64, 16, 4, 4>(true, false, c, c, r, Y, c, Y, c, C, c, 1.0, nullptr,
-                                                                nullptr, 0, 1, nullptr, st, true);
+  // few output tiles (a small n): split the sum over the r rows of Y
+  const int64_t total = c * c;
+  const size_t want = gram_scratch_bytes(r, c);
+  const int splits = (scratch && want > 0 && scratch_bytes >= want) ? (int)(want / (sizeof(double) * total)) : 1;
+  if (splits < 2) {
+    return launch_gemm<double, double, double, 64, 64, 16, 4, 4>(true, false, c, c, r, Y, c, Y, c, C, c, 1.0,
+                                                                  nullptr, nullptr, 0, 1, nullptr, st, true);
+  }
+  double* part = static_cast<double*>(scratch);
+  TK_TRY((launch_gemm<double, double, double, 64, 64, 16, 4, 4>(true, false, c, c, r, Y, c, Y, c, nullptr, 0, 1.0,
+                                                                 nullptr, nullptr, 0, splits, part, st, true)));
+  k_gram_reduce<<<(unsigned)std::min<int64_t>(cdiv(total, 256), 152 * 8), 256, 0, st>>>(part, splits, c, C);
+  TK_LAUNCH_CHECK();
+  return TK_OK;
 }
 
 template <typename TA, typename TB, typename TC>
@@ -666,7 +699,7 @@ tk_status gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const 
 int splitk_count(int64_t M, int64_t N, int64_t K) {
   int64_t tiles = cdiv(M, 32) * cdiv(N, 256);
   int64_t want = cdiv(152 * 4, std::max<int64_t>(tiles, 1));
-  int64_t maxs = std::max<int64_t>(1, K / 512);
+  int64_t maxs = std::max<int64_t>(1, K / 64);  // at least 64 rows of K per split
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, maxs, 4096}));
 }
 
@@ -697,34 +730,41 @@ template tk_status gemm_splitk<float, double>(bool, bool, int64_t, int64_t, int6
 template tk_status gemm_splitk<double, float>(bool, bool, int64_t, int64_t, int64_t, const double*, int64_t,
                                               const float*, int64_t, double*, int, cudaStream_t);
 
-tk_status tri_inverse_f32(const double* R, int64_t n, int64_t ldr, int64_t rstride, int N, float* M, float* Mt,
-                          cudaStream_t st) {
+template <typename T>
+tk_status tri_inverse(const double* R, int64_t n, int64_t ldr, int64_t rstride, int N, T* M, T* Mt, cudaStream_t st) {
   if (N == 0 || n == 0) return TK_OK;
   const int64_t np = cdiv(n, CB) * CB;
   const int nt = (int)(np / CB);
-  TK_CUDA(cudaMemsetAsync(M, 0, sizeof(float) * (size_t)N * np * np, st));
-  k_tinv_diag<<<dim3((unsigned)nt, (unsigned)N), CB, 0, st>>>(R, ldr, rstride, M, Mt, np, np * np);
+  TK_CUDA(cudaMemsetAsync(M, 0, sizeof(T) * (size_t)N * np * np, st));
+  k_tinv_diag<T><<<dim3((unsigned)nt, (unsigned)N), CB, 0, st>>>(R, ldr, rstride, M, Mt, np, np * np);
   TK_LAUNCH_CHECK();
   for (int k = nt - 1; k >= 1; --k) {
-    k_tinv_update<<<dim3((unsigned)(k * (nt - k)), (unsigned)N), 256, 0, st>>>(R, ldr, rstride, M, np, np * np, k,
-                                                                              nt);
+    k_tinv_update<T><<<dim3((unsigned)(k * (nt - k)), (unsigned)N), 256, 0, st>>>(R, ldr, rstride, M, np, np * np,
+                                                                                 k, nt);
     TK_LAUNCH_CHECK();
-    k_tinv_final<<<dim3((unsigned)(nt - k), (unsigned)N), 256, 0, st>>>(M, Mt, np, np * np, k - 1);
+    k_tinv_final<T><<<dim3((unsigned)(nt - k), (unsigned)N), 256, 0, st>>>(M, Mt, np, np * np, k - 1);
     TK_LAUNCH_CHECK();
   }
   return TK_OK;
 }
+template tk_status tri_inverse<float>(const double*, int64_t, int64_t, int64_t, int, float*, float*, cudaStream_t);
+template tk_status tri_inverse<double>(const double*, int64_t, int64_t, int64_t, int, double*, double*, cudaStream_t);
 
-tk_status trmv_batched(bool transposed, int64_t n, const float* M, const float* Mt, int64_t ldm, int64_t mstride,
-                       const int* idx, const float* in, float* out, int64_t ldx, int count, cudaStream_t st) {
+template <typename T>
+tk_status trmv_batched(bool transposed, int64_t n, const T* M, const T* Mt, int64_t ldm, int64_t mstride,
+                       const int* idx, const T* in, T* out, int64_t ldx, int count, cudaStream_t st) {
   if (count == 0 || n == 0) return TK_OK;
   const dim3 grid((unsigned)cdiv(n, tiles::kTrmvRows), (unsigned)count);
-  const size_t smem = sizeof(float) * 4 * (size_t)cdiv(n, 4);
-  if (!transposed) k_trmv<true><<<grid, 256, smem, st>>>(n, M, ldm, mstride, idx, in, out, ldx);
-  else k_trmv<false><<<grid, 256, smem, st>>>(n, Mt, ldm, mstride, idx, in, out, ldx);
+  const size_t smem = tiles::trmv_smem_bytes<T>(n);
+  if (!transposed) k_trmv<T, true><<<grid, 256, smem, st>>>(n, M, ldm, mstride, idx, in, out, ldx);
+  else k_trmv<T, false><<<grid, 256, smem, st>>>(n, Mt, ldm, mstride, idx, in, out, ldx);
   TK_LAUNCH_CHECK();
   return TK_OK;
 }
+template tk_status trmv_batched<float>(bool, int64_t, const float*, const float*, int64_t, int64_t, const int*,
+                                       const float*, float*, int64_t, int, cudaStream_t);
+template tk_status trmv_batched<double>(bool, int64_t, const double*, const double*, int64_t, int64_t, const int*,
+                                        const double*, double*, int64_t, int, cudaStream_t);
 
 size_t chol_workspace(int64_t n, int N) {
   Arena a;

@@ -268,35 +268,60 @@ __device__ __forceinline__ void gemm_lm_tile(LmSmem<BM>& sm, bool vec, int64_t M
 // ---------------------------------------------------------------------------
 // Triangular matrix-vector rows: out[i] = M[i, :] x for rows
 // i0 <= i < min(n, i0 + kTrmvRows), UPPER over columns i..n-1, else (the
-// stored transpose, lower) over 0..i.  The vector is staged in `v4`
-// (4*ceil(n/4) floats, zero past n); rows are read as float4 (row stride and
-// base 16-byte aligned), starting at the float4 that holds column i (upper)
-// or ending at it (lower): the extra entries lie in the 64-aligned diagonal
-// block, where that triangle is stored as zeros.  256 threads.
+// stored transpose, lower) over 0..i.  The vector is staged in shared memory
+// (rounded up to 16 bytes, zero past n); rows are read in 16-byte vectors
+// (row stride and base 16-byte aligned), starting at the vector that holds
+// column i (upper) or ending at it (lower): the extra entries lie in the
+// 64-aligned diagonal block, where that triangle is stored as zeros.  256 threads.
 constexpr int kTrmvRows = 64;  // rows per CTA (8 warps x 8 rows)
 
-template <bool UPPER>
-__device__ __forceinline__ void trmv_rows(int64_t n, const float* __restrict__ Ml, int64_t ldm, const float* x,
-                                          float* out, int64_t i0, float4* v4) {
-  float* v = reinterpret_cast<float*>(v4);
-  const int64_t n4 = cdiv(n, 4);
-  for (int64_t j = threadIdx.x; j < 4 * n4; j += blockDim.x) v[j] = j < n ? x[j] : 0.f;
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int W = 4;
+  __device__ static float dot(const float4& a, const float4& b, float acc) {
+    acc = fmaf(a.x, b.x, acc);
+    acc = fmaf(a.y, b.y, acc);
+    acc = fmaf(a.z, b.z, acc);
+    return fmaf(a.w, b.w, acc);
+  }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int W = 2;
+  __device__ static double dot(const double2& a, const double2& b, double acc) {
+    acc = fma(a.x, b.x, acc);
+    return fma(a.y, b.y, acc);
+  }
+};
+
+template <typename T>
+inline size_t trmv_smem_bytes(int64_t n) {
+  return sizeof(T) * (size_t)Vec16<T>::W * (size_t)cdiv(n, Vec16<T>::W);
+}
+
+template <typename T, bool UPPER>
+__device__ __forceinline__ void trmv_rows(int64_t n, const T* __restrict__ Ml, int64_t ldm, const T* x, T* out,
+                                          int64_t i0, void* smem) {
+  using V = typename Vec16<T>::type;
+  constexpr int W = Vec16<T>::W;
+  T* v = reinterpret_cast<T*>(smem);
+  const V* vv = reinterpret_cast<const V*>(smem);
+  const int64_t nv = cdiv(n, W);
+  for (int64_t j = threadIdx.x; j < W * nv; j += blockDim.x) v[j] = j < n ? x[j] : T(0);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int q = 0; q < kTrmvRows / 8; ++q) {
     const int64_t i = i0 + w + 8 * q;
     if (i >= n) break;
-    const float4* row = reinterpret_cast<const float4*>(Ml + i * ldm);
-    const int64_t j0 = UPPER ? (i >> 2) : 0, j1 = UPPER ? n4 : (i >> 2) + 1;
-    float acc = 0.f;
+    const V* row = reinterpret_cast<const V*>(Ml + i * ldm);
+    const int64_t j0 = UPPER ? (i / W) : 0, j1 = UPPER ? nv : (i / W) + 1;
+    T acc = T(0);
 #pragma unroll 4
-    for (int64_t j = j0 + lane; j < j1; j += 32) {
-      const float4 a = __ldg(row + j), b = v4[j];
-      acc = fmaf(a.x, b.x, acc);
-      acc = fmaf(a.y, b.y, acc);
-      acc = fmaf(a.z, b.z, acc);
-      acc = fmaf(a.w, b.w, acc);
-    }
+    for (int64_t j = j0 + lane; j < j1; j += 32) acc = Vec16<T>::dot(__ldg(row + j), vv[j], acc);
     acc = warp_sum(acc);
     if (lane == 0) out[i] = acc;
   }

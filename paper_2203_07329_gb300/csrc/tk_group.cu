@@ -217,14 +217,14 @@ __global__ void __launch_bounds__(kThreads)
 template <bool UPPER>
 __global__ void __launch_bounds__(256)
     k_g_trmv(const GDesc* __restrict__ Dd, const GSlot* __restrict__ sl, int fsrc, int fdst) {
-  extern __shared__ float4 g_trmv_v4[];
+  extern __shared__ float4 g_trmv_v4[];  // 16-byte aligned staging
   const GSlot q = sl[blockIdx.y];
   const GDesc& d = Dd[q.p];
   const int64_t i0 = (int64_t)blockIdx.x * tiles::kTrmvRows;
   if (d.lowrank || i0 >= d.n) return;
   const float* Ml = (UPPER ? d.Mi : d.Mti) + (int64_t)d.slot_lam[q.k] * d.np * d.np;
-  tiles::trmv_rows<UPPER>(d.n, Ml, d.np, field(d, fsrc) + (int64_t)q.k * d.n, field(d, fdst) + (int64_t)q.k * d.n,
-                          i0, g_trmv_v4);
+  tiles::trmv_rows<float, UPPER>(d.n, Ml, d.np, field(d, fsrc) + (int64_t)q.k * d.n,
+                                 field(d, fdst) + (int64_t)q.k * d.n, i0, g_trmv_v4);
 }
 
 // Low-rank problems (Section 3.1): out = l^{-1/2} (x - V diag(S_l) V^T x),
@@ -543,7 +543,7 @@ tk_status launch_prec(const GState& S, bool transposed, const GSlot* sl, int nsl
   if (nsl == 0) return TK_OK;
   if (any_chol) {
     const dim3 grid((unsigned)cdiv(S.maxn, tiles::kTrmvRows), (unsigned)nsl);
-    const size_t smem = sizeof(float) * 4 * (size_t)cdiv(S.maxn, 4);
+    const size_t smem = tiles::trmv_smem_bytes<float>(S.maxn);
     if (!transposed) k_g_trmv<true><<<grid, 256, smem, st>>>(S.dd, sl, fsrc, fdst);
     else k_g_trmv<false><<<grid, 256, smem, st>>>(S.dd, sl, fsrc, fdst);
     TK_LAUNCH_CHECK();

@@ -190,21 +190,27 @@ tk_status gemm_splitk(bool transA, bool transB, int64_t M, int64_t N, int64_t K,
                       const TB* B, int64_t ldb, double* partial, int splits, cudaStream_t st);
 int splitk_count(int64_t M, int64_t N, int64_t K);
 // Gram matrix C = Y^T Y, upper triangle only (what the Cholesky reads).
-tk_status gram_upper(const double* Y, int64_t r, int64_t c, double* C, cudaStream_t st);
+// scratch (optional, gram_scratch_bytes(r, c)): split-K partials when the
+// upper triangle has few 64 x 64 tiles (a small n).
+size_t gram_scratch_bytes(int64_t r, int64_t c);
+tk_status gram_upper(const double* Y, int64_t r, int64_t c, double* C, void* scratch, size_t scratch_bytes,
+                     cudaStream_t st);
 
 size_t chol_workspace(int64_t n, int N);
 tk_status chol_shifted(const double* C, int64_t n, const double* lambdas_dev, int N, double* R, int64_t ldr,
                        int64_t rstride, int* info_dev, Arena& ar, cudaStream_t st);
 
-// M = R^-1 (upper) and Mt = M^T (lower) in float32 for N factors R (float64,
-// padded order np = ceil(n/64)*64, row stride ldr, matrix stride rstride);
-// M and Mt: N x np x np, row stride np.
-tk_status tri_inverse_f32(const double* R, int64_t n, int64_t ldr, int64_t rstride, int N, float* M, float* Mt,
-                          cudaStream_t st);
+// M = R^-1 (upper) and Mt = M^T (lower), arithmetic in T, for N factors R
+// (float64, padded order np = ceil(n/64)*64, row stride ldr, matrix stride
+// rstride); M and Mt: N x np x np, row stride np.
+template <typename T>
+tk_status tri_inverse(const double* R, int64_t n, int64_t ldr, int64_t rstride, int N, T* M, T* Mt, cudaStream_t st);
 // out_k = M_l in_k (or Mt_l in_k when transposed) for slots k < count,
-// l = idx[k] (idx null: l = k); in/out vectors of length n at stride ldx.
-tk_status trmv_batched(bool transposed, int64_t n, const float* M, const float* Mt, int64_t ldm, int64_t mstride,
-                       const int* idx, const float* in, float* out, int64_t ldx, int count, cudaStream_t st);
+// l = idx[k] (idx null: l = k); in/out vectors of length n at stride ldx
+// (out must not overlap in).
+template <typename T>
+tk_status trmv_batched(bool transposed, int64_t n, const T* M, const T* Mt, int64_t ldm, int64_t mstride,
+                       const int* idx, const T* in, T* out, int64_t ldx, int count, cudaStream_t st);
 
 // Batched triangular solves on slots: vector of slot j is X + j*ldx (length
 // n); its factor is R + idx[j]*rstride (row stride ldr, upper triangular).

@@ -332,12 +332,10 @@ tk_status Lsqr<T>::apply_prec(bool transposed, const T* in, T* out, int count, i
   if (prec_kind == TK_PRECOND_CHOL) {
     int tok = prof_begin(TK_PHASE_PRECOND, st);
     tk_status r;
-    if constexpr (std::is_same<T, float>::value) {
-      if (Mi) {
-        r = trmv_batched(transposed, len, Mi, Mti, ldm, mstride, slot_lam, in, out, len, count, st);
-        prof_end(tok, st, (double)count * len * len, es * count * (len * (len + 1) / 2 + 2 * len));
-        return r;
-      }
+    if (Mi) {
+      r = trmv_batched<T>(transposed, len, Mi, Mti, ldm, mstride, slot_lam, in, out, len, count, st);
+      prof_end(tok, st, (double)count * len * len, es * count * (len * (len + 1) / 2 + 2 * len));
+      return r;
     }
     r = trsv_batched<T, T>(transposed, len, R, ldr, rstride, slot_lam, in, out, len, count, trsv_p, st);
     prof_end(tok, st, (double)count * len * len, es * count * (len * (len + 1) / 2 + 2 * len));
@@ -448,14 +446,8 @@ tk_status Lsqr<T>::run(const double* b, int64_t ldbt, const double* bbot, int64_
         for (int k = 0; k < nr; ++k) hlam[k] = hsc[ret[k]].lam_idx;
         TK_CUDA(cudaMemcpyAsync(d_src, hlam.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
         if (prec_kind == TK_PRECOND_CHOL) {
-          bool done = false;
-          if constexpr (std::is_same<T, float>::value) {
-            if (Mi) {
-              TK_TRY(trmv_batched(false, n, Mi, Mti, ldm, mstride, d_src, Vraw, xtmp, n, nr, st));
-              done = true;
-            }
-          }
-          if (!done) TK_TRY((trsv_batched<T, T>(false, n, R, ldr, rstride, d_src, Vraw, xtmp, n, nr, trsv_p, st)));
+          if (Mi) TK_TRY(trmv_batched<T>(false, n, Mi, Mti, ldm, mstride, d_src, Vraw, xtmp, n, nr, st));
+          else TK_TRY((trsv_batched<T, T>(false, n, R, ldr, rstride, d_src, Vraw, xtmp, n, nr, trsv_p, st)));
         } else {
           TK_TRY(lr_apply<T>(nr, n, lr_s, lrV, lrS, d_src, lam_all, Vraw, xtmp, lr_tmp, lr_inv, st));
         }

@@ -129,8 +129,8 @@ struct Lsqr {
   tk_precond prec_kind = TK_PRECOND_CHOL;
   const T* R = nullptr;
   int64_t ldr = 0, rstride = 0;
-  // explicit inverse (float32 engine): Mi = R^-1, Mti = R^-T, row stride ldm,
-  // matrix stride mstride; when set it replaces the substitutions with R
+  // explicit inverse: Mi = R^-1, Mti = R^-T (row stride ldm, matrix stride
+  // mstride); when set it replaces the substitutions with R (overdetermined)
   const T* Mi = nullptr;
   const T* Mti = nullptr;
   int64_t ldm = 0, mstride = 0;

@@ -171,17 +171,42 @@ tk_status srht_impl(const TIn* A, int64_t L, int64_t cols, int64_t ld, uint64_t 
   return TK_OK;
 }
 
+// Split count of the float64 Gaussian sketch product Y (s x cols) = G A:
+// enough 64 x 64 output tiles x splits for two CTAs per SM, >= 256 rows each.
+int gauss_splits(int64_t L, int64_t cols, int64_t s) {
+  const int64_t tiles = cdiv(s, 64) * cdiv(cols, 64);
+  if (tiles >= 152) return 1;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(2 * 152, tiles), L / 256));
+}
+
+// Y[k] = sum_z part[z][k]
+__global__ void k_sum_planes(const double* __restrict__ part, int splits, int64_t total, double* __restrict__ Y) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < splits; ++z) acc += part[(int64_t)z * total + k];
+    Y[k] = acc;
+  }
+}
+
 template <typename TIn, typename TC>
 tk_status gauss_impl(const TIn* A, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s, double* Y,
                      Arena& ar, cudaStream_t st) {
   TC* G = ar.take<TC>((size_t)s * (size_t)L);
   TC* Yc = std::is_same<TC, double>::value ? nullptr : ar.take<TC>((size_t)s * (size_t)cols);
+  const int splits = std::is_same<TC, double>::value ? gauss_splits(L, cols, s) : 1;
+  double* part = splits > 1 ? ar.take<double>((size_t)splits * s * cols) : nullptr;
   if (!ar.ok()) return TK_ENOMEM;
   if (s == 0 || cols == 0) return TK_OK;
   k_gauss_fill<TC><<<grid_for(s * L, 256), 256, 0, st>>>(seed, s, L, 1.0 / sqrt((double)s), G);
   TK_LAUNCH_CHECK();
   if (std::is_same<TC, double>::value) {
-    TK_TRY((gemm<TC, TIn, double>(false, false, s, cols, L, G, L, A, ld, Y, cols, 1.0, nullptr, nullptr, 0, st)));
+    if (splits > 1) {  // few output tiles: split the sum over the long axis, then add the planes
+      TK_TRY((gemm_splitk<TC, TIn>(false, false, s, cols, L, G, L, A, ld, part, splits, st)));
+      k_sum_planes<<<grid_for(s * cols, 256), 256, 0, st>>>(part, splits, s * cols, Y);
+      TK_LAUNCH_CHECK();
+    } else {
+      TK_TRY((gemm<TC, TIn, double>(false, false, s, cols, L, G, L, A, ld, Y, cols, 1.0, nullptr, nullptr, 0, st)));
+    }
   } else {
     TK_TRY((gemm<TC, TIn, TC>(false, false, s, cols, L, G, L, A, ld, Yc, cols, 1.0, nullptr, nullptr, 0, st)));
     k_f32_to_f64<<<grid_for(s * cols, 256), 256, 0, st>>>(reinterpret_cast<const float*>(Yc), Y, s * cols);
@@ -207,6 +232,8 @@ size_t gauss_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s) {
   size_t es = dt == TK_F64 ? 8 : 4;
   a.take<char>((size_t)s * (size_t)L * es);
   if (dt != TK_F64) a.take<char>((size_t)s * (size_t)cols * es);
+  const int splits = dt == TK_F64 ? gauss_splits(L, cols, s) : 1;
+  if (splits > 1) a.take<double>((size_t)splits * s * cols);
   return a.used + 512;
 }
 
