@@ -262,6 +262,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core LSQR comparison step")
     ap.add_argument("--no-uneven", action="store_true", help="skip the 256 uneven problems batch")
+    ap.add_argument("--no-small", action="store_true", help="skip the 4096 x 256 workload")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="where the synthetic problem is generated (cpu for profiler runs)")
     args = ap.parse_args()
@@ -399,7 +400,8 @@ def main():
         extra["speedup_mixed_vs_fp64_batched"] = value / ws / extra["fp64_batched"]["value"]
 
     # ---- the small 4096 x 256 workload (fits in L2: launch/latency-bound)
-    extra["small_4096x256_f64"] = small_workload_step(tk, datagen, stream, barrier)
+    if not args.no_small:
+        extra["small_4096x256_f64"] = small_workload_step(tk, datagen, stream, barrier)
 
     # ---- many independent problems of uneven size in one batched call (one step)
     if not args.no_uneven:

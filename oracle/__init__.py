@@ -71,6 +71,7 @@ def lib():
                 "orc_lsqr_over_chol": (_int, [_p, _i64, _i64, _i64, _p, _d, _p, _d, _int, _p, _p]),
                 "orc_lsqr_over_lr": (_int, [_p, _i64, _i64, _i64, _p, _d, _p, _i64, _p, _i64, _d, _int, _p, _p]),
                 "orc_lsqr_under_chol": (_int, [_p, _i64, _i64, _i64, _p, _d, _p, _d, _int, _p, _p]),
+                "orc_lsqr_under_lr": (_int, [_p, _i64, _i64, _i64, _p, _d, _p, _i64, _p, _i64, _d, _int, _p, _p]),
                 "orc_jacobi_svd": (_int, [_p, _i64, _i64, _d, _int, _p, _p]),
                 "orc_sd_estimate": (_d, [_p, _i64, _d]),
                 "orc_truncation": (_i64, [_d, _d, _i64]),
@@ -78,6 +79,8 @@ def lib():
                 "orc_alg1": (_int, [_p, _i64, _i64, _i64, _p, _p, _int, _int, _i64, _u64, _d, _int, _p, _p, _p]),
                 "orc_alg2": (_int, [_p, _i64, _i64, _i64, _p, _p, _int, _int, _i64, _u64, _d, _int, _p, _p, _p]),
                 "orc_alg3": (_int, [_p, _i64, _i64, _i64, _p, _p, _int, _int, _i64, _d, _u64, _d, _int, _p, _p, _p,
+                                    _p, _p]),
+                "orc_alg4": (_int, [_p, _i64, _i64, _i64, _p, _p, _int, _int, _i64, _d, _u64, _d, _int, _p, _p, _p,
                                     _p, _p]),
                 "orc_two_prod": (None, [_d, _d, _p, _p]),
                 "orc_two_sum": (None, [_d, _d, _p, _p]),
@@ -303,6 +306,19 @@ def lr_diag(sigma, si: int, lam: float) -> np.ndarray:
     return S[:si]
 
 
+def lsqr_under_lr(A, b, lam: float, U, S, tol: float, maxiter: int):
+    """Section 3.2 / Algorithm 4 step 8: min-norm LSQR with R^-T = l^{-1/2}(I - U S U^T)."""
+    A, m, n, lda = _dims(A)
+    b = _f64(b)
+    U = _f64(U)
+    S = _f64(S)
+    x = np.zeros(n)
+    ist = C.c_int(0)
+    it = lib().orc_lsqr_under_lr(_ptr(A), m, n, lda, _ptr(b), lam, _ptr(U), U.shape[1], _ptr(S), S.shape[0], tol,
+                                 maxiter, _ptr(x), C.byref(ist))
+    return x, int(it), int(ist.value)
+
+
 # ------------------------------------------------------- whole algorithms --
 def alg1(A, b, lambdas, sketch_kind: int, s: int, seed: int, tol: float, maxiter: int):
     """Algorithm 1 (overdetermined, Cholesky).  Returns (X n x N, iters, istops, rc)."""
@@ -401,3 +417,19 @@ def ref_ridge_under(A, b, lam: float, refine: int = 2) -> np.ndarray:
     U, sig, Vt = np.linalg.svd(A, full_matrices=False)
     x0 = Vt.T @ ((sig / (sig * sig + lam)) * (U.T @ b))
     return ref_ridge_refine(A, b, lam, Vt.T, sig, x0, steps=refine)
+
+
+def alg4(A, b, lambdas, sketch_kind: int, s: int, alpha: float, seed: int, tol: float, maxiter: int):
+    """Algorithm 4 (underdetermined, low rank).  Returns (X n x N, iters, istops, s_i, sigma(Y))."""
+    A, m, n, lda = _dims(A)
+    b = _f64(b)
+    lam = _f64(lambdas)
+    N = lam.shape[0]
+    X = np.zeros((n, N))
+    it = np.zeros(N, dtype=np.int32)
+    st = np.zeros(N, dtype=np.int32)
+    si = np.zeros(N, dtype=np.int64)
+    sig = np.zeros(s)
+    lib().orc_alg4(_ptr(A), m, n, lda, _ptr(b), _ptr(lam), N, sketch_kind, s, alpha, seed, tol, maxiter, _ptr(X),
+                   _ptr(it), _ptr(st), _ptr(si), _ptr(sig))
+    return X, it, st, si, sig

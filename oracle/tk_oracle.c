@@ -400,17 +400,20 @@ typedef struct {
   const double* A; int64_t m, n, lda;
   double sqrtl;
   const double* R;     /* Cholesky variants: upper triangular, order n (over) or m (under) */
-  const double* V;     /* low-rank variant: n x s_i basis (row-major, leading dim ldv) */
+  const double* V;     /* low-rank variants: n x s_i (over) or m x s_i (under) basis, row-major, ld ldv */
   const double* S;     /* low-rank diagonal */
   int64_t si, ldv;
   double inv_sqrtl;
   double* tmp;         /* scratch, length max(m, n) */
   double* tmp2;
+  int under_lr;        /* low-rank preconditioner of the underdetermined form */
 } precond_ctx;
 
-/* Low-rank inverse of eq. (RinvOver): out = l^{-1/2} (in - V S V^T in). */
+/* Low-rank inverse of eq. (RinvOver): out = l^{-1/2} (in - V S V^T in); the
+ * vectors have length n (overdetermined) or m (underdetermined, Section 3.2:
+ * R^-T = l^{-1/2} (I_m - U S U^T), symmetric). */
 static void lr_apply(const precond_ctx* c, const double* in, double* out) {
-  int64_t n = c->n;
+  const int64_t n = c->under_lr ? c->m : c->n;
   for (int64_t j = 0; j < n; ++j) out[j] = in[j];
   for (int64_t k = 0; k < c->si; ++k) {
     double dot = 0.0;
@@ -453,12 +456,14 @@ static void under_mv(const void* vc, const double* z, double* out) {
     for (int64_t j = 0; j < c->n; ++j) acc += c->A[i * c->lda + j] * z[j];
     p[i] = acc;
   }
-  orc_trsv_upper_t(c->R, c->m, p, out);
+  if (c->R) orc_trsv_upper_t(c->R, c->m, p, out);
+  else lr_apply(c, p, out);
 }
 static void under_rmv(const void* vc, const double* u, double* out) {
   const precond_ctx* c = (const precond_ctx*)vc;
   double* t = c->tmp;
-  orc_trsv_upper(c->R, c->m, u, t);
+  if (c->R) orc_trsv_upper(c->R, c->m, u, t);
+  else lr_apply(c, u, t); /* the low-rank R^-1 is symmetric */
   for (int64_t j = 0; j < c->n; ++j) out[j] = 0.0;
   for (int64_t i = 0; i < c->m; ++i)
     for (int64_t j = 0; j < c->n; ++j) out[j] += c->A[i * c->lda + j] * t[i];
@@ -541,6 +546,27 @@ ORC_API int orc_lsqr_under_chol(const double* A, int64_t m, int64_t n, int64_t l
   double* rb = (double*)malloc(sizeof(double) * (size_t)m);
   double* z = (double*)malloc(sizeof(double) * (size_t)(n + m));
   orc_trsv_upper_t(R, m, b, rb);
+  orc_op op = {m, n + m, under_mv, under_rmv, &c};
+  int it = orc_lsqr(&op, rb, tol, tol, maxiter, z, istop);
+  for (int64_t j = 0; j < n; ++j) x[j] = z[j];
+  free(c.tmp); free(rb); free(z);
+  return it;
+}
+
+/* Underdetermined LSQR with the low-rank preconditioner of Section 3.2
+ * (Algorithm 4 step 8): R^-T = l^{-1/2} (I_m - U S U^T) with U (m x s_i, ld
+ * ldu); min-norm [x; y] of R^-T D [x; y] = R^-T b; x is the top n coordinates. */
+ORC_API int orc_lsqr_under_lr(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, double lambda,
+                              const double* U, int64_t ldu, const double* S, int64_t si, double tol, int maxiter,
+                              double* x, int* istop) {
+  precond_ctx c;
+  memset(&c, 0, sizeof c);
+  c.A = A; c.m = m; c.n = n; c.lda = lda; c.sqrtl = sqrt(lambda); c.inv_sqrtl = 1.0 / sqrt(lambda);
+  c.V = U; c.ldv = ldu; c.S = S; c.si = si; c.under_lr = 1;
+  c.tmp = (double*)malloc(sizeof(double) * (size_t)(m > n ? m : n));
+  double* rb = (double*)malloc(sizeof(double) * (size_t)m);
+  double* z = (double*)malloc(sizeof(double) * (size_t)(n + m));
+  lr_apply(&c, b, rb);
   orc_op op = {m, n + m, under_mv, under_rmv, &c};
   int it = orc_lsqr(&op, rb, tol, tol, maxiter, z, istop);
   for (int64_t j = 0; j < n; ++j) x[j] = z[j];
@@ -716,6 +742,38 @@ ORC_API int orc_alg3(const double* A, int64_t m, int64_t n, int64_t lda, const d
     for (int64_t j = 0; j < n; ++j) X_out[j * N + i] = x[j];
   }
   free(Y); free(sig); free(V); free(S); free(x);
+  return 0;
+}
+
+/* Algorithm 4 (underdetermined, low rank): Y = AX (m x s, step 3), the SVD
+ * [U, Sigma, ~] = svd(Y, 'econ') (step 4) taken as the one-sided Jacobi SVD of
+ * Y^T (its right singular vectors are U); for each lambda_i the sd estimate
+ * gives s_i (step 5), U_i, Sigma_i the leading s_i factors (6), S_i (7), and
+ * min-norm LSQR with R_i^-T = l_i^{-1/2}(I - U_i S_i U_i^T) (8) returns x (9). */
+ORC_API int orc_alg4(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, const double* lambdas,
+                     int N, int sketch_kind, int64_t s, double alpha, uint64_t seed, double tol, int maxiter,
+                     double* X_out, int* iters, int* istops, int64_t* si_out, double* sigma_out) {
+  double* Y = (double*)malloc(sizeof(double) * (size_t)(m * s));
+  double* Yt = (double*)malloc(sizeof(double) * (size_t)(s * m));
+  double* sig = (double*)malloc(sizeof(double) * (size_t)s);
+  double* U = (double*)malloc(sizeof(double) * (size_t)(m * s));
+  double* S = (double*)malloc(sizeof(double) * (size_t)s);
+  double* x = (double*)malloc(sizeof(double) * (size_t)n);
+  sketch_under(sketch_kind, A, m, n, lda, seed, s, Y);
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < s; ++j) Yt[j * m + i] = Y[i * s + j];
+  orc_jacobi_svd(Yt, s, m, 1e-15, 80, sig, U);
+  if (sigma_out)
+    for (int64_t j = 0; j < s; ++j) sigma_out[j] = sig[j];
+  for (int i = 0; i < N; ++i) {
+    double sd = orc_sd_estimate(sig, s, lambdas[i]);
+    int64_t si = orc_truncation(sd, alpha, s);
+    si_out[i] = si;
+    orc_lr_diag(sig, si, lambdas[i], S);
+    iters[i] = orc_lsqr_under_lr(A, m, n, lda, b, lambdas[i], U, s, S, si, tol, maxiter, x, &istops[i]);
+    for (int64_t j = 0; j < n; ++j) X_out[j * N + i] = x[j];
+  }
+  free(Y); free(Yt); free(sig); free(U); free(S); free(x);
   return 0;
 }
 

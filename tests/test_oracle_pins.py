@@ -304,6 +304,56 @@ def test_alg3_lowrank_reaches_ridge_solution(orc):
     assert np.all(np.diff(si) >= 0) and si.max() <= s
 
 
+def test_alg4_lowrank_underdetermined_reaches_ridge_solution(orc):
+    # Algorithm 4: the top block of the min-norm solution of the low-rank-preconditioned
+    # underdetermined system is the dual ridge solution A^T (A A^T + l I)^-1 b
+    m, n = 60, 400
+    sig = datagen.spectrum("exp", m, tau=5.0)
+    p = datagen.make_ridge_problem(m, n, sig, datagen.log_lambdas(4, 1e-6, 1.0), seed=19)
+    A, b = p.A.numpy(), p.b.numpy()
+    lams = p.lambdas.numpy()[::-1].copy()
+    s = 40
+    for kind in (0, 1):
+        X, it, st, si, sigY = orc.alg4(A, b, lams, kind, s, 2.0, 8, 1e-14, 400)
+        for i, lam in enumerate(lams):
+            x_dual = A.T @ np.linalg.solve(A @ A.T + lam * np.eye(m), b)
+            assert rel(X[:, i], x_dual) < 1e-9, (kind, lam, rel(X[:, i], x_dual))
+        assert np.all(np.diff(si) >= 0) and si.max() <= s
+        # sigma(Y) of Y = A X equals LAPACK's on the same sketch
+        Y = orc.sketch_under(A, kind, 8, s)
+        np.testing.assert_allclose(sigY, np.linalg.svd(Y, compute_uv=False), rtol=1e-11, atol=1e-14)
+
+
+def test_lemma_3_3_and_theorem_3_4_condition_bound(orc):
+    # Lemma 3.3: ||V_1||_F^2 = sd_l(A), V_1 the first n rows of the right singular vectors of
+    # D = [A sqrt(l) I_m]; Theorem 3.4: kappa(R^-T D) <= sqrt((1+eps)/(1-eps)) with
+    # eps = ||V_1^T X X^T V_1 - V_1^T V_1||, for R R^T = AX (AX)^T + l I_m (no truncation)
+    m, n, s = 40, 300, 30
+    sig = datagen.spectrum("exp", m, tau=4.0)
+    p = datagen.make_ridge_problem(m, n, sig, datagen.log_lambdas(2, 1e-3, 1e-1), seed=23)
+    A = p.A.numpy()
+    G = orc.draw_gauss(11, s, n)  # X = G^T (n x s)
+    Y = orc.gauss_under(A, 11, s)
+    np.testing.assert_allclose(Y, A @ G.T, atol=1e-13)
+    sY, U, _ = orc.jacobi_svd(Y.T)  # right singular vectors of Y^T = left singular vectors of Y
+    sA = np.linalg.svd(A, compute_uv=False)
+    checked = 0
+    for lam in [1e-1, 1e-2]:
+        D = np.hstack([A, math.sqrt(lam) * np.eye(m)])
+        V1 = np.linalg.svd(D, full_matrices=False)[2].T[:n]
+        assert abs(np.linalg.norm(V1) ** 2 - np.sum(sA ** 2 / (sA ** 2 + lam))) < 1e-11
+        eps = np.linalg.norm(V1.T @ G.T @ G @ V1 - V1.T @ V1, 2)
+        if eps >= 1:
+            continue
+        S = orc.lr_diag(sY, s, lam)
+        RinvT = (np.eye(m) - U @ np.diag(S) @ U.T) / math.sqrt(lam)
+        # R^-T is the inverse transpose of a root of Y Y^T + l I: (R^-T)^T R^-T = (Y Y^T + l I)^-1
+        np.testing.assert_allclose(RinvT.T @ RinvT, np.linalg.inv(Y @ Y.T + lam * np.eye(m)), rtol=1e-8, atol=1e-8)
+        assert np.linalg.cond(RinvT @ D) <= math.sqrt((1 + eps) / (1 - eps)) * (1 + 1e-8)
+        checked += 1
+    assert checked >= 1
+
+
 # ------------------------------------------------------------ low rank -----
 def test_jacobi_svd_against_lapack(orc):
     Y = RNG.standard_normal((9, 25)) @ np.diag(np.logspace(0, -6, 25))
