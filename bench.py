@@ -40,6 +40,14 @@ PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, 65536 x 2048 float64 case
+# (profiles/k_gemm_f64_refinement_65536x2048.md): (elements of A, bytes)
+MEASURED_TRAFFIC = {
+    "refine_residual64": (65536 * 2048, 1.094704e9 + 16.558592e6),
+    "refine_normal64": (65536 * 2048, 1.092536e9 + 34.980864e6),
+}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -415,8 +423,14 @@ def main():
     per_launch_ms = st["ms"] / max(st["launches"], 1)
     achieved = st["flops"] / (st["ms"] / 1e3) / 1e12 if st["ms"] > 0 else 0.0
     peak = PEAK_FP64_TFLOPS if name in fp64_phases else PEAK_FP32_TFLOPS
+    # DRAM bytes (read + write) of one launch from an ncu capture of the same kernel on a smaller
+    # case (profiles/), scaled by the elements of A it streams; None for kernels not captured
+    traffic = None
+    if name in MEASURED_TRAFFIC:
+        case_elems, case_bytes = MEASURED_TRAFFIC[name]
+        traffic = case_bytes * (m * n) / case_elems
     roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
+                "frac": achieved / peak if peak else None, "traffic": traffic,
                 "per_launch_ms": per_launch_ms, "launches": st["launches"],
                 "peak_source": "derived from unit counts and max clock (FP64 2 DFMA/clk/SM, FP32 128 FFMA/clk/SM)"}
     a_stream_gbs = None

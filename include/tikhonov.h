@@ -8,8 +8,8 @@
  * A, b, the lambda_i and a tolerance in; x_{lambda_i} and iteration counts out.
  * A is sketched once (Section 2.1.1: SRHT or Gaussian embedding), a
  * preconditioner is formed per lambda_i from the partly exact sketch
- * (Algorithm 1 / 2: Cholesky of C + lambda_i I; Algorithm 3: the low-rank
- * Woodbury form of Section 3.1), and preconditioned LSQR runs for every lambda_i.
+ * (Algorithm 1 / 2: Cholesky of C + lambda_i I; Algorithms 3 / 4: the low-rank
+ * Woodbury form of Sections 3.1 / 3.2), and preconditioned LSQR runs for every lambda_i.
  *
  * Conventions shared by every call:
  *  - Matrices are row-major.  A is m x n with row stride lda >= n (elements).
@@ -25,7 +25,7 @@
  *    host before any launch (TK_EINVAL, nothing written).  TK_ECUDA reports a
  *    CUDA error; tk_last_error() returns its text.
  *  - m >= n selects the overdetermined algorithms (1 and 3); m < n selects the
- *    underdetermined Algorithm 2.
+ *    underdetermined ones (2 and 4).
  */
 #ifndef TIKHONOV_H
 #define TIKHONOV_H
@@ -72,8 +72,8 @@ typedef struct {
 typedef struct {
   tk_sketch sketch;       /* [SRHT] embedding of Section 2.1.1 */
   int64_t s;              /* sketch size; 0 = 4 * min(m, n) for Cholesky, see alpha for low rank [0] */
-  tk_precond precond;     /* [CHOL] Algorithm 1/2, or LOWRANK = Algorithm 3 */
-  double alpha;           /* [2] oversampling of Algorithm 3: s_i = alpha * ceil(sd_i) */
+  tk_precond precond;     /* [CHOL] Algorithm 1/2, or LOWRANK = Algorithm 3 (m >= n) / 4 (m < n, FP64) */
+  double alpha;           /* [2] oversampling of Algorithms 3/4: s_i = alpha * ceil(sd_i) */
   tk_precision precision; /* [FP64] or MIXED (FP32 LSQR + FP64 refinement) */
   double tol;             /* [1e-14] LSQR stopping tolerance (Paige-Saunders atol = btol) */
   int maxiter;            /* [500] LSQR iteration cap per lambda */
@@ -96,7 +96,7 @@ typedef struct {
   int iters;          /* LSQR iterations (summed over refinement steps for MIXED) */
   int refine_steps;   /* MIXED: corrections applied; FP64: 0 */
   int istop;          /* Paige-Saunders stop reason of the last LSQR run: 1 test 1, 2 test 2, 7 maxiter */
-  int64_t rank;       /* LOWRANK: truncation s_i of Algorithm 3 step 5; else 0 */
+  int64_t rank;       /* LOWRANK: truncation s_i of Algorithm 3 / 4 step 5; else 0 */
   double rnorm;       /* LSQR estimate of ||B x - b_hat|| (last run) */
   double arnorm;      /* LSQR estimate of ||M^T r|| (last run) */
   double ne_norm;     /* MIXED: ||A^T (A x - b) + lambda x|| in float64 at the last refinement check; else 0 */

@@ -87,7 +87,6 @@ tk_status make_plan(const tk_problem* p, int N, const tk_opts* o, Plan& P) {
   P.N = N;
   P.mixed = o->precision == TK_PREC_MIXED;
   P.lowrank = o->precond == TK_PRECOND_LOWRANK;
-  if (P.under && P.lowrank) return einval("the low-rank preconditioner is built for m >= n (Algorithm 3)");
   if (P.under && P.mixed) return einval("the mixed-precision form is built for m >= n");
   int64_t s = o->s;
   if (s == 0) s = P.lowrank ? P.c : std::min<int64_t>(4 * P.c, P.L);

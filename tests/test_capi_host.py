@@ -72,8 +72,10 @@ def test_bad_shapes_and_options_rejected(tk):
     assert L.tk_workspace_size(C.byref(_prob(tk, 100, 10)), 2, C.byref(o2), C.byref(out)) == tk.TK_EINVAL
     o3 = tk.opts_default(s=1000)  # SRHT sketch larger than the padded length 128
     assert L.tk_workspace_size(C.byref(_prob(tk, 100, 10)), 2, C.byref(o3), C.byref(out)) == tk.TK_EINVAL
-    o4 = tk.opts_default(precond=tk.TK_PRECOND_LOWRANK)
+    o4 = tk.opts_default(precond=tk.TK_PRECOND_LOWRANK, precision=tk.TK_PREC_MIXED)  # mixed: m >= n only
     assert L.tk_workspace_size(C.byref(_prob(tk, 10, 100)), 2, C.byref(o4), C.byref(out)) == tk.TK_EINVAL
+    o5 = tk.opts_default(precond=tk.TK_PRECOND_LOWRANK)  # Algorithm 4
+    assert L.tk_workspace_size(C.byref(_prob(tk, 10, 100)), 2, C.byref(o5), C.byref(out)) == tk.TK_OK
     assert L.tk_workspace_size(C.byref(_prob(tk, 100, 10)), 2, C.byref(o), C.byref(out)) == tk.TK_OK
     assert out.value > 100 * 10 * 8
 

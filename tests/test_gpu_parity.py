@@ -225,6 +225,30 @@ def test_alg2_underdetermined_matches_oracle(tk):
     assert np.all(np.abs(its - it_o) <= 2), (its, it_o)
 
 
+@pytest.mark.parametrize("sketch", ["gauss", "srht"])
+def test_alg4_lowrank_underdetermined_matches_oracle(tk, sketch):
+    # Algorithm 4: Y = A X (m x s), U from its SVD, R^-T = l^-1/2 (I - U S U^T), min-norm LSQR
+    m, n = 120, 3000
+    p = problem(m, n, kind="exp", tau=8.0, N=5, lam=(1e-6, 1.0))
+    lams = p.lambdas.numpy()[::-1].copy()
+    A, b = to_dev(p)
+    s = 64
+    kind = tk.TK_SKETCH_GAUSS if sketch == "gauss" else tk.TK_SKETCH_SRHT
+    o = tk.opts_default(sketch=kind, s=s, seed=6, precond=tk.TK_PRECOND_LOWRANK, alpha=2.0, tol=1e-14)
+    res = tk.tk_solve(A, b, lams, o)
+    X = res.X.cpu().numpy()
+    Ad, bd = p.A.numpy(), p.b.numpy()
+    for i, lam in enumerate(lams):
+        xr = oracle.ref_ridge_under(Ad, bd, float(lam))
+        assert rel(X[i], xr) < TOL_X, (lam, rel(X[i], xr), res.info[i])
+    okind = 1 if sketch == "gauss" else 0
+    Xo, it_o, st_o, si_o, sig_o = oracle.alg4(Ad, bd, lams, okind, s, 2.0, 6, 1e-14, 500)
+    ranks = np.array([r["rank"] for r in res.info])
+    assert np.all(ranks == si_o), (ranks, si_o)
+    its = np.array([r["iters"] for r in res.info])
+    assert np.all(np.abs(its - it_o) <= 2), (its, it_o)
+
+
 def test_alg3_lowrank_matches_oracle(tk):
     m, n = 3000, 120
     p = problem(m, n, kind="exp", tau=8.0, N=5, lam=(1e-6, 1.0))
