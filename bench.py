@@ -271,6 +271,7 @@ def main():
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core LSQR comparison step")
     ap.add_argument("--no-uneven", action="store_true", help="skip the 256 uneven problems batch")
     ap.add_argument("--no-small", action="store_true", help="skip the 4096 x 256 workload")
+    ap.add_argument("--no-tune", action="store_true", help="keep the fixed tile rules (no tk_autotune)")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="where the synthetic problem is generated (cpu for profiler runs)")
     args = ap.parse_args()
@@ -312,6 +313,14 @@ def main():
 
     def step(o, Xo=X):
         return tk.tk_solve(A, b, lams, o, work=work, X=Xo, stream=stream)
+
+    # measured tile shapes / split counts for this workload's products (outside the timed region)
+    t_tune = time.perf_counter()
+    tuned = 0
+    if not args.no_tune:
+        for o in (o_mixed, o_fp64):
+            tuned = tk.tk_autotune(A, b, N, o, work=work, stream=stream)
+    t_tune = time.perf_counter() - t_tune
 
     for _ in range(args.warmup):
         res = step(o_mixed)
@@ -476,6 +485,7 @@ def main():
                 "gpu_launches": int(launches), "clocks": clk,
                 "iters_mean": float(np.mean([q["iters"] for q in info_mixed])),
                 "refine_steps_max": int(max(q["refine_steps"] for q in info_mixed)),
+                "autotune": {"entries": tuned, "seconds": round(t_tune, 2)},
                 "peaks_source": peak_src}
         line.update(extra)
         print(json.dumps(line), flush=True)

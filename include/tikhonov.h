@@ -230,6 +230,25 @@ TK_API size_t tk_lowrank_ranks_workspace(int N);
 TK_API tk_status tk_lowrank_ranks(const double* sigma, int64_t s, const double* lambdas, int N, double alpha,
                                   double* sd, int64_t* ranks, void* work, size_t work_bytes, void* stream);
 
+/* tk_autotune -- measured tile shapes for the products of the LSQR and
+ * refinement passes (no counterpart in the paper: a tuning step of this
+ * library).  For the problem's shape and options it runs, on the workspace
+ * (tk_workspace_size() bytes, contents overwritten), every candidate tile
+ * shape of the lambda-row products and every candidate split count of the
+ * split-K products, for 1, 2, 4, ... and N active lambdas, times each with
+ * CUDA events on `stream`, and keeps the fastest in a process-wide table that
+ * every later solve of the same shapes uses (thread-safe).  A and b are read
+ * but not modified.  Synchronizes the stream.  Shapes never tuned keep the
+ * library's fixed rules.  tk_autotune_entries() = table size;
+ * tk_autotune_clear() empties it. */
+TK_API tk_status tk_autotune(const tk_problem* p, int N, const tk_opts* o, void* work, size_t work_bytes,
+                             void* stream);
+TK_API size_t tk_autotune_entries(void);
+TK_API void tk_autotune_clear(void);
+/* The table as text (one line per shape), NUL-terminated into buf (len bytes);
+ * returns the length the whole text needs, NUL included. */
+TK_API size_t tk_autotune_describe(char* buf, size_t len);
+
 /* ---- phase profiler (tracing) ----
  * When enabled, each instrumented launch is bracketed by CUDA events on its
  * stream and tagged with its algorithmic flops and bytes (the counts of the

@@ -584,14 +584,14 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
                                               B.ones, B.Rres, P.m, st)));
         prof_end(tok, st, fl, ea * P.m * P.n + 8.0 * (2.0 * cnt * P.m + cnt * P.n));
         tok = prof_begin(TK_PHASE_NE64, st);
+        const int sp = P.dt == TK_F64 ? splitk_tuned<double, double>(cnt, P.n, P.m, B.splits)
+                                      : splitk_tuned<double, float>(cnt, P.n, P.m, B.splits);
         if (P.dt == TK_F64)
-          TK_TRY((gemm_splitk<double, double>(false, false, cnt, P.n, P.m, B.Rres, P.m, A64, lda64, B.part, B.splits,
-                                              st)));
+          TK_TRY((gemm_splitk<double, double>(false, false, cnt, P.n, P.m, B.Rres, P.m, A64, lda64, B.part, sp, st)));
         else
-          TK_TRY((gemm_splitk<double, float>(false, false, cnt, P.n, P.m, B.Rres, P.m, A32, lda32, B.part, B.splits,
-                                             st)));
-        prof_end(tok, st, fl, ea * P.m * P.n + 8.0 * (cnt * P.m + (double)B.splits * cnt * P.n));
-        k_ne_finish<<<cnt, 256, 0, st>>>(B.part, B.splits, cnt, P.n, B.ids, B.lam, B.Xa, B.G, B.nrm);
+          TK_TRY((gemm_splitk<double, float>(false, false, cnt, P.n, P.m, B.Rres, P.m, A32, lda32, B.part, sp, st)));
+        prof_end(tok, st, fl, ea * P.m * P.n + 8.0 * (cnt * P.m + (double)sp * cnt * P.n));
+        k_ne_finish<<<cnt, 256, 0, st>>>(B.part, sp, cnt, P.n, B.ids, B.lam, B.Xa, B.G, B.nrm);
         TK_LAUNCH_CHECK();
         // correction: min ||B d - [0; g/sqrt(l)]||, whose normal equations are
         // (A^T A + l I) d = g; the right-hand side shrinks with the error of x.
@@ -899,6 +899,72 @@ TK_API tk_status tk_solve_batched(const tk_problem* ps, int P, const double* lam
   }
   return worst;
 }
+
+TK_API tk_status tk_autotune(const tk_problem* p, int N, const tk_opts* o, void* work, size_t work_bytes,
+                             void* stream) {
+  Plan P;
+  TK_TRY(make_plan(p, N, o, P));
+  if (N == 0) return TK_OK;
+  if (!p->A || !p->b) return einval("A and b must be non-NULL");
+  if (!work || work_bytes < plan_bytes(P)) {
+    set_error_msg("workspace smaller than tk_workspace_size()");
+    return TK_ENOMEM;
+  }
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  Bufs B;
+  carve(P, a, a, B);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int Nc = P.N_cap;
+  // the lambda-row counts a solve meets as lambdas retire: 1, 2, 4, ... and N
+  std::vector<int> Ms;
+  for (int q = 1; q < Nc; q *= 2) Ms.push_back(q);
+  Ms.push_back(Nc);
+  if (!P.mixed) {
+    if (P.under) return TK_OK;  // the underdetermined products keep the fixed rules
+    const double* A64 = (P.dt == TK_F64) ? (const double*)p->A : B.A64;
+    const int64_t lda = (P.dt == TK_F64) ? P.lda : P.n;
+    Lsqr<double>& e = B.e64;
+    for (int M : Ms) {
+      // U = T A^T (+ coef U)  and the split-K  G = U A
+      TK_TRY((tune_gemm<double, double, double>(false, true, M, P.m, P.n, e.Tt, P.n, A64, lda, e.Ut, P.m, 1.0,
+                                                nullptr, nullptr, 0, 1, nullptr, st)));
+      TK_TRY((tune_gemm<double, double, double>(false, false, M, P.n, P.m, e.Ut, P.m, A64, lda, nullptr, 0, 1.0,
+                                                nullptr, nullptr, 0, e.splits, e.part_g, st)));
+    }
+  } else {
+    k_fill<<<1, 256, 0, st>>>(B.ones, std::max(N, 1), 1.0);
+    TK_LAUNCH_CHECK();
+    const float* A32 = (P.dt == TK_F32) ? (const float*)p->A : B.A32;
+    const int64_t lda32 = (P.dt == TK_F32) ? P.lda : P.n;
+    Lsqr<float>& e = B.e32;
+    for (int M : Ms) {
+      // the float64 residual r = b - X A^T and the split-K A^T r
+      if (P.dt == TK_F64) {
+        TK_TRY((tune_gemm<double, double, double>(false, true, M, P.m, P.n, B.Xa, P.n, (const double*)p->A, P.lda,
+                                                  B.Rres, P.m, -1.0, B.ones, B.Rres, P.m, 1, nullptr, st)));
+        TK_TRY((tune_gemm<double, double, double>(false, false, M, P.n, P.m, B.Rres, P.m, (const double*)p->A, P.lda,
+                                                  nullptr, 0, 1.0, nullptr, nullptr, 0, B.splits, B.part, st)));
+      } else {
+        TK_TRY((tune_gemm<double, float, double>(false, true, M, P.m, P.n, B.Xa, P.n, A32, lda32, B.Rres, P.m, -1.0,
+                                                 B.ones, B.Rres, P.m, 1, nullptr, st)));
+        TK_TRY((tune_gemm<double, float, double>(false, false, M, P.n, P.m, B.Rres, P.m, A32, lda32, nullptr, 0, 1.0,
+                                                 nullptr, nullptr, 0, B.splits, B.part, st)));
+      }
+      // the split count of the float32 A^T U product
+      if (!P.lsqr_tc)
+        TK_TRY((tune_gemm<float, float, double>(false, false, M, P.n, P.m, e.Ut, P.m, A32, lda32, nullptr, 0, 1.0,
+                                                nullptr, nullptr, 0, e.splits, e.part_g, st)));
+    }
+  }
+  TK_CUDA(cudaStreamSynchronize(st));
+  return TK_OK;
+}
+
+TK_API size_t tk_autotune_entries(void) { return tune_size(); }
+TK_API void tk_autotune_clear(void) { tune_clear(); }
+TK_API size_t tk_autotune_describe(char* buf, size_t len) { return tune_describe(buf, len); }
 
 TK_API size_t tk_sketch_draw_workspace(int64_t mp) { return draw_workspace(mp > 0 ? mp : 1) + 1024; }
 

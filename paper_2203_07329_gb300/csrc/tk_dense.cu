@@ -10,6 +10,7 @@
 // pipe busy with enough resident warps, not to save bytes.
 #include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "tk_gemm_tiles.cuh"
 #include "tk_internal.cuh"
@@ -102,12 +103,46 @@ tk_status launch_gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K,
   return TK_OK;
 }
 
+// Candidate tile shapes of the generic kernel for the lambda-row products
+// (M <= 32 rows, double accumulation): the index the tuner records.
+constexpr int kTuneCfgs = 5;
+template <typename TA, typename TB, typename TC>
+tk_status launch_cfg(int cfg, bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda,
+                     const TB* B, int64_t ldb, TC* C, int64_t ldc, double alpha, const double* beta_row,
+                     const TC* Cin, int64_t ldcin, int splits, double* partial, cudaStream_t st) {
+#define TK_C(BM, BN, TM, TN)                                                                                    \
+  return launch_gemm<TA, TB, TC, BM, BN, 16, TM, TN>(transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, \
+                                                      beta_row, Cin, ldcin, splits, partial, st)
+  switch (cfg) {
+    case 0: TK_C(32, 128, 4, 4);
+    case 1: TK_C(32, 64, 4, 2);
+    case 2: TK_C(32, 32, 4, 1);
+    case 3: TK_C(8, 256, 1, 8);
+    default: TK_C(8, 64, 1, 2);
+  }
+#undef TK_C
+}
+
 template <typename TA, typename TB, typename TC>
 tk_status gemm_dispatch(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda,
                         const TB* B, int64_t ldb, TC* C, int64_t ldc, double alpha, const double* beta_row,
-                        const TC* Cin, int64_t ldcin, int splits, double* partial, cudaStream_t st) {
+                        const TC* Cin, int64_t ldcin, int splits, double* partial, cudaStream_t st,
+                        bool use_table = true) {
   if (M == 0 || N == 0) return TK_OK;
   constexpr bool f32 = std::is_same<TA, float>::value && std::is_same<TB, float>::value;
+  if constexpr (!f32) {
+    // a measured choice (tk_autotune) for this lambda-row shape
+    if (use_table && !transA && M <= 32) {
+      GemmKey key;
+      key.ta = dtype_code<TA>(); key.tb = dtype_code<TB>(); key.tc = dtype_code<TC>();
+      key.transA = 0; key.transB = transB ? 1 : 0; key.split = partial ? 1 : 0;
+      key.M = M; key.N = N; key.K = K;
+      TuneChoice ch;
+      if (tune_lookup(key, &ch) && ch.cfg >= 0)
+        return launch_cfg<TA, TB, TC>(ch.cfg, transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta_row, Cin,
+                                      ldcin, splits, partial, st);
+    }
+  }
   if constexpr (f32) {
     // the lambda-major products of LSQR (all active lambda in one tile)
     if (!transA && M <= 64 && N >= 256 && alpha == 1.0) {
@@ -702,6 +737,103 @@ int splitk_count(int64_t M, int64_t N, int64_t K) {
   int64_t maxs = std::max<int64_t>(1, K / 64);  // at least 64 rows of K per split
   return (int)std::max<int64_t>(1, std::min<int64_t>({want, maxs, 4096}));
 }
+
+template <typename TA, typename TB>
+int splitk_tuned(int64_t M, int64_t N, int64_t K, int cap) {
+  GemmKey key;
+  key.ta = dtype_code<TA>(); key.tb = dtype_code<TB>(); key.tc = 1;
+  key.split = 1;
+  key.M = M; key.N = N; key.K = K;
+  TuneChoice ch;
+  if (tune_lookup(key, &ch) && ch.splits > 0) return std::min(ch.splits, cap);
+  return cap;
+}
+template int splitk_tuned<double, double>(int64_t, int64_t, int64_t, int);
+template int splitk_tuned<double, float>(int64_t, int64_t, int64_t, int);
+template int splitk_tuned<float, float>(int64_t, int64_t, int64_t, int);
+
+template <typename TA, typename TB, typename TC>
+tk_status tune_gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
+                    int64_t ldb, TC* C, int64_t ldc, double alpha, const double* beta_row, const TC* Cin,
+                    int64_t ldcin, int split_cap, double* partial, cudaStream_t st) {
+  if (M == 0 || N == 0 || K == 0) return TK_OK;
+  constexpr bool f32 = std::is_same<TA, float>::value && std::is_same<TB, float>::value;
+  std::vector<int> cfgs;
+  if (!f32 && !transA && M <= 32) {
+    for (int c = 0; c < kTuneCfgs; ++c)
+      if (c < 3 || M <= 8) cfgs.push_back(c);
+  } else {
+    cfgs.push_back(-1);  // the fixed rule's tile (the lambda-major float32 kernel sizes its tile by M)
+  }
+  std::vector<int> sps{1};
+  if (partial) {
+    sps.assign(1, std::max(split_cap, 1));
+    for (int q = split_cap / 2; q >= 1 && sps.size() < 3; q /= 2) sps.push_back(q);
+  }
+  // candidates: (tile configuration, split count); index 0 is the fixed rule
+  std::vector<std::pair<int, int>> cand;
+  cand.push_back({-1, sps[0]});
+  for (int cfg : cfgs)
+    for (int sp : sps)
+      if (!(cfg == -1 && sp == sps[0])) cand.push_back({cfg, sp});
+  cudaEvent_t e0, e1;
+  TK_CUDA(cudaEventCreate(&e0));
+  TK_CUDA(cudaEventCreate(&e1));
+  std::vector<float> best(cand.size(), 1e30f);
+  tk_status err = TK_OK;
+  auto run = [&](int cfg, int sp) -> tk_status {
+    if (cfg >= 0) {
+      if constexpr (!f32)
+        return launch_cfg<TA, TB, TC>(cfg, transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta_row, Cin,
+                                      ldcin, sp, partial, st);
+    }
+    return gemm_dispatch<TA, TB, TC>(transA, transB, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta_row, Cin, ldcin,
+                                     sp, partial, st, false);
+  };
+  // three interleaved rounds over all candidates (clock drift hits every
+  // candidate alike); each candidate keeps its fastest of two launches
+  for (int round = 0; round < 3 && err == TK_OK; ++round) {
+    for (size_t c = 0; c < cand.size() && err == TK_OK; ++c) {
+      if (round == 0) err = run(cand[c].first, cand[c].second);  // warm-up
+      for (int r = 0; r < 2 && err == TK_OK; ++r) {
+        cudaEventRecord(e0, st);
+        err = run(cand[c].first, cand[c].second);
+        cudaEventRecord(e1, st);
+        if (err == TK_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          best[c] = std::min(best[c], ms);
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != TK_OK) return err;
+  // keep the fixed rule unless a candidate is at least 3 % faster
+  size_t win = 0;
+  for (size_t c = 1; c < cand.size(); ++c)
+    if (best[c] < best[win]) win = c;
+  if (best[win] > 0.97f * best[0]) win = 0;
+  TuneChoice bc;
+  bc.cfg = win == 0 ? -1 : cand[win].first;
+  bc.splits = partial ? cand[win].second : 0;
+  GemmKey key;
+  key.ta = dtype_code<TA>(); key.tb = dtype_code<TB>(); key.tc = dtype_code<TC>();
+  key.transA = transA ? 1 : 0; key.transB = transB ? 1 : 0; key.split = partial ? 1 : 0;
+  key.M = M; key.N = N; key.K = K;
+  tune_store(key, bc);
+  return TK_OK;
+}
+template tk_status tune_gemm<double, double, double>(bool, bool, int64_t, int64_t, int64_t, const double*, int64_t,
+                                                     const double*, int64_t, double*, int64_t, double, const double*,
+                                                     const double*, int64_t, int, double*, cudaStream_t);
+template tk_status tune_gemm<double, float, double>(bool, bool, int64_t, int64_t, int64_t, const double*, int64_t,
+                                                    const float*, int64_t, double*, int64_t, double, const double*,
+                                                    const double*, int64_t, int, double*, cudaStream_t);
+template tk_status tune_gemm<float, float, double>(bool, bool, int64_t, int64_t, int64_t, const float*, int64_t,
+                                                   const float*, int64_t, double*, int64_t, double, const double*,
+                                                   const double*, int64_t, int, double*, cudaStream_t);
 
 template <typename TA, typename TB>
 tk_status gemm_splitk(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda,

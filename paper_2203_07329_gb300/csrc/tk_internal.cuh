@@ -180,6 +180,27 @@ tk_status tc_lmaj_product(bool update, const float* X, int64_t rows, int64_t K, 
                           void* scratch, cudaStream_t st);
 tk_status tc_lmaj_check(void* scratch, int N, int64_t K, cudaStream_t st);
 
+// Measured GEMM choices (tk_tune.cu): key = operand types (0 float, 1
+// double), transposes, split-K or not, M (rounded up to a power of two), N, K.
+struct GemmKey {
+  int ta = 0, tb = 0, tc = 0, transA = 0, transB = 0, split = 0;
+  int64_t M = 0, N = 0, K = 0;
+};
+struct TuneChoice {
+  int cfg = -1;    // tile configuration index of the generic kernel (-1: the fixed rule)
+  int splits = 0;  // split count of a split-K product (0: the caller's)
+};
+int64_t tune_bucket(int64_t M);
+bool tune_lookup(GemmKey k, TuneChoice* out);
+void tune_store(GemmKey k, TuneChoice c);
+size_t tune_size();
+size_t tune_describe(char* buf, size_t len);
+void tune_clear();
+template <typename T>
+constexpr int dtype_code() {
+  return sizeof(T) == 8 ? 1 : 0;
+}
+
 // Dense kernels (tk_dense.cu)
 template <typename TA, typename TB, typename TC>
 tk_status gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
@@ -189,6 +210,16 @@ template <typename TA, typename TB>
 tk_status gemm_splitk(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda,
                       const TB* B, int64_t ldb, double* partial, int splits, cudaStream_t st);
 int splitk_count(int64_t M, int64_t N, int64_t K);
+// The split count a split-K product of this shape runs with: the measured one
+// (<= cap) when tk_autotune() recorded it, else cap (the buffer's capacity).
+template <typename TA, typename TB>
+int splitk_tuned(int64_t M, int64_t N, int64_t K, int cap);
+// Times the candidate tile shapes (and split counts <= split_cap when partial
+// is set) of one product shape on the stream and records the fastest.
+template <typename TA, typename TB, typename TC>
+tk_status tune_gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, const TA* A, int64_t lda, const TB* B,
+                    int64_t ldb, TC* C, int64_t ldc, double alpha, const double* beta_row, const TC* Cin,
+                    int64_t ldcin, int split_cap, double* partial, cudaStream_t st);
 // Gram matrix C = Y^T Y, upper triangle only (what the Cholesky reads).
 // scratch (optional, gram_scratch_bytes(r, c)): split-K partials when the
 // upper triangle has few 64 x 64 tiles (a small n).

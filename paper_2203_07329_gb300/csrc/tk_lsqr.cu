@@ -372,13 +372,15 @@ tk_status Lsqr<T>::prod_atu(const T* Uin, int count) {
   tk_status r;
   if constexpr (std::is_same<T, float>::value) {
     if (tc && AT) {
+      cur_splits = splits;
       r = tc_lmaj_product(false, AT, n, m, m, Uin, m, count, nullptr, 0, nullptr, part_g, splits, tc_scratch, st);
       prof_end(tok, st, 2.0 * count * m * n,
                (double)sizeof(T) * ((double)m * n + count * (double)m) + 8.0 * splits * count * n);
       return r;
     }
   }
-  r = gemm_splitk<T, T>(false, false, count, n, m, Uin, m, A, lda, part_g, splits, st);
+  cur_splits = splitk_tuned<T, T>(count, n, m, splits);
+  r = gemm_splitk<T, T>(false, false, count, n, m, Uin, m, A, lda, part_g, cur_splits, st);
   prof_end(tok, st, 2.0 * count * m * n,
            (double)sizeof(T) * ((double)m * n + count * (double)m) + 8.0 * splits * count * n);
   return r;
@@ -406,7 +408,7 @@ tk_status Lsqr<T>::run(const double* b, int64_t ldbt, const double* bbot, int64_
     k_over_init_beta<T><<<nact, kVecThreads, 0, st>>>(part_u, kSumChunks, Ub, n, sc);
     TK_LAUNCH_CHECK();
     TK_TRY(prod_atu(Ut, nact));
-    k_over_g<T><<<rows_grid(n, nact), 256, 0, st>>>(part_g, splits, nact, Ub, n, sc, Tt);
+    k_over_g<T><<<rows_grid(n, nact), 256, 0, st>>>(part_g, cur_splits, nact, Ub, n, sc, Tt);
     TK_LAUNCH_CHECK();
     TK_TRY(apply_prec(true, Tt, Vraw, nact, n));
   } else {
@@ -417,7 +419,7 @@ tk_status Lsqr<T>::run(const double* b, int64_t ldbt, const double* bbot, int64_
     TK_LAUNCH_CHECK();
     TK_TRY(apply_prec(false, Ut, Tt, nact, m));
     TK_TRY(prod_atu(Tt, nact));
-    k_under_vraw<T><<<rows_grid(nv, nact), 256, 0, st>>>(part_g, splits, nact, Tt, m, n, sc, Vraw);
+    k_under_vraw<T><<<rows_grid(nv, nact), 256, 0, st>>>(part_g, cur_splits, nact, Tt, m, n, sc, Vraw);
     TK_LAUNCH_CHECK();
   }
   k_vstep<T><<<nact, kVecThreads, 0, st>>>(Vraw, V, W, Y, nv, sc, atol, btol, maxiter, 1);
@@ -500,7 +502,7 @@ tk_status Lsqr<T>::run(const double* b, int64_t ldbt, const double* bbot, int64_
       k_over_beta<T><<<nact, kVecThreads, 0, st>>>(part_u, kSumChunks, Tt, Ub, n, sc);
       TK_LAUNCH_CHECK();
       TK_TRY(prod_atu(Ut, nact));
-      k_over_g<T><<<rows_grid(n, nact), 256, 0, st>>>(part_g, splits, nact, Ub, n, sc, Tt);
+      k_over_g<T><<<rows_grid(n, nact), 256, 0, st>>>(part_g, cur_splits, nact, Ub, n, sc, Tt);
       TK_LAUNCH_CHECK();
       TK_TRY(apply_prec(true, Tt, Vraw, nact, n));                                     // R^-T g
     } else {
@@ -512,7 +514,7 @@ tk_status Lsqr<T>::run(const double* b, int64_t ldbt, const double* bbot, int64_
       TK_LAUNCH_CHECK();
       TK_TRY(apply_prec(false, Ut, Tt, nact, m));
       TK_TRY(prod_atu(Tt, nact));
-      k_under_vraw<T><<<rows_grid(nv, nact), 256, 0, st>>>(part_g, splits, nact, Tt, m, n, sc, Vraw);
+      k_under_vraw<T><<<rows_grid(nv, nact), 256, 0, st>>>(part_g, cur_splits, nact, Tt, m, n, sc, Vraw);
       TK_LAUNCH_CHECK();
     }
     k_vstep<T><<<nact, kVecThreads, 0, st>>>(Vraw, V, W, Y, nv, sc, atol, btol, maxiter, 0);

@@ -144,7 +144,8 @@ struct Lsqr {
   cudaStream_t st = nullptr;
   // workspace
   int64_t nv = 0;
-  int splits = 1;
+  int splits = 1;      // split-K capacity of part_g
+  int cur_splits = 1;  // splits of the last A^T U product (the tuned count, <= splits)
   T *V = nullptr, *W = nullptr, *Y = nullptr, *Vraw = nullptr, *Ut = nullptr, *Tt = nullptr, *Ub = nullptr,
     *xtmp = nullptr, *lr_tmp = nullptr;
   double *part_u = nullptr, *part_g = nullptr, *coef_buf = nullptr, *lr_inv = nullptr, *trsv_p = nullptr;

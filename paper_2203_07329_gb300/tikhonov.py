@@ -92,6 +92,10 @@ def lib() -> C.CDLL:
             "tk_launch_count": (C.c_ulonglong, []),
             "tk_profile_enable": (INT, [INT]),
             "tk_profile_collect": (INT, [P]),
+            "tk_autotune": (INT, [P, INT, P, P, SZ, P]),
+            "tk_autotune_entries": (SZ, []),
+            "tk_autotune_clear": (None, []),
+            "tk_autotune_describe": (SZ, [C.c_char_p, SZ]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -319,3 +323,25 @@ def tk_profile_collect() -> dict:
 
 def tk_launch_count() -> int:
     return int(lib().tk_launch_count())
+
+
+def tk_autotune(A: torch.Tensor, b: torch.Tensor, N: int, opts: tk_opts, work=None, stream=None) -> int:
+    """Measure the tile shapes and split counts of this problem's LSQR / refinement
+    products (the table is process-wide); returns the number of table entries."""
+    prob = make_problem(A, b)
+    need = workspace_size(prob, N, opts)
+    if work is None or work.numel() < need:
+        work = _workspace(need, A.device)
+    _check(lib().tk_autotune(C.byref(prob), N, C.byref(opts), _ptr(work), work.numel(), _stream(stream)))
+    return int(lib().tk_autotune_entries())
+
+
+def tk_autotune_clear() -> None:
+    lib().tk_autotune_clear()
+
+
+def tk_autotune_describe() -> str:
+    n = int(lib().tk_autotune_describe(None, 0))
+    buf = C.create_string_buffer(n)
+    lib().tk_autotune_describe(buf, n)
+    return buf.value.decode()

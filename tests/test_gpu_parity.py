@@ -429,3 +429,26 @@ def test_mixed_tensor_core_lsqr_products(tk, m, n, N):
     it_tc = sum(q["iters"] for q in res.info)
     it_simt = sum(q["iters"] for q in res0.info)
     assert it_tc <= 1.3 * it_simt + 5, (it_tc, it_simt)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotuned_solve_matches_untuned(tk, precision):
+    # the tuner only changes tile shapes and split counts: the solution stays the same
+    p = problem(3000, 192, lo=1e-5, N=6, lam=(1e-6, 1.0))
+    lams = p.lambdas.numpy()
+    A, b = to_dev(p)
+    prec = tk.TK_PREC_FP64 if precision == "fp64" else tk.TK_PREC_MIXED
+    o = tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=768, seed=2, precision=prec, tol=1e-14)
+    tk.tk_autotune_clear()
+    X0 = tk.tk_solve(A, b, lams, o).X.cpu().numpy()
+    try:
+        entries = tk.tk_autotune(A, b, len(lams), o)
+        assert entries > 0
+        res = tk.tk_solve(A, b, lams, o)
+    finally:
+        tk.tk_autotune_clear()
+    X1 = res.X.cpu().numpy()
+    Xr = ref_over(p, lams)
+    for i in range(len(lams)):
+        assert rel(X1[i], Xr[i]) < TOL_X, (lams[i], rel(X1[i], Xr[i]))
+        assert rel(X1[i], X0[i]) < 1e-11
