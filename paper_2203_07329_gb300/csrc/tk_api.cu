@@ -620,11 +620,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
         q.refine_steps += 1;
         if (round > 0) q.ne_norm = hn[3 * k];
         const double dn = hn[3 * k + 1], xn = hn[3 * k + 2];
-        // converged: the correction is below refine_tol ||x||, or it stopped
-        // halving (x sits at the float64 floor of the residual; more passes
-        // only add rounding noise)
-        const bool stalled = round >= 2 && dn > 0.5 * prev_dn[act[k]];
-        const bool done = (dn <= P.o.refine_tol * xn) || stalled || !std::isfinite(dn);
+        const bool done = refine_done(round, dn, prev_dn[act[k]], xn, P.o.refine_tol);
         prev_dn[act[k]] = dn;
         if (!done) next.push_back(act[k]);
       }

@@ -591,20 +591,29 @@ tk_status group_solve_mixed(std::vector<GroupProblem>& g, int N, void* work, siz
   TK_CUDA(cudaMemcpyAsync(S.dd, S.hd.data(), sizeof(GDesc) * P, cudaMemcpyHostToDevice, st));
   k_g_fill<<<1, 64, 0, st>>>(S.ones, kGroupMaxLambda, 1.0);
   TK_LAUNCH_CHECK();
-  // static tile lists of the float32 products
-  {
-    std::vector<GTile> aw, atu;
+  // tile lists of the float32 products over the problems that still have
+  // active slots (rebuilt when that set shrinks by a quarter: a retired
+  // problem's tiles would only launch CTAs that exit at once)
+  std::vector<GTile> t_aw, t_atu;
+  int tiled_problems = 0;
+  auto build_tiles = [&](const std::vector<int>& live) -> tk_status {
+    t_aw.clear();
+    t_atu.clear();
+    tiled_problems = 0;
     for (int p = 0; p < P; ++p) {
-      for (int64_t n0 = 0; n0 < g[p].m; n0 += tiles::LM_BN) aw.push_back(GTile{p, 0, 0, 0, n0});
+      if (!live[p]) continue;
+      ++tiled_problems;
+      for (int64_t n0 = 0; n0 < g[p].m; n0 += tiles::LM_BN) t_aw.push_back(GTile{p, 0, 0, 0, n0});
       for (int64_t n0 = 0; n0 < g[p].n; n0 += tiles::LM_BN)
-        for (int z = 0; z < S.hd[p].splits; ++z) atu.push_back(GTile{p, z, 0, 0, n0});
+        for (int z = 0; z < S.hd[p].splits; ++z) t_atu.push_back(GTile{p, z, 0, 0, n0});
     }
-    S.n_aw = (int)aw.size();
-    S.n_atu = (int)atu.size();
-    TK_CUDA(cudaMemcpyAsync(S.t_aw, aw.data(), sizeof(GTile) * aw.size(), cudaMemcpyHostToDevice, st));
-    TK_CUDA(cudaMemcpyAsync(S.t_atu, atu.data(), sizeof(GTile) * atu.size(), cudaMemcpyHostToDevice, st));
-    TK_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
-  }
+    S.n_aw = (int)t_aw.size();
+    S.n_atu = (int)t_atu.size();
+    if (S.n_aw) TK_CUDA(cudaMemcpyAsync(S.t_aw, t_aw.data(), sizeof(GTile) * t_aw.size(), cudaMemcpyHostToDevice, st));
+    if (S.n_atu)
+      TK_CUDA(cudaMemcpyAsync(S.t_atu, t_atu.data(), sizeof(GTile) * t_atu.size(), cudaMemcpyHostToDevice, st));
+    return TK_OK;
+  };
   std::vector<std::vector<int>> act(P);
   std::vector<std::vector<double>> prev_dn(P, std::vector<double>(N, INFINITY));
   for (int p = 0; p < P; ++p) act[p] = g[p].ok_ids;
@@ -688,6 +697,11 @@ tk_status group_solve_mixed(std::vector<GroupProblem>& g, int N, void* work, siz
       mirror[p].assign(act[p].begin(), act[p].end());
     }
     TK_CUDA(cudaMemcpyAsync(S.nact, hnact.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+    {
+      std::vector<int> live(P);
+      for (int p = 0; p < P; ++p) live[p] = hnact[p] > 0;
+      TK_TRY(build_tiles(live));
+    }
     sl = rl;
     int nsl = nrl;
     k_g_init<<<chunk_grid(std::max<int64_t>(S.maxn, 1 << 14), nsl), 256, 0, st>>>(S.dd, S.rnd, round == 0);
@@ -784,6 +798,12 @@ tk_status group_solve_mixed(std::vector<GroupProblem>& g, int N, void* work, siz
         nsl = (int)sl.size();
         TK_CUDA(cudaMemcpyAsync(S.nact, hnact.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
         if (nsl > 0) TK_CUDA(cudaMemcpyAsync(S.slots, sl.data(), sizeof(GSlot) * nsl, cudaMemcpyHostToDevice, st));
+        {
+          std::vector<int> live(P);
+          int nlive = 0;
+          for (int p = 0; p < P; ++p) nlive += (live[p] = hnact[p] > 0);
+          if (nlive > 0 && 4 * nlive <= 3 * tiled_problems) TK_TRY(build_tiles(live));
+        }
         TK_CUDA(cudaStreamSynchronize(st));  // host lists are reused
       }
       if (nsl == 0) break;
@@ -823,10 +843,7 @@ tk_status group_solve_mixed(std::vector<GroupProblem>& g, int N, void* work, siz
         qi.refine_steps += 1;
         if (round > 0) qi.ne_norm = hn[3 * q];
         const double dn = hn[3 * q + 1], xn = hn[3 * q + 2];
-        // converged: the correction is below refine_tol ||x||, or it stopped
-        // halving (x sits at the float64 floor of the residual)
-        const bool stalled = round >= 2 && dn > 0.5 * prev_dn[p][l];
-        const bool done = (dn <= g[p].refine_tol * xn) || stalled || !std::isfinite(dn);
+        const bool done = refine_done(round, dn, prev_dn[p][l], xn, g[p].refine_tol);
         prev_dn[p][l] = dn;
         if (!done) next.push_back(l);
       }

@@ -53,6 +53,19 @@ inline int severity(tk_status s) {
 }
 inline tk_status worse(tk_status a, tk_status b) { return severity(b) > severity(a) ? b : a; }
 
+// Stop rule of the mixed form's refinement after round `round` produced a
+// correction of norm dn (the previous one pd; the first correction is x
+// itself) on x of norm xn: done when the correction is below tol ||x||, when
+// the next correction predicted from the observed contraction, dn * (dn / pd),
+// is below tol ||x|| / 10, when the corrections stopped halving (x sits at the
+// float64 floor of the residual), or when dn is not finite.
+inline bool refine_done(int round, double dn, double pd, double xn, double tol) {
+  if (!(dn == dn) || dn > 1e300) return true;
+  if (dn <= tol * xn) return true;
+  if (round >= 1 && pd > 0.0 && pd < 1e300 && dn * (dn / pd) <= 0.1 * tol * xn) return true;
+  return round >= 2 && dn > 0.5 * pd;
+}
+
 // ------------------------------------------------------------ workspace --
 // Bump allocator over a caller-provided device buffer (256-byte aligned
 // slices).  With base == nullptr it only measures.

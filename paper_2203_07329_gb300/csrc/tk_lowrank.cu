@@ -29,10 +29,14 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
 
 // Pair k of round `round` of the circle schedule over sp (even) players
 // (player sp-1 is a dummy when s is odd): rows p < q of W are rotated so that
-// they become orthogonal, unless already orthogonal to tol.  One CTA.
-__device__ __forceinline__ void jacobi_pair(double* __restrict__ W, int64_t s, int64_t n, int64_t sp, int64_t round,
-                                            int64_t k, double tol, double* __restrict__ off_max,
-                                            int* __restrict__ rotated, double* sh) {
+// they become orthogonal, unless already orthogonal to tol.  One warp per
+// pair; the squared row norms a = nrm2[p], b = nrm2[q] are carried from the
+// start of the sweep and updated by the rotation (a' = a - t g, b' = b + t g),
+// so only g = w_p . w_q is computed per pair.
+__device__ __forceinline__ void jacobi_pair_warp(double* __restrict__ W, double* __restrict__ nrm2, int64_t s,
+                                                 int64_t n, int64_t sp, int64_t round, int64_t k, double tol,
+                                                 double* __restrict__ off_max, int* __restrict__ rotated) {
+  const int lane = threadIdx.x & 31;
   int64_t p, q;
   if (k == 0) {
     p = sp - 1;
@@ -49,60 +53,85 @@ __device__ __forceinline__ void jacobi_pair(double* __restrict__ W, int64_t s, i
   if (q >= s) return;  // pair with the dummy
   double* wp = W + p * n;
   double* wq = W + q * n;
-  double a = 0.0, b = 0.0, g = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    double x = wp[i], y = wq[i];
-    a = fma(x, x, a);
-    b = fma(y, y, b);
-    g = fma(x, y, g);
-  }
-  a = block_sum(a, sh);
-  b = block_sum(b, sh);
-  g = block_sum(g, sh);
+  double g = 0.0;
+  for (int64_t i = lane; i < n; i += 32) g = fma(wp[i], wq[i], g);
+  g = warp_sum(g);
+  const double a = nrm2[p], b = nrm2[q];
   if (a == 0.0 || b == 0.0) return;
   const double rel = fabs(g) / sqrt(a * b);
   if (!(rel > tol)) return;
-  if (threadIdx.x == 0) {
-    atomic_max_pos(off_max, rel);
-    atomicAdd(rotated, 1);
-  }
   const double zeta = (b - a) / (2.0 * g);
   const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
   const double c = 1.0 / sqrt(1.0 + t * t);
   const double sn = c * t;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    double x = wp[i], y = wq[i];
+  for (int64_t i = lane; i < n; i += 32) {
+    const double x = wp[i], y = wq[i];
     wp[i] = c * x - sn * y;
     wq[i] = sn * x + c * y;
   }
+  if (lane == 0) {
+    nrm2[p] = a - t * g;
+    nrm2[q] = b + t * g;
+    atomic_max_pos(off_max, rel);
+    atomicAdd(rotated, 1);
+  }
 }
 
-// One round for one matrix: sp/2 disjoint pairs, one CTA each.
+constexpr int kPairsPerCta = kJacThreads / 32;
+
+// One round for one matrix: sp/2 disjoint pairs, one warp each.
 __global__ void __launch_bounds__(kJacThreads)
-    k_jacobi_round(double* __restrict__ W, int64_t s, int64_t n, int64_t sp, int64_t round, double tol,
-                   double* __restrict__ off_max, int* __restrict__ rotated) {
-  __shared__ double sh[32];
-  jacobi_pair(W, s, n, sp, round, blockIdx.x, tol, off_max, rotated, sh);
+    k_jacobi_round(double* __restrict__ W, double* __restrict__ nrm2, int64_t s, int64_t n, int64_t sp, int64_t round,
+                   double tol, double* __restrict__ off_max, int* __restrict__ rotated) {
+  const int64_t k = (int64_t)blockIdx.x * kPairsPerCta + (threadIdx.x >> 5);
+  if (k < sp / 2) jacobi_pair_warp(W, nrm2, s, n, sp, round, k, tol, off_max, rotated);
 }
 
-// One round for many matrices (grouped batch): CTA = (matrix, pair).
+// Squared row norms at the start of a sweep (one warp per row).
+__global__ void __launch_bounds__(kJacThreads)
+    k_row_norms2(const double* __restrict__ W, int64_t s, int64_t n, double* __restrict__ nrm2) {
+  const int64_t r = (int64_t)blockIdx.x * kPairsPerCta + (threadIdx.x >> 5);
+  if (r >= s) return;
+  const int lane = threadIdx.x & 31;
+  double a = 0.0;
+  for (int64_t i = lane; i < n; i += 32) a = fma(W[r * n + i], W[r * n + i], a);
+  a = warp_sum(a);
+  if (lane == 0) nrm2[r] = a;
+}
+
+// One round for many matrices (grouped batch): CTA = (matrix, 8 pairs).
 struct SvdDesc {
   double* W;
+  double* nrm2;
   int64_t s, n, sp;
   double* off_max;
   int* rotated;
   int done;
 };
 struct SvdTile {
-  int job, k;
+  int job, k0;
 };
 __global__ void __launch_bounds__(kJacThreads)
     k_jacobi_round_grouped(const SvdDesc* __restrict__ D, const SvdTile* __restrict__ tl, int64_t round, double tol) {
-  __shared__ double sh[32];
   const SvdTile t = tl[blockIdx.x];
   const SvdDesc& d = D[t.job];
-  if (d.done || round >= d.sp - 1) return;
-  jacobi_pair(d.W, d.s, d.n, d.sp, round, t.k, tol, d.off_max, d.rotated, sh);
+  const int64_t k = t.k0 + (threadIdx.x >> 5);
+  if (d.done || round >= d.sp - 1 || k >= d.sp / 2) return;
+  jacobi_pair_warp(d.W, d.nrm2, d.s, d.n, d.sp, round, k, tol, d.off_max, d.rotated);
+}
+
+// Squared row norms of every matrix still rotating (CTA = (matrix, 8 rows)).
+__global__ void __launch_bounds__(kJacThreads)
+    k_row_norms2_grouped(const SvdDesc* __restrict__ D, const SvdTile* __restrict__ tl) {
+  const SvdTile t = tl[blockIdx.x];
+  const SvdDesc& d = D[t.job];
+  const int64_t r = t.k0 + (threadIdx.x >> 5);
+  if (d.done || r >= d.s) return;
+  const int lane = threadIdx.x & 31;
+  double a = 0.0;
+  for (int64_t i = lane; i < d.n; i += 32) a = fma(d.W[r * d.n + i], d.W[r * d.n + i], a);
+  a = warp_sum(a);
+  if (lane == 0) d.nrm2[r] = a;
 }
 
 __global__ void k_svd_reset(SvdDesc* __restrict__ D, int J) {
@@ -186,6 +215,7 @@ size_t svd_workspace(int64_t s, int64_t n) {
   a.take<int>((size_t)s);
   a.take<double>(1);
   a.take<int>(1);
+  a.take<double>((size_t)s);  // squared row norms carried through a sweep
   return a.used + 512;
 }
 
@@ -216,6 +246,7 @@ tk_status jacobi_svd(const double* Y, int64_t s, int64_t n, double* sigma, doubl
   int* perm = ar.take<int>((size_t)s);
   double* off_max = ar.take<double>(1);
   int* rotated = ar.take<int>(1);
+  double* nrm2 = ar.take<double>((size_t)s);
   if (!ar.ok()) return TK_ENOMEM;
   if (s == 0) return TK_OK;
   TK_CUDA(cudaMemcpyAsync(W, Y, sizeof(double) * (size_t)s * n, cudaMemcpyDeviceToDevice, st));
@@ -226,8 +257,11 @@ tk_status jacobi_svd(const double* Y, int64_t s, int64_t n, double* sigma, doubl
   for (; sweep < max_sweeps && s > 1; ++sweep) {
     TK_CUDA(cudaMemsetAsync(rotated, 0, sizeof(int), st));
     TK_CUDA(cudaMemsetAsync(off_max, 0, sizeof(double), st));
+    k_row_norms2<<<(unsigned)cdiv(s, kPairsPerCta), kJacThreads, 0, st>>>(W, s, n, nrm2);
+    TK_LAUNCH_CHECK();
     for (int64_t r = 0; r < sp - 1; ++r) {
-      k_jacobi_round<<<(unsigned)(sp / 2), kJacThreads, 0, st>>>(W, s, n, sp, r, tol, off_max, rotated);
+      k_jacobi_round<<<(unsigned)cdiv(sp / 2, kPairsPerCta), kJacThreads, 0, st>>>(W, nrm2, s, n, sp, r, tol,
+                                                                                    off_max, rotated);
       TK_LAUNCH_CHECK();
     }
     int hrot = 0;
@@ -251,7 +285,8 @@ tk_status jacobi_svd_grouped(std::vector<SvdJob>& jobs, void* work, size_t work_
   double* offs = a.take<double>(J);
   int* rots = a.take<int>(J);
   size_t ntiles = 0;
-  for (const auto& j : jobs) ntiles += (size_t)((j.s % 2 == 0) ? j.s : j.s + 1) / 2;
+  for (const auto& j : jobs) ntiles += (size_t)cdiv(std::max<int64_t>(((j.s % 2 == 0) ? j.s : j.s + 1) / 2, j.s),
+                                                    kPairsPerCta);
   SvdTile* dt = a.take<SvdTile>(std::max<size_t>(ntiles, 1));
   if (!a.ok()) {
     set_error_msg("grouped SVD: workspace too small");
@@ -266,11 +301,14 @@ tk_status jacobi_svd_grouped(std::vector<SvdJob>& jobs, void* work, size_t work_
     q.W = sa.take<double>((size_t)q.s * q.n);
     q.nrm = sa.take<double>((size_t)q.s);
     q.perm = sa.take<int>((size_t)q.s);
+    sa.take<double>(1);
+    sa.take<int>(1);
+    double* nrm2 = sa.take<double>((size_t)q.s);
     if (!sa.ok()) return TK_ENOMEM;
     if (q.s > 0) TK_CUDA(cudaMemcpyAsync(q.W, q.Y, sizeof(double) * (size_t)q.s * q.n, cudaMemcpyDeviceToDevice, st));
     const int64_t sp = (q.s % 2 == 0) ? q.s : q.s + 1;
-    hd[j] = SvdDesc{q.W, q.s, q.n, sp, offs + j, rots + j, q.s <= 1 ? 1 : 0};
-    for (int64_t k = 0; k < sp / 2; ++k) tiles.push_back(SvdTile{j, (int)k});
+    hd[j] = SvdDesc{q.W, nrm2, q.s, q.n, sp, offs + j, rots + j, q.s <= 1 ? 1 : 0};
+    for (int64_t k = 0; k < std::max<int64_t>(sp / 2, q.s); k += kPairsPerCta) tiles.push_back(SvdTile{j, (int)k});
     if (q.s > 1) max_rounds = std::max(max_rounds, sp - 1);
     q.sweeps = 0;
   }
@@ -281,6 +319,8 @@ tk_status jacobi_svd_grouped(std::vector<SvdJob>& jobs, void* work, size_t work_
   std::vector<int> hrot(J);
   for (int sweep = 0; sweep < max_sweeps && max_rounds > 0; ++sweep) {
     k_svd_reset<<<cdiv(J, 128), 128, 0, st>>>(dd, J);
+    TK_LAUNCH_CHECK();
+    k_row_norms2_grouped<<<(unsigned)tiles.size(), kJacThreads, 0, st>>>(dd, dt);
     TK_LAUNCH_CHECK();
     for (int64_t r = 0; r < max_rounds; ++r) {
       k_jacobi_round_grouped<<<(unsigned)tiles.size(), kJacThreads, 0, st>>>(dd, dt, r, tol);
@@ -307,7 +347,8 @@ tk_status jacobi_svd_grouped(std::vector<SvdJob>& jobs, void* work, size_t work_
 size_t svd_grouped_workspace(const std::vector<SvdJob>& jobs) {
   Arena a;
   size_t ntiles = 0;
-  for (const auto& j : jobs) ntiles += (size_t)((j.s % 2 == 0) ? j.s : j.s + 1) / 2;
+  for (const auto& j : jobs) ntiles += (size_t)cdiv(std::max<int64_t>(((j.s % 2 == 0) ? j.s : j.s + 1) / 2, j.s),
+                                                    kPairsPerCta);
   a.take<SvdDesc>(std::max<size_t>(jobs.size(), 1));
   a.take<double>(std::max<size_t>(jobs.size(), 1));
   a.take<int>(std::max<size_t>(jobs.size(), 1));
