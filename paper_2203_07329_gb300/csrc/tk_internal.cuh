@@ -29,6 +29,7 @@ void set_error_msg(const char* msg);
 // Every kernel launch of the library is followed by TK_LAUNCH_CHECK(), which
 // also counts it (tk_launch_count()).
 void count_launch();
+void count_launches(size_t n);  // n kernels of a replayed graph
 #define TK_LAUNCH_CHECK()   \
   do {                      \
     ::tk::count_launch();   \
@@ -158,6 +159,7 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 }
 
 // ------------------------------------------------------------ profiler --
+bool prof_enabled();
 int prof_begin(int phase, cudaStream_t st);
 void prof_end(int tok, cudaStream_t st, double flops, double bytes);
 

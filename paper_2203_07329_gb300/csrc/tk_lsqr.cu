@@ -98,6 +98,7 @@ __global__ void k_over_beta(const double* __restrict__ part, int chunks, const T
                             T* __restrict__ Ub, int64_t n, Scal* __restrict__ sc) {
   __shared__ double sh[32];
   const int s = blockIdx.x;
+  if (sc[s].istop != 0) return;  // retired inside a chunk of steps
   const double sl = sc[s].sqrtl, coef = sc[s].coef;
   double acc = 0.0;
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(kVecThreads)
   __shared__ double sh[32];
   const int s = blockIdx.x;
   Scal q = sc[s];
+  if (!init && q.istop != 0) return;  // retired inside a chunk of steps
   const int64_t off = (int64_t)s * m;
   double acc = 0.0;
   for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
@@ -425,6 +427,9 @@ tk_status Lsqr<T>::run(const double* b, int64_t ldbt, const double* bbot, int64_
   k_vstep<T><<<nact, kVecThreads, 0, st>>>(Vraw, V, W, Y, nv, sc, atol, btol, maxiter, 1);
   TK_LAUNCH_CHECK();
 
+  // steps per read of the scalars: several for problems whose steps are
+  // launch-bound (A of at most 2^24 elements), one otherwise
+  chunk = ((int64_t)m * n <= (int64_t(1) << 24)) ? 4 : 1;
   std::vector<Scal> hsc(N_cap);
   std::vector<int> hlam(N_cap);
   int* d_src = idx_buf;
@@ -492,36 +497,118 @@ tk_status Lsqr<T>::run(const double* b, int64_t ldbt, const double* bbot, int64_
       TK_CUDA(cudaStreamSynchronize(st));
     }
     if (nact == 0) break;
-    // ------------------------------------------------------- one step
-    if (!under) {
-      TK_TRY(apply_prec(false, V, Tt, nact, n));                                       // T = R^-1 v
-      TK_TRY(gather_coef(nact));
-      TK_TRY(prod_aw(Tt, n, Ut, coef_buf, nact));
-      k_sumsq_rows<T><<<dim3(kSumChunks, nact), 256, 0, st>>>(Ut, m, m, kSumChunks, part_u);
-      TK_LAUNCH_CHECK();
-      k_over_beta<T><<<nact, kVecThreads, 0, st>>>(part_u, kSumChunks, Tt, Ub, n, sc);
-      TK_LAUNCH_CHECK();
-      TK_TRY(prod_atu(Ut, nact));
-      k_over_g<T><<<rows_grid(n, nact), 256, 0, st>>>(part_g, cur_splits, nact, Ub, n, sc, Tt);
-      TK_LAUNCH_CHECK();
-      TK_TRY(apply_prec(true, Tt, Vraw, nact, n));                                     // R^-T g
-    } else {
-      TK_TRY(prod_aw(V, nv, Tt, nullptr, nact));
-      k_under_addv2<T><<<rows_grid(m, nact), 256, 0, st>>>(Tt, m, V, nv, n, sc);
-      TK_LAUNCH_CHECK();
-      TK_TRY(apply_prec(true, Tt, Tt, nact, m));
-      k_under_ustep<T><<<nact, kVecThreads, 0, st>>>(Tt, Ut, m, sc, 0);
-      TK_LAUNCH_CHECK();
-      TK_TRY(apply_prec(false, Ut, Tt, nact, m));
-      TK_TRY(prod_atu(Tt, nact));
-      k_under_vraw<T><<<rows_grid(nv, nact), 256, 0, st>>>(part_g, cur_splits, nact, Tt, m, n, sc, Vraw);
-      TK_LAUNCH_CHECK();
+    // ------------------------------------------- `chunk` steps, one replay
+    // Small problems run several steps between two reads of the scalars (a
+    // slot that converges inside the chunk stays as it is: its kernels skip
+    // it), replayed from a CUDA graph captured once per active count.
+    const tk_status sr = steps(nact, chunk);
+    if (sr != TK_OK) {
+      release_graphs();
+      return sr;
     }
-    k_vstep<T><<<nact, kVecThreads, 0, st>>>(Vraw, V, W, Y, nv, sc, atol, btol, maxiter, 0);
-    TK_LAUNCH_CHECK();
   }
+  release_graphs();
   if (tc) TK_TRY(tc_lmaj_check(tc_scratch, N_cap, std::max(n, m), st));
   return TK_OK;
+}
+
+template <typename T>
+tk_status Lsqr<T>::step(int nact) {
+  if (!under) {
+    TK_TRY(apply_prec(false, V, Tt, nact, n));  // T = R^-1 v
+    TK_TRY(gather_coef(nact));
+    TK_TRY(prod_aw(Tt, n, Ut, coef_buf, nact));
+    k_sumsq_rows<T><<<dim3(kSumChunks, nact), 256, 0, st>>>(Ut, m, m, kSumChunks, part_u);
+    TK_LAUNCH_CHECK();
+    k_over_beta<T><<<nact, kVecThreads, 0, st>>>(part_u, kSumChunks, Tt, Ub, n, sc);
+    TK_LAUNCH_CHECK();
+    TK_TRY(prod_atu(Ut, nact));
+    k_over_g<T><<<rows_grid(n, nact), 256, 0, st>>>(part_g, cur_splits, nact, Ub, n, sc, Tt);
+    TK_LAUNCH_CHECK();
+    TK_TRY(apply_prec(true, Tt, Vraw, nact, n));  // R^-T g
+  } else {
+    TK_TRY(prod_aw(V, nv, Tt, nullptr, nact));
+    k_under_addv2<T><<<rows_grid(m, nact), 256, 0, st>>>(Tt, m, V, nv, n, sc);
+    TK_LAUNCH_CHECK();
+    TK_TRY(apply_prec(true, Tt, Tt, nact, m));
+    k_under_ustep<T><<<nact, kVecThreads, 0, st>>>(Tt, Ut, m, sc, 0);
+    TK_LAUNCH_CHECK();
+    TK_TRY(apply_prec(false, Ut, Tt, nact, m));
+    TK_TRY(prod_atu(Tt, nact));
+    k_under_vraw<T><<<rows_grid(nv, nact), 256, 0, st>>>(part_g, cur_splits, nact, Tt, m, n, sc, Vraw);
+    TK_LAUNCH_CHECK();
+  }
+  k_vstep<T><<<nact, kVecThreads, 0, st>>>(Vraw, V, W, Y, nv, sc, atol, btol, maxiter, 0);
+  TK_LAUNCH_CHECK();
+  return TK_OK;
+}
+
+// `count` steps for `nact` active slots: launched directly (count 1, a
+// profiling run, or the tensor-core products), else replayed from a graph
+// captured the first time this active count is met.
+template <typename T>
+tk_status Lsqr<T>::steps(int nact, int count) {
+  if (count <= 1 || prof_enabled() || tc) {
+    for (int c = 0; c < count; ++c) TK_TRY(step(nact));
+    return TK_OK;
+  }
+  // graphs are captured and replayed on a stream of the engine's own (the
+  // caller's may be the legacy default stream, which cannot be captured),
+  // ordered after the caller's stream and before its next work by events
+  if (!gstream) {
+    TK_CUDA(cudaStreamCreateWithFlags(&gstream, cudaStreamNonBlocking));
+    TK_CUDA(cudaEventCreateWithFlags(&gev[0], cudaEventDisableTiming));
+    TK_CUDA(cudaEventCreateWithFlags(&gev[1], cudaEventDisableTiming));
+  }
+  auto it = graphs.find(nact);
+  if (it == graphs.end()) {
+    cudaStream_t caller = st;
+    st = gstream;
+    TK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    tk_status r = TK_OK;
+    for (int c = 0; c < count && r == TK_OK; ++c) r = step(nact);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &g);
+    st = caller;
+    if (r != TK_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (ce != cudaSuccess) {
+      set_error(ce, __FILE__, __LINE__);
+      return TK_ECUDA;
+    }
+    size_t nodes = 0;
+    cudaGraphGetNodes(g, nullptr, &nodes);
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      set_error(ie, __FILE__, __LINE__);
+      return TK_ECUDA;
+    }
+    it = graphs.emplace(nact, std::make_pair(ge, nodes)).first;
+  }
+  TK_CUDA(cudaEventRecord(gev[0], st));
+  TK_CUDA(cudaStreamWaitEvent(gstream, gev[0], 0));
+  TK_CUDA(cudaGraphLaunch(it->second.first, gstream));
+  TK_CUDA(cudaEventRecord(gev[1], gstream));
+  TK_CUDA(cudaStreamWaitEvent(st, gev[1], 0));
+  count_launches(it->second.second);
+  return TK_OK;
+}
+
+template <typename T>
+void Lsqr<T>::release_graphs() {
+  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.first);
+  graphs.clear();
+  if (gstream) {
+    cudaStreamSynchronize(gstream);
+    cudaStreamDestroy(gstream);
+    cudaEventDestroy(gev[0]);
+    cudaEventDestroy(gev[1]);
+    gstream = nullptr;
+  }
 }
 
 // The GEMM epilogue takes a dense per-row coefficient array; Scal.coef is

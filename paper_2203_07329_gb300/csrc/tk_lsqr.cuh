@@ -1,6 +1,8 @@
 // Batched preconditioned LSQR engine (internal).
 #pragma once
 
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "tk_internal.cuh"
@@ -43,6 +45,7 @@ __device__ __forceinline__ void vstep_block(const T* __restrict__ Vraw, T* __res
                                             T* __restrict__ Y, int64_t nv, Scal* __restrict__ sq, double atol,
                                             double btol, int maxiter, int init, double* sh) {
   Scal q = *sq;
+  if (!init && q.istop != 0) return;  // retired inside a chunk of steps: left as it is
   const int64_t off = 0;
   const double beta = q.beta;
   // v' = Vraw - beta v  (init: v' = Vraw)
@@ -171,6 +174,14 @@ struct Lsqr {
   tk_status prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, int count);
   tk_status prod_atu(const T* Uin, int count);
   tk_status gather_coef(int count);
+  // one LSQR step for slots 0..nact-1; `count` of them (see steps())
+  tk_status step(int nact);
+  tk_status steps(int nact, int count);
+  void release_graphs();
+  int chunk = 1;
+  std::map<int, std::pair<cudaGraphExec_t, size_t>> graphs;  // active count -> (replay, kernel nodes)
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
 };
 
 }  // namespace tk

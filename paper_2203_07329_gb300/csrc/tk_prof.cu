@@ -39,6 +39,12 @@ std::atomic<unsigned long long> g_launches{0};
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(size_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+bool prof_enabled() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_on;
+}
 
 int prof_begin(int phase, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_mu);
