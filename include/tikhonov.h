@@ -89,6 +89,11 @@ typedef struct {
                              N <= 64 and lsqr_tc = 0, the problems advance together in one grouped LSQR and
                              refinement (one launch per phase for all problems); 0 in any problem's options =
                              each problem solved on its own (host lanes) */
+  int emulate_fp64;       /* [1] MIXED: the two float64 passes of the refinement (r = b - A x and
+                             A^T r) on the BF16 tensor cores, split into exact integer slices (see
+                             tk_residual) instead of the float64 pipe; the same float64 accuracy.
+                             Costs 32 bytes of workspace per element of A (two sets of slices);
+                             0 = float64 FMA.  The grouped batch keeps its float64 passes. */
 } tk_opts;
 
 /* Per-lambda report. */
@@ -229,6 +234,26 @@ TK_API tk_status tk_sketch_svd(const double* Y, int64_t s, int64_t n, double* si
 TK_API size_t tk_lowrank_ranks_workspace(int N);
 TK_API tk_status tk_lowrank_ranks(const double* sigma, int64_t s, const double* lambdas, int N, double alpha,
                                   double* sd, int64_t* ranks, void* work, size_t work_bytes, void* stream);
+
+/* tk_residual -- R = b - X A^T for M rows of X and, when G is not NULL,
+ * G = R A (the two float64 passes of the refinement of the mixed form:
+ * residuals b - A x_l and A^T (b - A x_l); no counterpart in the paper's
+ * algorithms).  emulate = 0: float64 FMA.  emulate = 1: on the BF16
+ * tensor cores: every row of A (and of X) is scaled by a power of two and
+ * split into 8 signed 7-bit integer slices (exact in BF16, 56 bits), the 36
+ * slice products whose weight is at least 2^-56 of the row maxima are
+ * accumulated exactly in FP32 over chunks of 128 and added into float64;
+ * the error is that of a float64 GEMM.
+ *   p:   A (device, m x n, row stride lda, float64 or float32) and b (device, m).
+ *   X:   device, M x n float64, row stride ldx >= n.
+ *   R:   device, M x m float64 (row l = b - A x_l), written.
+ *   G:   device, M x n float64 (row l = A^T (b - A x_l)), written; may be NULL.
+ *        Emulated, A^T r is formed from the same slices of A, the row scale of A
+ *        moved onto r.
+ *   work: device, tk_residual_workspace(m, n, M) bytes.  Synchronizes `stream`. */
+TK_API size_t tk_residual_workspace(int64_t m, int64_t n, int M);
+TK_API tk_status tk_residual(const tk_problem* p, const double* X, int M, int64_t ldx, int emulate, double* R,
+                             double* G, void* work, size_t work_bytes, void* stream);
 
 /* tk_autotune -- measured tile shapes for the products of the LSQR and
  * refinement passes (no counterpart in the paper: a tuning step of this

@@ -136,6 +136,15 @@ struct Bufs {
   double* Rres = nullptr;
   double* part = nullptr;
   double* nrm = nullptr;
+  void* Aoz = nullptr;      // mixed, emulate_fp64: BF16 slices of A and their row exponents
+  int* EA = nullptr;
+  void* Xoz = nullptr;      // ... and of the lambda rows of x
+  int* EX = nullptr;
+  void* AozC = nullptr;     // ... the column-scaled slices of A, their column exponents
+  int* EC = nullptr;
+  void* colmax = nullptr;
+  void* Roz = nullptr;      // ... and of the residuals (normal-equation pass)
+  int* ER = nullptr;
   char* scratch = nullptr;  // sketch scratch
   size_t scratch_bytes = 0;
   char* svd = nullptr;      // SVD scratch (low rank)
@@ -199,8 +208,21 @@ void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
       B.lrS32 = a.take<float>((size_t)N * P.s);
     }
   }
+  if (P.mixed && !P.prep_only && P.o.emulate_fp64) {
+    B.Aoz = a.take<char>(oz_slices_bytes(P.m, P.n));
+    B.EA = a.take<int>(P.m);
+    B.Xoz = a.take<char>(oz_slices_bytes(N, P.n));
+    B.EX = a.take<int>(N);
+    B.AozC = a.take<char>(oz_slices_bytes(P.m, P.n));
+    B.EC = a.take<int>(P.n);
+    B.colmax = a.take<char>(oz_colmax_bytes(P.n));
+    B.Roz = a.take<char>(oz_slices_bytes(N, P.m));
+    B.ER = a.take<int>(N);
+  }
   if (P.mixed && !P.prep_only) {
     B.splits = splitk_count(N, P.n, P.m);
+    // the emulated A^T r wants the most splits when the fewest lambdas remain
+    if (P.o.emulate_fp64) B.splits = std::max(B.splits, oz_normal_splits(P.m, P.n, 1));
     B.D = a.take<double>((size_t)N * P.n);
     B.Xa = a.take<double>((size_t)N * P.n);
     B.G = a.take<double>((size_t)N * P.n);
@@ -560,6 +582,12 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     std::vector<int> act = ok_ids;
     std::vector<double> hn(3 * std::max(N, 1));
     std::vector<double> prev_dn(std::max(N, 1), INFINITY);
+    if (P.o.emulate_fp64 && !act.empty()) {  // A is split once (by rows and by columns); x, r on every pass
+      const int tok = prof_begin(TK_PHASE_RES64, st);
+      TK_TRY(oz_prepare(p->A, P.dt, P.m, P.n, P.lda, B.Aoz, B.EA, st));
+      TK_TRY(oz_prepare_cols(p->A, P.dt, P.m, P.n, P.lda, B.AozC, B.EC, B.colmax, st));
+      prof_end(tok, st, 0.0, 2.0 * ((P.dt == TK_F64 ? 16.0 : 8.0) * P.m * P.n + 16.0 * P.m * P.n));
+    }
     for (int round = 0; round < P.o.max_refine && !act.empty(); ++round) {
       const int cnt = (int)act.size();
       TK_CUDA(cudaMemcpyAsync(B.ids, act.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, st));
@@ -571,26 +599,36 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       } else {
         // FP64 pass: Rres = b - Xa A^T, G = Rres A - lambda Xa
         k_gather_x<<<rgrid(P.n, cnt), 256, 0, st>>>(X, P.n, B.ids, B.Xa);
-        k_bcast<<<rgrid(P.m, cnt), 256, 0, st>>>(p->b, P.m, B.Rres, cnt);
+        if (!P.o.emulate_fp64) k_bcast<<<rgrid(P.m, cnt), 256, 0, st>>>(p->b, P.m, B.Rres, cnt);
         TK_LAUNCH_CHECK();
         const double ea = P.dt == TK_F64 ? 8.0 : 4.0;
         const double fl = 2.0 * cnt * P.m * P.n;
         int tok = prof_begin(TK_PHASE_RES64, st);
-        if (P.dt == TK_F64)
+        if (P.o.emulate_fp64) {
+          TK_TRY(oz_prepare(B.Xa, TK_F64, cnt, P.n, P.n, B.Xoz, B.EX, st));
+          TK_TRY(oz_residual(B.Aoz, B.EA, P.m, P.n, B.Xoz, B.EX, cnt, p->b, B.Rres, P.m, st));
+        } else if (P.dt == TK_F64) {
           TK_TRY((gemm<double, double, double>(false, true, cnt, P.m, P.n, B.Xa, P.n, A64, lda64, B.Rres, P.m, -1.0,
                                                B.ones, B.Rres, P.m, st)));
-        else
+        } else {
           TK_TRY((gemm<double, float, double>(false, true, cnt, P.m, P.n, B.Xa, P.n, A32, lda32, B.Rres, P.m, -1.0,
                                               B.ones, B.Rres, P.m, st)));
-        prof_end(tok, st, fl, ea * P.m * P.n + 8.0 * (2.0 * cnt * P.m + cnt * P.n));
+        }
+        prof_end(tok, st, fl, (P.o.emulate_fp64 ? 16.0 : ea) * P.m * P.n + 8.0 * (2.0 * cnt * P.m + cnt * P.n));
         tok = prof_begin(TK_PHASE_NE64, st);
-        const int sp = P.dt == TK_F64 ? splitk_tuned<double, double>(cnt, P.n, P.m, B.splits)
-                                      : splitk_tuned<double, float>(cnt, P.n, P.m, B.splits);
-        if (P.dt == TK_F64)
-          TK_TRY((gemm_splitk<double, double>(false, false, cnt, P.n, P.m, B.Rres, P.m, A64, lda64, B.part, sp, st)));
-        else
-          TK_TRY((gemm_splitk<double, float>(false, false, cnt, P.n, P.m, B.Rres, P.m, A32, lda32, B.part, sp, st)));
-        prof_end(tok, st, fl, ea * P.m * P.n + 8.0 * (cnt * P.m + (double)sp * cnt * P.n));
+        int sp;
+        if (P.o.emulate_fp64) {
+          sp = std::min(B.splits, oz_normal_splits(P.m, P.n, cnt));
+          TK_TRY(oz_normal(B.AozC, B.EC, P.m, P.n, B.Rres, P.m, cnt, B.Roz, B.ER, B.part, sp, st));
+        } else {
+          sp = P.dt == TK_F64 ? splitk_tuned<double, double>(cnt, P.n, P.m, B.splits)
+                              : splitk_tuned<double, float>(cnt, P.n, P.m, B.splits);
+          if (P.dt == TK_F64)
+            TK_TRY((gemm_splitk<double, double>(false, false, cnt, P.n, P.m, B.Rres, P.m, A64, lda64, B.part, sp, st)));
+          else
+            TK_TRY((gemm_splitk<double, float>(false, false, cnt, P.n, P.m, B.Rres, P.m, A32, lda32, B.part, sp, st)));
+        }
+        prof_end(tok, st, fl, (P.o.emulate_fp64 ? 16.0 : ea) * P.m * P.n + 8.0 * (cnt * P.m + (double)sp * cnt * P.n));
         k_ne_finish<<<cnt, 256, 0, st>>>(B.part, sp, cnt, P.n, B.ids, B.lam, B.Xa, B.G, B.nrm);
         TK_LAUNCH_CHECK();
         // correction: min ||B d - [0; g/sqrt(l)]||, whose normal equations are
@@ -660,6 +698,7 @@ TK_API tk_status tk_opts_default(tk_opts* o) {
   o->schedule = TK_SCHED_BATCHED;
   o->lsqr_tc = 0;
   o->group = 1;
+  o->emulate_fp64 = 1;
   return TK_OK;
 }
 
@@ -952,6 +991,94 @@ TK_API tk_status tk_autotune(const tk_problem* p, int N, const tk_opts* o, void*
       if (!P.lsqr_tc)
         TK_TRY((tune_gemm<float, float, double>(false, false, M, P.n, P.m, e.Ut, P.m, A32, lda32, nullptr, 0, 1.0,
                                                 nullptr, nullptr, 0, e.splits, e.part_g, st)));
+    }
+  }
+  TK_CUDA(cudaStreamSynchronize(st));
+  return TK_OK;
+}
+
+namespace tk {
+struct ResidualBufs {
+  void *Aoz, *Xoz, *AozC, *colmax, *Roz;
+  int *EA, *EX, *EC, *ER;
+  double *ones, *part;
+  int splits;
+};
+static void residual_carve(Arena& a, int64_t m, int64_t n, int M, ResidualBufs& w) {
+  w.splits = oz_normal_splits(m, n, M);
+  w.Aoz = a.take<char>(oz_slices_bytes(m, n));
+  w.EA = a.take<int>(m);
+  w.Xoz = a.take<char>(oz_slices_bytes(M, n));
+  w.EX = a.take<int>(M);
+  w.AozC = a.take<char>(oz_slices_bytes(m, n));
+  w.EC = a.take<int>(n);
+  w.colmax = a.take<char>(oz_colmax_bytes(n));
+  w.Roz = a.take<char>(oz_slices_bytes(M, m));
+  w.ER = a.take<int>(M);
+  w.ones = a.take<double>(std::max(M, 1));
+  w.part = a.take<double>((size_t)w.splits * M * n);
+}
+__global__ void k_residual_sum_splits(const double* __restrict__ part, int splits, int64_t total,
+                                      double* __restrict__ G) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < splits; ++z) acc += part[(int64_t)z * total + k];
+    G[k] = acc;
+  }
+}
+}  // namespace tk
+
+TK_API size_t tk_residual_workspace(int64_t m, int64_t n, int M) {
+  Arena a;
+  ResidualBufs w;
+  residual_carve(a, m, n, M, w);
+  return a.used + 1024;
+}
+
+TK_API tk_status tk_residual(const tk_problem* p, const double* X, int M, int64_t ldx, int emulate, double* R,
+                             double* G, void* work, size_t work_bytes, void* stream) {
+  if (!p || !p->A || !p->b || (M > 0 && (!X || !R))) return einval("A, b, X and R must be non-NULL");
+  if (p->m < 1 || p->n < 1 || p->lda < p->n || M < 0 || (M > 0 && ldx < p->n))
+    return einval("bad shapes (m, n >= 1, lda >= n, ldx >= n)");
+  if (p->dtype != TK_F64 && p->dtype != TK_F32) return einval("unknown dtype");
+  if (M == 0) return TK_OK;
+  if (!work || work_bytes < tk_residual_workspace(p->m, p->n, M)) {
+    set_error_msg("workspace smaller than tk_residual_workspace()");
+    return TK_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  ResidualBufs w;
+  residual_carve(a, p->m, p->n, M, w);
+  const int64_t m = p->m, n = p->n;
+  if (emulate) {
+    TK_TRY(oz_prepare(p->A, p->dtype, m, n, p->lda, w.Aoz, w.EA, st));
+    TK_TRY(oz_prepare(X, TK_F64, M, n, ldx, w.Xoz, w.EX, st));
+    TK_TRY(oz_residual(w.Aoz, w.EA, m, n, w.Xoz, w.EX, M, p->b, R, m, st));
+    if (G) {
+      TK_TRY(oz_prepare_cols(p->A, p->dtype, m, n, p->lda, w.AozC, w.EC, w.colmax, st));
+      TK_TRY(oz_normal(w.AozC, w.EC, m, n, R, m, M, w.Roz, w.ER, w.part, w.splits, st));
+      k_residual_sum_splits<<<(unsigned)std::min<int64_t>(cdiv((int64_t)M * n, 256), 152 * 8), 256, 0, st>>>(
+          w.part, w.splits, (int64_t)M * n, G);
+      TK_LAUNCH_CHECK();
+    }
+  } else {
+    double* ones = w.ones;
+    k_fill<<<1, 256, 0, st>>>(ones, M, 1.0);
+    TK_LAUNCH_CHECK();
+    // R = 1 * broadcast(b) - X A^T;  G = R A
+    if (p->dtype == TK_F64) {
+      TK_TRY((gemm<double, double, double>(false, true, M, m, n, X, ldx, (const double*)p->A, p->lda, R, m, -1.0,
+                                           ones, p->b, 0, st)));
+      if (G) TK_TRY((gemm<double, double, double>(false, false, M, n, m, R, m, (const double*)p->A, p->lda, G, n, 1.0,
+                                                  nullptr, nullptr, 0, st)));
+    } else {
+      TK_TRY((gemm<double, float, double>(false, true, M, m, n, X, ldx, (const float*)p->A, p->lda, R, m, -1.0, ones,
+                                          p->b, 0, st)));
+      if (G) TK_TRY((gemm<double, float, double>(false, false, M, n, m, R, m, (const float*)p->A, p->lda, G, n, 1.0,
+                                                 nullptr, nullptr, 0, st)));
     }
   }
   TK_CUDA(cudaStreamSynchronize(st));

@@ -36,7 +36,7 @@ class tk_opts(C.Structure):
     _fields_ = [("sketch", C.c_int), ("s", C.c_int64), ("precond", C.c_int), ("alpha", C.c_double),
                 ("precision", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int), ("max_refine", C.c_int),
                 ("inner_tol", C.c_double), ("refine_tol", C.c_double), ("seed", C.c_uint64),
-                ("schedule", C.c_int), ("lsqr_tc", C.c_int), ("group", C.c_int)]
+                ("schedule", C.c_int), ("lsqr_tc", C.c_int), ("group", C.c_int), ("emulate_fp64", C.c_int)]
 
 
 class tk_info(C.Structure):
@@ -94,6 +94,8 @@ def lib() -> C.CDLL:
             "tk_profile_collect": (INT, [P]),
             "tk_autotune": (INT, [P, INT, P, P, SZ, P]),
             "tk_autotune_entries": (SZ, []),
+            "tk_residual_workspace": (SZ, [I64, I64, INT]),
+            "tk_residual": (INT, [P, P, INT, I64, INT, P, P, P, SZ, P]),
             "tk_autotune_clear": (None, []),
             "tk_autotune_describe": (SZ, [C.c_char_p, SZ]),
         }
@@ -345,3 +347,19 @@ def tk_autotune_describe() -> str:
     buf = C.create_string_buffer(n)
     lib().tk_autotune_describe(buf, n)
     return buf.value.decode()
+
+
+def tk_residual(A: torch.Tensor, b: torch.Tensor, X: torch.Tensor, emulate: bool, with_g: bool = False,
+                stream=None):
+    """R = b - X A^T (M x m) and, with with_g, G = R A (M x n), float64, for the M rows
+    of X: float64 FMA (emulate=False) or the BF16 tensor cores with float64 accuracy."""
+    prob = make_problem(A, b)
+    X = X.contiguous()
+    M = X.shape[0]
+    R = torch.empty((M, A.shape[0]), dtype=torch.float64, device=A.device)
+    G = torch.empty((M, A.shape[1]), dtype=torch.float64, device=A.device) if with_g else None
+    need = int(lib().tk_residual_workspace(A.shape[0], A.shape[1], M))
+    work = _workspace(need, A.device)
+    _check(lib().tk_residual(C.byref(prob), _ptr(X), M, X.shape[1], 1 if emulate else 0, _ptr(R), _ptr(G),
+                             _ptr(work), work.numel(), _stream(stream)))
+    return (R, G) if with_g else R

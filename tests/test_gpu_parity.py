@@ -452,3 +452,76 @@ def test_autotuned_solve_matches_untuned(tk, precision):
     for i in range(len(lams)):
         assert rel(X1[i], Xr[i]) < TOL_X, (lams[i], rel(X1[i], Xr[i]))
         assert rel(X1[i], X0[i]) < 1e-11
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_emulated_residual_has_float64_accuracy(tk, dtype):
+    # R = b - X A^T on the BF16 tensor cores (8 exact 7-bit slices per value) against an
+    # extended-precision reference: its error must be that of the float64 FMA residual
+    gen = torch.Generator().manual_seed(17)
+    m, n, M = 2999, 777, 6  # ragged in every dimension (n not a multiple of 8 or of 32)
+    A = torch.randn(m, n, generator=gen, dtype=torch.float64)
+    A *= torch.logspace(0, -6, n, dtype=torch.float64)  # wide dynamic range along each row
+    A = A.to(dtype)
+    X = torch.randn(M, n, generator=gen, dtype=torch.float64) * torch.logspace(2, -3, M, dtype=torch.float64)[:, None]
+    b = (X[0] @ A.double().T) + 1e-3 * torch.randn(m, generator=gen, dtype=torch.float64)  # nearly consistent
+    Ad, bd, Xd = A.cuda(), b.cuda(), X.cuda()
+    Re = tk.tk_residual(Ad, bd, Xd, True).cpu().numpy()
+    Rn = tk.tk_residual(Ad, bd, Xd, False).cpu().numpy()
+    Al = A.double().numpy().astype(np.longdouble)
+    Rref = b.numpy().astype(np.longdouble)[None, :] - X.numpy().astype(np.longdouble) @ Al.T
+    scale = np.abs(b.numpy())[None, :] + np.abs(X.numpy()) @ np.abs(A.double().numpy()).T
+    err_e = float(np.max(np.abs((Re - Rref).astype(np.float64)) / scale))
+    err_n = float(np.max(np.abs((Rn - Rref).astype(np.float64)) / scale))
+    assert err_e < 8 * 2.0 ** -53 * math.sqrt(n), (err_e, err_n)
+    assert err_e <= 4 * err_n + 1e-16, (err_e, err_n)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_emulated_normal_product_has_float64_accuracy(tk, dtype):
+    # G = R A (the rows A^T r_l) on the BF16 tensor cores: every column of G within the
+    # float64 error of its own column, however different the scales of A's columns
+    gen = torch.Generator().manual_seed(19)
+    m, n, M = 4133, 333, 5  # m spans several 128-row chunks and a ragged split; n ragged
+    A = torch.randn(m, n, generator=gen, dtype=torch.float64)
+    A *= torch.logspace(0, -8, n, dtype=torch.float64)  # column scales over 8 decades
+    A[:, 7] = 0.0  # a zero column
+    A = A.to(dtype)
+    X = torch.randn(M, n, generator=gen, dtype=torch.float64)
+    b = torch.randn(m, generator=gen, dtype=torch.float64) * torch.logspace(0, -3, m, dtype=torch.float64)
+    Ad, bd, Xd = A.cuda(), b.cuda(), X.cuda()
+    Re, Ge = tk.tk_residual(Ad, bd, Xd, True, with_g=True)
+    Rn, Gn = tk.tk_residual(Ad, bd, Xd, False, with_g=True)
+    Al = A.double().numpy().astype(np.longdouble)
+    for R, G in ((Re, Ge), (Rn, Gn)):
+        assert G.shape == (M, n)
+    Rl = Re.cpu().numpy().astype(np.longdouble)  # the product of the residuals actually formed
+    Gref = Rl @ Al
+    scale = np.abs(Re.cpu().numpy()) @ np.abs(A.double().numpy())
+    scale[:, 7] = 1.0
+    err_e = np.max(np.abs((Ge.cpu().numpy() - Gref).astype(np.float64)) / scale, axis=0)
+    assert np.all(Ge.cpu().numpy()[:, 7] == 0.0)
+    assert float(err_e.max()) < 8 * 2.0 ** -53 * math.sqrt(m), float(err_e.max())
+    Rl = Rn.cpu().numpy().astype(np.longdouble)
+    scale = np.abs(Rn.cpu().numpy()) @ np.abs(A.double().numpy())
+    scale[:, 7] = 1.0
+    err_n = np.max(np.abs((Gn.cpu().numpy() - Rl @ Al).astype(np.float64)) / scale, axis=0)
+    assert float(err_n.max()) < 8 * 2.0 ** -53 * math.sqrt(m), float(err_n.max())
+    # the columns of smallest scale are as accurate as the largest
+    assert float(err_e[-20:].max()) <= 4 * float(err_n.max()) + 1e-16
+
+
+@pytest.mark.parametrize("emulate", [1, 0])
+def test_mixed_with_emulated_residual_matches_reference(tk, emulate):
+    # the mixed form with both float64 passes of its refinement on the tensor cores
+    # (r = b - A x and A^T r; the default) or on the float64 pipe reaches 1e-10
+    p = problem(4000, 192, lo=1e-6, N=8, lam=(1e-8, 1.0))
+    lams = p.lambdas.numpy()
+    A, b = to_dev(p)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=768, seed=3, precision=tk.TK_PREC_MIXED, emulate_fp64=emulate)
+    res = tk.tk_solve(A, b, lams, o)
+    X = res.X.cpu().numpy()
+    Xr = ref_over(p, lams)
+    for i in range(len(lams)):
+        assert rel(X[i], Xr[i]) < TOL_X, (lams[i], rel(X[i], Xr[i]), res.info[i])
+        assert res.info[i]["status"] == 0
