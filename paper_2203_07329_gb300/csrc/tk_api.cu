@@ -143,6 +143,7 @@ struct Bufs {
   void* AozC = nullptr;     // ... the column-scaled slices of A, their column exponents
   int* EC = nullptr;
   void* colmax = nullptr;
+  int* oz_err = nullptr;    // set by a timed-out wait of the emulated products
   void* Roz = nullptr;      // ... and of the residuals (normal-equation pass)
   int* ER = nullptr;
   char* scratch = nullptr;  // sketch scratch
@@ -213,7 +214,8 @@ void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
     B.EA = a.take<int>(P.m);
     B.Xoz = a.take<char>(oz_slices_bytes(N, P.n));
     B.EX = a.take<int>(N);
-    B.AozC = a.take<char>(oz_slices_bytes(P.m, P.n));
+    B.AozC = a.take<char>(oz_slices_bytes(P.n, P.m));  // A^T, column exponents
+    B.oz_err = a.take<int>(4);
     B.EC = a.take<int>(P.n);
     B.colmax = a.take<char>(oz_colmax_bytes(P.n));
     B.Roz = a.take<char>(oz_slices_bytes(N, P.m));
@@ -586,6 +588,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       const int tok = prof_begin(TK_PHASE_RES64, st);
       TK_TRY(oz_prepare(p->A, P.dt, P.m, P.n, P.lda, B.Aoz, B.EA, st));
       TK_TRY(oz_prepare_cols(p->A, P.dt, P.m, P.n, P.lda, B.AozC, B.EC, B.colmax, st));
+      TK_CUDA(cudaMemsetAsync(B.oz_err, 0, sizeof(int), st));
       prof_end(tok, st, 0.0, 2.0 * ((P.dt == TK_F64 ? 16.0 : 8.0) * P.m * P.n + 16.0 * P.m * P.n));
     }
     for (int round = 0; round < P.o.max_refine && !act.empty(); ++round) {
@@ -606,7 +609,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
         int tok = prof_begin(TK_PHASE_RES64, st);
         if (P.o.emulate_fp64) {
           TK_TRY(oz_prepare(B.Xa, TK_F64, cnt, P.n, P.n, B.Xoz, B.EX, st));
-          TK_TRY(oz_residual(B.Aoz, B.EA, P.m, P.n, B.Xoz, B.EX, cnt, p->b, B.Rres, P.m, st));
+          TK_TRY(oz_residual(B.Aoz, B.EA, P.m, P.n, B.Xoz, B.EX, cnt, p->b, B.Rres, P.m, B.oz_err, st));
         } else if (P.dt == TK_F64) {
           TK_TRY((gemm<double, double, double>(false, true, cnt, P.m, P.n, B.Xa, P.n, A64, lda64, B.Rres, P.m, -1.0,
                                                B.ones, B.Rres, P.m, st)));
@@ -619,7 +622,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
         int sp;
         if (P.o.emulate_fp64) {
           sp = std::min(B.splits, oz_normal_splits(P.m, P.n, cnt));
-          TK_TRY(oz_normal(B.AozC, B.EC, P.m, P.n, B.Rres, P.m, cnt, B.Roz, B.ER, B.part, sp, st));
+          TK_TRY(oz_normal(B.AozC, B.EC, P.m, P.n, B.Rres, P.m, cnt, B.Roz, B.ER, B.part, sp, B.oz_err, st));
         } else {
           sp = P.dt == TK_F64 ? splitk_tuned<double, double>(cnt, P.n, P.m, B.splits)
                               : splitk_tuned<double, float>(cnt, P.n, P.m, B.splits);
@@ -643,7 +646,14 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       k_refine_update<<<cnt, 256, 0, st>>>(X, B.D, P.n, B.ids, B.nrm);
       TK_LAUNCH_CHECK();
       TK_CUDA(cudaMemcpyAsync(hn.data(), B.nrm, sizeof(double) * 3 * cnt, cudaMemcpyDeviceToHost, st));
+      int oz_err = 0;
+      if (P.o.emulate_fp64 && round > 0)
+        TK_CUDA(cudaMemcpyAsync(&oz_err, B.oz_err, sizeof(int), cudaMemcpyDeviceToHost, st));
       TK_CUDA(cudaStreamSynchronize(st));
+      if (oz_err) {
+        set_error_msg("emulated float64 product: a pipeline wait timed out");
+        return TK_ETIMEOUT;
+      }
       for (const auto& r : res) {
         tk_info& q = inf[r.lam_idx];
         q.iters += r.iters;
@@ -1000,7 +1010,7 @@ TK_API tk_status tk_autotune(const tk_problem* p, int N, const tk_opts* o, void*
 namespace tk {
 struct ResidualBufs {
   void *Aoz, *Xoz, *AozC, *colmax, *Roz;
-  int *EA, *EX, *EC, *ER;
+  int *EA, *EX, *EC, *ER, *err;
   double *ones, *part;
   int splits;
 };
@@ -1010,13 +1020,14 @@ static void residual_carve(Arena& a, int64_t m, int64_t n, int M, ResidualBufs& 
   w.EA = a.take<int>(m);
   w.Xoz = a.take<char>(oz_slices_bytes(M, n));
   w.EX = a.take<int>(M);
-  w.AozC = a.take<char>(oz_slices_bytes(m, n));
+  w.AozC = a.take<char>(oz_slices_bytes(n, m));
   w.EC = a.take<int>(n);
   w.colmax = a.take<char>(oz_colmax_bytes(n));
   w.Roz = a.take<char>(oz_slices_bytes(M, m));
   w.ER = a.take<int>(M);
   w.ones = a.take<double>(std::max(M, 1));
   w.part = a.take<double>((size_t)w.splits * M * n);
+  w.err = a.take<int>(4);
 }
 __global__ void k_residual_sum_splits(const double* __restrict__ part, int splits, int64_t total,
                                       double* __restrict__ G) {
@@ -1053,13 +1064,15 @@ TK_API tk_status tk_residual(const tk_problem* p, const double* X, int M, int64_
   ResidualBufs w;
   residual_carve(a, p->m, p->n, M, w);
   const int64_t m = p->m, n = p->n;
+  int herr = 0;
   if (emulate) {
+    TK_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     TK_TRY(oz_prepare(p->A, p->dtype, m, n, p->lda, w.Aoz, w.EA, st));
     TK_TRY(oz_prepare(X, TK_F64, M, n, ldx, w.Xoz, w.EX, st));
-    TK_TRY(oz_residual(w.Aoz, w.EA, m, n, w.Xoz, w.EX, M, p->b, R, m, st));
+    TK_TRY(oz_residual(w.Aoz, w.EA, m, n, w.Xoz, w.EX, M, p->b, R, m, w.err, st));
     if (G) {
       TK_TRY(oz_prepare_cols(p->A, p->dtype, m, n, p->lda, w.AozC, w.EC, w.colmax, st));
-      TK_TRY(oz_normal(w.AozC, w.EC, m, n, R, m, M, w.Roz, w.ER, w.part, w.splits, st));
+      TK_TRY(oz_normal(w.AozC, w.EC, m, n, R, m, M, w.Roz, w.ER, w.part, w.splits, w.err, st));
       k_residual_sum_splits<<<(unsigned)std::min<int64_t>(cdiv((int64_t)M * n, 256), 152 * 8), 256, 0, st>>>(
           w.part, w.splits, (int64_t)M * n, G);
       TK_LAUNCH_CHECK();
@@ -1081,7 +1094,12 @@ TK_API tk_status tk_residual(const tk_problem* p, const double* X, int M, int64_
                                                  nullptr, nullptr, 0, st)));
     }
   }
+  if (emulate) TK_CUDA(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TK_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error_msg("emulated float64 product: a pipeline wait timed out");
+    return TK_ETIMEOUT;
+  }
   return TK_OK;
 }
 

@@ -216,25 +216,28 @@ constexpr int dtype_code() {
   return sizeof(T) == 8 ? 1 : 0;
 }
 
-// Float64-accurate residual on the BF16 tensor cores (tk_oz.cu): the rows of
-// X (rows x cols, row stride ld) split into 8 exact BF16 slices with row
-// exponents E; R[l][i] = b[i] - sum_k X[l][k] A[i][k] from the slices of A
-// (m x n) and of X (M x n).
+// Float64-accurate products on the BF16 tensor cores (tk_oz.cu).  The rows of
+// X (rows x cols, row stride ld) are split into 8 exact BF16 slice planes
+// (row stride cols rounded up to 64) with row exponents E (oz_prepare), or the
+// columns of X into planes of X^T with column exponents (oz_prepare_cols:
+// slices bytes oz_slices_bytes(cols, rows), E: cols ints, colmax:
+// oz_colmax_bytes(cols)).  *err (device) is set if a pipeline wait timed out.
 size_t oz_slices_bytes(int64_t rows, int64_t cols);
 tk_status oz_prepare(const void* X, tk_dtype dt, int64_t rows, int64_t cols, int64_t ld, void* slices, int* E,
                      cudaStream_t st);
-tk_status oz_residual(const void* Aslices, const int* EA, int64_t m, int64_t n, const void* Xslices, const int* EX,
-                      int64_t M, const double* b, double* R, int64_t ldr, cudaStream_t st);
-// Slices with one exponent per column (E: cols ints; colmax: oz_colmax_bytes).
 size_t oz_colmax_bytes(int64_t cols);
 tk_status oz_prepare_cols(const void* X, tk_dtype dt, int64_t rows, int64_t cols, int64_t ld, void* slices, int* E,
                           void* colmax, cudaStream_t st);
+// R[l][i] = b[i] - sum_k X[l][k] A[i][k] from the row slices of A (m x n) and
+// of X (M x n).
+tk_status oz_residual(const void* Aslices, const int* EA, int64_t m, int64_t n, const void* Xslices, const int* EX,
+                      int64_t M, const double* b, double* R, int64_t ldr, int* err, cudaStream_t st);
 // The normal-equation pass: partial[z][l][j] (z < splits; unused planes zero)
-// of sum_i A[i][j] R[l][i], from the column-scaled slices of A (oz_prepare_cols)
-// and R (M x m, row stride ldr); Rslices: oz_slices_bytes(M, m), EX: M ints.
+// of sum_i A[i][j] R[l][i], from the column slices of A (oz_prepare_cols) and
+// R (M x m, row stride ldr); Rslices: oz_slices_bytes(M, m), EX: M ints.
 int oz_normal_splits(int64_t m, int64_t n, int64_t M);
-tk_status oz_normal(const void* AslicesC, const int* EC, int64_t m, int64_t n, const double* R, int64_t ldr,
-                    int64_t M, void* Rslices, int* EX, double* partial, int splits, cudaStream_t st);
+tk_status oz_normal(const void* AslicesT, const int* EC, int64_t m, int64_t n, const double* R, int64_t ldr,
+                    int64_t M, void* Rslices, int* EX, double* partial, int splits, int* err, cudaStream_t st);
 
 // Dense kernels (tk_dense.cu)
 template <typename TA, typename TB, typename TC>

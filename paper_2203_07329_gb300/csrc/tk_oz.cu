@@ -2,36 +2,36 @@
 // integer slices, in the manner of Ozaki's error-free matrix multiplication).
 //
 // GB300 issues about two float64 FMA per clock per SM, so the float64 passes
-// of the mixed form's refinement (r = b - X A^T, a float64 GEMM with 32 lambda
-// rows) are bound by that pipe.  Here every row of A is scaled by a power of
-// two so that its entries lie in (-1, 1) and split into S = 8 signed 7-bit
-// integer slices,  a = sum_p s_p 2^(-7(p+1)),  |s_p| <= 127,  exactly
-// representable in BF16; the lambda rows of X are split the same way.  A
-// product of two slices is an integer below 2^14; the pairs (p, q) with
-// p + q = t share one FP32 accumulator ("level" t), and a level sum of at most
-// 8 pairs over 128 values of K stays below 2^24, so the tensor core's FP32
-// accumulation is exact.  Every 128 values of K the level sums are scaled by
-// 2^(-7(t+2)) and added into float64 accumulators (smallest level first).
-// Pairs with p + q > 7 are dropped: their contribution is below
-// 9 * 2^-56 of max|a| max|x| per product, and the 56-bit slicing of a and x
-// rounds at 2^-57 of their row maxima: the float64 accuracy of a float64
-// GEMM.  The products are mma.sync m16n8k16 BF16 (FP32 accumulate).
+// of the mixed form's refinement (r = b - X A^T and A^T r, float64 GEMMs with
+// up to 32 lambda rows) are bound by that pipe.  Here every row of an operand
+// is scaled by a power of two so that its entries lie in (-1, 1), rounded to
+// 56 bits and split into S = 8 signed 7-bit integer slices,
+//   a = sum_p s_p 2^(-7(p+1)),  |s_p| <= 127,
+// each exactly representable in BF16.  A product of two slices is an integer
+// below 2^14; the pairs (p, q) with p + q = t share one FP32 accumulator
+// ("level" t), and a level sum of at most 8 pairs over 128 values of K stays
+// below 2^24, so the tensor core's FP32 accumulation is exact.  Every 128
+// values of K the level sums are scaled by 2^(-7(t+2)) and added into float64
+// accumulators.  Pairs with p + q > 7 are dropped: their contribution is below
+// 9 * 2^-56 of max|a| max|x| per product, and the 56-bit rounding of a and x
+// is at 2^-57 of their row maxima: the accuracy of a float64 GEMM.
+//
+// The products run on tcgen05 (kind::f16, M = 128, N = 32, K = 16), operands
+// brought in by TMA in the 128-byte swizzle layout, the 8 level accumulators
+// in tensor memory, double-buffered so that four epilogue warps flush one
+// 128-value chunk of K into float64 while the MMAs of the next chunk run.
 #include <algorithm>
 #include <cuda_bf16.h>
 
 #include "tk_internal.cuh"
+#include "tk_tcgen05.cuh"
 
 namespace tk {
 namespace {
 
 constexpr int OZ_S = 8;          // slices
 constexpr int OZ_LV = OZ_S;      // levels t = p + q in 0..7 kept
-constexpr int OZ_BM = 64;        // rows of A per CTA
-constexpr int OZ_BN = 32;        // lambda rows per CTA
-constexpr int OZ_BK = 32;        // K per pipeline stage
-constexpr int OZ_STAGES = 3;
-constexpr int OZ_LDS = OZ_BK + 8;  // padded smem row (bf16): 80 bytes
-constexpr int OZ_CHUNK = 128;    // K per exact level accumulation
+constexpr int OZ_KPAD = 64;      // slice rows are padded to a multiple of 64 values of K (one TMA box)
 
 // Exponent E with max_j |row_j| < 2^E (0 for a zero row); one warp per row.
 template <typename T>
@@ -73,319 +73,327 @@ __global__ void k_oz_colexp(const unsigned long long* __restrict__ mx, int64_t c
   E[c] = e;
 }
 
-// Slices of X: planes out[p][r][c] (bf16, row stride cols_pad, zero in the
-// padding) with X[r][c] 2^-E = sum_p out[p][r][c] 2^(-7(p+1)) to within 2^-57
-// (rounded to nearest, so the errors of a row do not share a sign), E = E[r]
-// (row exponents) or E[c] (column exponents, COLS).  The fixed-point value is
-// formed with one scaling by a power of two and one conversion to int64.
-template <typename T, bool COLS>
+// The 8 slices of one value x 2^-E (|x 2^-E| < 1): round to 56 bits (to
+// nearest, so the errors of a row do not share a sign), then 7 bits per slice
+// from the top, all with the sign of the value.
+__device__ __forceinline__ void oz_split(double x, int E, __nv_bfloat16 (&s)[OZ_S]) {
+  const long long v = llrint(ldexp(x, 7 * OZ_S - E));  // |v| <= 2^56
+  const bool neg = v < 0;
+  unsigned long long u = neg ? (unsigned long long)(-v) : (unsigned long long)v;
+  u = u < (1ull << (7 * OZ_S)) ? u : (1ull << (7 * OZ_S)) - 1;  // 56 bits
+#pragma unroll
+  for (int p = 0; p < OZ_S; ++p) {
+    const int q = (int)((u >> (7 * (OZ_S - 1 - p))) & 127u);
+    s[p] = __int2bfloat16_rn(neg ? -q : q);
+  }
+}
+
+// Slices of the rows of X with row exponents E: planes out[p][r][c] (row
+// stride cols_pad, zero in the padding) with X[r][c] 2^-E[r] = sum_p
+// out[p][r][c] 2^(-7(p+1)) to within 2^-57.
+template <typename T>
 __global__ void k_oz_slice(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld, const int* __restrict__ E,
                            int64_t cols_pad, __nv_bfloat16* __restrict__ out) {
   const int64_t total = rows * cols_pad;
-  const int64_t plane = total;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = k / cols_pad, c = k - r * cols_pad;
-    long long v = 0;
-    if (c < cols) v = llrint(ldexp((double)X[r * ld + c], 7 * OZ_S - E[COLS ? c : r]));  // |v| <= 2^56
-    const bool neg = v < 0;
-    unsigned long long u = neg ? (unsigned long long)(-v) : (unsigned long long)v;
-    u = u < (1ull << (7 * OZ_S)) ? u : (1ull << (7 * OZ_S)) - 1;  // 56 bits
+    __nv_bfloat16 s[OZ_S];
+    oz_split(c < cols ? (double)X[r * ld + c] : 0.0, c < cols ? E[r] : 0, s);
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) {
-      const int s = (int)((u >> (7 * (OZ_S - 1 - p))) & 127u);
-      out[p * plane + k] = __int2bfloat16_rn(neg ? -s : s);
+    for (int p = 0; p < OZ_S; ++p) out[p * total + k] = s[p];
+  }
+}
+
+// Slices of the COLUMNS of X (rows x cols) with column exponents E, stored
+// transposed: planes out[p][c][r] (row stride rows_pad, zero in the padding).
+// 32 x 32 tiles through shared memory so that reads and writes are coalesced;
+// grid.x runs over row tiles, grid.y over column tiles.
+template <typename T>
+__global__ void k_oz_slice_t(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                             const int* __restrict__ E, int64_t rows_pad, __nv_bfloat16* __restrict__ out) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t r = r0 + ty + 8 * i, c = c0 + tx;
+    tile[ty + 8 * i][tx] = (r < rows && c < cols) ? (double)X[r * ld + c] : 0.0;
+  }
+  __syncthreads();
+  const int64_t plane = cols * rows_pad;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t c = c0 + ty + 8 * i, r = r0 + tx;
+    if (c < cols && r < rows_pad) {
+      __nv_bfloat16 s[OZ_S];
+      oz_split(tile[tx][ty + 8 * i], E[c], s);
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p) out[p * plane + c * rows_pad + r] = s[p];
     }
   }
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
-  const int n = valid ? 16 : 0;  // zero-fill when out of range
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
+// ---- the product on tcgen05 ---------------------------------------------------
+// D[r][l] = sum_k P[r][k] Q[l][k] from the slices of P (rows x K, row
+// exponents EP) and Q (M x K, row exponents EQ), both K-major planes.
+// CTA: 128 rows of P x 32 rows of Q x one K split (blockIdx.z).
+//   warp 0 (one lane): TMA producer -- per 64 values of K the 8 slices of Q
+//     (4 KiB each) into a 2-slot ring, then the 8 slices of P one by one
+//     (16 KiB each) into an 8-slot ring;
+//   warp 1 (one lane): MMA issuer -- for slice p of P and q <= 7 - p,
+//     D_(p+q) += P_p Q_q^T (4 MMAs of K = 16); the level accumulators of a
+//     chunk of 128 values of K sit in one of two tensor-memory buffers;
+//   warp 2: allocates / frees the 512 tensor-memory columns;
+//   warps 4-7: epilogue -- per chunk, read the 8 levels (lanes 32(w-4) ..),
+//     add them into 32 float64 accumulators per row, release the buffer;
+//     at the end write the result (MODE 0: R[l][r] = b[r] - D; MODE 1:
+//     partial[z][l][r] = D).
+// Every mbarrier wait is bounded; a wait that gives up sets *err and the
+// roles stop.
+constexpr int OT_M = 128;
+constexpr int OT_N = 32;
+constexpr int OT_KB = 64;
+constexpr int OT_CHUNK = 128;
+constexpr int OT_PST = 8;
+constexpr uint32_t OT_P_BYTES = OT_M * OT_KB * 2;   // 16 KiB
+constexpr uint32_t OT_QS_BYTES = OT_N * OT_KB * 2;  // 4 KiB
+constexpr uint32_t OT_Q_BYTES = OZ_S * OT_QS_BYTES;
+constexpr uint32_t OT_TMEM_COLS = 2 * OZ_LV * OT_N;  // 512
 
-struct OzSmem {
-  __nv_bfloat16 a[OZ_STAGES][OZ_S][OZ_BM][OZ_LDS];  // A slices: rows x K
-  __nv_bfloat16 x[OZ_STAGES][OZ_S][OZ_BN][OZ_LDS];  // X slices: lambda rows x K
+struct OtSmem {
+  uint8_t p[OT_PST][OT_P_BYTES];
+  uint8_t q[2][OT_Q_BYTES];
+  uint64_t p_full[OT_PST];
+  uint64_t p_empty[OT_PST];
+  uint64_t q_full[2];
+  uint64_t q_empty[2];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint32_t tmem_base;
 };
 
-// R[l][i] = b[i] - sum_k X[l][k] A[i][k] for i < m, l < M (float64 result).
-// A slices: OZ_S planes of m x kp (kp = K rounded up to 8, zero padded), row
-// exponents EA; X slices: OZ_S planes of M x kp, row exponents EX.  CTA: 64
-// rows of A x 32 lambda rows; 8 warps = 4 (16 rows) x 2 (16 lambda).
-__global__ void __launch_bounds__(256, 1)
-    k_oz_residual(const __nv_bfloat16* __restrict__ As, const int* __restrict__ EA, int64_t m, int64_t kp,
-                  const __nv_bfloat16* __restrict__ Xs, const int* __restrict__ EX, int64_t M,
-                  const double* __restrict__ b, double* __restrict__ R, int64_t ldr) {
-  extern __shared__ __align__(16) unsigned char oz_raw[];
-  OzSmem& S = *reinterpret_cast<OzSmem*>(oz_raw);
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int wr = w & 3, wc = w >> 2;
-  const int64_t i0 = (int64_t)blockIdx.x * OZ_BM, l0 = (int64_t)blockIdx.y * OZ_BN;
-  const int64_t planeA = m * kp, planeX = M * kp;
-  const int nk = (int)(kp / OZ_BK) + (kp % OZ_BK ? 1 : 0);
-
-  auto load = [&](int stage, int kt) {
-    const int64_t k0 = (int64_t)kt * OZ_BK;
-    // A: OZ_S x 64 rows x 4 chunks of 8 bf16; X: OZ_S x 32 rows x 4 chunks
-    for (int q = tid; q < OZ_S * OZ_BM * 4; q += 256) {
-      const int p = q / (OZ_BM * 4), rem = q % (OZ_BM * 4), r = rem >> 2, c = (rem & 3) * 8;
-      const int64_t gi = i0 + r, gk = k0 + c;
-      const bool ok = gi < m && gk < kp;
-      cp_async16(&S.a[stage][p][r][c], ok ? (const void*)(As + p * planeA + gi * kp + gk) : (const void*)As, ok);
-    }
-    for (int q = tid; q < OZ_S * OZ_BN * 4; q += 256) {
-      const int p = q / (OZ_BN * 4), rem = q % (OZ_BN * 4), r = rem >> 2, c = (rem & 3) * 8;
-      const int64_t gl = l0 + r, gk = k0 + c;
-      const bool ok = gl < M && gk < kp;
-      cp_async16(&S.x[stage][p][r][c], ok ? (const void*)(Xs + p * planeX + gl * kp + gk) : (const void*)Xs, ok);
-    }
-  };
-
-  float acc[OZ_LV][2][4];
-  double acc64[2][4];
-#pragma unroll
-  for (int t = 0; t < OZ_LV; ++t)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[t][j][e] = 0.f;
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) acc64[j][e] = 0.0;
-
-  auto flush = [&]() {
-#pragma unroll
-    for (int t = OZ_LV - 1; t >= 0; --t) {
-      const double sc = ldexp(1.0, -7 * (t + 2));
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          acc64[j][e] = fma((double)acc[t][j][e], sc, acc64[j][e]);
-          acc[t][j][e] = 0.f;
-        }
-    }
-  };
-
-  // prologue
-#pragma unroll
-  for (int s = 0; s < OZ_STAGES - 1; ++s) {
-    if (s < nk) load(s, s);
-    cp_commit();
-  }
-  const int steps_per_chunk = OZ_CHUNK / OZ_BK;
-  for (int kt = 0; kt < nk; ++kt) {
-    cp_wait<OZ_STAGES - 2>();
-    __syncthreads();
-    {
-      const int nt = kt + OZ_STAGES - 1;
-      if (nt < nk) load(nt % OZ_STAGES, nt);
-      cp_commit();
-    }
-    const int st = kt % OZ_STAGES;
-#pragma unroll
-    for (int kk = 0; kk < OZ_BK; kk += 16) {
-      uint32_t af[OZ_S][4], xf[OZ_S][4];
-      // A: rows 16 wr + (lane & 15), k kk + 8 (lane >> 4); X: lambda rows 16 wc + ..., same k pattern
-      const int ar = wr * 16 + (lane & 15), ac = kk + (lane >> 4) * 8;
-      const int xr = wc * 16 + (lane & 7) + ((lane >> 4) << 3), xc = kk + ((lane >> 3) & 1) * 8;
-#pragma unroll
-      for (int p = 0; p < OZ_S; ++p) {
-        ldsm_x4(af[p], &S.a[st][p][ar][ac]);
-        ldsm_x4(xf[p], &S.x[st][p][xr][xc]);
-      }
-#pragma unroll
-      for (int p = 0; p < OZ_S; ++p)
-#pragma unroll
-        for (int q = 0; q < OZ_S - p; ++q) {
-          mma_bf16(acc[p + q][0], af[p], xf[q][0], xf[q][1]);
-          mma_bf16(acc[p + q][1], af[p], xf[q][2], xf[q][3]);
-        }
-    }
-    if ((kt + 1) % steps_per_chunk == 0 || kt + 1 == nk) flush();
-  }
-  cp_wait<0>();
-
-  // epilogue: fragment (row g = lane / 4 (+8), col 2 (lane % 4) (+1)) of each n8 tile
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int64_t i = i0 + wr * 16 + (lane >> 2) + ((e >> 1) << 3);
-      const int64_t l = l0 + wc * 16 + j * 8 + (lane & 3) * 2 + (e & 1);
-      if (i < m && l < M) R[l * ldr + i] = b[i] - ldexp(acc64[j][e], EA[i] + EX[l]);
-    }
+// An FP32 value holding an integer (|v| < 2^24), times 2^(-7(t+2)), as a
+// double: the float's fields moved into the double's, the power of two added
+// to the exponent (exact; no conversion instruction).
+__device__ __forceinline__ double level_to_double(uint32_t bits, int t) {
+  const uint32_t a = bits & 0x7fffffffu;
+  const uint32_t mag = a ? (a >> 3) + ((uint32_t)(896 - 7 * (t + 2)) << 20) : 0u;
+  return __hiloint2double((int)(mag | (bits & 0x80000000u)), (int)(bits << 29));
 }
 
-// ---- the normal-equation pass -----------------------------------------------
-// G = R A (g_l = A^T r_l): the slices of A here are scaled per COLUMN (the
-// output index), those of R per row, so every output carries the float64
-// accuracy of its own column whatever the scales of A's columns.
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t* r, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
+template <int MODE>
+__global__ void __launch_bounds__(256, 1)
+    k_oz_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
+            const int* __restrict__ EP, const int* __restrict__ EQ, int64_t rows, int M, int64_t K, int64_t kps,
+            const double* __restrict__ b, double* __restrict__ out, int64_t ldo, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t ot_raw[];
+  OtSmem& S = *reinterpret_cast<OtSmem*>((reinterpret_cast<uintptr_t>(ot_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * OT_M;
+  const int l0 = (int)blockIdx.y * OT_N;
+  const int64_t kbeg = (int64_t)blockIdx.z * kps;
+  const int64_t kend = K < kbeg + kps ? K : kbeg + kps;
+  const int nkb = kend > kbeg ? (int)((kend - kbeg + OT_KB - 1) / OT_KB) : 0;
+  const int nch = (nkb + 1) / 2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OT_PST; ++s) {
+      mbar_init(&S.p_full[s], 1);
+      mbar_init(&S.p_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&S.q_full[s], 1);
+      mbar_init(&S.q_empty[s], 1);
+      mbar_init(&S.acc_full[s], 1);
+      mbar_init(&S.acc_empty[s], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "r"(OT_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    int g = 0;
+    bool live = true;
+    for (int kb = 0; kb < nkb && live; ++kb) {
+      const int kc = (int)(kbeg + (int64_t)kb * OT_KB);
+      const int qs = kb & 1;
+      if (!mbar_wait(&S.q_empty[qs], ((uint32_t)(kb >> 1) & 1u) ^ 1u, err)) break;
+      mbar_expect_tx(&S.q_full[qs], OT_Q_BYTES);
+      for (int p = 0; p < OZ_S; ++p) tma_load_3d(&tmQ, &S.q_full[qs], S.q[qs] + p * OT_QS_BYTES, kc, l0, p);
+      for (int p = 0; p < OZ_S; ++p, ++g) {
+        const int ps = g % OT_PST;
+        if (!mbar_wait(&S.p_empty[ps], ((uint32_t)(g / OT_PST) & 1u) ^ 1u, err)) {
+          live = false;
+          break;
+        }
+        mbar_expect_tx(&S.p_full[ps], OT_P_BYTES);
+        tma_load_3d(&tmP, &S.p_full[ps], S.p[ps], kc, (int)r0, p);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(OT_M, OT_N);
+    int g = 0;
+    bool live = true;
+    for (int c = 0; c < nch && live; ++c) {
+      const int bsel = c & 1, use = c >> 1;
+      if (use > 0 && !mbar_wait(&S.acc_empty[bsel], (uint32_t)(use - 1) & 1u, err)) break;
+      tc_fence_after();
+      const uint32_t dbase = tmem + (uint32_t)(bsel * OZ_LV * OT_N);
+      const int kb_end = nkb < 2 * c + 2 ? nkb : 2 * c + 2;
+      for (int kb = 2 * c; kb < kb_end && live; ++kb) {
+        const int qs = kb & 1;
+        if (!mbar_wait(&S.q_full[qs], (uint32_t)(kb >> 1) & 1u, err)) {
+          live = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t qa = smem_u32(S.q[qs]);
+        for (int p = 0; p < OZ_S; ++p, ++g) {
+          const int ps = g % OT_PST;
+          if (!mbar_wait(&S.p_full[ps], (uint32_t)(g / OT_PST) & 1u, err)) {
+            live = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t pd = sdesc_sw128(smem_u32(S.p[ps]));
+          for (int q = 0; q < OZ_S - p; ++q) {
+            const uint64_t qd = sdesc_sw128(qa + (uint32_t)q * OT_QS_BYTES);
+            const uint32_t d = dbase + (uint32_t)((p + q) * OT_N);
+#pragma unroll
+            for (int k = 0; k < OT_KB / 16; ++k) {
+              // the first MMA of each level in a chunk (p = 0) overwrites the buffer
+              const uint32_t acc = (kb == 2 * c && p == 0 && k == 0) ? 0u : 1u;
+              tc_mma_bf16(d, pd + 2ull * k, qd + 2ull * k, idesc, acc);
+            }
+          }
+          tc_commit(&S.p_empty[ps]);
+        }
+        if (live) tc_commit(&S.q_empty[qs]);
+      }
+      if (live) tc_commit(&S.acc_full[bsel]);
+    }
+  } else if (warp >= 4) {
+    const int ew = warp - 4;
+    double acc64[OT_N];
+#pragma unroll
+    for (int j = 0; j < OT_N; ++j) acc64[j] = 0.0;
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+      const int bsel = c & 1, use = c >> 1;
+      if (!mbar_wait(&S.acc_full[bsel], (uint32_t)use & 1u, err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(bsel * OZ_LV * OT_N);
+#pragma unroll 1
+      for (int t = OZ_LV - 1; t >= 0; --t) {  // smallest level first
+        uint32_t v[32];
+        tmem_ld32_nowait(base + (uint32_t)(t * OT_N), v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < OT_N; ++j) acc64[j] += level_to_double(v[j], t);
+      }
+      tc_fence_before();
+      mbar_arrive(&S.acc_empty[bsel]);
+    }
+    const int64_t r = r0 + ew * 32 + lane;
+    if (ok && r < rows) {
+      const int er = EP[r];
+      const double br = MODE == 0 ? b[r] : 0.0;
+#pragma unroll
+      for (int j = 0; j < OT_N; ++j) {
+        const int l = l0 + j;
+        if (l < M) {
+          const double v = ldexp(acc64[j], er + EQ[l]);
+          if (MODE == 0) out[(int64_t)l * ldo + r] = br - v;
+          else out[((int64_t)blockIdx.z * M + l) * ldo + r] = v;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OT_TMEM_COLS) : "memory");
+  }
 }
 
-constexpr int OZ_NJ = 64;           // columns of A (outputs) per CTA
-constexpr int OZ_LDT = OZ_NJ + 8;   // padded smem row (bf16): 144 bytes
-
-struct OzSmemT {
-  __nv_bfloat16 a[OZ_STAGES][OZ_S][OZ_BK][OZ_LDT];  // A slices: K (rows of A) x 64 columns
-  __nv_bfloat16 x[OZ_STAGES][OZ_S][OZ_BN][OZ_LDS];  // R slices: lambda rows x K
-};
-
-// partial[z][l][j] = sum_{i in split z} A[i][j] R[l][i] for j < n, l < M, from
-// the slices of A (OZ_S planes m x kpA, column exponents EC) and of R (OZ_S
-// planes M x kpR, row exponents EX).  Split z covers rows [z kps, (z+1) kps)
-// of A, kps a multiple of 128.  CTA: 64 columns x 32 lambda; warps 4 x 2.
-__global__ void __launch_bounds__(256, 1)
-    k_oz_normal(const __nv_bfloat16* __restrict__ As, const int* __restrict__ EC, int64_t m, int64_t n, int64_t kpA,
-                const __nv_bfloat16* __restrict__ Rs, const int* __restrict__ EX, int64_t M, int64_t kpR,
-                int64_t kps, double* __restrict__ partial) {
-  extern __shared__ __align__(16) unsigned char oz_raw_t[];
-  OzSmemT& S = *reinterpret_cast<OzSmemT*>(oz_raw_t);
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int wr = w & 3, wc = w >> 2;
-  const int64_t j0 = (int64_t)blockIdx.x * OZ_NJ, l0 = (int64_t)blockIdx.y * OZ_BN;
-  const int64_t kb = (int64_t)blockIdx.z * kps, ke = std::min<int64_t>(m, kb + kps);
-  const int64_t planeA = m * kpA, planeR = M * kpR;
-  const int nk = ke > kb ? (int)((ke - kb + OZ_BK - 1) / OZ_BK) : 0;
-
-  auto load = [&](int stage, int kt) {
-    const int64_t k0 = kb + (int64_t)kt * OZ_BK;
-    // A: OZ_S x 32 rows (i) x 8 chunks of 8 columns
-    for (int q = tid; q < OZ_S * OZ_BK * 8; q += 256) {
-      const int p = q / (OZ_BK * 8), rem = q % (OZ_BK * 8), r = rem >> 3, c = (rem & 7) * 8;
-      const int64_t gi = k0 + r, gj = j0 + c;
-      const bool ok = gi < ke && gj < kpA;
-      cp_async16(&S.a[stage][p][r][c], ok ? (const void*)(As + p * planeA + gi * kpA + gj) : (const void*)As, ok);
-    }
-    // R: OZ_S x 32 lambda rows x 4 chunks of 8 values of K
-    for (int q = tid; q < OZ_S * OZ_BN * 4; q += 256) {
-      const int p = q / (OZ_BN * 4), rem = q % (OZ_BN * 4), r = rem >> 2, c = (rem & 3) * 8;
-      const int64_t gl = l0 + r, gk = k0 + c;
-      const bool ok = gl < M && gk < ke;
-      cp_async16(&S.x[stage][p][r][c], ok ? (const void*)(Rs + p * planeR + gl * kpR + gk) : (const void*)Rs, ok);
-    }
-  };
-
-  float acc[OZ_LV][2][4];
-  double acc64[2][4];
-#pragma unroll
-  for (int t = 0; t < OZ_LV; ++t)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[t][j][e] = 0.f;
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) acc64[j][e] = 0.0;
-  auto flush = [&]() {
-#pragma unroll
-    for (int t = OZ_LV - 1; t >= 0; --t) {
-      const double sc = ldexp(1.0, -7 * (t + 2));
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          acc64[j][e] = fma((double)acc[t][j][e], sc, acc64[j][e]);
-          acc[t][j][e] = 0.f;
-        }
-    }
-  };
-
-#pragma unroll
-  for (int s = 0; s < OZ_STAGES - 1; ++s) {
-    if (s < nk) load(s, s);
-    cp_commit();
+// 3D map over the slice planes (K fastest, then rows, then the slice index),
+// box = 64 values of K x box_rows x 1 slice, 128-byte swizzle.
+tk_status make_slice_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, uint32_t box_rows) {
+  EncodeTiledFn fn;
+  TK_TRY(encode_fn(&fn));
+  const cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)OZ_S};
+  const cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)rows * kp * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)OT_KB, box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error_msg("cuTensorMapEncodeTiled rejected the slice layout");
+    return TK_ECUDA;
   }
-  const int steps_per_chunk = OZ_CHUNK / OZ_BK;
-  for (int kt = 0; kt < nk; ++kt) {
-    cp_wait<OZ_STAGES - 2>();
-    __syncthreads();
-    {
-      const int nt = kt + OZ_STAGES - 1;
-      if (nt < nk) load(nt % OZ_STAGES, nt);
-      cp_commit();
-    }
-    const int st = kt % OZ_STAGES;
-#pragma unroll
-    for (int kk = 0; kk < OZ_BK; kk += 16) {
-      uint32_t af[OZ_S][4], xf[OZ_S][4];
-      // A^T fragment (rows j, K i): transposed 8x8 loads of rows i, 8 columns j each
-      const int ai = kk + (lane & 7) + ((lane >> 4) << 3), aj = wr * 16 + ((lane >> 3) & 1) * 8;
-      const int xr = wc * 16 + (lane & 7) + ((lane >> 4) << 3), xc = kk + ((lane >> 3) & 1) * 8;
-#pragma unroll
-      for (int p = 0; p < OZ_S; ++p) {
-        ldsm_x4_trans(af[p], &S.a[st][p][ai][aj]);
-        ldsm_x4(xf[p], &S.x[st][p][xr][xc]);
-      }
-#pragma unroll
-      for (int p = 0; p < OZ_S; ++p)
-#pragma unroll
-        for (int q = 0; q < OZ_S - p; ++q) {
-          mma_bf16(acc[p + q][0], af[p], xf[q][0], xf[q][1]);
-          mma_bf16(acc[p + q][1], af[p], xf[q][2], xf[q][3]);
-        }
-    }
-    if ((kt + 1) % steps_per_chunk == 0 || kt + 1 == nk) flush();
+  return TK_OK;
+}
+
+template <int MODE>
+tk_status launch_oz_tc(const void* Ps, const int* EP, int64_t rows, const void* Qs, const int* EQ, int M, int64_t K,
+                       int splits, const double* b, double* out, int64_t ldo, int* err, cudaStream_t st) {
+  const int64_t kp = cdiv(K, OZ_KPAD) * OZ_KPAD;
+  if (rows > INT32_MAX || kp > INT32_MAX || M > 65535 * OT_N) {
+    set_error_msg("emulated float64 product: dimensions exceed the 32-bit TMA coordinates");
+    return TK_EINVAL;
   }
-  cp_wait<0>();
-  double* P = partial + (int64_t)blockIdx.z * M * n;
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int64_t jj = j0 + wr * 16 + (lane >> 2) + ((e >> 1) << 3);
-      const int64_t l = l0 + wc * 16 + j * 8 + (lane & 3) * 2 + (e & 1);
-      if (jj < n && l < M) P[l * n + jj] = ldexp(acc64[j][e], EX[l] + EC[jj]);
-    }
+  CUtensorMap mP, mQ;
+  TK_TRY(make_slice_map(&mP, Ps, rows, kp, OT_M));
+  TK_TRY(make_slice_map(&mQ, Qs, M, kp, OT_N));
+  const int64_t kps = cdiv(cdiv(K, splits), OT_CHUNK) * OT_CHUNK;  // whole chunks per split
+  const int sp = (int)cdiv(K, kps);
+  const size_t smem = sizeof(OtSmem) + 1024;
+  TK_CUDA(cudaFuncSetAttribute(k_oz_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const dim3 grid((unsigned)cdiv(rows, OT_M), (unsigned)cdiv(M, OT_N), (unsigned)sp);
+  k_oz_tc<MODE><<<grid, 256, smem, st>>>(mP, mQ, EP, EQ, rows, M, kp, kps, b, out, ldo, err);
+  TK_LAUNCH_CHECK();
+  if (MODE == 1 && sp < splits) {  // the caller sums `splits` planes: the unused ones are zero
+    TK_CUDA(cudaMemsetAsync(out + (int64_t)sp * M * ldo, 0, sizeof(double) * (size_t)(splits - sp) * M * ldo, st));
+  }
+  return TK_OK;
 }
 
 }  // namespace
 
 size_t oz_slices_bytes(int64_t rows, int64_t cols) {
-  return sizeof(__nv_bfloat16) * (size_t)OZ_S * (size_t)rows * (size_t)(cdiv(cols, 8) * 8);
+  return sizeof(__nv_bfloat16) * (size_t)OZ_S * (size_t)rows * (size_t)(cdiv(cols, OZ_KPAD) * OZ_KPAD);
 }
 
 tk_status oz_prepare(const void* X, tk_dtype dt, int64_t rows, int64_t cols, int64_t ld, void* slices, int* E,
                      cudaStream_t st) {
   if (rows == 0 || cols == 0) return TK_OK;
-  const int64_t kp = cdiv(cols, 8) * 8;
+  const int64_t kp = cdiv(cols, OZ_KPAD) * OZ_KPAD;
   const unsigned gr = (unsigned)cdiv(rows, 8);
   const unsigned gs = (unsigned)std::min<int64_t>(cdiv(rows * kp, 256), 152 * 32);
   __nv_bfloat16* out = static_cast<__nv_bfloat16*>(slices);
   if (dt == TK_F64) {
     k_oz_rowexp<double><<<gr, 256, 0, st>>>((const double*)X, rows, cols, ld, E);
     TK_LAUNCH_CHECK();
-    k_oz_slice<double, false><<<gs, 256, 0, st>>>((const double*)X, rows, cols, ld, E, kp, out);
+    k_oz_slice<double><<<gs, 256, 0, st>>>((const double*)X, rows, cols, ld, E, kp, out);
   } else {
     k_oz_rowexp<float><<<gr, 256, 0, st>>>((const float*)X, rows, cols, ld, E);
     TK_LAUNCH_CHECK();
-    k_oz_slice<float, false><<<gs, 256, 0, st>>>((const float*)X, rows, cols, ld, E, kp, out);
+    k_oz_slice<float><<<gs, 256, 0, st>>>((const float*)X, rows, cols, ld, E, kp, out);
   }
   TK_LAUNCH_CHECK();
   return TK_OK;
@@ -396,7 +404,7 @@ size_t oz_colmax_bytes(int64_t cols) { return sizeof(unsigned long long) * (size
 tk_status oz_prepare_cols(const void* X, tk_dtype dt, int64_t rows, int64_t cols, int64_t ld, void* slices, int* E,
                           void* colmax, cudaStream_t st) {
   if (rows == 0 || cols == 0) return TK_OK;
-  const int64_t kp = cdiv(cols, 8) * 8;
+  const int64_t rp = cdiv(rows, OZ_KPAD) * OZ_KPAD;
   unsigned long long* mx = static_cast<unsigned long long*>(colmax);
   TK_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * (size_t)cols, st));
   // about 4 CTAs of 256 columns per SM, each over a band of rows
@@ -404,56 +412,41 @@ tk_status oz_prepare_cols(const void* X, tk_dtype dt, int64_t rows, int64_t cols
   const int64_t bands = std::max<int64_t>(1, std::min<int64_t>(cdiv(4 * 152, cb), cdiv(rows, 64)));
   const int64_t rows_per = cdiv(rows, bands);
   const dim3 gm((unsigned)cb, (unsigned)cdiv(rows, rows_per));
-  const unsigned gs = (unsigned)std::min<int64_t>(cdiv(rows * kp, 256), 152 * 32);
+  if (cdiv(cols, 32) > 65535) {
+    set_error_msg("emulated float64 product: too many columns for the slicing grid");
+    return TK_EINVAL;
+  }
+  const dim3 gt((unsigned)cdiv(rp, 32), (unsigned)cdiv(cols, 32));
   __nv_bfloat16* out = static_cast<__nv_bfloat16*>(slices);
   if (dt == TK_F64) k_oz_colmax<double><<<gm, 256, 0, st>>>((const double*)X, rows, cols, ld, rows_per, mx);
   else k_oz_colmax<float><<<gm, 256, 0, st>>>((const float*)X, rows, cols, ld, rows_per, mx);
   TK_LAUNCH_CHECK();
   k_oz_colexp<<<(unsigned)cb, 256, 0, st>>>(mx, cols, E);
   TK_LAUNCH_CHECK();
-  if (dt == TK_F64) k_oz_slice<double, true><<<gs, 256, 0, st>>>((const double*)X, rows, cols, ld, E, kp, out);
-  else k_oz_slice<float, true><<<gs, 256, 0, st>>>((const float*)X, rows, cols, ld, E, kp, out);
+  if (dt == TK_F64) k_oz_slice_t<double><<<gt, dim3(32, 8), 0, st>>>((const double*)X, rows, cols, ld, E, rp, out);
+  else k_oz_slice_t<float><<<gt, dim3(32, 8), 0, st>>>((const float*)X, rows, cols, ld, E, rp, out);
   TK_LAUNCH_CHECK();
   return TK_OK;
 }
 
 tk_status oz_residual(const void* Aslices, const int* EA, int64_t m, int64_t n, const void* Xslices, const int* EX,
-                      int64_t M, const double* b, double* R, int64_t ldr, cudaStream_t st) {
+                      int64_t M, const double* b, double* R, int64_t ldr, int* err, cudaStream_t st) {
   if (m == 0 || M == 0) return TK_OK;
-  const int64_t kp = cdiv(n, 8) * 8;
-  const size_t smem = sizeof(OzSmem);
-  TK_CUDA(cudaFuncSetAttribute(k_oz_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(OzSmem)));
-  const dim3 grid((unsigned)cdiv(m, OZ_BM), (unsigned)cdiv(M, OZ_BN));
-  k_oz_residual<<<grid, 256, smem, st>>>(static_cast<const __nv_bfloat16*>(Aslices), EA, m, kp,
-                                        static_cast<const __nv_bfloat16*>(Xslices), EX, M, b, R, ldr);
-  TK_LAUNCH_CHECK();
-  return TK_OK;
+  return launch_oz_tc<0>(Aslices, EA, m, Xslices, EX, (int)M, n, 1, b, R, ldr, err, st);
 }
 
 int oz_normal_splits(int64_t m, int64_t n, int64_t M) {
-  const int64_t tiles = cdiv(n, OZ_NJ) * cdiv(M, OZ_BN);
-  const int64_t want = cdiv(4 * 152, std::max<int64_t>(tiles, 1));  // one CTA per SM: four full waves
-  const int64_t maxs = std::max<int64_t>(1, cdiv(m, OZ_CHUNK));
+  const int64_t tiles = cdiv(n, OT_M) * cdiv(M, OT_N);
+  const int64_t want = cdiv(2 * 152, std::max<int64_t>(tiles, 1));  // one CTA per SM: two full waves
+  const int64_t maxs = std::max<int64_t>(1, cdiv(m, OT_CHUNK));
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, maxs));
 }
 
-tk_status oz_normal(const void* AslicesC, const int* EC, int64_t m, int64_t n, const double* R, int64_t ldr,
-                    int64_t M, void* Rslices, int* EX, double* partial, int splits, cudaStream_t st) {
+tk_status oz_normal(const void* AslicesT, const int* EC, int64_t m, int64_t n, const double* R, int64_t ldr,
+                    int64_t M, void* Rslices, int* EX, double* partial, int splits, int* err, cudaStream_t st) {
   if (M == 0 || n == 0) return TK_OK;
-  const int64_t kpA = cdiv(n, 8) * 8, kpR = cdiv(m, 8) * 8;
   TK_TRY(oz_prepare(R, TK_F64, M, m, ldr, Rslices, EX, st));
-  const int64_t kps = cdiv(cdiv(m, splits), OZ_CHUNK) * OZ_CHUNK;
-  const int sp = (int)cdiv(m, kps);
-  TK_CUDA(cudaFuncSetAttribute(k_oz_normal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(OzSmemT)));
-  const dim3 grid((unsigned)cdiv(n, OZ_NJ), (unsigned)cdiv(M, OZ_BN), (unsigned)sp);
-  k_oz_normal<<<grid, 256, sizeof(OzSmemT), st>>>(static_cast<const __nv_bfloat16*>(AslicesC), EC, m, n, kpA,
-                                                  static_cast<const __nv_bfloat16*>(Rslices), EX, M, kpR, kps,
-                                                  partial);
-  TK_LAUNCH_CHECK();
-  if (sp < splits) {  // the caller sums `splits` planes: the unused ones are zero
-    TK_CUDA(cudaMemsetAsync(partial + (int64_t)sp * M * n, 0, sizeof(double) * (size_t)(splits - sp) * M * n, st));
-  }
-  return TK_OK;
+  return launch_oz_tc<1>(AslicesT, EC, n, Rslices, EX, (int)M, m, splits, nullptr, partial, n, err, st);
 }
 
 }  // namespace tk
