@@ -204,6 +204,19 @@ TK_API tk_status tk_sketch_apply(const tk_problem* p, const tk_opts* o, double* 
 TK_API tk_status tk_gram(const double* Y, int64_t r, int64_t c, int transpose_first, double* C, void* stream);
 
 /*
+ * tk_gram_emulated -- C = Y^T Y as tk_gram with transpose_first, formed on
+ * the BF16 tensor cores from exact integer slices of the columns of Y with
+ * float64 accuracy (the Gram matrix of the mixed form with emulate_fp64; no
+ * counterpart in the paper's algorithms beyond Algorithm 1 step 3 itself).
+ * Only the upper triangle (j >= i) of C is defined on return.
+ *   work: device, tk_gram_emulated_workspace(r, c) bytes.
+ *   Returns TK_ETIMEOUT if a device-side pipeline wait gave up.
+ */
+TK_API size_t tk_gram_emulated_workspace(int64_t r, int64_t c);
+TK_API tk_status tk_gram_emulated(const double* Y, int64_t r, int64_t c, double* C, void* work, size_t work_bytes,
+                                  void* stream);
+
+/*
  * tk_cholesky_shifted -- R_i = chol(C + lambda_i I) for i = 0..N-1
  * (Algorithm 1 step 4), upper triangular, float64.
  *   C: device n x n (symmetric, only the upper triangle is read).
@@ -214,6 +227,18 @@ TK_API tk_status tk_gram(const double* Y, int64_t r, int64_t c, int transpose_fi
 TK_API size_t tk_cholesky_workspace(int64_t n, int N);
 TK_API tk_status tk_cholesky_shifted(const double* C, int64_t n, const double* lambdas, int N, double* R,
                                      int* breakdown, void* work, size_t work_bytes, void* stream);
+
+/*
+ * tk_cholesky_shifted_emulated -- as tk_cholesky_shifted, with the trailing
+ * updates of the blocked factorization (R_22 -= R_12^T R_12) formed on the
+ * BF16 tensor cores from exact integer slices with float64 accuracy (the
+ * Cholesky of the mixed form with emulate_fp64).  The diagonal blocks and the
+ * panel solves stay float64.  work: tk_cholesky_emulated_workspace(n, N)
+ * bytes; TK_ETIMEOUT if a device-side pipeline wait gave up.
+ */
+TK_API size_t tk_cholesky_emulated_workspace(int64_t n, int N);
+TK_API tk_status tk_cholesky_shifted_emulated(const double* C, int64_t n, const double* lambdas, int N, double* R,
+                                              int* breakdown, void* work, size_t work_bytes, void* stream);
 
 /*
  * tk_sketch_svd -- [~, Sigma, V] = svd(Y, 'econ') of Algorithm 3 step 4 by

@@ -159,6 +159,10 @@ struct Bufs {
 // cores (BF16 operands, FP32 accumulation); every other sketch is SIMT.
 bool tc_sketch(const Plan& P) { return P.mixed && P.o.sketch == TK_SKETCH_GAUSS && !P.under; }
 
+// The mixed form with emulate_fp64 forms its Gram matrix from exact slices on
+// the tensor cores (float64 accuracy).
+bool emulated_gram(const Plan& P) { return P.mixed && P.o.emulate_fp64 && !P.lowrank; }
+
 size_t sketch_scratch(const Plan& P) {
   tk_dtype dt = P.mixed ? TK_F32 : P.dt;
   if (tc_sketch(P)) return tc_sketch_workspace(P.L, P.c, P.s);
@@ -209,13 +213,13 @@ void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
       B.lrS32 = a.take<float>((size_t)N * P.s);
     }
   }
+  if (P.mixed && P.o.emulate_fp64) B.oz_err = a.take<int>(4);
   if (P.mixed && !P.prep_only && P.o.emulate_fp64) {
     B.Aoz = a.take<char>(oz_slices_bytes(P.m, P.n));
     B.EA = a.take<int>(P.m);
     B.Xoz = a.take<char>(oz_slices_bytes(N, P.n));
     B.EX = a.take<int>(N);
     B.AozC = a.take<char>(oz_slices_bytes(P.n, P.m));  // A^T, column exponents
-    B.oz_err = a.take<int>(4);
     B.EC = a.take<int>(P.n);
     B.colmax = a.take<char>(oz_colmax_bytes(P.n));
     B.Roz = a.take<char>(oz_slices_bytes(N, P.m));
@@ -233,7 +237,8 @@ void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
     B.nrm = a.take<double>((size_t)3 * N);
   }
   // the sketch's scratch is free again when the Gram matrix is formed
-  const size_t sc = std::max(sketch_scratch(P), P.lowrank ? size_t(0) : gram_scratch_bytes(P.s, P.c));
+  size_t sc = std::max(sketch_scratch(P), P.lowrank ? size_t(0) : gram_scratch_bytes(P.s, P.c));
+  if (emulated_gram(P)) sc = std::max({sc, oz_gram_workspace(P.s, P.c), oz_chol_workspace(P.np, N)});
   B.scratch_bytes = sc;
   B.scratch = t.take<char>(sc);
   if (P.prep_only) return;
@@ -465,15 +470,30 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
   std::vector<int> ok_ids;
   if (!P.lowrank) {
     int tok = prof_begin(TK_PHASE_GRAM, st);
-    TK_TRY(gram_upper(B.Y, P.s, P.c, B.C, B.scratch, B.scratch_bytes, st));  // the Cholesky reads only j >= i
+    if (emulated_gram(P)) {  // the Cholesky reads only j >= i
+      TK_CUDA(cudaMemsetAsync(B.oz_err, 0, sizeof(int), st));
+      TK_TRY(oz_gram(B.Y, P.s, P.c, B.C, B.scratch, B.scratch_bytes, B.oz_err, st));
+    } else {
+      TK_TRY(gram_upper(B.Y, P.s, P.c, B.C, B.scratch, B.scratch_bytes, st));
+    }
     prof_end(tok, st, (double)P.s * P.c * (P.c + 1), 8.0 * (P.s * P.c + P.c * (P.c + 1) / 2));
     Arena none;
     tok = prof_begin(TK_PHASE_CHOLESKY, st);
-    TK_TRY(chol_shifted(B.C, P.c, B.lam, N, B.R, P.np, P.np * P.np, B.info, none, st));
+    OzCholPlan ozp;  // the trailing updates on the tensor cores (the Gram scratch is free again)
+    if (emulated_gram(P))
+      TK_TRY(oz_chol_begin(B.R, P.np, P.np * P.np, N, P.np, B.scratch, B.scratch_bytes, B.oz_err, &ozp, st));
+    TK_TRY(chol_shifted(B.C, P.c, B.lam, N, B.R, P.np, P.np * P.np, B.info, none, st,
+                        emulated_gram(P) ? &ozp : nullptr));
     prof_end(tok, st, (double)N * P.c * P.c * P.c / 3.0, 8.0 * N * P.c * P.c);
     std::vector<int> hinfo(N);
     TK_CUDA(cudaMemcpyAsync(hinfo.data(), B.info, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    int gerr = 0;
+    if (emulated_gram(P)) TK_CUDA(cudaMemcpyAsync(&gerr, B.oz_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     TK_CUDA(cudaStreamSynchronize(st));
+    if (gerr) {
+      set_error_msg("emulated float64 Gram matrix: a pipeline wait timed out");
+      return TK_ETIMEOUT;
+    }
     for (int i = 0; i < N; ++i) {
       if (hinfo[i] != 0) inf[i].status = TK_ENOTSPD;
       else ok_ids.push_back(i);
@@ -1183,6 +1203,40 @@ TK_API tk_status tk_gram(const double* Y, int64_t r, int64_t c, int transpose_fi
   return TK_OK;
 }
 
+TK_API size_t tk_gram_emulated_workspace(int64_t r, int64_t c) {
+  if (r < 1 || c < 1) return 0;
+  Arena a;
+  a.take<char>(oz_gram_workspace(r, c));
+  a.take<int>(4);
+  return a.used + 512;
+}
+
+TK_API tk_status tk_gram_emulated(const double* Y, int64_t r, int64_t c, double* C, void* work, size_t work_bytes,
+                                  void* stream) {
+  if (!Y || !C || r < 1 || c < 1) return einval("bad Gram arguments");
+  if (!work || work_bytes < tk_gram_emulated_workspace(r, c)) {
+    set_error_msg("workspace smaller than tk_gram_emulated_workspace()");
+    return TK_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  const size_t gb = oz_gram_workspace(r, c);
+  void* gw = a.take<char>(gb);
+  int* err = a.take<int>(4);
+  TK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  TK_TRY(oz_gram(Y, r, c, C, gw, gb, err, st));
+  int herr = 0;
+  TK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error_msg("emulated float64 Gram matrix: a pipeline wait timed out");
+    return TK_ETIMEOUT;
+  }
+  return TK_OK;
+}
+
 TK_API size_t tk_cholesky_workspace(int64_t n, int N) {
   if (n < 1 || N < 1) return 0;
   const int64_t np = cdiv(n, 64) * 64;
@@ -1193,13 +1247,21 @@ TK_API size_t tk_cholesky_workspace(int64_t n, int N) {
   return a.used + 1024;
 }
 
-TK_API tk_status tk_cholesky_shifted(const double* C, int64_t n, const double* lambdas, int N, double* R,
-                                     int* breakdown, void* work, size_t work_bytes, void* stream) {
+TK_API size_t tk_cholesky_emulated_workspace(int64_t n, int N) {
+  if (n < 1 || N < 1) return 0;
+  const int64_t np = cdiv(n, 64) * 64;
+  return tk_cholesky_workspace(n, N) + oz_chol_workspace(np, N) + 1024;
+}
+
+namespace {
+tk_status cholesky_common(const double* C, int64_t n, const double* lambdas, int N, double* R, int* breakdown,
+                          void* work, size_t work_bytes, void* stream, bool emulate) {
   if (!C || !R || !lambdas || n < 1 || n > kMaxShort || N < 1) return einval("bad Cholesky arguments");
   for (int i = 0; i < N; ++i)
     if (!std::isfinite(lambdas[i])) return einval("lambda must be finite");
-  if (!work || work_bytes < tk_cholesky_workspace(n, N)) {
-    set_error_msg("workspace smaller than tk_cholesky_workspace()");
+  const size_t need = emulate ? tk_cholesky_emulated_workspace(n, N) : tk_cholesky_workspace(n, N);
+  if (!work || work_bytes < need) {
+    set_error_msg("workspace smaller than the Cholesky workspace query");
     return TK_ENOMEM;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -1210,21 +1272,47 @@ TK_API tk_status tk_cholesky_shifted(const double* C, int64_t n, const double* l
   double* lam = a.take<double>(N);
   int* info = a.take<int>(N);
   double* Rp = a.take<double>((size_t)N * np * np);
+  int* err = a.take<int>(4);
   TK_CUDA(cudaMemcpyAsync(lam, lambdas, sizeof(double) * N, cudaMemcpyHostToDevice, st));
   Arena none;
-  TK_TRY(chol_shifted(C, n, lam, N, Rp, np, np * np, info, none, st));
+  OzCholPlan plan;
+  if (emulate) {
+    const size_t ob = oz_chol_workspace(np, N);
+    void* ow = a.take<char>(ob);
+    if (!a.ok()) return TK_ENOMEM;
+    TK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    TK_TRY(oz_chol_begin(Rp, np, np * np, N, np, ow, ob, err, &plan, st));
+  }
+  TK_TRY(chol_shifted(C, n, lam, N, Rp, np, np * np, info, none, st, emulate ? &plan : nullptr));
   for (int i = 0; i < N; ++i)
     TK_CUDA(cudaMemcpy2DAsync(R + (size_t)i * n * n, sizeof(double) * n, Rp + (size_t)i * np * np,
                               sizeof(double) * np, sizeof(double) * n, n, cudaMemcpyDeviceToDevice, st));
   std::vector<int> h(N);
+  int herr = 0;
   TK_CUDA(cudaMemcpyAsync(h.data(), info, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+  if (emulate) TK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TK_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error_msg("emulated Cholesky update: a pipeline wait timed out");
+    return TK_ETIMEOUT;
+  }
   tk_status worst = TK_OK;
   for (int i = 0; i < N; ++i) {
     if (breakdown) breakdown[i] = h[i];
     if (h[i]) worst = TK_ENOTSPD;
   }
   return worst;
+}
+}  // namespace
+
+TK_API tk_status tk_cholesky_shifted(const double* C, int64_t n, const double* lambdas, int N, double* R,
+                                     int* breakdown, void* work, size_t work_bytes, void* stream) {
+  return cholesky_common(C, n, lambdas, N, R, breakdown, work, work_bytes, stream, false);
+}
+
+TK_API tk_status tk_cholesky_shifted_emulated(const double* C, int64_t n, const double* lambdas, int N, double* R,
+                                              int* breakdown, void* work, size_t work_bytes, void* stream) {
+  return cholesky_common(C, n, lambdas, N, R, breakdown, work, work_bytes, stream, true);
 }
 
 TK_API size_t tk_sketch_svd_workspace(int64_t s, int64_t n) { return svd_workspace(s, n) + 1024; }

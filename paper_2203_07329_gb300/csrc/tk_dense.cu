@@ -908,7 +908,7 @@ size_t chol_workspace(int64_t n, int N) {
 // R: N matrices of padded order np = ceil(n/64)*64, row stride ldr >= np,
 // matrix stride rstride.  lambdas_dev: device N.  info_dev: device N.
 tk_status chol_shifted(const double* Cm, int64_t n, const double* lambdas_dev, int N, double* R, int64_t ldr,
-                       int64_t rstride, int* info_dev, Arena& ar, cudaStream_t st) {
+                       int64_t rstride, int* info_dev, Arena& ar, cudaStream_t st, const OzCholPlan* oz) {
   (void)ar;
   if (N == 0 || n == 0) return TK_OK;
   const int64_t np = cdiv(n, CB) * CB;
@@ -923,8 +923,12 @@ tk_status chol_shifted(const double* Cm, int64_t n, const double* lambdas_dev, i
     if (r == 0) break;
     k_chol_trsm<<<dim3((unsigned)r, (unsigned)N), CB, 0, st>>>(R, ldr, rstride, kb);
     TK_LAUNCH_CHECK();
-    k_chol_update<<<dim3((unsigned)(r * (r + 1) / 2), (unsigned)N), 256, 0, st>>>(R, ldr, rstride, kb, nt);
-    TK_LAUNCH_CHECK();
+    if (oz) {
+      TK_TRY(oz_chol_step(*oz, kb, st));
+    } else {
+      k_chol_update<<<dim3((unsigned)(r * (r + 1) / 2), (unsigned)N), 256, 0, st>>>(R, ldr, rstride, kb, nt);
+      TK_LAUNCH_CHECK();
+    }
   }
   return TK_OK;
 }

@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (include/tikhonov.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -236,6 +237,29 @@ tk_status oz_residual(const void* Aslices, const int* EA, int64_t m, int64_t n, 
 // of sum_i A[i][j] R[l][i], from the column slices of A (oz_prepare_cols) and
 // R (M x m, row stride ldr); Rslices: oz_slices_bytes(M, m), EX: M ints.
 int oz_normal_splits(int64_t m, int64_t n, int64_t M);
+// Cholesky of C + lambda I (chol_shifted) with the trailing updates on the
+// tensor cores: oz_chol_begin prepares the slice buffers and tensor maps
+// (work: oz_chol_workspace(np, N) bytes), oz_chol_step(kb) replaces the
+// float64 update of block step kb.
+struct OzCholPlan {
+  CUtensorMap mP;
+  CUtensorMap mQ;
+  double* R = nullptr;
+  int64_t ldr = 0, rstride = 0, np = 0;
+  int N = 0;
+  void* slices = nullptr;
+  int* EC = nullptr;
+  int* err = nullptr;
+};
+size_t oz_chol_workspace(int64_t np, int N);
+tk_status oz_chol_begin(double* R, int64_t ldr, int64_t rstride, int N, int64_t np, void* work, size_t bytes,
+                        int* err, OzCholPlan* plan, cudaStream_t st);
+tk_status oz_chol_step(const OzCholPlan& plan, int kb, cudaStream_t st);
+// C = Y^T Y (Y: r x c float64, row stride c), the upper triangle (j >= i) of
+// C (c x c) written, float64-accurate; work: oz_gram_workspace(r, c) bytes.
+size_t oz_gram_workspace(int64_t r, int64_t c);
+tk_status oz_gram(const double* Y, int64_t r, int64_t c, double* C, void* work, size_t bytes, int* err,
+                  cudaStream_t st);
 tk_status oz_normal(const void* AslicesT, const int* EC, int64_t m, int64_t n, const double* R, int64_t ldr,
                     int64_t M, void* Rslices, int* EX, double* partial, int splits, int* err, cudaStream_t st);
 
@@ -267,7 +291,7 @@ tk_status gram_upper(const double* Y, int64_t r, int64_t c, double* C, void* scr
 
 size_t chol_workspace(int64_t n, int N);
 tk_status chol_shifted(const double* C, int64_t n, const double* lambdas_dev, int N, double* R, int64_t ldr,
-                       int64_t rstride, int* info_dev, Arena& ar, cudaStream_t st);
+                       int64_t rstride, int* info_dev, Arena& ar, cudaStream_t st, const OzCholPlan* oz = nullptr);
 
 // M = R^-1 (upper) and Mt = M^T (lower), arithmetic in T, for N factors R
 // (float64, padded order np = ceil(n/64)*64, row stride ldr, matrix stride

@@ -185,12 +185,15 @@ template <int MODE>
 __global__ void __launch_bounds__(256, 1)
     k_oz_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
             const int* __restrict__ EP, const int* __restrict__ EQ, int64_t rows, int M, int64_t K, int64_t kps,
-            const double* __restrict__ b, double* __restrict__ out, int64_t ldo, int* __restrict__ err) {
+            const double* __restrict__ b, double* __restrict__ out, int64_t ldo, int upper_only,
+            int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t ot_raw[];
   OtSmem& S = *reinterpret_cast<OtSmem*>((reinterpret_cast<uintptr_t>(ot_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r0 = (int64_t)blockIdx.x * OT_M;
   const int l0 = (int)blockIdx.y * OT_N;
+  // a symmetric product (P = Q) needs out[l][r] for l <= r only
+  if (upper_only && l0 > r0 + OT_M - 1) return;
   const int64_t kbeg = (int64_t)blockIdx.z * kps;
   const int64_t kend = K < kbeg + kps ? K : kbeg + kps;
   const int nkb = kend > kbeg ? (int)((kend - kbeg + OT_KB - 1) / OT_KB) : 0;
@@ -351,7 +354,8 @@ tk_status make_slice_map(CUtensorMap* map, const void* base, int64_t rows, int64
 
 template <int MODE>
 tk_status launch_oz_tc(const void* Ps, const int* EP, int64_t rows, const void* Qs, const int* EQ, int M, int64_t K,
-                       int splits, const double* b, double* out, int64_t ldo, int* err, cudaStream_t st) {
+                       int splits, const double* b, double* out, int64_t ldo, int* err, cudaStream_t st,
+                       int upper_only = 0) {
   const int64_t kp = cdiv(K, OZ_KPAD) * OZ_KPAD;
   if (rows > INT32_MAX || kp > INT32_MAX || M > 65535 * OT_N) {
     set_error_msg("emulated float64 product: dimensions exceed the 32-bit TMA coordinates");
@@ -365,12 +369,176 @@ tk_status launch_oz_tc(const void* Ps, const int* EP, int64_t rows, const void* 
   const size_t smem = sizeof(OtSmem) + 1024;
   TK_CUDA(cudaFuncSetAttribute(k_oz_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const dim3 grid((unsigned)cdiv(rows, OT_M), (unsigned)cdiv(M, OT_N), (unsigned)sp);
-  k_oz_tc<MODE><<<grid, 256, smem, st>>>(mP, mQ, EP, EQ, rows, M, kp, kps, b, out, ldo, err);
+  k_oz_tc<MODE><<<grid, 256, smem, st>>>(mP, mQ, EP, EQ, rows, M, kp, kps, b, out, ldo, upper_only, err);
   TK_LAUNCH_CHECK();
   if (MODE == 1 && sp < splits) {  // the caller sums `splits` planes: the unused ones are zero
     TK_CUDA(cudaMemsetAsync(out + (int64_t)sp * M * ldo, 0, sizeof(double) * (size_t)(splits - sp) * M * ldo, st));
   }
   return TK_OK;
+}
+
+// ---- Cholesky trailing update -------------------------------------------------
+// Right-looking blocked Cholesky (upper, R^T R = C + lambda I), 64-row block
+// step kb: with the row panel P = R[kb rows, columns > kb] (64 x w) already
+// solved, the trailing upper triangle T -= P^T P.  The panel's columns are
+// sliced with one exponent per column (the output index), stored K-major
+// (planes [lambda][p][column][64]); one CTA then forms a 128 x 64 tile of
+// P^T P for one lambda from all 8 + 8 slice planes at once (K = 64: a single
+// chunk, exact in FP32), flushes the 8 levels into float64 and subtracts the
+// scaled result from T through shared memory (coalesced).
+
+// Panel slices of block row kb for every lambda (grid: column tiles of 32 x
+// lambda).  Rows c >= w of the slice planes are not written.
+__global__ void __launch_bounds__(256) k_oz_panel_slice(const double* __restrict__ R, int64_t ldr, int64_t rstride,
+                                                        int64_t np, int kb, __nv_bfloat16* __restrict__ out,
+                                                        int* __restrict__ EC) {
+  __shared__ double tile[64][33];
+  __shared__ int ex[32];
+  const int l = blockIdx.y;
+  const int64_t c0 = (int64_t)(kb + 1) * 64, w = np - c0;
+  const int64_t ct = (int64_t)blockIdx.x * 32;
+  const double* Rl = R + (int64_t)l * rstride + (int64_t)kb * 64 * ldr + c0;
+  for (int idx = threadIdx.x; idx < 64 * 32; idx += blockDim.x) {
+    const int k = idx >> 5, cc = idx & 31;
+    const int64_t c = ct + cc;
+    tile[k][cc] = c < w ? Rl[(int64_t)k * ldr + c] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double mx = 0.0;
+    for (int k = 0; k < 64; ++k) mx = fmax(mx, fabs(tile[k][threadIdx.x]));
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);
+    ex[threadIdx.x] = e;
+    const int64_t c = ct + threadIdx.x;
+    if (c < w) EC[(int64_t)l * np + c] = e;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 64 * 32; idx += blockDim.x) {
+    const int cc = idx >> 6, k = idx & 63;
+    const int64_t c = ct + cc;
+    if (c < w) {
+      __nv_bfloat16 sl[OZ_S];
+      oz_split(tile[k][cc], ex[cc], sl);
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p) out[(((int64_t)l * OZ_S + p) * np + c) * 64 + k] = sl[p];
+    }
+  }
+}
+
+constexpr int CS_M = 128;
+constexpr int CS_N = 64;
+constexpr uint32_t CS_P_BYTES = CS_M * 64 * 2;  // 16 KiB per slice
+constexpr uint32_t CS_Q_BYTES = CS_N * 64 * 2;  // 8 KiB per slice
+constexpr uint32_t CS_TMEM_COLS = OZ_LV * CS_N;  // 512
+constexpr int CS_LDD = CS_N + 1;                 // staged result row (doubles)
+
+struct CsSmem {
+  uint8_t p[OZ_S][CS_P_BYTES];
+  uint8_t q[OZ_S][CS_Q_BYTES];
+  uint64_t full;
+  uint64_t accum;
+  uint32_t tmem_base;
+};
+static_assert(sizeof(double) * CS_M * CS_LDD <= sizeof(((CsSmem*)nullptr)->p), "staging fits in the P slices");
+
+// Grid: (row tiles of 128, column tiles of 64, lambda) over the w x w
+// trailing block; tiles wholly below the diagonal exit at once.
+__global__ void __launch_bounds__(256, 1)
+    k_oz_syrk(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
+              const int* __restrict__ EC, int64_t np, int kb, double* __restrict__ R, int64_t ldr, int64_t rstride,
+              int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t cs_raw[];
+  CsSmem& S = *reinterpret_cast<CsSmem*>((reinterpret_cast<uintptr_t>(cs_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = blockIdx.z;
+  const int i0 = (int)blockIdx.x * CS_M, j0 = (int)blockIdx.y * CS_N;
+  if (j0 + CS_N - 1 < i0) return;
+  const int64_t c0 = (int64_t)(kb + 1) * 64, w = np - c0;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&S.full, 1);
+    mbar_init(&S.accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "r"(CS_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    mbar_expect_tx(&S.full, OZ_S * (CS_P_BYTES + CS_Q_BYTES));
+    for (int p = 0; p < OZ_S; ++p) {
+      tma_load_3d(&tmP, &S.full, S.p[p], 0, i0, l * OZ_S + p);
+      tma_load_3d(&tmQ, &S.full, S.q[p], 0, j0, l * OZ_S + p);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(CS_M, CS_N);
+    if (mbar_wait(&S.full, 0u, err)) {
+      tc_fence_after();
+      for (int p = 0; p < OZ_S; ++p) {
+        const uint64_t pd = sdesc_sw128(smem_u32(S.p[p]));
+        for (int q = 0; q < OZ_S - p; ++q) {
+          const uint64_t qd = sdesc_sw128(smem_u32(S.q[q]));
+          const uint32_t d = tmem + (uint32_t)((p + q) * CS_N);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) tc_mma_bf16(d, pd + 2ull * k, qd + 2ull * k, idesc, (p == 0 && k == 0) ? 0u : 1u);
+        }
+      }
+      tc_commit(&S.accum);
+    }
+  }
+  __syncwarp();
+  double* D = reinterpret_cast<double*>(&S.p[0][0]);  // the slices are dead once the MMAs completed
+  if (warp >= 4) {
+    const int ew = warp - 4, row = ew * 32 + lane;
+    if (mbar_wait(&S.accum, 0u, err)) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int h = 0; h < CS_N / 32; ++h) {
+        double acc64[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc64[j] = 0.0;
+#pragma unroll 1
+        for (int t = OZ_LV - 1; t >= 0; --t) {
+          uint32_t v[32];
+          tmem_ld32_nowait(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(t * CS_N + h * 32), v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc64[j] += level_to_double(v[j], t);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) D[row * CS_LDD + h * 32 + j] = acc64[j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (!*(volatile int*)err) {
+    const int* El = EC + (int64_t)l * np;
+    double* T = R + (int64_t)l * rstride + c0 * ldr + c0;
+    for (int rr = warp; rr < CS_M; rr += 8) {
+      const int64_t i = i0 + rr;
+      if (i >= w) break;
+      const int ei = El[i];
+#pragma unroll
+      for (int jj = lane; jj < CS_N; jj += 32) {
+        const int64_t j = j0 + jj;
+        if (j < w && j >= i) T[i * ldr + j] -= ldexp(D[rr * CS_LDD + jj], ei + El[j]);
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CS_TMEM_COLS) : "memory");
+  }
 }
 
 }  // namespace
@@ -447,6 +615,94 @@ tk_status oz_normal(const void* AslicesT, const int* EC, int64_t m, int64_t n, c
   if (M == 0 || n == 0) return TK_OK;
   TK_TRY(oz_prepare(R, TK_F64, M, m, ldr, Rslices, EX, st));
   return launch_oz_tc<1>(AslicesT, EC, n, Rslices, EX, (int)M, m, splits, nullptr, partial, n, err, st);
+}
+
+size_t oz_gram_workspace(int64_t r, int64_t c) {
+  Arena a;
+  a.take<char>(oz_slices_bytes(c, r));
+  a.take<int>(c);
+  a.take<char>(oz_colmax_bytes(c));
+  return a.used + 256;
+}
+
+tk_status oz_gram(const double* Y, int64_t r, int64_t c, double* C, void* work, size_t bytes, int* err,
+                  cudaStream_t st) {
+  if (c == 0) return TK_OK;
+  if (r == 0) {
+    TK_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)c * c, st));
+    return TK_OK;
+  }
+  Arena a;
+  a.base = static_cast<char*>(work);
+  a.cap = bytes;
+  void* Ys = a.take<char>(oz_slices_bytes(c, r));
+  int* E = a.take<int>(c);
+  void* mx = a.take<char>(oz_colmax_bytes(c));
+  if (!a.ok()) return TK_ENOMEM;
+  TK_TRY(oz_prepare_cols(Y, TK_F64, r, c, c, Ys, E, mx, st));
+  return launch_oz_tc<1>(Ys, E, c, Ys, E, (int)c, r, 1, nullptr, C, c, err, st, 1);
+}
+
+size_t oz_chol_workspace(int64_t np, int N) {
+  Arena a;
+  a.take<__nv_bfloat16>((size_t)N * OZ_S * np * 64);
+  a.take<int>((size_t)N * np);
+  return a.used + 256;
+}
+
+tk_status oz_chol_begin(double* R, int64_t ldr, int64_t rstride, int N, int64_t np, void* work, size_t bytes,
+                        int* err, OzCholPlan* plan, cudaStream_t st) {
+  if (np % 64 || (int64_t)N * OZ_S > 65535 || np > INT32_MAX) {
+    set_error_msg("emulated Cholesky: unsupported order or lambda count");
+    return TK_EINVAL;
+  }
+  Arena a;
+  a.base = static_cast<char*>(work);
+  a.cap = bytes;
+  const size_t sb = sizeof(__nv_bfloat16) * (size_t)N * OZ_S * np * 64;
+  plan->slices = a.take<__nv_bfloat16>((size_t)N * OZ_S * np * 64);
+  plan->EC = a.take<int>((size_t)N * np);
+  if (!a.ok()) return TK_ENOMEM;
+  plan->R = R;
+  plan->ldr = ldr;
+  plan->rstride = rstride;
+  plan->N = N;
+  plan->np = np;
+  plan->err = err;
+  // rows of the slice planes beyond a step's panel width are read by the
+  // edge tiles (their products are discarded): keep them finite
+  TK_CUDA(cudaMemsetAsync(plan->slices, 0, sb, st));
+  EncodeTiledFn fn;
+  TK_TRY(encode_fn(&fn));
+  const cuuint64_t dims[3] = {64, (cuuint64_t)np, (cuuint64_t)N * OZ_S};
+  const cuuint64_t strides[2] = {128, (cuuint64_t)np * 128};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int which = 0; which < 2; ++which) {
+    const cuuint32_t box[3] = {64, which == 0 ? (cuuint32_t)CS_M : (cuuint32_t)CS_N, 1};
+    CUresult r = fn(which == 0 ? &plan->mP : &plan->mQ, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, plan->slices, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error_msg("cuTensorMapEncodeTiled rejected the panel slice layout");
+      return TK_ECUDA;
+    }
+  }
+  TK_CUDA(cudaFuncSetAttribute(k_oz_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(CsSmem) + 1024)));
+  return TK_OK;
+}
+
+tk_status oz_chol_step(const OzCholPlan& plan, int kb, cudaStream_t st) {
+  const int64_t w = plan.np - (int64_t)(kb + 1) * 64;
+  if (w <= 0) return TK_OK;
+  __nv_bfloat16* sl = static_cast<__nv_bfloat16*>(plan.slices);
+  k_oz_panel_slice<<<dim3((unsigned)cdiv(w, 32), (unsigned)plan.N), 256, 0, st>>>(plan.R, plan.ldr, plan.rstride,
+                                                                                   plan.np, kb, sl, plan.EC);
+  TK_LAUNCH_CHECK();
+  const dim3 grid((unsigned)cdiv(w, CS_M), (unsigned)(w / CS_N), (unsigned)plan.N);
+  k_oz_syrk<<<grid, 256, sizeof(CsSmem) + 1024, st>>>(plan.mP, plan.mQ, plan.EC, plan.np, kb, plan.R, plan.ldr,
+                                                     plan.rstride, plan.err);
+  TK_LAUNCH_CHECK();
+  return TK_OK;
 }
 
 }  // namespace tk

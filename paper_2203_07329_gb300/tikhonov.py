@@ -83,6 +83,8 @@ def lib() -> C.CDLL:
             "tk_gram": (INT, [P, I64, I64, INT, P, P]),
             "tk_cholesky_workspace": (SZ, [I64, INT]),
             "tk_cholesky_shifted": (INT, [P, I64, P, INT, P, P, P, SZ, P]),
+            "tk_cholesky_emulated_workspace": (SZ, [I64, INT]),
+            "tk_cholesky_shifted_emulated": (INT, [P, I64, P, INT, P, P, P, SZ, P]),
             "tk_sketch_svd_workspace": (SZ, [I64, I64]),
             "tk_sketch_svd": (INT, [P, I64, I64, P, P, P, P, SZ, P]),
             "tk_lowrank_ranks_workspace": (SZ, [INT]),
@@ -94,6 +96,8 @@ def lib() -> C.CDLL:
             "tk_profile_collect": (INT, [P]),
             "tk_autotune": (INT, [P, INT, P, P, SZ, P]),
             "tk_autotune_entries": (SZ, []),
+            "tk_gram_emulated_workspace": (SZ, [I64, I64]),
+            "tk_gram_emulated": (INT, [P, I64, I64, P, P, SZ, P]),
             "tk_residual_workspace": (SZ, [I64, I64, INT]),
             "tk_residual": (INT, [P, P, INT, I64, INT, P, P, P, SZ, P]),
             "tk_autotune_clear": (None, []),
@@ -266,23 +270,38 @@ def tk_sketch_apply(A: torch.Tensor, opts: tk_opts, stream=None) -> torch.Tensor
     return Y
 
 
-def tk_gram(Y: torch.Tensor, transpose_first: bool = True, stream=None) -> torch.Tensor:
+def tk_gram(Y: torch.Tensor, transpose_first: bool = True, stream=None, emulate: bool = False) -> torch.Tensor:
+    """C = Y^T Y (transpose_first) or Y Y^T; emulate: Y^T Y on the BF16 tensor cores with
+    float64 accuracy, only the upper triangle defined."""
     r, c = Y.shape
     Cm = torch.empty((c, c) if transpose_first else (r, r), dtype=torch.float64, device=Y.device)
+    if emulate:
+        if not transpose_first:
+            raise ValueError("the emulated Gram matrix is Y^T Y")
+        work = _workspace(int(lib().tk_gram_emulated_workspace(r, c)), Y.device)
+        _check(lib().tk_gram_emulated(_ptr(Y.contiguous()), r, c, _ptr(Cm), _ptr(work), work.numel(),
+                                      _stream(stream)))
+        return Cm
     _check(lib().tk_gram(_ptr(Y.contiguous()), r, c, 1 if transpose_first else 0, _ptr(Cm), _stream(stream)))
     return Cm
 
 
-def tk_cholesky_shifted(Cm: torch.Tensor, lambdas, stream=None):
-    """R_i = chol(C + lambda_i I): returns (R N x n x n, breakdown list)."""
+def tk_cholesky_shifted(Cm: torch.Tensor, lambdas, stream=None, emulate: bool = False):
+    """R_i = chol(C + lambda_i I): returns (R N x n x n, breakdown list); emulate: the trailing
+    updates on the BF16 tensor cores with float64 accuracy."""
     n = Cm.shape[0]
     lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
     N = lam.shape[0]
     R = torch.empty((N, n, n), dtype=torch.float64, device=Cm.device)
     brk = (C.c_int * N)()
-    work = _workspace(lib().tk_cholesky_workspace(n, N), Cm.device)
-    st = lib().tk_cholesky_shifted(_ptr(Cm.contiguous()), n, lam.ctypes.data_as(C.c_void_p), N, _ptr(R), brk,
-                                   _ptr(work), work.numel(), _stream(stream))
+    if emulate:
+        work = _workspace(lib().tk_cholesky_emulated_workspace(n, N), Cm.device)
+        fn = lib().tk_cholesky_shifted_emulated
+    else:
+        work = _workspace(lib().tk_cholesky_workspace(n, N), Cm.device)
+        fn = lib().tk_cholesky_shifted
+    st = fn(_ptr(Cm.contiguous()), n, lam.ctypes.data_as(C.c_void_p), N, _ptr(R), brk, _ptr(work), work.numel(),
+            _stream(stream))
     _check(st, (TK_OK, TK_ENOTSPD))
     return R, list(brk)
 

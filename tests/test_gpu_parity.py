@@ -114,6 +114,24 @@ def test_gram_matches_oracle(tk, r, c):
     np.testing.assert_allclose(G2, oracle.gram_nt(Y.T.contiguous().numpy()), rtol=1e-12, atol=1e-12 * r)
 
 
+@pytest.mark.parametrize("r,c", [(300, 70), (1000, 129), (2100, 333), (5, 1)])
+def test_emulated_gram_has_float64_accuracy(tk, r, c):
+    # C = Y^T Y on the BF16 tensor cores from exact column slices: every upper entry within the
+    # float64 GEMM bound relative to (|Y|^T |Y|), columns of Y over 8 decades of scale
+    gen = torch.Generator().manual_seed(r + c)
+    Y = torch.randn(r, c, generator=gen, dtype=torch.float64) * torch.logspace(0, -8, c, dtype=torch.float64)
+    G = tk.tk_gram(Y.cuda(), True, emulate=True).cpu().numpy()
+    Yl = Y.numpy().astype(np.longdouble)
+    Gref = Yl.T @ Yl
+    scale = np.abs(Y.numpy()).T @ np.abs(Y.numpy())
+    iu = np.triu_indices(c)
+    err = np.abs((G[iu] - Gref[iu]).astype(np.float64)) / scale[iu]
+    assert float(err.max()) < 8 * 2.0 ** -53 * math.sqrt(r), float(err.max())
+    # the oracle's Gram matrix agrees on the upper triangle, relative to the same scale
+    d = np.abs(G[iu] - oracle.gram_tn(Y.numpy())[iu]) / scale[iu]
+    assert float(d.max()) < 16 * 2.0 ** -53 * math.sqrt(r), float(d.max())
+
+
 @pytest.mark.parametrize("n", [1, 63, 64, 100, 200])
 def test_cholesky_matches_oracle(tk, n):
     Y = torch.randn(3 * n + 5, n, dtype=torch.float64, generator=torch.Generator().manual_seed(n))
@@ -127,6 +145,37 @@ def test_cholesky_matches_oracle(tk, n):
         assert info == 0
         np.testing.assert_allclose(R[i], Ro, rtol=1e-9, atol=1e-11 * np.abs(Ro).max())
         np.testing.assert_allclose(R[i].T @ R[i], Cm + lam * np.eye(n), rtol=1e-12, atol=1e-12 * np.abs(Cm).max())
+
+
+@pytest.mark.parametrize("n", [63, 64, 129, 333, 700])
+def test_emulated_cholesky_matches_oracle(tk, n):
+    # trailing updates on the tensor cores (exact slices, float64 accuracy): the factors agree with
+    # the oracle's and with the float64 factorization to float64 rounding
+    gen = torch.Generator().manual_seed(n + 1)
+    Y = torch.randn(3 * n + 5, n, dtype=torch.float64, generator=gen) * torch.logspace(0, -3, n, dtype=torch.float64)
+    Cm = (Y.T @ Y).numpy()
+    lams = [1e-8, 1e-4, 1.0]
+    Re, brk = tk.tk_cholesky_shifted(torch.from_numpy(Cm).cuda(), lams, emulate=True)
+    Rn, _ = tk.tk_cholesky_shifted(torch.from_numpy(Cm).cuda(), lams)
+    Re, Rn = Re.cpu().numpy(), Rn.cpu().numpy()
+    assert brk == [0, 0, 0]
+    for i, lam in enumerate(lams):
+        Ro, info = oracle.cholesky_shifted(Cm, lam)
+        assert info == 0
+        np.testing.assert_allclose(Re[i], Ro, rtol=1e-9, atol=1e-11 * np.abs(Ro).max())
+        np.testing.assert_allclose(Re[i], Rn[i], rtol=1e-9, atol=1e-12 * np.abs(Rn[i]).max())
+        assert np.all(np.tril(Re[i], -1) == 0.0)
+        np.testing.assert_allclose(Re[i].T @ Re[i], Cm + lam * np.eye(n), rtol=1e-12, atol=1e-12 * np.abs(Cm).max())
+
+
+def test_emulated_cholesky_reports_breakdown(tk):
+    n = 200
+    Cm = np.eye(n)
+    Cm[140, 140] = -3.0
+    _, brk = tk.tk_cholesky_shifted(torch.from_numpy(Cm).cuda(), [0.5, 5.0], emulate=True)
+    _, info = oracle.cholesky_shifted(Cm, 0.5)
+    assert brk[0] == info == 141
+    assert brk[1] == 0
 
 
 def test_cholesky_reports_breakdown(tk):
