@@ -2,24 +2,27 @@
 // integer slices, in the manner of Ozaki's error-free matrix multiplication).
 //
 // GB300 issues about two float64 FMA per clock per SM, so the float64 passes
-// of the mixed form's refinement (r = b - X A^T and A^T r, float64 GEMMs with
-// up to 32 lambda rows) are bound by that pipe.  Here every row of an operand
-// is scaled by a power of two so that its entries lie in (-1, 1), rounded to
-// 56 bits and split into S = 8 signed 7-bit integer slices,
-//   a = sum_p s_p 2^(-7(p+1)),  |s_p| <= 127,
-// each exactly representable in BF16.  A product of two slices is an integer
-// below 2^14; the pairs (p, q) with p + q = t share one FP32 accumulator
-// ("level" t), and a level sum of at most 8 pairs over 128 values of K stays
-// below 2^24, so the tensor core's FP32 accumulation is exact.  Every 128
-// values of K the level sums are scaled by 2^(-7(t+2)) and added into float64
-// accumulators.  Pairs with p + q > 7 are dropped: their contribution is below
-// 9 * 2^-56 of max|a| max|x| per product, and the 56-bit rounding of a and x
-// is at 2^-57 of their row maxima: the accuracy of a float64 GEMM.
+// of the mixed form (the Gram matrix, the Cholesky trailing updates, and the
+// refinement's r = b - X A^T and A^T r) are bound by that pipe.  Here every
+// row of an operand is scaled by a power of two 2^E (E one above the exponent
+// of its largest entry, so that |x 2^-E| < 1/2), rounded to 55 bits and
+// written with S = 8 balanced base-128 digits,
+//   x 2^-E = sum_p d_p 2^(-7(p+1)),  d_p in [-64, 64],
+// taken from the least significant end with carries; each digit is exact in
+// BF16.  A product of two digits is an integer of magnitude <= 2^12; the pairs
+// (p, q) with p + q = t share one FP32 accumulator ("level" t), and a level
+// sum of at most 8 pairs over 256 values of K stays below 2^24, so the tensor
+// core's FP32 accumulation is exact.  Every 256 values of K the level sums
+// are scaled by 2^(-7(t+2)) and added into float64 accumulators.  Pairs with
+// p + q > 7 are dropped: their contribution is below 2^-55 of max|a| max|x|
+// per product, and the 55-bit rounding of a and x is at 2^-56 of their row
+// maxima: the accuracy of a float64 GEMM.  Cut after 4 digits, the same
+// slices are a round-to-nearest (unbiased) 28-bit representation.
 //
 // The products run on tcgen05 (kind::f16, M = 128, N = 32, K = 16), operands
 // brought in by TMA in the 128-byte swizzle layout, the 8 level accumulators
 // in tensor memory, double-buffered so that four epilogue warps flush one
-// 128-value chunk of K into float64 while the MMAs of the next chunk run.
+// 256-value chunk of K into float64 while the MMAs of the next chunk run.
 #include <algorithm>
 #include <cuda_bf16.h>
 
@@ -33,7 +36,7 @@ constexpr int OZ_S = 8;          // slices
 constexpr int OZ_LV = OZ_S;      // levels t = p + q in 0..7 kept
 constexpr int OZ_KPAD = 64;      // slice rows are padded to a multiple of 64 values of K (one TMA box)
 
-// Exponent E with max_j |row_j| < 2^E (0 for a zero row); one warp per row.
+// Exponent E with max_j |row_j| < 2^(E-1) (0 for a zero row); one warp per row.
 template <typename T>
 __global__ void k_oz_rowexp(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld, int* __restrict__ E) {
   const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -45,12 +48,15 @@ __global__ void k_oz_rowexp(const T* __restrict__ X, int64_t rows, int64_t cols,
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) {
     int e = 0;
-    if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, 0.5 <= f < 1, so mx < 2^e
+    if (mx > 0.0) {
+      frexp(mx, &e);  // mx = f 2^e, 0.5 <= f < 1
+      ++e;            // so mx < 2^(e-1)
+    }
     E[r] = e;
   }
 }
 
-// Exponent E with max_r |X[r][c]| < 2^E per column (0 for a zero column):
+// Exponent E with max_r |X[r][c]| < 2^(E-1) per column (0 for a zero column):
 // the bit patterns of non-negative doubles order like the values, so the
 // column maxima are combined with an integer atomicMax (mx zeroed first).
 template <typename T>
@@ -69,53 +75,100 @@ __global__ void k_oz_colexp(const unsigned long long* __restrict__ mx, int64_t c
   if (c >= cols) return;
   const double v = __longlong_as_double((long long)mx[c]);
   int e = 0;
-  if (v > 0.0) frexp(v, &e);
+  if (v > 0.0) {
+    frexp(v, &e);
+    ++e;
+  }
   E[c] = e;
 }
 
-// The 8 slices of one value x 2^-E (|x 2^-E| < 1): round to 56 bits (to
-// nearest, so the errors of a row do not share a sign), then 7 bits per slice
-// from the top, all with the sign of the value.
+// The 8 balanced digits of one value x 2^-E (|x 2^-E| < 1/2): round to 55
+// bits (to nearest), then d = ((u + 64) mod 128) - 64 from the bottom, carry
+// (u - d) / 128; the last carry is the top digit, |d_0| <= 64.
 __device__ __forceinline__ void oz_split(double x, int E, __nv_bfloat16 (&s)[OZ_S]) {
-  const long long v = llrint(ldexp(x, 7 * OZ_S - E));  // |v| <= 2^56
-  const bool neg = v < 0;
-  unsigned long long u = neg ? (unsigned long long)(-v) : (unsigned long long)v;
-  u = u < (1ull << (7 * OZ_S)) ? u : (1ull << (7 * OZ_S)) - 1;  // 56 bits
+  long long u = llrint(ldexp(x, 7 * OZ_S - E));  // |u| <= 2^55
 #pragma unroll
-  for (int p = 0; p < OZ_S; ++p) {
-    const int q = (int)((u >> (7 * (OZ_S - 1 - p))) & 127u);
-    s[p] = __int2bfloat16_rn(neg ? -q : q);
+  for (int p = OZ_S - 1; p >= 1; --p) {
+    const int d = (int)((u + 64) & 127) - 64;
+    s[p] = __int2bfloat16_rn(d);
+    u = (u - d) >> 7;  // exact: u - d is a multiple of 128
   }
+  s[0] = __int2bfloat16_rn((int)u);
 }
 
 // Slices of the rows of X with row exponents E: planes out[p][r][c] (row
 // stride cols_pad, zero in the padding) with X[r][c] 2^-E[r] = sum_p
-// out[p][r][c] 2^(-7(p+1)) to within 2^-57.
+// out[p][r][c] 2^(-7(p+1)) to within 2^-56.
+// Grid: rows over blockIdx.x (grid-stride) and column chunks of 2 x 256 over
+// blockIdx.y; each thread splits two adjacent values (one 4-byte store per plane).
 template <typename T>
-__global__ void k_oz_slice(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld, const int* __restrict__ E,
-                           int64_t cols_pad, __nv_bfloat16* __restrict__ out) {
-  const int64_t total = rows * cols_pad;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = k / cols_pad, c = k - r * cols_pad;
-    __nv_bfloat16 s[OZ_S];
-    oz_split(c < cols ? (double)X[r * ld + c] : 0.0, c < cols ? E[r] : 0, s);
+__global__ void __launch_bounds__(256) k_oz_slice(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                                                  const int* __restrict__ E, int64_t cols_pad,
+                                                  __nv_bfloat16* __restrict__ out) {
+  const int64_t plane = rows * cols_pad;
+  const int64_t c = ((int64_t)blockIdx.y * blockDim.x + threadIdx.x) * 2;
+  if (c >= cols_pad) return;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int e = E[r];
+    const T* xr = X + r * ld;
+    __nv_bfloat16 s0[OZ_S], s1[OZ_S];
+    oz_split(c < cols ? (double)xr[c] : 0.0, e, s0);
+    oz_split(c + 1 < cols ? (double)xr[c + 1] : 0.0, e, s1);
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + r * cols_pad + c);
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) out[p * total + k] = s[p];
+    for (int p = 0; p < OZ_S; ++p) o[p * (plane / 2)] = __halves2bfloat162(s0[p], s1[p]);
   }
+}
+
+// Exponents of long rows (cols much larger than rows): E[r] = max over the
+// blocks of a row of the exponent of their largest |value| (atomicMax; E
+// filled with OZ_EMIN first, then zero rows set to 0).
+constexpr int OZ_EMIN = -4096;
+__global__ void k_oz_fill_emin(int* __restrict__ E, int64_t rows) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < rows) E[r] = OZ_EMIN;
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_oz_rowexp_long(const T* __restrict__ X, int64_t cols, int64_t ld,
+                                                        int64_t per_block, int* __restrict__ E) {
+  __shared__ double sh[32];
+  const int64_t r = blockIdx.y;
+  const int64_t c0 = (int64_t)blockIdx.x * per_block;
+  const int64_t c1 = c0 + per_block < cols ? c0 + per_block : cols;
+  double mx = 0.0;
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) mx = fmax(mx, fabs((double)X[r * ld + c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, sh[w]);
+    if (mx > 0.0) {
+      int e = 0;
+      frexp(mx, &e);
+      atomicMax(&E[r], e + 1);
+    }
+  }
+}
+__global__ void k_oz_fix_zero_rows(int* __restrict__ E, int64_t rows) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < rows && E[r] == OZ_EMIN) E[r] = 0;
 }
 
 // Slices of the COLUMNS of X (rows x cols) with column exponents E, stored
 // transposed: planes out[p][c][r] (row stride rows_pad, zero in the padding).
-// 32 x 32 tiles through shared memory so that reads and writes are coalesced;
-// grid.x runs over row tiles, grid.y over column tiles.
+// 64 x 32 tiles through shared memory: reads of 32 consecutive columns, and
+// per plane 128-byte stores of 64 consecutive rows (two per thread); grid.x
+// runs over row tiles, grid.y over column tiles.
 template <typename T>
-__global__ void k_oz_slice_t(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                             const int* __restrict__ E, int64_t rows_pad, __nv_bfloat16* __restrict__ out) {
-  __shared__ double tile[32][33];
+__global__ void __launch_bounds__(256) k_oz_slice_t(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                                                    const int* __restrict__ E, int64_t rows_pad,
+                                                    __nv_bfloat16* __restrict__ out) {
+  __shared__ double tile[64][33];
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  const int64_t r0 = (int64_t)blockIdx.x * 64, c0 = (int64_t)blockIdx.y * 32;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 8; ++i) {
     const int64_t r = r0 + ty + 8 * i, c = c0 + tx;
     tile[ty + 8 * i][tx] = (r < rows && c < cols) ? (double)X[r * ld + c] : 0.0;
   }
@@ -123,12 +176,16 @@ __global__ void k_oz_slice_t(const T* __restrict__ X, int64_t rows, int64_t cols
   const int64_t plane = cols * rows_pad;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int64_t c = c0 + ty + 8 * i, r = r0 + tx;
-    if (c < cols && r < rows_pad) {
-      __nv_bfloat16 s[OZ_S];
-      oz_split(tile[tx][ty + 8 * i], E[c], s);
+    const int cc = ty + 8 * i;
+    const int64_t c = c0 + cc, r = r0 + 2 * tx;
+    if (c < cols && r < rows_pad) {  // rows_pad is a multiple of 64: r + 1 < rows_pad too
+      const int e = E[c];
+      __nv_bfloat16 s0[OZ_S], s1[OZ_S];
+      oz_split(tile[2 * tx][cc], e, s0);
+      oz_split(tile[2 * tx + 1][cc], e, s1);
+      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + c * rows_pad + r);
 #pragma unroll
-      for (int p = 0; p < OZ_S; ++p) out[p * plane + c * rows_pad + r] = s[p];
+      for (int p = 0; p < OZ_S; ++p) o[p * (plane / 2)] = __halves2bfloat162(s0[p], s1[p]);
     }
   }
 }
@@ -142,7 +199,7 @@ __global__ void k_oz_slice_t(const T* __restrict__ X, int64_t rows, int64_t cols
 //     (16 KiB each) into an 8-slot ring;
 //   warp 1 (one lane): MMA issuer -- for slice p of P and q <= 7 - p,
 //     D_(p+q) += P_p Q_q^T (4 MMAs of K = 16); the level accumulators of a
-//     chunk of 128 values of K sit in one of two tensor-memory buffers;
+//     chunk of 256 values of K sit in one of two tensor-memory buffers;
 //   warp 2: allocates / frees the 512 tensor-memory columns;
 //   warps 4-7: epilogue -- per chunk, read the 8 levels (lanes 32(w-4) ..),
 //     add them into 32 float64 accumulators per row, release the buffer;
@@ -153,7 +210,8 @@ __global__ void k_oz_slice_t(const T* __restrict__ X, int64_t rows, int64_t cols
 constexpr int OT_M = 128;
 constexpr int OT_N = 32;
 constexpr int OT_KB = 64;
-constexpr int OT_CHUNK = 128;
+constexpr int OT_CHUNK = 256;
+constexpr int OT_KB_PER_CHUNK = OT_CHUNK / 64;
 constexpr int OT_PST = 8;
 constexpr uint32_t OT_P_BYTES = OT_M * OT_KB * 2;   // 16 KiB
 constexpr uint32_t OT_QS_BYTES = OT_N * OT_KB * 2;  // 4 KiB
@@ -197,7 +255,7 @@ __global__ void __launch_bounds__(256, 1)
   const int64_t kbeg = (int64_t)blockIdx.z * kps;
   const int64_t kend = K < kbeg + kps ? K : kbeg + kps;
   const int nkb = kend > kbeg ? (int)((kend - kbeg + OT_KB - 1) / OT_KB) : 0;
-  const int nch = (nkb + 1) / 2;
+  const int nch = (nkb + OT_KB_PER_CHUNK - 1) / OT_KB_PER_CHUNK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OT_PST; ++s) {
@@ -251,8 +309,9 @@ __global__ void __launch_bounds__(256, 1)
       if (use > 0 && !mbar_wait(&S.acc_empty[bsel], (uint32_t)(use - 1) & 1u, err)) break;
       tc_fence_after();
       const uint32_t dbase = tmem + (uint32_t)(bsel * OZ_LV * OT_N);
-      const int kb_end = nkb < 2 * c + 2 ? nkb : 2 * c + 2;
-      for (int kb = 2 * c; kb < kb_end && live; ++kb) {
+      const int kb0 = OT_KB_PER_CHUNK * c;
+      const int kb_end = nkb < kb0 + OT_KB_PER_CHUNK ? nkb : kb0 + OT_KB_PER_CHUNK;
+      for (int kb = kb0; kb < kb_end && live; ++kb) {
         const int qs = kb & 1;
         if (!mbar_wait(&S.q_full[qs], (uint32_t)(kb >> 1) & 1u, err)) {
           live = false;
@@ -274,7 +333,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
             for (int k = 0; k < OT_KB / 16; ++k) {
               // the first MMA of each level in a chunk (p = 0) overwrites the buffer
-              const uint32_t acc = (kb == 2 * c && p == 0 && k == 0) ? 0u : 1u;
+              const uint32_t acc = (kb == kb0 && p == 0 && k == 0) ? 0u : 1u;
               tc_mma_bf16(d, pd + 2ull * k, qd + 2ull * k, idesc, acc);
             }
           }
@@ -408,7 +467,10 @@ __global__ void __launch_bounds__(256) k_oz_panel_slice(const double* __restrict
     double mx = 0.0;
     for (int k = 0; k < 64; ++k) mx = fmax(mx, fabs(tile[k][threadIdx.x]));
     int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
+    if (mx > 0.0) {
+      frexp(mx, &e);
+      ++e;
+    }
     ex[threadIdx.x] = e;
     const int64_t c = ct + threadIdx.x;
     if (c < w) EC[(int64_t)l * np + c] = e;
@@ -521,16 +583,37 @@ __global__ void __launch_bounds__(256, 1)
   tc_fence_before();
   __syncthreads();
   if (!*(volatile int*)err) {
+    // T -= 2^(E_i + E_j) D on the upper triangle: warp w takes rows w, w + 8, ..., lanes the
+    // columns; all loads of a thread are issued before the first update (16 x 2 in flight)
+    constexpr int RPW = CS_M / 8;
     const int* El = EC + (int64_t)l * np;
     double* T = R + (int64_t)l * rstride + c0 * ldr + c0;
-    for (int rr = warp; rr < CS_M; rr += 8) {
-      const int64_t i = i0 + rr;
-      if (i >= w) break;
-      const int ei = El[i];
+    int ej[2];
 #pragma unroll
-      for (int jj = lane; jj < CS_N; jj += 32) {
-        const int64_t j = j0 + jj;
-        if (j < w && j >= i) T[i * ldr + j] -= ldexp(D[rr * CS_LDD + jj], ei + El[j]);
+    for (int h = 0; h < 2; ++h) {
+      const int64_t j = j0 + lane + 32 * h;
+      ej[h] = j < w ? El[j] : 0;
+    }
+    double tv[RPW][2];
+    int ei[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      const int64_t i = i0 + warp + 8 * q;
+      ei[q] = i < w ? El[i] : 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t j = j0 + lane + 32 * h;
+        tv[q][h] = (i < w && j < w && j >= i) ? T[i * ldr + j] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      const int64_t i = i0 + warp + 8 * q;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t j = j0 + lane + 32 * h;
+        if (i < w && j < w && j >= i)
+          T[i * ldr + j] = tv[q][h] - ldexp(D[(warp + 8 * q) * CS_LDD + lane + 32 * h], ei[q] + ej[h]);
       }
     }
   }
@@ -551,18 +634,32 @@ tk_status oz_prepare(const void* X, tk_dtype dt, int64_t rows, int64_t cols, int
                      cudaStream_t st) {
   if (rows == 0 || cols == 0) return TK_OK;
   const int64_t kp = cdiv(cols, OZ_KPAD) * OZ_KPAD;
-  const unsigned gr = (unsigned)cdiv(rows, 8);
-  const unsigned gs = (unsigned)std::min<int64_t>(cdiv(rows * kp, 256), 152 * 32);
-  __nv_bfloat16* out = static_cast<__nv_bfloat16*>(slices);
-  if (dt == TK_F64) {
-    k_oz_rowexp<double><<<gr, 256, 0, st>>>((const double*)X, rows, cols, ld, E);
+  const bool f64 = dt == TK_F64;
+  if (cols >= 16384 && rows <= 65535) {
+    // few long rows (the residuals of the normal-equation pass): blocks of 8192 values per row
+    const int64_t per = 8192;
+    k_oz_fill_emin<<<(unsigned)cdiv(rows, 256), 256, 0, st>>>(E, rows);
     TK_LAUNCH_CHECK();
-    k_oz_slice<double><<<gs, 256, 0, st>>>((const double*)X, rows, cols, ld, E, kp, out);
+    const dim3 g((unsigned)cdiv(cols, per), (unsigned)rows);
+    if (f64) k_oz_rowexp_long<double><<<g, 256, 0, st>>>((const double*)X, cols, ld, per, E);
+    else k_oz_rowexp_long<float><<<g, 256, 0, st>>>((const float*)X, cols, ld, per, E);
+    TK_LAUNCH_CHECK();
+    k_oz_fix_zero_rows<<<(unsigned)cdiv(rows, 256), 256, 0, st>>>(E, rows);
   } else {
-    k_oz_rowexp<float><<<gr, 256, 0, st>>>((const float*)X, rows, cols, ld, E);
-    TK_LAUNCH_CHECK();
-    k_oz_slice<float><<<gs, 256, 0, st>>>((const float*)X, rows, cols, ld, E, kp, out);
+    const unsigned gr = (unsigned)cdiv(rows, 8);
+    if (f64) k_oz_rowexp<double><<<gr, 256, 0, st>>>((const double*)X, rows, cols, ld, E);
+    else k_oz_rowexp<float><<<gr, 256, 0, st>>>((const float*)X, rows, cols, ld, E);
   }
+  TK_LAUNCH_CHECK();
+  const int64_t chunks = cdiv(kp, 512);  // 256 threads x 2 values
+  if (chunks > 65535) {
+    set_error_msg("emulated float64 product: rows too long for the slicing grid");
+    return TK_EINVAL;
+  }
+  const dim3 gs((unsigned)std::min<int64_t>(rows, std::max<int64_t>(1, 152 * 16 / chunks)), (unsigned)chunks);
+  __nv_bfloat16* out = static_cast<__nv_bfloat16*>(slices);
+  if (f64) k_oz_slice<double><<<gs, 256, 0, st>>>((const double*)X, rows, cols, ld, E, kp, out);
+  else k_oz_slice<float><<<gs, 256, 0, st>>>((const float*)X, rows, cols, ld, E, kp, out);
   TK_LAUNCH_CHECK();
   return TK_OK;
 }
@@ -584,7 +681,7 @@ tk_status oz_prepare_cols(const void* X, tk_dtype dt, int64_t rows, int64_t cols
     set_error_msg("emulated float64 product: too many columns for the slicing grid");
     return TK_EINVAL;
   }
-  const dim3 gt((unsigned)cdiv(rp, 32), (unsigned)cdiv(cols, 32));
+  const dim3 gt((unsigned)cdiv(rp, 64), (unsigned)cdiv(cols, 32));
   __nv_bfloat16* out = static_cast<__nv_bfloat16*>(slices);
   if (dt == TK_F64) k_oz_colmax<double><<<gm, 256, 0, st>>>((const double*)X, rows, cols, ld, rows_per, mx);
   else k_oz_colmax<float><<<gm, 256, 0, st>>>((const float*)X, rows, cols, ld, rows_per, mx);
