@@ -41,7 +41,8 @@ struct Plan {
   int N = 0, N_cap = 0;
   tk_opts o{};
   bool mixed = false, lowrank = false;
-  bool lsqr_tc = false;  // tensor-core float32 LSQR products
+  bool lsqr_tc = false;  // tensor-core float32 LSQR products (3-term TF32)
+  bool lsqr_oz = false;  // float32 LSQR products from the 4-digit slices of A
   bool prep_only = false;  // grouped batch: build the preconditioner only
   bool inv64 = false;      // float64 form: explicit float64 R^-1 (small factors)
 };
@@ -101,8 +102,9 @@ tk_status make_plan(const tk_problem* p, int N, const tk_opts* o, Plan& P) {
   // turns each preconditioner apply into one launch (substitution on a
   // factor of order <= 512 runs in a single CTA per lambda)
   P.inv64 = !P.mixed && !P.lowrank && !P.under && P.c <= 512;
-  P.lsqr_tc = P.mixed && o->lsqr_tc != 0 && P.N_cap <= 64 && !P.under && P.m % 4 == 0 && P.n % 4 == 0 &&
+  P.lsqr_tc = P.mixed && o->lsqr_tc == 1 && P.N_cap <= 64 && !P.under && P.m % 4 == 0 && P.n % 4 == 0 &&
               (P.dt == TK_F64 || P.lda % 4 == 0);
+  P.lsqr_oz = P.mixed && o->lsqr_tc == 2 && o->emulate_fp64 && !P.under;
   return TK_OK;
 }
 
@@ -246,6 +248,7 @@ void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
   if (P.mixed) {
     B.e32.m = P.m; B.e32.n = P.n; B.e32.N_cap = P.N_cap; B.e32.under = false; B.e32.lr_s = lr_s;
     B.e32.tc = P.lsqr_tc;
+    B.e32.oz = P.lsqr_oz;
     B.e32.carve(a);
   } else {
     B.e64.m = P.m; B.e64.n = P.n; B.e64.N_cap = P.N_cap; B.e64.under = P.under; B.e64.lr_s = lr_s;
@@ -610,6 +613,9 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       TK_TRY(oz_prepare_cols(p->A, P.dt, P.m, P.n, P.lda, B.AozC, B.EC, B.colmax, st));
       TK_CUDA(cudaMemsetAsync(B.oz_err, 0, sizeof(int), st));
       prof_end(tok, st, 0.0, 2.0 * ((P.dt == TK_F64 ? 16.0 : 8.0) * P.m * P.n + 16.0 * P.m * P.n));
+      if (P.lsqr_oz) {  // the LSQR products read the first 4 digits of the same slices
+        e.oz_A = B.Aoz; e.oz_EA = B.EA; e.oz_AT = B.AozC; e.oz_EAT = B.EC; e.oz_err = B.oz_err;
+      }
     }
     for (int round = 0; round < P.o.max_refine && !act.empty(); ++round) {
       const int cnt = (int)act.size();
@@ -667,7 +673,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       TK_LAUNCH_CHECK();
       TK_CUDA(cudaMemcpyAsync(hn.data(), B.nrm, sizeof(double) * 3 * cnt, cudaMemcpyDeviceToHost, st));
       int oz_err = 0;
-      if (P.o.emulate_fp64 && round > 0)
+      if (P.o.emulate_fp64 && (round > 0 || e.use_oz()))
         TK_CUDA(cudaMemcpyAsync(&oz_err, B.oz_err, sizeof(int), cudaMemcpyDeviceToHost, st));
       TK_CUDA(cudaStreamSynchronize(st));
       if (oz_err) {
@@ -796,7 +802,7 @@ tk_status batch_layout(const tk_problem* ps, int P, int N, const tk_opts* o, int
   for (int i = 0; i < P; ++i) {
     TK_TRY(make_plan(&ps[i], N, opts_of(o, n_opts, i), pl[i]));
     const Plan& q = pl[i];
-    grouped = grouped && q.mixed && !q.under && q.o.schedule == TK_SCHED_BATCHED && !q.lsqr_tc &&
+    grouped = grouped && q.mixed && !q.under && q.o.schedule == TK_SCHED_BATCHED && !q.lsqr_tc && !q.lsqr_oz &&
               q.n <= kGroupMaxN && q.o.group != 0;
   }
   L.grouped = grouped;

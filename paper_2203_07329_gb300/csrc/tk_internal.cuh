@@ -223,9 +223,10 @@ constexpr int dtype_code() {
 // columns of X into planes of X^T with column exponents (oz_prepare_cols:
 // slices bytes oz_slices_bytes(cols, rows), E: cols ints, colmax:
 // oz_colmax_bytes(cols)).  *err (device) is set if a pipeline wait timed out.
-size_t oz_slices_bytes(int64_t rows, int64_t cols);
+constexpr int OZ_LSQR_DIGITS = 4;  // digits of the float32-accurate LSQR products
+size_t oz_slices_bytes(int64_t rows, int64_t cols, int planes = 8);
 tk_status oz_prepare(const void* X, tk_dtype dt, int64_t rows, int64_t cols, int64_t ld, void* slices, int* E,
-                     cudaStream_t st);
+                     cudaStream_t st, int planes = 8);
 size_t oz_colmax_bytes(int64_t cols);
 tk_status oz_prepare_cols(const void* X, tk_dtype dt, int64_t rows, int64_t cols, int64_t ld, void* slices, int* E,
                           void* colmax, cudaStream_t st);
@@ -255,6 +256,15 @@ size_t oz_chol_workspace(int64_t np, int N);
 tk_status oz_chol_begin(double* R, int64_t ldr, int64_t rstride, int N, int64_t np, void* work, size_t bytes,
                         int* err, OzCholPlan* plan, cudaStream_t st);
 tk_status oz_chol_step(const OzCholPlan& plan, int kb, cudaStream_t st);
+// The two float32 LSQR products from the first 4 digits of the slices of A
+// (the 28-bit rounded A) and of the lambda-major vectors, sliced here
+// (Wslices / Uslices: oz_slices_bytes(count, n or m, 4); EW / EU: count ints):
+//   aw:  U[l][i] = sum_k W[l][k] A[i][k] + coef[l] U[l][i]  (coef may be null);
+//   atu: partial[z][l][j] = sum_{i in split z} U[l][i] A[i][j].
+tk_status oz_lsqr_aw(const void* Aslices, const int* EA, int64_t m, int64_t n, const float* W, int64_t ldw, int count,
+                     void* Wslices, int* EW, float* U, int64_t ldu, const double* coef, int* err, cudaStream_t st);
+tk_status oz_lsqr_atu(const void* AslicesT, const int* EC, int64_t m, int64_t n, const float* U, int64_t ldu,
+                      int count, void* Uslices, int* EU, double* partial, int splits, int* err, cudaStream_t st);
 // C = Y^T Y (Y: r x c float64, row stride c), the upper triangle (j >= i) of
 // C (c x c) written, float64-accurate; work: oz_gram_workspace(r, c) bytes.
 size_t oz_gram_workspace(int64_t r, int64_t c);

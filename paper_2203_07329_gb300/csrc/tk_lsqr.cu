@@ -326,6 +326,10 @@ void Lsqr<T>::carve(Arena& a) {
     lr_inv = a.take<double>((size_t)N_cap);
   }
   if (tc) tc_scratch = a.take<char>(tc_lmaj_workspace(N_cap, std::max(n, m)));
+  if (oz) {
+    oz_q = a.take<char>(oz_slices_bytes(N_cap, std::max(n, m), OZ_LSQR_DIGITS));
+    oz_e = a.take<int>((size_t)N_cap);
+  }
 }
 
 template <typename T>
@@ -356,6 +360,11 @@ tk_status Lsqr<T>::prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, 
   int tok = prof_begin(TK_PHASE_AW, st);
   tk_status r;
   if constexpr (std::is_same<T, float>::value) {
+    if (use_oz()) {
+      r = oz_lsqr_aw(oz_A, oz_EA, m, n, Win, ldw, count, oz_q, oz_e, C, m, beta, oz_err, st);
+      prof_end(tok, st, 2.0 * count * m * n, 8.0 * m * n + 4.0 * count * (double)n + 8.0 * count * m);
+      return r;
+    }
     if (tc && beta) {
       r = tc_lmaj_product(true, A, m, n, lda, Win, ldw, count, C, m, beta, nullptr, 1, tc_scratch, st);
       prof_end(tok, st, 2.0 * count * m * n, (double)sizeof(T) * ((double)m * n + count * (double)n + 2.0 * count * m));
@@ -373,6 +382,12 @@ tk_status Lsqr<T>::prod_atu(const T* Uin, int count) {
   int tok = prof_begin(TK_PHASE_ATU, st);
   tk_status r;
   if constexpr (std::is_same<T, float>::value) {
+    if (use_oz()) {
+      cur_splits = std::min(splits, oz_normal_splits(m, n, count));
+      r = oz_lsqr_atu(oz_AT, oz_EAT, m, n, Uin, m, count, oz_q, oz_e, part_g, cur_splits, oz_err, st);
+      prof_end(tok, st, 2.0 * count * m * n, 8.0 * m * n + 4.0 * count * (double)m + 8.0 * cur_splits * count * n);
+      return r;
+    }
     if (tc && AT) {
       cur_splits = splits;
       r = tc_lmaj_product(false, AT, n, m, m, Uin, m, count, nullptr, 0, nullptr, part_g, splits, tc_scratch, st);

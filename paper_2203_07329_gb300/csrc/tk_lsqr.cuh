@@ -160,6 +160,18 @@ struct Lsqr {
   bool tc = false;
   const T* AT = nullptr;
   void* tc_scratch = nullptr;
+  // products from the 4-digit slices of A on the tensor cores (float32
+  // engine, large problems): row-exponent slices of A (m x n) and
+  // column-exponent slices of A^T (n x m) as made for the float64 passes
+  bool oz = false;
+  const void* oz_A = nullptr;
+  const int* oz_EA = nullptr;
+  const void* oz_AT = nullptr;
+  const int* oz_EAT = nullptr;
+  int* oz_err = nullptr;
+  void* oz_q = nullptr;  // slices of the lambda-major vector of a product
+  int* oz_e = nullptr;
+  bool use_oz() const { return oz && oz_A && oz_AT && (int64_t)m * n > (int64_t(1) << 24); }
 
   static size_t workspace(int64_t m, int64_t n, int N_cap, bool under, int64_t lr_s);
   void carve(Arena& a);

@@ -24,6 +24,7 @@
 // in tensor memory, double-buffered so that four epilogue warps flush one
 // 256-value chunk of K into float64 while the MMAs of the next chunk run.
 #include <algorithm>
+#include <type_traits>
 #include <cuda_bf16.h>
 
 #include "tk_internal.cuh"
@@ -103,7 +104,7 @@ __device__ __forceinline__ void oz_split(double x, int E, __nv_bfloat16 (&s)[OZ_
 // blockIdx.y; each thread splits two adjacent values (one 4-byte store per plane).
 template <typename T>
 __global__ void __launch_bounds__(256) k_oz_slice(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                                                  const int* __restrict__ E, int64_t cols_pad,
+                                                  const int* __restrict__ E, int64_t cols_pad, int planes,
                                                   __nv_bfloat16* __restrict__ out) {
   const int64_t plane = rows * cols_pad;
   const int64_t c = ((int64_t)blockIdx.y * blockDim.x + threadIdx.x) * 2;
@@ -116,7 +117,8 @@ __global__ void __launch_bounds__(256) k_oz_slice(const T* __restrict__ X, int64
     oz_split(c + 1 < cols ? (double)xr[c + 1] : 0.0, e, s1);
     __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + r * cols_pad + c);
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) o[p * (plane / 2)] = __halves2bfloat162(s0[p], s1[p]);
+    for (int p = 0; p < OZ_S; ++p)
+      if (p < planes) o[p * (plane / 2)] = __halves2bfloat162(s0[p], s1[p]);
   }
 }
 
@@ -191,36 +193,38 @@ __global__ void __launch_bounds__(256) k_oz_slice_t(const T* __restrict__ X, int
 }
 
 // ---- the product on tcgen05 ---------------------------------------------------
-// D[r][l] = sum_k P[r][k] Q[l][k] from the slices of P (rows x K, row
-// exponents EP) and Q (M x K, row exponents EQ), both K-major planes.
+// D[r][l] = sum_k P[r][k] Q[l][k] from the first S digit planes of P (rows x
+// K, row exponents EP) and of Q (M x K, row exponents EQ), both K-major.
+// S = 8: float64 accuracy (levels flushed into float64); S = 4: the 28-bit
+// rounded operands, float32 accuracy (levels flushed into float32).
 // CTA: 128 rows of P x 32 rows of Q x one K split (blockIdx.z).
-//   warp 0 (one lane): TMA producer -- per 64 values of K the 8 slices of Q
-//     (4 KiB each) into a 2-slot ring, then the 8 slices of P one by one
+//   warp 0 (one lane): TMA producer -- per 64 values of K the S planes of Q
+//     (4 KiB each) into a 2-slot ring, then the S planes of P one by one
 //     (16 KiB each) into an 8-slot ring;
-//   warp 1 (one lane): MMA issuer -- for slice p of P and q <= 7 - p,
-//     D_(p+q) += P_p Q_q^T (4 MMAs of K = 16); the level accumulators of a
-//     chunk of 256 values of K sit in one of two tensor-memory buffers;
-//   warp 2: allocates / frees the 512 tensor-memory columns;
-//   warps 4-7: epilogue -- per chunk, read the 8 levels (lanes 32(w-4) ..),
-//     add them into 32 float64 accumulators per row, release the buffer;
-//     at the end write the result (MODE 0: R[l][r] = b[r] - D; MODE 1:
-//     partial[z][l][r] = D).
+//   warp 1 (one lane): MMA issuer -- for plane p of P, D_(p+q) += P_p Q_q^T
+//     for every q <= S-1-p as one MMA of N = 32 (S - p) (4 of K = 16); the
+//     level accumulators of a chunk of 256 values of K sit in one of two
+//     tensor-memory buffers;
+//   warp 2: allocates / frees the 2 S 32 tensor-memory columns;
+//   warps 4-7: epilogue -- per chunk, read the S levels (lanes 32(w-4) ..),
+//     add them into 32 accumulators per row, release the buffer; at the end
+//     write the result: MODE 0 R[l][r] = b[r] - D (float64); MODE 1
+//     partial[z][l][r] = D (float64); MODE 2 U[l][r] = D + coef[l] U[l][r]
+//     (float32 U; coef == nullptr: U = D).
 // Every mbarrier wait is bounded; a wait that gives up sets *err and the
 // roles stop.
 constexpr int OT_M = 128;
 constexpr int OT_N = 32;
 constexpr int OT_KB = 64;
 constexpr int OT_CHUNK = 256;
-constexpr int OT_KB_PER_CHUNK = OT_CHUNK / 64;
+constexpr int OT_KB_PER_CHUNK = OT_CHUNK / OT_KB;
 constexpr int OT_PST = 8;
 constexpr uint32_t OT_P_BYTES = OT_M * OT_KB * 2;   // 16 KiB
 constexpr uint32_t OT_QS_BYTES = OT_N * OT_KB * 2;  // 4 KiB
-constexpr uint32_t OT_Q_BYTES = OZ_S * OT_QS_BYTES;
-constexpr uint32_t OT_TMEM_COLS = 2 * OZ_LV * OT_N;  // 512
 
 struct OtSmem {
   uint8_t p[OT_PST][OT_P_BYTES];
-  uint8_t q[2][OT_Q_BYTES];
+  uint8_t q[2][OZ_S * OT_QS_BYTES];
   uint64_t p_full[OT_PST];
   uint64_t p_empty[OT_PST];
   uint64_t q_full[2];
@@ -239,14 +243,17 @@ __device__ __forceinline__ double level_to_double(uint32_t bits, int t) {
   return __hiloint2double((int)(mag | (bits & 0x80000000u)), (int)(bits << 29));
 }
 
-template <int MODE>
+template <int S, int MODE>
 __global__ void __launch_bounds__(256, 1)
     k_oz_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
             const int* __restrict__ EP, const int* __restrict__ EQ, int64_t rows, int M, int64_t K, int64_t kps,
-            const double* __restrict__ b, double* __restrict__ out, int64_t ldo, int upper_only,
-            int* __restrict__ err) {
+            const double* __restrict__ b, void* __restrict__ out, int64_t ldo, const double* __restrict__ coef,
+            int upper_only, int* __restrict__ err) {
+  using Acc = typename std::conditional<S == OZ_S, double, float>::type;
+  constexpr uint32_t TMEM_COLS = 2 * S * OT_N;
+  constexpr uint32_t Q_BYTES = S * OT_QS_BYTES;
   extern __shared__ __align__(1024) uint8_t ot_raw[];
-  OtSmem& S = *reinterpret_cast<OtSmem*>((reinterpret_cast<uintptr_t>(ot_raw) + 1023) & ~uintptr_t(1023));
+  OtSmem& Sm = *reinterpret_cast<OtSmem*>((reinterpret_cast<uintptr_t>(ot_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r0 = (int64_t)blockIdx.x * OT_M;
   const int l0 = (int)blockIdx.y * OT_N;
@@ -259,27 +266,27 @@ __global__ void __launch_bounds__(256, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OT_PST; ++s) {
-      mbar_init(&S.p_full[s], 1);
-      mbar_init(&S.p_empty[s], 1);
+      mbar_init(&Sm.p_full[s], 1);
+      mbar_init(&Sm.p_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&S.q_full[s], 1);
-      mbar_init(&S.q_empty[s], 1);
-      mbar_init(&S.acc_full[s], 1);
-      mbar_init(&S.acc_empty[s], 128);
+      mbar_init(&Sm.q_full[s], 1);
+      mbar_init(&Sm.q_empty[s], 1);
+      mbar_init(&Sm.acc_full[s], 1);
+      mbar_init(&Sm.acc_empty[s], 128);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 2) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
-                 "r"(OT_TMEM_COLS)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&Sm.tmem_base)),
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = S.tmem_base;
+  const uint32_t tmem = Sm.tmem_base;
 
   if (warp == 0 && lane == 0) {
     int g = 0;
@@ -287,86 +294,93 @@ __global__ void __launch_bounds__(256, 1)
     for (int kb = 0; kb < nkb && live; ++kb) {
       const int kc = (int)(kbeg + (int64_t)kb * OT_KB);
       const int qs = kb & 1;
-      if (!mbar_wait(&S.q_empty[qs], ((uint32_t)(kb >> 1) & 1u) ^ 1u, err)) break;
-      mbar_expect_tx(&S.q_full[qs], OT_Q_BYTES);
-      for (int p = 0; p < OZ_S; ++p) tma_load_3d(&tmQ, &S.q_full[qs], S.q[qs] + p * OT_QS_BYTES, kc, l0, p);
-      for (int p = 0; p < OZ_S; ++p, ++g) {
+      if (!mbar_wait(&Sm.q_empty[qs], ((uint32_t)(kb >> 1) & 1u) ^ 1u, err)) break;
+      mbar_expect_tx(&Sm.q_full[qs], Q_BYTES);
+      for (int p = 0; p < S; ++p) tma_load_3d(&tmQ, &Sm.q_full[qs], Sm.q[qs] + p * OT_QS_BYTES, kc, l0, p);
+      for (int p = 0; p < S; ++p, ++g) {
         const int ps = g % OT_PST;
-        if (!mbar_wait(&S.p_empty[ps], ((uint32_t)(g / OT_PST) & 1u) ^ 1u, err)) {
+        if (!mbar_wait(&Sm.p_empty[ps], ((uint32_t)(g / OT_PST) & 1u) ^ 1u, err)) {
           live = false;
           break;
         }
-        mbar_expect_tx(&S.p_full[ps], OT_P_BYTES);
-        tma_load_3d(&tmP, &S.p_full[ps], S.p[ps], kc, (int)r0, p);
+        mbar_expect_tx(&Sm.p_full[ps], OT_P_BYTES);
+        tma_load_3d(&tmP, &Sm.p_full[ps], Sm.p[ps], kc, (int)r0, p);
       }
     }
   } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = idesc_bf16(OT_M, OT_N);
     int g = 0;
     bool live = true;
     for (int c = 0; c < nch && live; ++c) {
       const int bsel = c & 1, use = c >> 1;
-      if (use > 0 && !mbar_wait(&S.acc_empty[bsel], (uint32_t)(use - 1) & 1u, err)) break;
+      if (use > 0 && !mbar_wait(&Sm.acc_empty[bsel], (uint32_t)(use - 1) & 1u, err)) break;
       tc_fence_after();
-      const uint32_t dbase = tmem + (uint32_t)(bsel * OZ_LV * OT_N);
+      const uint32_t dbase = tmem + (uint32_t)(bsel * S * OT_N);
       const int kb0 = OT_KB_PER_CHUNK * c;
       const int kb_end = nkb < kb0 + OT_KB_PER_CHUNK ? nkb : kb0 + OT_KB_PER_CHUNK;
       for (int kb = kb0; kb < kb_end && live; ++kb) {
         const int qs = kb & 1;
-        if (!mbar_wait(&S.q_full[qs], (uint32_t)(kb >> 1) & 1u, err)) {
+        if (!mbar_wait(&Sm.q_full[qs], (uint32_t)(kb >> 1) & 1u, err)) {
           live = false;
           break;
         }
         tc_fence_after();
-        const uint32_t qa = smem_u32(S.q[qs]);
-        for (int p = 0; p < OZ_S; ++p, ++g) {
+        const uint32_t qa = smem_u32(Sm.q[qs]);
+        for (int p = 0; p < S; ++p, ++g) {
           const int ps = g % OT_PST;
-          if (!mbar_wait(&S.p_full[ps], (uint32_t)(g / OT_PST) & 1u, err)) {
+          if (!mbar_wait(&Sm.p_full[ps], (uint32_t)(g / OT_PST) & 1u, err)) {
             live = false;
             break;
           }
           tc_fence_after();
-          const uint64_t pd = sdesc_sw128(smem_u32(S.p[ps]));
-          for (int q = 0; q < OZ_S - p; ++q) {
-            const uint64_t qd = sdesc_sw128(qa + (uint32_t)q * OT_QS_BYTES);
-            const uint32_t d = dbase + (uint32_t)((p + q) * OT_N);
+          // the planes Q_0 .. Q_(S-1-p) lie one after another (32 rows each), and the levels
+          // p .. S-1 are consecutive 32-column blocks of the buffer: all pairs (p, q) are one
+          // MMA with N = 32 (S - p) whose column block q lands on level p + q
+          const uint64_t pd = sdesc_sw128(smem_u32(Sm.p[ps]));
+          const uint64_t qd = sdesc_sw128(qa);
+          const uint32_t idesc = idesc_bf16(OT_M, OT_N * (S - p));
+          const uint32_t d = dbase + (uint32_t)(p * OT_N);
 #pragma unroll
-            for (int k = 0; k < OT_KB / 16; ++k) {
-              // the first MMA of each level in a chunk (p = 0) overwrites the buffer
-              const uint32_t acc = (kb == kb0 && p == 0 && k == 0) ? 0u : 1u;
-              tc_mma_bf16(d, pd + 2ull * k, qd + 2ull * k, idesc, acc);
-            }
+          for (int k = 0; k < OT_KB / 16; ++k) {
+            // the first MMA of a chunk (p = 0) overwrites every level of the buffer
+            const uint32_t acc = (kb == kb0 && p == 0 && k == 0) ? 0u : 1u;
+            tc_mma_bf16(d, pd + 2ull * k, qd + 2ull * k, idesc, acc);
           }
-          tc_commit(&S.p_empty[ps]);
+          tc_commit(&Sm.p_empty[ps]);
         }
-        if (live) tc_commit(&S.q_empty[qs]);
+        if (live) tc_commit(&Sm.q_empty[qs]);
       }
-      if (live) tc_commit(&S.acc_full[bsel]);
+      if (live) tc_commit(&Sm.acc_full[bsel]);
     }
   } else if (warp >= 4) {
     const int ew = warp - 4;
-    double acc64[OT_N];
+    Acc acc[OT_N];
 #pragma unroll
-    for (int j = 0; j < OT_N; ++j) acc64[j] = 0.0;
+    for (int j = 0; j < OT_N; ++j) acc[j] = Acc(0);
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
       const int bsel = c & 1, use = c >> 1;
-      if (!mbar_wait(&S.acc_full[bsel], (uint32_t)use & 1u, err)) {
+      if (!mbar_wait(&Sm.acc_full[bsel], (uint32_t)use & 1u, err)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(bsel * OZ_LV * OT_N);
+      const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(bsel * S * OT_N);
 #pragma unroll 1
-      for (int t = OZ_LV - 1; t >= 0; --t) {  // smallest level first
+      for (int t = S - 1; t >= 0; --t) {  // smallest level first
         uint32_t v[32];
         tmem_ld32_nowait(base + (uint32_t)(t * OT_N), v);
         tmem_wait_ld();
+        if constexpr (S == OZ_S) {
 #pragma unroll
-        for (int j = 0; j < OT_N; ++j) acc64[j] += level_to_double(v[j], t);
+          for (int j = 0; j < OT_N; ++j) acc[j] += level_to_double(v[j], t);
+        } else {
+          const float sc = __int_as_float((127 - 7 * (t + 2)) << 23);  // 2^(-7(t+2)), exact
+#pragma unroll
+          for (int j = 0; j < OT_N; ++j) acc[j] = fmaf(__uint_as_float(v[j]), sc, acc[j]);
+        }
       }
       tc_fence_before();
-      mbar_arrive(&S.acc_empty[bsel]);
+      mbar_arrive(&Sm.acc_empty[bsel]);
     }
     const int64_t r = r0 + ew * 32 + lane;
     if (ok && r < rows) {
@@ -376,9 +390,15 @@ __global__ void __launch_bounds__(256, 1)
       for (int j = 0; j < OT_N; ++j) {
         const int l = l0 + j;
         if (l < M) {
-          const double v = ldexp(acc64[j], er + EQ[l]);
-          if (MODE == 0) out[(int64_t)l * ldo + r] = br - v;
-          else out[((int64_t)blockIdx.z * M + l) * ldo + r] = v;
+          const double v = ldexp((double)acc[j], er + EQ[l]);
+          if (MODE == 0) {
+            static_cast<double*>(out)[(int64_t)l * ldo + r] = br - v;
+          } else if (MODE == 1) {
+            static_cast<double*>(out)[((int64_t)blockIdx.z * M + l) * ldo + r] = v;
+          } else {
+            float* u = static_cast<float*>(out) + (int64_t)l * ldo + r;
+            *u = coef ? (float)(v + coef[l] * (double)*u) : (float)v;
+          }
         }
       }
     }
@@ -388,16 +408,17 @@ __global__ void __launch_bounds__(256, 1)
   __syncthreads();
   if (warp == 2) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OT_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
-// 3D map over the slice planes (K fastest, then rows, then the slice index),
-// box = 64 values of K x box_rows x 1 slice, 128-byte swizzle.
-tk_status make_slice_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, uint32_t box_rows) {
+// 3D map over the slice planes (K fastest, then rows, then the plane index),
+// box = 64 values of K x box_rows x 1 plane, 128-byte swizzle.
+tk_status make_slice_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, uint32_t box_rows,
+                         int planes) {
   EncodeTiledFn fn;
   TK_TRY(encode_fn(&fn));
-  const cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)OZ_S};
+  const cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)planes};
   const cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)rows * kp * 2};
   const cuuint32_t box[3] = {(cuuint32_t)OT_KB, box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
@@ -411,27 +432,30 @@ tk_status make_slice_map(CUtensorMap* map, const void* base, int64_t rows, int64
   return TK_OK;
 }
 
-template <int MODE>
-tk_status launch_oz_tc(const void* Ps, const int* EP, int64_t rows, const void* Qs, const int* EQ, int M, int64_t K,
-                       int splits, const double* b, double* out, int64_t ldo, int* err, cudaStream_t st,
-                       int upper_only = 0) {
+// P: planesP digit planes of rows x K, Q: planesQ planes of M x K (both K
+// rounded up to 64); S digits of each are used.
+template <int S, int MODE>
+tk_status launch_oz_tc(const void* Ps, const int* EP, int64_t rows, int planesP, const void* Qs, const int* EQ, int M,
+                       int planesQ, int64_t K, int splits, const double* b, void* out, int64_t ldo,
+                       const double* coef, int* err, cudaStream_t st, int upper_only = 0) {
   const int64_t kp = cdiv(K, OZ_KPAD) * OZ_KPAD;
   if (rows > INT32_MAX || kp > INT32_MAX || M > 65535 * OT_N) {
-    set_error_msg("emulated float64 product: dimensions exceed the 32-bit TMA coordinates");
+    set_error_msg("emulated product: dimensions exceed the 32-bit TMA coordinates");
     return TK_EINVAL;
   }
   CUtensorMap mP, mQ;
-  TK_TRY(make_slice_map(&mP, Ps, rows, kp, OT_M));
-  TK_TRY(make_slice_map(&mQ, Qs, M, kp, OT_N));
+  TK_TRY(make_slice_map(&mP, Ps, rows, kp, OT_M, planesP));
+  TK_TRY(make_slice_map(&mQ, Qs, M, kp, OT_N, planesQ));
   const int64_t kps = cdiv(cdiv(K, splits), OT_CHUNK) * OT_CHUNK;  // whole chunks per split
   const int sp = (int)cdiv(K, kps);
   const size_t smem = sizeof(OtSmem) + 1024;
-  TK_CUDA(cudaFuncSetAttribute(k_oz_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TK_CUDA(cudaFuncSetAttribute(k_oz_tc<S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const dim3 grid((unsigned)cdiv(rows, OT_M), (unsigned)cdiv(M, OT_N), (unsigned)sp);
-  k_oz_tc<MODE><<<grid, 256, smem, st>>>(mP, mQ, EP, EQ, rows, M, kp, kps, b, out, ldo, upper_only, err);
+  k_oz_tc<S, MODE><<<grid, 256, smem, st>>>(mP, mQ, EP, EQ, rows, M, kp, kps, b, out, ldo, coef, upper_only, err);
   TK_LAUNCH_CHECK();
   if (MODE == 1 && sp < splits) {  // the caller sums `splits` planes: the unused ones are zero
-    TK_CUDA(cudaMemsetAsync(out + (int64_t)sp * M * ldo, 0, sizeof(double) * (size_t)(splits - sp) * M * ldo, st));
+    double* o = static_cast<double*>(out);
+    TK_CUDA(cudaMemsetAsync(o + (int64_t)sp * M * ldo, 0, sizeof(double) * (size_t)(splits - sp) * M * ldo, st));
   }
   return TK_OK;
 }
@@ -541,14 +565,17 @@ __global__ void __launch_bounds__(256, 1)
       tma_load_3d(&tmQ, &S.full, S.q[p], 0, j0, l * OZ_S + p);
     }
   } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = idesc_bf16(CS_M, CS_N);
     if (mbar_wait(&S.full, 0u, err)) {
       tc_fence_after();
       for (int p = 0; p < OZ_S; ++p) {
         const uint64_t pd = sdesc_sw128(smem_u32(S.p[p]));
-        for (int q = 0; q < OZ_S - p; ++q) {
-          const uint64_t qd = sdesc_sw128(smem_u32(S.q[q]));
-          const uint32_t d = tmem + (uint32_t)((p + q) * CS_N);
+        // the planes Q_q (64 rows each) are contiguous and levels p + q consecutive column
+        // blocks: pairs (p, q0 .. q0+3) are one MMA of N = 64 x (planes), at most 256
+        for (int q0 = 0; q0 < OZ_S - p; q0 += 4) {
+          const int nq = OZ_S - p - q0 < 4 ? OZ_S - p - q0 : 4;
+          const uint64_t qd = sdesc_sw128(smem_u32(S.q[q0]));
+          const uint32_t idesc = idesc_bf16(CS_M, CS_N * nq);
+          const uint32_t d = tmem + (uint32_t)((p + q0) * CS_N);
 #pragma unroll
           for (int k = 0; k < 4; ++k) tc_mma_bf16(d, pd + 2ull * k, qd + 2ull * k, idesc, (p == 0 && k == 0) ? 0u : 1u);
         }
@@ -626,12 +653,12 @@ __global__ void __launch_bounds__(256, 1)
 
 }  // namespace
 
-size_t oz_slices_bytes(int64_t rows, int64_t cols) {
-  return sizeof(__nv_bfloat16) * (size_t)OZ_S * (size_t)rows * (size_t)(cdiv(cols, OZ_KPAD) * OZ_KPAD);
+size_t oz_slices_bytes(int64_t rows, int64_t cols, int planes) {
+  return sizeof(__nv_bfloat16) * (size_t)planes * (size_t)rows * (size_t)(cdiv(cols, OZ_KPAD) * OZ_KPAD);
 }
 
 tk_status oz_prepare(const void* X, tk_dtype dt, int64_t rows, int64_t cols, int64_t ld, void* slices, int* E,
-                     cudaStream_t st) {
+                     cudaStream_t st, int planes) {
   if (rows == 0 || cols == 0) return TK_OK;
   const int64_t kp = cdiv(cols, OZ_KPAD) * OZ_KPAD;
   const bool f64 = dt == TK_F64;
@@ -658,8 +685,8 @@ tk_status oz_prepare(const void* X, tk_dtype dt, int64_t rows, int64_t cols, int
   }
   const dim3 gs((unsigned)std::min<int64_t>(rows, std::max<int64_t>(1, 152 * 16 / chunks)), (unsigned)chunks);
   __nv_bfloat16* out = static_cast<__nv_bfloat16*>(slices);
-  if (f64) k_oz_slice<double><<<gs, 256, 0, st>>>((const double*)X, rows, cols, ld, E, kp, out);
-  else k_oz_slice<float><<<gs, 256, 0, st>>>((const float*)X, rows, cols, ld, E, kp, out);
+  if (f64) k_oz_slice<double><<<gs, 256, 0, st>>>((const double*)X, rows, cols, ld, E, kp, planes, out);
+  else k_oz_slice<float><<<gs, 256, 0, st>>>((const float*)X, rows, cols, ld, E, kp, planes, out);
   TK_LAUNCH_CHECK();
   return TK_OK;
 }
@@ -697,7 +724,7 @@ tk_status oz_prepare_cols(const void* X, tk_dtype dt, int64_t rows, int64_t cols
 tk_status oz_residual(const void* Aslices, const int* EA, int64_t m, int64_t n, const void* Xslices, const int* EX,
                       int64_t M, const double* b, double* R, int64_t ldr, int* err, cudaStream_t st) {
   if (m == 0 || M == 0) return TK_OK;
-  return launch_oz_tc<0>(Aslices, EA, m, Xslices, EX, (int)M, n, 1, b, R, ldr, err, st);
+  return launch_oz_tc<OZ_S, 0>(Aslices, EA, m, OZ_S, Xslices, EX, (int)M, OZ_S, n, 1, b, R, ldr, nullptr, err, st);
 }
 
 int oz_normal_splits(int64_t m, int64_t n, int64_t M) {
@@ -711,7 +738,24 @@ tk_status oz_normal(const void* AslicesT, const int* EC, int64_t m, int64_t n, c
                     int64_t M, void* Rslices, int* EX, double* partial, int splits, int* err, cudaStream_t st) {
   if (M == 0 || n == 0) return TK_OK;
   TK_TRY(oz_prepare(R, TK_F64, M, m, ldr, Rslices, EX, st));
-  return launch_oz_tc<1>(AslicesT, EC, n, Rslices, EX, (int)M, m, splits, nullptr, partial, n, err, st);
+  return launch_oz_tc<OZ_S, 1>(AslicesT, EC, n, OZ_S, Rslices, EX, (int)M, OZ_S, m, splits, nullptr, partial, n,
+                               nullptr, err, st);
+}
+
+tk_status oz_lsqr_aw(const void* Aslices, const int* EA, int64_t m, int64_t n, const float* W, int64_t ldw, int count,
+                     void* Wslices, int* EW, float* U, int64_t ldu, const double* coef, int* err, cudaStream_t st) {
+  if (m == 0 || count == 0) return TK_OK;
+  TK_TRY(oz_prepare(W, TK_F32, count, n, ldw, Wslices, EW, st, OZ_LSQR_DIGITS));
+  return launch_oz_tc<OZ_LSQR_DIGITS, 2>(Aslices, EA, m, OZ_S, Wslices, EW, count, OZ_LSQR_DIGITS, n, 1, nullptr, U,
+                                         ldu, coef, err, st);
+}
+
+tk_status oz_lsqr_atu(const void* AslicesT, const int* EC, int64_t m, int64_t n, const float* U, int64_t ldu,
+                      int count, void* Uslices, int* EU, double* partial, int splits, int* err, cudaStream_t st) {
+  if (n == 0 || count == 0) return TK_OK;
+  TK_TRY(oz_prepare(U, TK_F32, count, m, ldu, Uslices, EU, st, OZ_LSQR_DIGITS));
+  return launch_oz_tc<OZ_LSQR_DIGITS, 1>(AslicesT, EC, n, OZ_S, Uslices, EU, count, OZ_LSQR_DIGITS, m, splits,
+                                         nullptr, partial, n, nullptr, err, st);
 }
 
 size_t oz_gram_workspace(int64_t r, int64_t c) {
@@ -737,7 +781,7 @@ tk_status oz_gram(const double* Y, int64_t r, int64_t c, double* C, void* work, 
   void* mx = a.take<char>(oz_colmax_bytes(c));
   if (!a.ok()) return TK_ENOMEM;
   TK_TRY(oz_prepare_cols(Y, TK_F64, r, c, c, Ys, E, mx, st));
-  return launch_oz_tc<1>(Ys, E, c, Ys, E, (int)c, r, 1, nullptr, C, c, err, st, 1);
+  return launch_oz_tc<OZ_S, 1>(Ys, E, c, OZ_S, Ys, E, (int)c, OZ_S, r, 1, nullptr, C, c, nullptr, err, st, 1);
 }
 
 size_t oz_chol_workspace(int64_t np, int N) {

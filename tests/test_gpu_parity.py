@@ -480,6 +480,29 @@ def test_mixed_tensor_core_lsqr_products(tk, m, n, N):
     assert it_tc <= 1.3 * it_simt + 5, (it_tc, it_simt)
 
 
+@pytest.mark.parametrize("m,n,N,dtype", [(32768, 640, 8, torch.float64), (40000, 500, 33, torch.float32)])
+def test_mixed_sliced_lsqr_products(tk, m, n, N, dtype):
+    # the two products with A of every LSQR step from the first 4 exact digits of the slices of A
+    # (lsqr_tc = 2; m n > 2^24 so the sliced path is taken), then the float64 refinement: x must
+    # reach the same 1e-10 as with the SIMT float32 products, with comparable iteration counts
+    p = problem(m, n, lo=1e-5, N=N, lam=(1e-6, 1.0), dtype=dtype)
+    lams = p.lambdas.numpy()
+    A, b = to_dev(p)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=4 * n, seed=9, precision=tk.TK_PREC_MIXED, lsqr_tc=2)
+    res = tk.tk_solve(A, b, lams, o)
+    X = res.X.cpu().numpy()
+    o0 = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=4 * n, seed=9, precision=tk.TK_PREC_MIXED, lsqr_tc=0)
+    res0 = tk.tk_solve(A, b, lams, o0)
+    Ad, bd = p.A.double().numpy(), p.b.numpy()
+    for i in sorted({0, N // 2, N - 1}):
+        xr = oracle.ref_ridge_qr(Ad, bd, float(lams[i]), refine=3)
+        assert rel(X[i], xr) < TOL_X, (lams[i], rel(X[i], xr), res.info[i])
+        assert res.info[i]["status"] == 0
+    it_oz = sum(q["iters"] for q in res.info)
+    it_simt = sum(q["iters"] for q in res0.info)
+    assert it_oz <= 1.2 * it_simt + 5, (it_oz, it_simt)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_autotuned_solve_matches_untuned(tk, precision):
     # the tuner only changes tile shapes and split counts: the solution stays the same
