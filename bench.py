@@ -272,6 +272,9 @@ def main():
     ap.add_argument("--no-uneven", action="store_true", help="skip the 256 uneven problems batch")
     ap.add_argument("--no-small", action="store_true", help="skip the 4096 x 256 workload")
     ap.add_argument("--no-tune", action="store_true", help="keep the fixed tile rules (no tk_autotune)")
+    ap.add_argument("--lsqr-tc", type=int, default=None, choices=[0, 1, 2],
+                    help="LSQR products of the timed mixed step: 0 SIMT float32, 1 TF32 x3, 2 4-digit slices "
+                         "(default: the library's)")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="where the synthetic problem is generated (cpu for profiler runs)")
     args = ap.parse_args()
@@ -302,7 +305,8 @@ def main():
     lams = prob.lambdas.numpy()
     N = len(lams)
     s = w["s"]
-    o_mixed = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, precision=tk.TK_PREC_MIXED)
+    extra_opts = {} if args.lsqr_tc is None else {"lsqr_tc": args.lsqr_tc}
+    o_mixed = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, precision=tk.TK_PREC_MIXED, **extra_opts)
     o_fp64 = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, tol=1e-14)
     o_fp64_one = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, tol=1e-14,
                                  schedule=tk.TK_SCHED_ONE_AT_A_TIME)

@@ -83,19 +83,71 @@ __global__ void k_oz_colexp(const unsigned long long* __restrict__ mx, int64_t c
   E[c] = e;
 }
 
-// The 8 balanced digits of one value x 2^-E (|x 2^-E| < 1/2): round to 55
-// bits (to nearest), then d = ((u + 64) mod 128) - 64 from the bottom, carry
-// (u - d) / 128; the last carry is the top digit, |d_0| <= 64.
-__device__ __forceinline__ void oz_split(double x, int E, __nv_bfloat16 (&s)[OZ_S]) {
-  long long u = llrint(ldexp(x, 7 * OZ_S - E));  // |u| <= 2^55
-#pragma unroll
-  for (int p = OZ_S - 1; p >= 1; --p) {
-    const int d = (int)((u + 64) & 127) - 64;
-    s[p] = __int2bfloat16_rn(d);
-    u = (u - d) >> 7;  // exact: u - d is a multiple of 128
-  }
-  s[0] = __int2bfloat16_rn((int)u);
+// round(x 2^(56-E)) (|x 2^-E| < 1/2, so |result| <= 2^55) from the bit
+// pattern of x: no float64 instruction (GB300 issues those at a fraction of
+// the integer rate).  Ties round away from zero.
+__device__ __forceinline__ long long oz_fixed(double x, int E) {
+  const long long bits = __double_as_longlong(x);
+  int ex = (int)((bits >> 52) & 0x7ff);
+  long long mant = bits & ((1ll << 52) - 1);
+  if (ex) mant |= 1ll << 52;
+  else ex = 1;  // subnormal: same scale as the smallest normal exponent
+  const int sh = ex - 1019 - E;  // |x| 2^(56-E) = mant 2^sh
+  long long u;
+  if (sh >= 0) u = mant << sh;  // mant 2^sh < 2^55: sh < 55
+  else if (sh > -63) u = (mant + (1ll << (-sh - 1))) >> (-sh);
+  else u = 0;
+  return bits < 0 ? -u : u;
 }
+__device__ __forceinline__ long long oz_fixed(float x, int E) {
+  const int bits = __float_as_int(x);
+  int ex = (bits >> 23) & 0xff;
+  long long mant = bits & 0x7fffff;
+  if (ex) mant |= 0x800000;
+  else ex = 1;
+  const int sh = ex - 94 - E;  // |x| 2^(56-E) = mant 2^sh
+  long long u;
+  if (sh >= 0) u = mant << sh;  // mant 2^sh < 2^55: sh < 55 (subnormal x: small mant)
+  else if (sh > -63) u = (mant + (1ll << (-sh - 1))) >> (-sh);
+  else u = 0;
+  return bits < 0 ? -u : u;
+}
+
+// BF16 bits of a small integer (|d| <= 2^8): through the float with the
+// 1.5 * 2^23 offset; its low 16 bits are zero, so the top half is exact.
+__device__ __forceinline__ unsigned short oz_bf16_bits(int d) {
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+  return (unsigned short)(__float_as_uint(f) >> 16);
+}
+
+// The 8 balanced base-128 digits of v (|v| <= 2^55): d = ((u + 64) mod 128)
+// - 64 from the bottom, carry (u - d) / 128, on two 32-bit halves (the low 28
+// bits, then the rest plus the carry); the last carry is the top digit,
+// |d_0| <= 64.  bits[p] = BF16 bit pattern of d_p.
+__device__ __forceinline__ void oz_digits(long long v, unsigned short (&bits)[OZ_S]) {
+  int lo = (int)(v & ((1ll << 28) - 1));
+  int hi = (int)(v >> 28);
+#pragma unroll
+  for (int p = OZ_S - 1; p >= 4; --p) {
+    const int d = ((lo + 64) & 127) - 64;
+    bits[p] = oz_bf16_bits(d);
+    lo = (lo - d) >> 7;
+  }
+  hi += lo;
+#pragma unroll
+  for (int p = 3; p >= 1; --p) {
+    const int d = ((hi + 64) & 127) - 64;
+    bits[p] = oz_bf16_bits(d);
+    hi = (hi - d) >> 7;
+  }
+  bits[0] = oz_bf16_bits(hi);
+}
+
+template <typename T>
+__device__ __forceinline__ void oz_split(T x, int E, unsigned short (&bits)[OZ_S]) {
+  oz_digits(oz_fixed(x, E), bits);
+}
+__device__ __forceinline__ unsigned oz_pack(unsigned short a, unsigned short b) { return (unsigned)a | ((unsigned)b << 16); }
 
 // Slices of the rows of X with row exponents E: planes out[p][r][c] (row
 // stride cols_pad, zero in the padding) with X[r][c] 2^-E[r] = sum_p
@@ -112,13 +164,13 @@ __global__ void __launch_bounds__(256) k_oz_slice(const T* __restrict__ X, int64
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
     const int e = E[r];
     const T* xr = X + r * ld;
-    __nv_bfloat16 s0[OZ_S], s1[OZ_S];
-    oz_split(c < cols ? (double)xr[c] : 0.0, e, s0);
-    oz_split(c + 1 < cols ? (double)xr[c + 1] : 0.0, e, s1);
-    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + r * cols_pad + c);
+    unsigned short s0[OZ_S], s1[OZ_S];
+    oz_split(c < cols ? xr[c] : T(0), e, s0);
+    oz_split(c + 1 < cols ? xr[c + 1] : T(0), e, s1);
+    unsigned* o = reinterpret_cast<unsigned*>(out + r * cols_pad + c);
 #pragma unroll
     for (int p = 0; p < OZ_S; ++p)
-      if (p < planes) o[p * (plane / 2)] = __halves2bfloat162(s0[p], s1[p]);
+      if (p < planes) o[p * (plane / 2)] = oz_pack(s0[p], s1[p]);
   }
 }
 
@@ -166,13 +218,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_oz_slice_t(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
                                                     const int* __restrict__ E, int64_t rows_pad,
                                                     __nv_bfloat16* __restrict__ out) {
-  __shared__ double tile[64][33];
+  __shared__ T tile[64][33];
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   const int64_t r0 = (int64_t)blockIdx.x * 64, c0 = (int64_t)blockIdx.y * 32;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int64_t r = r0 + ty + 8 * i, c = c0 + tx;
-    tile[ty + 8 * i][tx] = (r < rows && c < cols) ? (double)X[r * ld + c] : 0.0;
+    tile[ty + 8 * i][tx] = (r < rows && c < cols) ? X[r * ld + c] : T(0);
   }
   __syncthreads();
   const int64_t plane = cols * rows_pad;
@@ -182,12 +234,12 @@ __global__ void __launch_bounds__(256) k_oz_slice_t(const T* __restrict__ X, int
     const int64_t c = c0 + cc, r = r0 + 2 * tx;
     if (c < cols && r < rows_pad) {  // rows_pad is a multiple of 64: r + 1 < rows_pad too
       const int e = E[c];
-      __nv_bfloat16 s0[OZ_S], s1[OZ_S];
+      unsigned short s0[OZ_S], s1[OZ_S];
       oz_split(tile[2 * tx][cc], e, s0);
       oz_split(tile[2 * tx + 1][cc], e, s1);
-      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + c * rows_pad + r);
+      unsigned* o = reinterpret_cast<unsigned*>(out + c * rows_pad + r);
 #pragma unroll
-      for (int p = 0; p < OZ_S; ++p) o[p * (plane / 2)] = __halves2bfloat162(s0[p], s1[p]);
+      for (int p = 0; p < OZ_S; ++p) o[p * (plane / 2)] = oz_pack(s0[p], s1[p]);
     }
   }
 }
@@ -504,10 +556,11 @@ __global__ void __launch_bounds__(256) k_oz_panel_slice(const double* __restrict
     const int cc = idx >> 6, k = idx & 63;
     const int64_t c = ct + cc;
     if (c < w) {
-      __nv_bfloat16 sl[OZ_S];
+      unsigned short sl[OZ_S];
       oz_split(tile[k][cc], ex[cc], sl);
+      unsigned short* o = reinterpret_cast<unsigned short*>(out);
 #pragma unroll
-      for (int p = 0; p < OZ_S; ++p) out[(((int64_t)l * OZ_S + p) * np + c) * 64 + k] = sl[p];
+      for (int p = 0; p < OZ_S; ++p) o[(((int64_t)l * OZ_S + p) * np + c) * 64 + k] = sl[p];
     }
   }
 }

@@ -24,24 +24,36 @@ namespace {
 constexpr int kFwhtThreads = 256;
 constexpr int kFwhtMaxBits = 9;
 
+// Tile width: 128 bytes of one row (16 doubles or 32 floats); a power of two,
+// so every index below is a shift or a mask.
+template <typename TC>
+constexpr int fwht_cb() {
+  return (int)(128 / sizeof(TC));
+}
+template <typename TC>
+constexpr int fwht_lcb() {
+  return sizeof(TC) == 8 ? 4 : 5;
+}
+
 template <typename TIn, typename TC, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kFwhtThreads)
     k_fwht_pass(const TIn* src, int64_t ld_src, TC* dst, double* __restrict__ Y,
                 const int8_t* __restrict__ signs, const int32_t* __restrict__ rowmap, int64_t L, int64_t cols,
-                int b0, int t, int CB, int64_t ncb, double scale) {
+                int b0, int t, int64_t ncb, double scale) {
+  constexpr int CB = fwht_cb<TC>(), LCB = fwht_lcb<TC>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* tile = reinterpret_cast<TC*>(smem_raw);
   const int64_t g = blockIdx.x / ncb;
-  const int64_t cb = blockIdx.x % ncb;
+  const int64_t cb = blockIdx.x - g * ncb;
   const int64_t lo = g & ((int64_t(1) << b0) - 1);
   const int64_t hi = g >> b0;
   const int rows_t = 1 << t;
   const int64_t c0 = cb * CB;
-  const int tile_elems = rows_t * CB;
+  const int tile_elems = rows_t << LCB;
   for (int idx = threadIdx.x; idx < tile_elems; idx += blockDim.x) {
-    int mid = idx / CB, c = idx - mid * CB;
-    int64_t r = (hi << (b0 + t)) | ((int64_t)mid << b0) | lo;
-    int64_t col = c0 + c;
+    const int mid = idx >> LCB, c = idx & (CB - 1);
+    const int64_t r = (hi << (b0 + t)) | ((int64_t)mid << b0) | lo;
+    const int64_t col = c0 + c;
     TC v = TC(0);
     if (col < cols) {
       if (FIRST) {
@@ -53,25 +65,27 @@ __global__ void __launch_bounds__(kFwhtThreads)
     tile[idx] = v;
   }
   __syncthreads();
-  const int pairs = (rows_t >> 1) * CB;
-  for (int h = 1; h < rows_t; h <<= 1) {
+  const int pairs = (rows_t >> 1) << LCB;
+  for (int lv = 0; lv < t; ++lv) {
+    const int h = 1 << lv;
     for (int p = threadIdx.x; p < pairs; p += blockDim.x) {
-      int q = p / CB, c = p - q * CB;
-      int i = (q / h) * 2 * h + (q % h);
-      int j = i + h;
-      TC a = tile[i * CB + c], b = tile[j * CB + c];
-      tile[i * CB + c] = a + b;
-      tile[j * CB + c] = a - b;
+      const int q = p >> LCB, c = p & (CB - 1);
+      const int i = ((q >> lv) << (lv + 1)) | (q & (h - 1));  // rows i and i + h differ in bit lv
+      TC* a = tile + (i << LCB) + c;
+      TC* b = a + (h << LCB);
+      const TC x = *a, y = *b;
+      *a = x + y;
+      *b = x - y;
     }
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < tile_elems; idx += blockDim.x) {
-    int mid = idx / CB, c = idx - mid * CB;
-    int64_t r = (hi << (b0 + t)) | ((int64_t)mid << b0) | lo;
-    int64_t col = c0 + c;
+    const int mid = idx >> LCB, c = idx & (CB - 1);
+    const int64_t r = (hi << (b0 + t)) | ((int64_t)mid << b0) | lo;
+    const int64_t col = c0 + c;
     if (col >= cols) continue;
     if (LAST) {
-      int32_t k = rowmap[r];
+      const int32_t k = rowmap[r];
       if (k >= 0) Y[(int64_t)k * cols + col] = scale * (double)tile[idx];
     } else {
       dst[r * cols + col] = tile[idx];
@@ -83,7 +97,7 @@ template <typename TIn, typename TC>
 tk_status run_fwht_pass(bool first, bool last, const TIn* srcA, const TC* srcZ, int64_t ld_src, TC* Z, double* Y,
                         const int8_t* signs, const int32_t* rowmap, int64_t L, int64_t Lp, int64_t cols, int b0,
                         int t, double scale, cudaStream_t st) {
-  const int CB = (int)(64 * 16 / sizeof(TC) / 8);  // 16 doubles or 32 floats = 128 bytes per row
+  const int CB = fwht_cb<TC>();
   const int64_t ncb = cdiv(cols, CB);
   const int64_t groups = Lp >> t;
   const int64_t blocks = groups * ncb;
@@ -94,7 +108,7 @@ tk_status run_fwht_pass(bool first, bool last, const TIn* srcA, const TC* srcZ, 
     /* one constant cap for every caller (concurrent host threads must not race on it) */                 \
     TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));          \
     kern<<<(unsigned)blocks, kFwhtThreads, smem, st>>>(SRC, ld_src, Z, Y, signs, rowmap, L, cols, b0, t, \
-                                                       CB, ncb, scale);                                   \
+                                                       ncb, scale);                                       \
   } while (0)
   if (first && last) TK_FWHT_LAUNCH(true, true, srcA);
   else if (first) TK_FWHT_LAUNCH(true, false, srcA);
