@@ -82,14 +82,15 @@ typedef struct {
   double refine_tol;      /* [1e-11] MIXED stops when ||d|| <= refine_tol ||x|| */
   uint64_t seed;          /* [1] Philox key of every draw */
   tk_schedule schedule;   /* [BATCHED]: all lambda advance together; ONE_AT_A_TIME: one lambda per LSQR run */
-  int lsqr_tc;            /* [0] MIXED: the two products with A of each LSQR step on the tensor cores:
+  int lsqr_tc;            /* [2] MIXED: the two products with A of each LSQR step on the tensor cores:
                              1 = tcgen05 kind::tf32, 3-term split (float32 accuracy; needs 16-byte aligned
                              rows of A and keeps a float32 copy of A^T); 2 = BF16 products of the first 4
                              exact digits of the slices that emulate_fp64 makes (A rounded to 28 bits,
-                             exact level sums; needs emulate_fp64 and m >= n; used when m n > 2^24);
-                             0 = SIMT float32 */
+                             exact level sums; needs emulate_fp64 and m >= n; used when m n > 2^24 and
+                             more than 16 lambda are active, SIMT float32 otherwise; the grouped batch
+                             keeps its own products); 0 = SIMT float32 */
   int group;              /* [1] tk_solve_batched: when every problem is MIXED, m >= n, BATCHED, n <= 4096,
-                             N <= 64 and lsqr_tc = 0, the problems advance together in one grouped LSQR and
+                             N <= 64 and lsqr_tc != 1, the problems advance together in one grouped LSQR and
                              refinement (one launch per phase for all problems); 0 in any problem's options =
                              each problem solved on its own (host lanes) */
   int emulate_fp64;       /* [1] MIXED: the two float64 passes of the refinement (r = b - A x and

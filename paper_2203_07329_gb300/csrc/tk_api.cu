@@ -673,7 +673,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       TK_LAUNCH_CHECK();
       TK_CUDA(cudaMemcpyAsync(hn.data(), B.nrm, sizeof(double) * 3 * cnt, cudaMemcpyDeviceToHost, st));
       int oz_err = 0;
-      if (P.o.emulate_fp64 && (round > 0 || e.use_oz()))
+      if (P.o.emulate_fp64 && (round > 0 || P.lsqr_oz))
         TK_CUDA(cudaMemcpyAsync(&oz_err, B.oz_err, sizeof(int), cudaMemcpyDeviceToHost, st));
       TK_CUDA(cudaStreamSynchronize(st));
       if (oz_err) {
@@ -732,7 +732,7 @@ TK_API tk_status tk_opts_default(tk_opts* o) {
   o->refine_tol = 1e-11;
   o->seed = 1;
   o->schedule = TK_SCHED_BATCHED;
-  o->lsqr_tc = 0;
+  o->lsqr_tc = 2;
   o->group = 1;
   o->emulate_fp64 = 1;
   return TK_OK;
@@ -802,7 +802,7 @@ tk_status batch_layout(const tk_problem* ps, int P, int N, const tk_opts* o, int
   for (int i = 0; i < P; ++i) {
     TK_TRY(make_plan(&ps[i], N, opts_of(o, n_opts, i), pl[i]));
     const Plan& q = pl[i];
-    grouped = grouped && q.mixed && !q.under && q.o.schedule == TK_SCHED_BATCHED && !q.lsqr_tc && !q.lsqr_oz &&
+    grouped = grouped && q.mixed && !q.under && q.o.schedule == TK_SCHED_BATCHED && !q.lsqr_tc &&
               q.n <= kGroupMaxN && q.o.group != 0;
   }
   L.grouped = grouped;

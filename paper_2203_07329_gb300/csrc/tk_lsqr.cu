@@ -360,7 +360,7 @@ tk_status Lsqr<T>::prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, 
   int tok = prof_begin(TK_PHASE_AW, st);
   tk_status r;
   if constexpr (std::is_same<T, float>::value) {
-    if (use_oz()) {
+    if (use_oz(count)) {
       r = oz_lsqr_aw(oz_A, oz_EA, m, n, Win, ldw, count, oz_q, oz_e, C, m, beta, oz_err, st);
       prof_end(tok, st, 2.0 * count * m * n, 8.0 * m * n + 4.0 * count * (double)n + 8.0 * count * m);
       return r;
@@ -382,7 +382,7 @@ tk_status Lsqr<T>::prod_atu(const T* Uin, int count) {
   int tok = prof_begin(TK_PHASE_ATU, st);
   tk_status r;
   if constexpr (std::is_same<T, float>::value) {
-    if (use_oz()) {
+    if (use_oz(count)) {
       cur_splits = std::min(splits, oz_normal_splits(m, n, count));
       r = oz_lsqr_atu(oz_AT, oz_EAT, m, n, Uin, m, count, oz_q, oz_e, part_g, cur_splits, oz_err, st);
       prof_end(tok, st, 2.0 * count * m * n, 8.0 * m * n + 4.0 * count * (double)m + 8.0 * cur_splits * count * n);

@@ -171,7 +171,10 @@ struct Lsqr {
   int* oz_err = nullptr;
   void* oz_q = nullptr;  // slices of the lambda-major vector of a product
   int* oz_e = nullptr;
-  bool use_oz() const { return oz && oz_A && oz_AT && (int64_t)m * n > (int64_t(1) << 24); }
+  // the digit products read 8 bytes per element of A whatever the number of
+  // lambdas, the float32 SIMT products 4 bytes but with work proportional to
+  // it: the digits pay off for large A and more than 16 active lambdas
+  bool use_oz(int count) const { return oz && oz_A && oz_AT && (int64_t)m * n > (int64_t(1) << 24) && count > 16; }
 
   static size_t workspace(int64_t m, int64_t n, int N_cap, bool under, int64_t lr_s);
   void carve(Arena& a);
