@@ -320,7 +320,10 @@ enum {
   TK_PHASE_RES64 = 7,         /* MIXED: float64 residual b - A x */
   TK_PHASE_NE64 = 8,          /* MIXED: float64 A^T (b - A x) */
   TK_PHASE_TRINV = 9,         /* explicit R^-1 and R^-T from the float64 factors (MIXED: float32; FP64: n <= 512) */
-  TK_PHASE_COUNT = 10
+  TK_PHASE_AW_DIGITS = 10,    /* MIXED, lsqr_tc = 2: TK_PHASE_AW on the tensor cores from digits of A */
+  TK_PHASE_ATU_DIGITS = 11,   /* MIXED, lsqr_tc = 2: TK_PHASE_ATU on the tensor cores from digits of A */
+  TK_PHASE_SLICE = 12,        /* MIXED, emulate_fp64: the digit planes of A (rows and columns), once per solve */
+  TK_PHASE_COUNT = 13
 };
 typedef struct {
   double ms;      /* summed event time */

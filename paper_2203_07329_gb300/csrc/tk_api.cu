@@ -608,7 +608,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     std::vector<double> hn(3 * std::max(N, 1));
     std::vector<double> prev_dn(std::max(N, 1), INFINITY);
     if (P.o.emulate_fp64 && !act.empty()) {  // A is split once (by rows and by columns); x, r on every pass
-      const int tok = prof_begin(TK_PHASE_RES64, st);
+      const int tok = prof_begin(TK_PHASE_SLICE, st);
       TK_TRY(oz_prepare(p->A, P.dt, P.m, P.n, P.lda, B.Aoz, B.EA, st));
       TK_TRY(oz_prepare_cols(p->A, P.dt, P.m, P.n, P.lda, B.AozC, B.EC, B.colmax, st));
       TK_CUDA(cudaMemsetAsync(B.oz_err, 0, sizeof(int), st));

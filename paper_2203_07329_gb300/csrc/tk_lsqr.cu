@@ -357,10 +357,11 @@ tk_status Lsqr<T>::apply_prec(bool transposed, const T* in, T* out, int count, i
 template <typename T>
 tk_status Lsqr<T>::prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, int count) {
   // C (count x m) = Win (count x n) A^T  [+ beta_row * C]
-  int tok = prof_begin(TK_PHASE_AW, st);
+  const bool digits = use_oz(count);
+  int tok = prof_begin(digits ? TK_PHASE_AW_DIGITS : TK_PHASE_AW, st);
   tk_status r;
   if constexpr (std::is_same<T, float>::value) {
-    if (use_oz(count)) {
+    if (digits) {
       r = oz_lsqr_aw(oz_A, oz_EA, m, n, Win, ldw, count, oz_q, oz_e, C, m, beta, oz_err, st);
       prof_end(tok, st, 2.0 * count * m * n, 8.0 * m * n + 4.0 * count * (double)n + 8.0 * count * m);
       return r;
@@ -379,10 +380,11 @@ tk_status Lsqr<T>::prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, 
 template <typename T>
 tk_status Lsqr<T>::prod_atu(const T* Uin, int count) {
   // part_g (splits x count x n) = Uin (count x m) A
-  int tok = prof_begin(TK_PHASE_ATU, st);
+  const bool digits = use_oz(count);
+  int tok = prof_begin(digits ? TK_PHASE_ATU_DIGITS : TK_PHASE_ATU, st);
   tk_status r;
   if constexpr (std::is_same<T, float>::value) {
-    if (use_oz(count)) {
+    if (digits) {
       cur_splits = std::min(splits, oz_normal_splits(m, n, count));
       r = oz_lsqr_atu(oz_AT, oz_EAT, m, n, Uin, m, count, oz_q, oz_e, part_g, cur_splits, oz_err, st);
       prof_end(tok, st, 2.0 * count * m * n, 8.0 * m * n + 4.0 * count * (double)m + 8.0 * cur_splits * count * n);

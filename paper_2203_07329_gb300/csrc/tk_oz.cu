@@ -565,24 +565,43 @@ __global__ void __launch_bounds__(256) k_oz_panel_slice(const double* __restrict
   }
 }
 
-constexpr int CS_M = 128;
-constexpr int CS_N = 64;
-constexpr uint32_t CS_P_BYTES = CS_M * 64 * 2;  // 16 KiB per slice
-constexpr uint32_t CS_Q_BYTES = CS_N * 64 * 2;  // 8 KiB per slice
-constexpr uint32_t CS_TMEM_COLS = OZ_LV * CS_N;  // 512
-constexpr int CS_LDD = CS_N + 1;                 // staged result row (doubles)
+constexpr int CS_M = 128;                        // rows of a CTA's slab
+constexpr int CS_N = 32;                         // columns of one tile
+constexpr int CS_TILES = 8;                      // column tiles per CTA
+constexpr uint32_t CS_P_BYTES = CS_M * 64 * 2;   // 16 KiB per digit plane of the slab
+constexpr uint32_t CS_Q_BYTES = CS_N * 64 * 2;   // 4 KiB per digit plane of a tile
+constexpr uint32_t CS_TMEM_COLS = 2 * OZ_LV * CS_N;  // two buffers of 8 levels x 32 columns
 
 struct CsSmem {
   uint8_t p[OZ_S][CS_P_BYTES];
-  uint8_t q[OZ_S][CS_Q_BYTES];
-  uint64_t full;
-  uint64_t accum;
+  uint8_t q[2][OZ_S * CS_Q_BYTES];
+  uint64_t p_full;
+  uint64_t q_full[2];
+  uint64_t q_empty[2];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
   uint32_t tmem_base;
 };
-static_assert(sizeof(double) * CS_M * CS_LDD <= sizeof(((CsSmem*)nullptr)->p), "staging fits in the P slices");
 
-// Grid: (row tiles of 128, column tiles of 64, lambda) over the w x w
-// trailing block; tiles wholly below the diagonal exit at once.
+// A level sum of K = 64 products (|L| <= 8 * 64 * 64 * 64 = 2^21) as an
+// int: the float's integer read back through the 1.5 * 2^23 offset (exact for
+// |L| < 2^22).
+__device__ __forceinline__ int level_int(uint32_t bits) {
+  return __float_as_int(__fadd_rn(__uint_as_float(bits), 12582912.0f)) - 0x4B400000;
+}
+
+// 2^e as a double (e within the normal range).
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// Grid: (row slabs of 128, chunks of 8 column tiles of 32, lambda) over the
+// w x w trailing block.  Slab i0 needs the tiles j0 >= i0 (j >= i); a CTA
+// whose chunk holds none exits at once.  The slab's digit planes are loaded
+// once; the tiles stream through a 2-slot ring and two tensor-memory buffers,
+// so the flush and the update of one tile overlap the products of the next.
+// Flush: the 8 exact level sums are combined in int64 by Horner,
+// hi = ((L0 128 + L1) 128 + L2) 128 + L3 and lo likewise from L4..L7 (both
+// below 2^43), and the tile value is hi 2^-35 + lo 2^-63 (exact products of
+// exact integers), scaled by 2^(E_i + E_j).
 __global__ void __launch_bounds__(256, 1)
     k_oz_syrk(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
               const int* __restrict__ EC, int64_t np, int kb, double* __restrict__ R, int64_t ldr, int64_t rstride,
@@ -591,13 +610,21 @@ __global__ void __launch_bounds__(256, 1)
   CsSmem& S = *reinterpret_cast<CsSmem*>((reinterpret_cast<uintptr_t>(cs_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int l = blockIdx.z;
-  const int i0 = (int)blockIdx.x * CS_M, j0 = (int)blockIdx.y * CS_N;
-  if (j0 + CS_N - 1 < i0) return;
   const int64_t c0 = (int64_t)(kb + 1) * 64, w = np - c0;
+  const int i0 = (int)blockIdx.x * CS_M;
+  const int t_first = i0 / CS_N + (int)blockIdx.y * CS_TILES;
+  const int t_all = (int)(w / CS_N);
+  const int nt = t_all - t_first < CS_TILES ? t_all - t_first : CS_TILES;
+  if (nt <= 0) return;
 
   if (threadIdx.x == 0) {
-    mbar_init(&S.full, 1);
-    mbar_init(&S.accum, 1);
+    mbar_init(&S.p_full, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&S.q_full[s], 1);
+      mbar_init(&S.q_empty[s], 1);
+      mbar_init(&S.acc_full[s], 1);
+      mbar_init(&S.acc_empty[s], 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 2) {
@@ -612,91 +639,85 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t tmem = S.tmem_base;
 
   if (warp == 0 && lane == 0) {
-    mbar_expect_tx(&S.full, OZ_S * (CS_P_BYTES + CS_Q_BYTES));
-    for (int p = 0; p < OZ_S; ++p) {
-      tma_load_3d(&tmP, &S.full, S.p[p], 0, i0, l * OZ_S + p);
-      tma_load_3d(&tmQ, &S.full, S.q[p], 0, j0, l * OZ_S + p);
+    mbar_expect_tx(&S.p_full, OZ_S * CS_P_BYTES);
+    for (int p = 0; p < OZ_S; ++p) tma_load_3d(&tmP, &S.p_full, S.p[p], 0, i0, l * OZ_S + p);
+    for (int t = 0; t < nt; ++t) {
+      const int s = t & 1;
+      if (!mbar_wait(&S.q_empty[s], ((uint32_t)(t >> 1) & 1u) ^ 1u, err)) break;
+      mbar_expect_tx(&S.q_full[s], OZ_S * CS_Q_BYTES);
+      const int j0 = (t_first + t) * CS_N;
+      for (int p = 0; p < OZ_S; ++p) tma_load_3d(&tmQ, &S.q_full[s], S.q[s] + p * CS_Q_BYTES, 0, j0, l * OZ_S + p);
     }
   } else if (warp == 1 && lane == 0) {
-    if (mbar_wait(&S.full, 0u, err)) {
-      tc_fence_after();
-      for (int p = 0; p < OZ_S; ++p) {
-        const uint64_t pd = sdesc_sw128(smem_u32(S.p[p]));
-        // the planes Q_q (64 rows each) are contiguous and levels p + q consecutive column
-        // blocks: pairs (p, q0 .. q0+3) are one MMA of N = 64 x (planes), at most 256
-        for (int q0 = 0; q0 < OZ_S - p; q0 += 4) {
-          const int nq = OZ_S - p - q0 < 4 ? OZ_S - p - q0 : 4;
-          const uint64_t qd = sdesc_sw128(smem_u32(S.q[q0]));
-          const uint32_t idesc = idesc_bf16(CS_M, CS_N * nq);
-          const uint32_t d = tmem + (uint32_t)((p + q0) * CS_N);
+    if (mbar_wait(&S.p_full, 0u, err)) {
+      for (int t = 0; t < nt; ++t) {
+        const int s = t & 1;
+        if (!mbar_wait(&S.q_full[s], (uint32_t)(t >> 1) & 1u, err)) break;
+        if (t >= 2 && !mbar_wait(&S.acc_empty[s], (uint32_t)((t >> 1) - 1) & 1u, err)) break;
+        tc_fence_after();
+        const uint64_t qd = sdesc_sw128(smem_u32(S.q[s]));
+        const uint32_t dbase = tmem + (uint32_t)(s * OZ_LV * CS_N);
+        for (int p = 0; p < OZ_S; ++p) {
+          // planes Q_0 .. Q_(7-p) are contiguous: one MMA of N = 32 (8 - p) onto levels p .. 7
+          const uint64_t pd = sdesc_sw128(smem_u32(S.p[p]));
+          const uint32_t idesc = idesc_bf16(CS_M, CS_N * (OZ_S - p));
+          const uint32_t d = dbase + (uint32_t)(p * CS_N);
 #pragma unroll
           for (int k = 0; k < 4; ++k) tc_mma_bf16(d, pd + 2ull * k, qd + 2ull * k, idesc, (p == 0 && k == 0) ? 0u : 1u);
         }
+        tc_commit(&S.q_empty[s]);
+        tc_commit(&S.acc_full[s]);
       }
-      tc_commit(&S.accum);
+    }
+  } else if (warp >= 4) {
+    const int ew = warp - 4;
+    const int64_t i = i0 + ew * 32 + lane;
+    const int* El = EC + (int64_t)l * np;
+    const int ei = i < w ? El[i] : 0;
+    double* Trow = R + (int64_t)l * rstride + (c0 + i) * ldr + c0;
+    for (int t = 0; t < nt; ++t) {
+      const int s = t & 1;
+      if (!mbar_wait(&S.acc_full[s], (uint32_t)(t >> 1) & 1u, err)) break;
+      tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(s * OZ_LV * CS_N);
+      long long hi[CS_N], lo[CS_N];
+#pragma unroll
+      for (int j = 0; j < CS_N; ++j) hi[j] = lo[j] = 0;
+#pragma unroll 1
+      for (int lv = 0; lv < OZ_LV; ++lv) {
+        uint32_t v[32];
+        tmem_ld32_nowait(base + (uint32_t)(lv * CS_N), v);
+        tmem_wait_ld();
+        if (lv < 4) {
+#pragma unroll
+          for (int j = 0; j < CS_N; ++j) hi[j] = hi[j] * 128 + level_int(v[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < CS_N; ++j) lo[j] = lo[j] * 128 + level_int(v[j]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&S.acc_empty[s]);  // the levels are in registers: the buffer is free
+      const int64_t j0 = (int64_t)(t_first + t) * CS_N;
+      if (i < w) {
+        double val[CS_N];
+#pragma unroll
+        for (int j = 0; j < CS_N; ++j) {
+          const double vhi = (double)hi[j] * 0x1p-35, vlo = (double)lo[j] * 0x1p-63;  // exact
+          const int e = ei + (j0 + j < w ? El[j0 + j] : 0);
+          val[j] = (vhi + vlo) * (e >= -1022 && e <= 1023 ? pow2d(e) : ldexp(1.0, e));
+        }
+        double tv[CS_N];
+#pragma unroll
+        for (int j = 0; j < CS_N; ++j) tv[j] = (j0 + j < w && j0 + j >= i) ? Trow[j0 + j] : 0.0;
+#pragma unroll
+        for (int j = 0; j < CS_N; ++j)
+          if (j0 + j < w && j0 + j >= i) Trow[j0 + j] = tv[j] - val[j];
+      }
     }
   }
   __syncwarp();
-  double* D = reinterpret_cast<double*>(&S.p[0][0]);  // the slices are dead once the MMAs completed
-  if (warp >= 4) {
-    const int ew = warp - 4, row = ew * 32 + lane;
-    if (mbar_wait(&S.accum, 0u, err)) {
-      tc_fence_after();
-#pragma unroll 1
-      for (int h = 0; h < CS_N / 32; ++h) {
-        double acc64[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc64[j] = 0.0;
-#pragma unroll 1
-        for (int t = OZ_LV - 1; t >= 0; --t) {
-          uint32_t v[32];
-          tmem_ld32_nowait(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(t * CS_N + h * 32), v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 32; ++j) acc64[j] += level_to_double(v[j], t);
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) D[row * CS_LDD + h * 32 + j] = acc64[j];
-      }
-    }
-  }
   tc_fence_before();
-  __syncthreads();
-  if (!*(volatile int*)err) {
-    // T -= 2^(E_i + E_j) D on the upper triangle: warp w takes rows w, w + 8, ..., lanes the
-    // columns; all loads of a thread are issued before the first update (16 x 2 in flight)
-    constexpr int RPW = CS_M / 8;
-    const int* El = EC + (int64_t)l * np;
-    double* T = R + (int64_t)l * rstride + c0 * ldr + c0;
-    int ej[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t j = j0 + lane + 32 * h;
-      ej[h] = j < w ? El[j] : 0;
-    }
-    double tv[RPW][2];
-    int ei[RPW];
-#pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-      const int64_t i = i0 + warp + 8 * q;
-      ei[q] = i < w ? El[i] : 0;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t j = j0 + lane + 32 * h;
-        tv[q][h] = (i < w && j < w && j >= i) ? T[i * ldr + j] : 0.0;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-      const int64_t i = i0 + warp + 8 * q;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t j = j0 + lane + 32 * h;
-        if (i < w && j < w && j >= i)
-          T[i * ldr + j] = tv[q][h] - ldexp(D[(warp + 8 * q) * CS_LDD + lane + 32 * h], ei[q] + ej[h]);
-      }
-    }
-  }
   __syncthreads();
   if (warp == 2) {
     tc_fence_after();
@@ -892,7 +913,7 @@ tk_status oz_chol_step(const OzCholPlan& plan, int kb, cudaStream_t st) {
   k_oz_panel_slice<<<dim3((unsigned)cdiv(w, 32), (unsigned)plan.N), 256, 0, st>>>(plan.R, plan.ldr, plan.rstride,
                                                                                    plan.np, kb, sl, plan.EC);
   TK_LAUNCH_CHECK();
-  const dim3 grid((unsigned)cdiv(w, CS_M), (unsigned)(w / CS_N), (unsigned)plan.N);
+  const dim3 grid((unsigned)cdiv(w, CS_M), (unsigned)cdiv(w / CS_N, CS_TILES), (unsigned)plan.N);
   k_oz_syrk<<<grid, 256, sizeof(CsSmem) + 1024, st>>>(plan.mP, plan.mQ, plan.EC, plan.np, kb, plan.R, plan.ldr,
                                                      plan.rstride, plan.err);
   TK_LAUNCH_CHECK();
