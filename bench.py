@@ -40,12 +40,29 @@ PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, 65536 x 2048 float64 case
-# (profiles/k_gemm_f64_refinement_65536x2048.md): (elements of A, bytes)
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the kernel behind a phase, from a
+# capture of the 65536 x 2048 float64 case (profiles/): (elements of A of that case, bytes).  A
+# launch streams every element of A once, so the figure scales with m n; kernels changed since
+# their capture are left out (traffic null).
 MEASURED_TRAFFIC = {
-    "refine_residual64": (65536 * 2048, 1.094704e9 + 16.558592e6),
-    "refine_normal64": (65536 * 2048, 1.092536e9 + 34.980864e6),
+    # k_oz_tc<4, 2>: profiles/k_oz_tc_digits_aw_65536x2048.md (1084611840 read + 10654208 written)
+    "A_times_W_digits": (65536 * 2048, 1084611840 + 10654208),
 }
+
+# How each phase is bounded: "hbm" phases are compared as algorithmic bytes / time with the
+# measured copy bandwidth; "fp32" / "fp64" as algorithmic flops / time with the peaks above.
+# The digit products read 8 bytes per element of A (4 BF16 digit planes); the emulated float64
+# passes 16 (8 planes) and flush at most 8 float64 adds per output and 256 values of K.
+PHASE_BOUND = {
+    "A_times_W_digits": "hbm", "At_times_U_digits": "hbm", "refine_residual64": "hbm",
+    "refine_normal64": "hbm", "slice_A": "hbm", "sketch": "hbm", "precond_apply": "hbm",
+    "A_times_W": "fp32", "At_times_U": "fp32", "precond_inverse": "fp32",
+    "cholesky": "fp64", "svd": "fp64",
+    # emulated float64 products: compared as the BF16 tensor work they issue (36 digit pairs per
+    # float64 multiply-add) with the measured BF16 peak
+    "gram": "tensor", "cholesky_update": "tensor",
+}
+EMULATED_PAIRS = 36
 
 
 def load_peaks():
@@ -432,29 +449,41 @@ def main():
     peaks, peak_src = load_peaks()
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     name, st = dom
-    fp64_phases = {"gram", "cholesky", "svd", "refine_residual64", "refine_normal64", "sketch"}
+    bound = PHASE_BOUND.get(name, "fp32")
     per_launch_ms = st["ms"] / max(st["launches"], 1)
-    achieved = st["flops"] / (st["ms"] / 1e3) / 1e12 if st["ms"] > 0 else 0.0
-    peak = PEAK_FP64_TFLOPS if name in fp64_phases else PEAK_FP32_TFLOPS
+    secs = st["ms"] / 1e3
+    if bound == "hbm":
+        achieved = st["bytes"] / secs / 1e9 if secs > 0 else 0.0
+        peak, unit = float(peaks["hbm_gbs"]), "GB/s"
+        psrc = f"{peak_src}: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"
+    elif bound == "tensor":
+        achieved = EMULATED_PAIRS * st["flops"] / secs / 1e12 if secs > 0 else 0.0
+        peak, unit = float(peaks["bf16_tflops_sustained"]), "TFLOP/s"
+        psrc = f"{peak_src}: MEASURED_PEAKS.json bf16_tflops_sustained"
+    else:
+        achieved = st["flops"] / secs / 1e12 if secs > 0 else 0.0
+        peak, unit = (PEAK_FP64_TFLOPS if bound == "fp64" else PEAK_FP32_TFLOPS), "TFLOP/s"
+        psrc = "derived from unit counts and max clock (FP64 2 DFMA/clk/SM, FP32 128 FFMA/clk/SM)"
     # DRAM bytes (read + write) of one launch from an ncu capture of the same kernel on a smaller
     # case (profiles/), scaled by the elements of A it streams; None for kernels not captured
     traffic = None
     if name in MEASURED_TRAFFIC:
         case_elems, case_bytes = MEASURED_TRAFFIC[name]
         traffic = case_bytes * (m * n) / case_elems
-    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": traffic,
-                "per_launch_ms": per_launch_ms, "launches": st["launches"],
-                "peak_source": "derived from unit counts and max clock (FP64 2 DFMA/clk/SM, FP32 128 FFMA/clk/SM)"}
+    roofline = {"bound": bound if bound in ("hbm", "tensor") else "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak if peak else None, "traffic": traffic,
+                "algorithmic_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
+                "per_launch_ms": per_launch_ms, "launches": st["launches"], "peak_source": psrc}
     a_stream_gbs = None
-    lsqr_bytes = prof["A_times_W"]["bytes"] + prof["At_times_U"]["bytes"] + prof["refine_residual64"]["bytes"] + \
-        prof["refine_normal64"]["bytes"]
-    lsqr_ms = prof["A_times_W"]["ms"] + prof["At_times_U"]["ms"] + prof["refine_residual64"]["ms"] + \
-        prof["refine_normal64"]["ms"]
+    streams = ("A_times_W", "At_times_U", "A_times_W_digits", "At_times_U_digits", "refine_residual64",
+               "refine_normal64")
+    lsqr_bytes = sum(prof[k]["bytes"] for k in streams if k in prof)
+    lsqr_ms = sum(prof[k]["ms"] for k in streams if k in prof)
     if lsqr_ms > 0:
         a_stream_gbs = lsqr_bytes / (lsqr_ms / 1e3) / 1e9
     phases = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
-                  "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0}
+                  "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0,
+                  "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0}
               for k, v in prof.items() if v["launches"]}
 
     # ---- CPU oracle sample (rank 0 only, N = 1 only)

@@ -323,7 +323,9 @@ enum {
   TK_PHASE_AW_DIGITS = 10,    /* MIXED, lsqr_tc = 2: TK_PHASE_AW on the tensor cores from digits of A */
   TK_PHASE_ATU_DIGITS = 11,   /* MIXED, lsqr_tc = 2: TK_PHASE_ATU on the tensor cores from digits of A */
   TK_PHASE_SLICE = 12,        /* MIXED, emulate_fp64: the digit planes of A (rows and columns), once per solve */
-  TK_PHASE_COUNT = 13
+  TK_PHASE_CHOL_UPDATE = 13,  /* MIXED, emulate_fp64: the Cholesky trailing updates on the tensor cores
+                                 (TK_PHASE_CHOLESKY then holds the diagonal blocks and panel solves) */
+  TK_PHASE_COUNT = 14
 };
 typedef struct {
   double ms;      /* summed event time */

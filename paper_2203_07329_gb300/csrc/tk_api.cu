@@ -481,13 +481,15 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     }
     prof_end(tok, st, (double)P.s * P.c * (P.c + 1), 8.0 * (P.s * P.c + P.c * (P.c + 1) / 2));
     Arena none;
-    tok = prof_begin(TK_PHASE_CHOLESKY, st);
     OzCholPlan ozp;  // the trailing updates on the tensor cores (the Gram scratch is free again)
-    if (emulated_gram(P))
+    if (emulated_gram(P)) {  // chol_shifted times its float64 and tensor-core parts itself
       TK_TRY(oz_chol_begin(B.R, P.np, P.np * P.np, N, P.np, B.scratch, B.scratch_bytes, B.oz_err, &ozp, st));
-    TK_TRY(chol_shifted(B.C, P.c, B.lam, N, B.R, P.np, P.np * P.np, B.info, none, st,
-                        emulated_gram(P) ? &ozp : nullptr));
-    prof_end(tok, st, (double)N * P.c * P.c * P.c / 3.0, 8.0 * N * P.c * P.c);
+      TK_TRY(chol_shifted(B.C, P.c, B.lam, N, B.R, P.np, P.np * P.np, B.info, none, st, &ozp));
+    } else {
+      tok = prof_begin(TK_PHASE_CHOLESKY, st);
+      TK_TRY(chol_shifted(B.C, P.c, B.lam, N, B.R, P.np, P.np * P.np, B.info, none, st));
+      prof_end(tok, st, (double)N * P.c * P.c * P.c / 3.0, 8.0 * N * P.c * P.c);
+    }
     std::vector<int> hinfo(N);
     TK_CUDA(cudaMemcpyAsync(hinfo.data(), B.info, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
     int gerr = 0;

@@ -917,14 +917,25 @@ tk_status chol_shifted(const double* Cm, int64_t n, const double* lambdas_dev, i
   k_chol_init<<<gi, 256, 0, st>>>(Cm, n, np, lambdas_dev, R, ldr, rstride, info_dev);
   TK_LAUNCH_CHECK();
   for (int kb = 0; kb < nt; ++kb) {
+    const int r = nt - kb - 1;
+    // with the update on the tensor cores the caller leaves the timing to this loop: the diagonal
+    // block and the panel solve are CHOLESKY, the update CHOL_UPDATE
+    const int tok = oz ? prof_begin(TK_PHASE_CHOLESKY, st) : -1;
     k_chol_diag<<<N, 256, 0, st>>>(R, ldr, rstride, kb, info_dev);
     TK_LAUNCH_CHECK();
-    const int r = nt - kb - 1;
+    if (r > 0) {
+      k_chol_trsm<<<dim3((unsigned)r, (unsigned)N), CB, 0, st>>>(R, ldr, rstride, kb);
+      TK_LAUNCH_CHECK();
+    }
+    prof_end(tok, st, (double)N * ((double)CB * CB * CB / 3.0 + (double)r * CB * CB * CB),
+             8.0 * N * ((double)CB * CB + 2.0 * r * CB * CB));
     if (r == 0) break;
-    k_chol_trsm<<<dim3((unsigned)r, (unsigned)N), CB, 0, st>>>(R, ldr, rstride, kb);
-    TK_LAUNCH_CHECK();
     if (oz) {
+      const int64_t w = np - (int64_t)(kb + 1) * CB;
+      const int tok = prof_begin(TK_PHASE_CHOL_UPDATE, st);
       TK_TRY(oz_chol_step(*oz, kb, st));
+      // algorithmic: the float64 update of the w x w trailing triangle (K = 64) read and written
+      prof_end(tok, st, (double)N * w * (w + 1) * CB, 16.0 * N * w * (w + 1) / 2);
     } else {
       k_chol_update<<<dim3((unsigned)(r * (r + 1) / 2), (unsigned)N), 256, 0, st>>>(R, ldr, rstride, kb, nt);
       TK_LAUNCH_CHECK();

@@ -44,7 +44,7 @@ class tk_info(C.Structure):
                 ("rnorm", C.c_double), ("arnorm", C.c_double), ("ne_norm", C.c_double), ("status", C.c_int)]
 
 
-TK_PHASE_COUNT = 13
+TK_PHASE_COUNT = 14
 
 
 class tk_phase_stats(C.Structure):
