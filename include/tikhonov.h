@@ -93,11 +93,13 @@ typedef struct {
                              N <= 64 and lsqr_tc != 1, the problems advance together in one grouped LSQR and
                              refinement (one launch per phase for all problems); 0 in any problem's options =
                              each problem solved on its own (host lanes) */
-  int emulate_fp64;       /* [1] MIXED: the two float64 passes of the refinement (r = b - A x and
-                             A^T r) on the BF16 tensor cores, split into exact integer slices (see
-                             tk_residual) instead of the float64 pipe; the same float64 accuracy.
-                             Costs 32 bytes of workspace per element of A (two sets of slices);
-                             0 = float64 FMA.  The grouped batch keeps its float64 passes. */
+  int emulate_fp64;       /* [1] MIXED: the float64 products -- the Gram matrix, the Cholesky trailing
+                             updates, and the refinement's r = b - A x and A^T r -- on the BF16 tensor
+                             cores from exact integer digits (see tk_gram_emulated,
+                             tk_cholesky_shifted_emulated, tk_residual) instead of the float64 pipe;
+                             the same float64 accuracy.  Costs 32 bytes of workspace per element of A
+                             (two sets of digit planes); 0 = float64 FMA.  The grouped batch uses the
+                             emulated Gram and Cholesky and keeps its float64 refinement passes. */
 } tk_opts;
 
 /* Per-lambda report. */

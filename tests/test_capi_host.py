@@ -43,6 +43,20 @@ def test_status_strings_and_defaults(tk):
         assert len(L.tk_status_str(s)) > 0
     o = tk.opts_default()
     assert o.tol == 1e-14 and o.maxiter == 500 and o.sketch == tk.TK_SKETCH_SRHT and o.seed == 1
+    # the mixed form's float64 products and large LSQR products from exact digits by default
+    assert o.emulate_fp64 == 1 and o.lsqr_tc == 2
+
+
+def test_workspace_counts_the_digit_planes(tk):
+    # 32 bytes per element of A for the two sets of digit planes (rows and columns) of the mixed form
+    m, n = 8192, 256
+    p = _prob(tk, m, n)
+    lam = np.array([1e-3, 1.0])
+    o_em = tk.opts_default(precision=tk.TK_PREC_MIXED, s=1024)
+    o_no = tk.opts_default(precision=tk.TK_PREC_MIXED, s=1024, emulate_fp64=0, lsqr_tc=0)
+    w_em = tk.workspace_size(p, len(lam), o_em)
+    w_no = tk.workspace_size(p, len(lam), o_no)
+    assert w_em - w_no >= 32 * m * n
 
 
 def _prob(tk, m, n, lda=None):
