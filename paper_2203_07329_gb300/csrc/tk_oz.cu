@@ -1,28 +1,32 @@
 // Float64-accurate products on the BF16 tensor cores (splitting into exact
 // integer slices, in the manner of Ozaki's error-free matrix multiplication).
 //
-// GB300 issues about two float64 FMA per clock per SM, so the float64 passes
+// GB300 issues about two float64 FMA per clock per SM, so the float64 products
 // of the mixed form (the Gram matrix, the Cholesky trailing updates, and the
 // refinement's r = b - X A^T and A^T r) are bound by that pipe.  Here every
 // row of an operand is scaled by a power of two 2^E (E one above the exponent
-// of its largest entry, so that |x 2^-E| < 1/2), rounded to 55 bits and
-// written with S = 8 balanced base-128 digits,
+// of its largest entry, so that 2^(E-2) <= max |x| < 2^(E-1)), rounded to
+// nearest at 2^(E-57) (within 2^-55 of the row maximum) and written with
+// S = 8 balanced base-128 digits,
 //   x 2^-E = sum_p d_p 2^(-7(p+1)),  d_p in [-64, 64],
 // taken from the least significant end with carries; each digit is exact in
 // BF16.  A product of two digits is an integer of magnitude <= 2^12; the pairs
 // (p, q) with p + q = t share one FP32 accumulator ("level" t), and a level
 // sum of at most 8 pairs over 256 values of K stays below 2^24, so the tensor
 // core's FP32 accumulation is exact.  Every 256 values of K the level sums
-// are scaled by 2^(-7(t+2)) and added into float64 accumulators.  Pairs with
-// p + q > 7 are dropped: their contribution is below 2^-55 of max|a| max|x|
-// per product, and the 55-bit rounding of a and x is at 2^-56 of their row
-// maxima: the accuracy of a float64 GEMM.  Cut after 4 digits, the same
-// slices are a round-to-nearest (unbiased) 28-bit representation.
+// are scaled by 2^(-7(t+2)) and added into float64 accumulators.  The 28
+// pairs with p + q > 7 are dropped: at most 7.1 * 2^-58 of 2^(Ea+Ex), i.e.
+// 2^-51 of max|a| max|x| per product when every digit is +-64 (typical digits
+// give far less).  The result carries errors of a few float64 units relative
+// to the row maxima: the normwise accuracy of a float64 GEMM (the tests check
+// it element by element against extended-precision products).  Cut after 4
+// digits, the same slices are a round-to-nearest 28-bit representation.
 //
-// The products run on tcgen05 (kind::f16, M = 128, N = 32, K = 16), operands
-// brought in by TMA in the 128-byte swizzle layout, the 8 level accumulators
-// in tensor memory, double-buffered so that four epilogue warps flush one
-// 256-value chunk of K into float64 while the MMAs of the next chunk run.
+// The products run on tcgen05 (kind::f16, M = 128, K = 16; per digit p of the
+// big operand one MMA of N = 32 (S - p) over the stacked digit planes of the
+// small one), operands brought in by TMA in the 128-byte swizzle layout, the
+// level accumulators in tensor memory, double-buffered so that four epilogue
+// warps flush one 256-value chunk of K while the MMAs of the next chunk run.
 #include <algorithm>
 #include <type_traits>
 #include <cuda_bf16.h>
@@ -151,7 +155,7 @@ __device__ __forceinline__ unsigned oz_pack(unsigned short a, unsigned short b) 
 
 // Slices of the rows of X with row exponents E: planes out[p][r][c] (row
 // stride cols_pad, zero in the padding) with X[r][c] 2^-E[r] = sum_p
-// out[p][r][c] 2^(-7(p+1)) to within 2^-56.
+// out[p][r][c] 2^(-7(p+1)) to within 2^-57 (rounded to nearest).
 // Grid: rows over blockIdx.x (grid-stride) and column chunks of 2 x 256 over
 // blockIdx.y; each thread splits two adjacent values (one 4-byte store per plane).
 template <typename T>
