@@ -579,6 +579,7 @@ constexpr uint32_t CS_TMEM_COLS = 2 * OZ_LV * CS_N;  // two buffers of 8 levels 
 struct CsSmem {
   uint8_t p[OZ_S][CS_P_BYTES];
   uint8_t q[2][OZ_S * CS_Q_BYTES];
+  int ecol[CS_TILES * CS_N];  // the column exponents of the CTA's tiles
   uint64_t p_full;
   uint64_t q_full[2];
   uint64_t q_empty[2];
@@ -679,8 +680,19 @@ __global__ void __launch_bounds__(256, 1)
     const int* El = EC + (int64_t)l * np;
     const int ei = i < w ? El[i] : 0;
     double* Trow = R + (int64_t)l * rstride + (c0 + i) * ldr + c0;
+    // the exponents of the CTA's columns, once, in shared memory (the four epilogue warps only)
+    for (int c = (int)threadIdx.x - 128; c < CS_TILES * CS_N; c += 128) {
+      const int64_t col = (int64_t)t_first * CS_N + c;
+      S.ecol[c] = col < w ? El[col] : 0;
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
     for (int t = 0; t < nt; ++t) {
       const int s = t & 1;
+      const int64_t j0 = (int64_t)(t_first + t) * CS_N;
+      // T of this tile first: its loads do not wait for the products
+      double tv[CS_N];
+#pragma unroll
+      for (int j = 0; j < CS_N; ++j) tv[j] = (i < w && j0 + j < w && j0 + j >= i) ? Trow[j0 + j] : 0.0;
       if (!mbar_wait(&S.acc_full[s], (uint32_t)(t >> 1) & 1u, err)) break;
       tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(s * OZ_LV * CS_N);
@@ -702,21 +714,15 @@ __global__ void __launch_bounds__(256, 1)
       }
       tc_fence_before();
       mbar_arrive(&S.acc_empty[s]);  // the levels are in registers: the buffer is free
-      const int64_t j0 = (int64_t)(t_first + t) * CS_N;
       if (i < w) {
-        double val[CS_N];
 #pragma unroll
         for (int j = 0; j < CS_N; ++j) {
-          const double vhi = (double)hi[j] * 0x1p-35, vlo = (double)lo[j] * 0x1p-63;  // exact
-          const int e = ei + (j0 + j < w ? El[j0 + j] : 0);
-          val[j] = (vhi + vlo) * (e >= -1022 && e <= 1023 ? pow2d(e) : ldexp(1.0, e));
+          if (j0 + j < w && j0 + j >= i) {
+            const double vhi = (double)hi[j] * 0x1p-35, vlo = (double)lo[j] * 0x1p-63;  // exact
+            const int e = ei + S.ecol[t * CS_N + j];
+            Trow[j0 + j] = tv[j] - (vhi + vlo) * (e >= -1022 && e <= 1023 ? pow2d(e) : ldexp(1.0, e));
+          }
         }
-        double tv[CS_N];
-#pragma unroll
-        for (int j = 0; j < CS_N; ++j) tv[j] = (j0 + j < w && j0 + j >= i) ? Trow[j0 + j] : 0.0;
-#pragma unroll
-        for (int j = 0; j < CS_N; ++j)
-          if (j0 + j < w && j0 + j >= i) Trow[j0 + j] = tv[j] - val[j];
       }
     }
   }
