@@ -111,3 +111,32 @@ def test_workspace_grows_with_lambda_count(tk):
         assert tk.lib().tk_workspace_size(C.byref(_prob(tk, 4096, 256)), N, C.byref(o), C.byref(out)) == 0
         sizes.append(out.value)
     assert sizes[0] < sizes[1] < sizes[2]
+
+
+def test_emulated_entry_points_validate_on_host(tk):
+    # the float64-accurate tensor-core entry points reject bad arguments and short workspaces
+    # before any launch (fake device addresses are never touched)
+    L = tk.lib()
+    fake = C.c_void_p(0x1000)
+    assert L.tk_gram_emulated(None, 10, 4, fake, fake, 1 << 20, None) == tk.TK_EINVAL
+    assert L.tk_gram_emulated(fake, 0, 4, fake, fake, 1 << 20, None) == tk.TK_EINVAL
+    need = L.tk_gram_emulated_workspace(300, 70)
+    assert need >= 8 * 2 * 70 * 320  # 8 BF16 digit planes of Y^T (rows padded to 64)
+    assert L.tk_gram_emulated(fake, 300, 70, fake, fake, need - 1, None) == tk.TK_ENOMEM
+    lam = np.array([1e-3, 1.0])
+    brk = (C.c_int * 2)()
+    need_c = L.tk_cholesky_emulated_workspace(200, 2)
+    assert need_c > L.tk_cholesky_workspace(200, 2)
+    st = L.tk_cholesky_shifted_emulated(fake, 200, lam.ctypes.data_as(C.c_void_p), 2, fake, brk, fake, need_c - 1,
+                                        None)
+    assert st == tk.TK_ENOMEM
+    bad = np.array([1.0, float("nan")])
+    st = L.tk_cholesky_shifted_emulated(fake, 200, bad.ctypes.data_as(C.c_void_p), 2, fake, brk, fake, need_c,
+                                        None)
+    assert st == tk.TK_EINVAL
+    p = _prob(tk, 1000, 100)
+    need_r = L.tk_residual_workspace(1000, 100, 4)
+    # two sets of 8 BF16 digit planes of A: rows (1000 x 128, n padded to 64), columns (100 x 1024)
+    assert need_r >= 8 * 2 * (1000 * 128 + 100 * 1024)
+    assert L.tk_residual(C.byref(p), fake, 4, 99, 1, fake, None, fake, need_r, None) == tk.TK_EINVAL  # ldx < n
+    assert L.tk_residual(C.byref(p), fake, 4, 100, 1, fake, None, fake, need_r - 1, None) == tk.TK_ENOMEM
