@@ -41,6 +41,27 @@ constexpr int OZ_S = 8;          // slices
 constexpr int OZ_LV = OZ_S;      // levels t = p + q in 0..7 kept
 constexpr int OZ_KPAD = 64;      // slice rows are padded to a multiple of 64 values of K (one TMA box)
 
+// Exponent marking a row or column with an inf or NaN: its digits are zero
+// and every output that uses it is NaN, so non-finite input is reported (the
+// LSQR stop tests and the refinement see it) instead of being dropped.
+constexpr int OZ_EBAD = 1 << 24;
+
+// max(m, |x|) that turns inf and NaN into +inf (fmax would ignore a NaN).
+__device__ __forceinline__ double oz_absmax(double m, double x) {
+  const double a = fabs(x);
+  return a <= m ? m : (a == a ? a : __longlong_as_double(0x7ff0000000000000ll));
+}
+// The exponent of a maximum: one above frexp's (0 for 0, OZ_EBAD if not finite).
+__device__ __forceinline__ int oz_exponent(double mx) {
+  if (!(mx <= 1.7976931348623157e308)) return OZ_EBAD;
+  int e = 0;
+  if (mx > 0.0) {
+    frexp(mx, &e);  // mx = f 2^e, 0.5 <= f < 1
+    ++e;            // so mx < 2^(e-1)
+  }
+  return e;
+}
+
 // Exponent E with max_j |row_j| < 2^(E-1) (0 for a zero row); one warp per row.
 template <typename T>
 __global__ void k_oz_rowexp(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld, int* __restrict__ E) {
@@ -48,17 +69,10 @@ __global__ void k_oz_rowexp(const T* __restrict__ X, int64_t rows, int64_t cols,
   if (r >= rows) return;
   const int lane = threadIdx.x & 31;
   double mx = 0.0;
-  for (int64_t j = lane; j < cols; j += 32) mx = fmax(mx, fabs((double)X[r * ld + j]));
+  for (int64_t j = lane; j < cols; j += 32) mx = oz_absmax(mx, (double)X[r * ld + j]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) {
-    int e = 0;
-    if (mx > 0.0) {
-      frexp(mx, &e);  // mx = f 2^e, 0.5 <= f < 1
-      ++e;            // so mx < 2^(e-1)
-    }
-    E[r] = e;
-  }
+  if (lane == 0) E[r] = oz_exponent(mx);
 }
 
 // Exponent E with max_r |X[r][c]| < 2^(E-1) per column (0 for a zero column):
@@ -72,19 +86,13 @@ __global__ void k_oz_colmax(const T* __restrict__ X, int64_t rows, int64_t cols,
   const int64_t r0 = (int64_t)blockIdx.y * rows_per, r1 = r0 + rows_per < rows ? r0 + rows_per : rows;
   double v = 0.0;
 #pragma unroll 8
-  for (int64_t r = r0; r < r1; ++r) v = fmax(v, fabs((double)X[r * ld + c]));
-  atomicMax(&mx[c], (unsigned long long)__double_as_longlong(v));
+  for (int64_t r = r0; r < r1; ++r) v = oz_absmax(v, (double)X[r * ld + c]);
+  atomicMax(&mx[c], (unsigned long long)__double_as_longlong(v));  // +inf orders above every finite value
 }
 __global__ void k_oz_colexp(const unsigned long long* __restrict__ mx, int64_t cols, int* __restrict__ E) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= cols) return;
-  const double v = __longlong_as_double((long long)mx[c]);
-  int e = 0;
-  if (v > 0.0) {
-    frexp(v, &e);
-    ++e;
-  }
-  E[c] = e;
+  E[c] = oz_exponent(__longlong_as_double((long long)mx[c]));
 }
 
 // round(x 2^(56-E)) (|x 2^-E| < 1/2, so |result| <= 2^55) from the bit
@@ -194,18 +202,14 @@ __global__ void __launch_bounds__(256) k_oz_rowexp_long(const T* __restrict__ X,
   const int64_t c0 = (int64_t)blockIdx.x * per_block;
   const int64_t c1 = c0 + per_block < cols ? c0 + per_block : cols;
   double mx = 0.0;
-  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) mx = fmax(mx, fabs((double)X[r * ld + c]));
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) mx = oz_absmax(mx, (double)X[r * ld + c]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, sh[w]);
-    if (mx > 0.0) {
-      int e = 0;
-      frexp(mx, &e);
-      atomicMax(&E[r], e + 1);
-    }
+    if (mx > 0.0) atomicMax(&E[r], oz_exponent(mx));  // OZ_EBAD wins
   }
 }
 __global__ void k_oz_fix_zero_rows(int* __restrict__ E, int64_t rows) {
@@ -446,7 +450,9 @@ __global__ void __launch_bounds__(256, 1)
       for (int j = 0; j < OT_N; ++j) {
         const int l = l0 + j;
         if (l < M) {
-          const double v = ldexp((double)acc[j], er + EQ[l]);
+          const int eq = EQ[l];
+          const double v = (er >= OZ_EBAD || eq >= OZ_EBAD) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                            : ldexp((double)acc[j], er + eq);
           if (MODE == 0) {
             static_cast<double*>(out)[(int64_t)l * ldo + r] = br - v;
           } else if (MODE == 1) {
@@ -545,12 +551,8 @@ __global__ void __launch_bounds__(256) k_oz_panel_slice(const double* __restrict
   __syncthreads();
   if (threadIdx.x < 32) {
     double mx = 0.0;
-    for (int k = 0; k < 64; ++k) mx = fmax(mx, fabs(tile[k][threadIdx.x]));
-    int e = 0;
-    if (mx > 0.0) {
-      frexp(mx, &e);
-      ++e;
-    }
+    for (int k = 0; k < 64; ++k) mx = oz_absmax(mx, tile[k][threadIdx.x]);
+    const int e = oz_exponent(mx);
     ex[threadIdx.x] = e;
     const int64_t c = ct + threadIdx.x;
     if (c < w) EC[(int64_t)l * np + c] = e;

@@ -583,6 +583,31 @@ def test_emulated_normal_product_has_float64_accuracy(tk, dtype):
     assert float(err_e[-20:].max()) <= 4 * float(err_n.max()) + 1e-16
 
 
+def test_emulated_products_propagate_non_finite(tk):
+    # an inf or NaN in the input reaches every output that uses it (the digits cannot hold it, so
+    # the rows and columns that contain one are marked): R = b - X A^T, G = R A and the Gram matrix
+    gen = torch.Generator().manual_seed(23)
+    A = torch.randn(700, 150, generator=gen, dtype=torch.float64)
+    A[5, 3] = float("inf")
+    A[7, 2] = float("nan")
+    b = torch.randn(700, generator=gen, dtype=torch.float64)
+    X = torch.randn(3, 150, generator=gen, dtype=torch.float64)
+    R, G = tk.tk_residual(A.cuda(), b.cuda(), X.cuda(), True, with_g=True)
+    R, G = R.cpu().numpy(), G.cpu().numpy()
+    bad = np.zeros(700, dtype=bool)
+    bad[[5, 7]] = True
+    assert not np.isfinite(R[:, bad]).any()
+    assert np.isfinite(R[:, ~bad]).all()
+    assert not np.isfinite(G).any()  # every residual row holds a non-finite entry
+    Y = torch.randn(300, 40, generator=gen, dtype=torch.float64)
+    Y[11, 4] = float("nan")
+    Cm = tk.tk_gram(Y.cuda(), True, emulate=True).cpu().numpy()
+    iu = np.triu_indices(40)
+    touched = (iu[0] == 4) | (iu[1] == 4)
+    assert not np.isfinite(Cm[iu][touched]).any()
+    assert np.isfinite(Cm[iu][~touched]).all()
+
+
 @pytest.mark.parametrize("emulate", [1, 0])
 def test_mixed_with_emulated_residual_matches_reference(tk, emulate):
     # the mixed form with both float64 passes of its refinement on the tensor cores
