@@ -5,6 +5,7 @@ library routine on a case that reduces to it, brute force on a tiny input, an
 exact rational computation, or an inequality the paper proves.
 """
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -26,6 +27,26 @@ def small_problem(m, n, sig_lo=1e-3, seed=7, noise=1e-3):
 
 
 # ------------------------------------------------------------ RNG / draws --
+def _kat_rows():
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    with open(here) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                rows.append([int(x, 16) for x in ln.split()])
+    return rows
+
+
+def test_philox_known_answer_vectors(orc):
+    # Salmon et al. (SC'11), Random123 known-answer vectors for philox4x32 with 10 rounds: a wrong
+    # multiplier, Weyl constant, word order or round count changes every output word
+    rows = _kat_rows()
+    assert len(rows) == 3
+    for w in rows:
+        out = orc.philox4x32_10(w[0:4], w[4:6])
+        assert [int(x) for x in out] == w[6:10], [hex(int(x)) for x in out]
+
+
 def test_philox_words_are_balanced_and_counter_sensitive(orc):
     # bit balance over many counters: every bit of every word ~ 1/2
     words = np.array([orc.philox4x32_10([i, 0, 0, 0], [1, 0]) for i in range(4000)], dtype=np.uint64)
