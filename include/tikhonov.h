@@ -15,9 +15,10 @@
  *  - Matrices are row-major.  A is m x n with row stride lda >= n (elements).
  *  - "device" pointers are CUDA device memory of the current device; "host"
  *    pointers are ordinary host memory.  The caller owns all memory passed in.
- *    The library never allocates device memory: every call that needs scratch
- *    takes a caller-provided device workspace whose size tk_workspace_size()
- *    (or the call's own size query) returns.
+ *    Apart from the handle calls (tk_create ... tk_handle_solve_batched, which
+ *    own a growing workspace), the library never allocates device memory:
+ *    every call that needs scratch takes a caller-provided device workspace
+ *    whose size tk_workspace_size() (or the call's own size query) returns.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Kernels are issued on it in order.  Calls that return host results
  *    synchronize the stream before returning.
@@ -100,6 +101,14 @@ typedef struct {
                              the same float64 accuracy.  Costs 32 bytes of workspace per element of A
                              (two sets of digit planes); 0 = float64 FMA.  The grouped batch uses the
                              emulated Gram and Cholesky and keeps its float64 refinement passes. */
+  const double* x0;       /* [NULL] warm start, device N x n float64 (row i for lambdas[i]; m >= n only):
+                             the solve starts from x = x0 instead of 0 and returns the same minimiser of
+                             problem (1.2).  FP64: LSQR solves for the correction d in
+                             min ||[A; sqrt(l) I] d - [b - A x0; -sqrt(l) x0]|| and returns x0 + d;
+                             MIXED: the refinement's first round already corrects x0.  A lambda whose
+                             preconditioner fails keeps x0 in X.  In tk_solve_batched each problem needs
+                             its own tk_opts (n_opts = P) when x0 is set, and such problems are not
+                             grouped.  The resumable state of a solve: pass a previous X back. */
 } tk_opts;
 
 /* Per-lambda report. */
@@ -151,6 +160,29 @@ TK_API tk_status tk_solve_batched(const tk_problem* ps, int P, const double* lam
                                   int n_opts, void* work, size_t work_bytes, void* stream, double* const* X,
                                   tk_info* info);
 
+/*
+ * Handle calls -- the same solves for callers that prefer the library to own
+ * the workspace (problem (1.2) as in tk_solve; no counterpart in the paper
+ * beyond the solve itself).  A handle holds a stream (void* cudaStream_t,
+ * NULL = legacy default stream) and the device that was current at
+ * tk_create.  Each solve queries the workspace size and grows the handle's
+ * device buffer with cudaMalloc when it is too small (after synchronizing the
+ * stream); a later solve of the same or smaller shapes allocates nothing.
+ * These are the only calls of the library that allocate device memory.
+ * Solves on one handle are serialized (a mutex); use one handle per host
+ * thread for concurrency.  tk_destroy synchronizes the stream, frees the
+ * buffer and the handle (NULL is a no-op).  Errors as tk_solve; TK_ENOMEM if
+ * cudaMalloc fails.
+ */
+typedef struct tk_handle tk_handle;
+TK_API tk_status tk_create(tk_handle** h, void* stream);
+TK_API tk_status tk_destroy(tk_handle* h);
+TK_API size_t tk_handle_workspace_bytes(const tk_handle* h);
+TK_API tk_status tk_handle_solve(tk_handle* h, const tk_problem* p, const double* lambdas, int N, const tk_opts* o,
+                                 double* X, tk_info* info);
+TK_API tk_status tk_handle_solve_batched(tk_handle* h, const tk_problem* ps, int P, const double* lambdas, int N,
+                                         const tk_opts* o, int n_opts, double* const* X, tk_info* info);
+
 /* ---- introspection calls for parity tests (each step of the path on its own) ---- */
 
 /*
@@ -180,9 +212,11 @@ TK_API tk_status tk_sketch_draw(uint64_t seed, int64_t mp, int64_t s, int8_t* si
  *   mp:    1 <= mp <= TK_DRAW_STATIC_MAX_MP, else TK_EINVAL (nothing launched).
  *   signs, rows: as tk_sketch_draw (device, caller-owned, may be NULL).
  * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  All calls share the one array, so
- * calls that overlap on the GPU (other streams, other host threads) race;
- * serialize them.  Synchronizes `stream` before returning.
+ * first call before any stream capture.  The address is kept for the life of
+ * the process: calling after cudaDeviceReset() (which reloads the library's
+ * device code, possibly elsewhere) is not supported.  All calls share the one
+ * array, so calls that overlap on the GPU (other streams, other host threads)
+ * race; serialize them.  Every call synchronizes `stream` before returning.
  */
 #define TK_DRAW_STATIC_MAX_MP ((int64_t)1 << 20)
 TK_API tk_status tk_sketch_draw_static(uint64_t seed, int64_t mp, int64_t s, int8_t* signs, int64_t* rows,
@@ -227,7 +261,8 @@ TK_API tk_status tk_gram_emulated(const double* Y, int64_t r, int64_t c, double*
  * (Algorithm 1 step 4), upper triangular, float64.
  *   C: device n x n (symmetric, only the upper triangle is read).
  *   lambdas: host N.   R: device N x n x n (zeros below the diagonal).
- *   breakdown: host N (may be NULL): 0, or j+1 if the pivot of row j was not positive.
+ *   breakdown: host N (may be NULL): 0, or j+1 if the pivot of row j was not positive
+ *              (TK_ENOTSPD), or -(j+1) if it was NaN (non-finite C: TK_ENUMERIC).
  *   work: device, tk_cholesky_workspace(n, N) bytes.
  */
 TK_API size_t tk_cholesky_workspace(int64_t n, int N);
@@ -305,10 +340,26 @@ TK_API void tk_autotune_clear(void);
  * returns the length the whole text needs, NUL included. */
 TK_API size_t tk_autotune_describe(char* buf, size_t len);
 
+/* tk_wait_selftest -- the bounded device-side wait that every pipelined
+ * tensor-core kernel of the library uses, on its own (no counterpart in the
+ * paper: the failure path of TK_ETIMEOUT).  One thread waits on an mbarrier
+ * that nothing arrives at, with a budget of budget_us microseconds (1 ..
+ * 2,000,000; the kernels use 1 s per wait); the wait gives up, sets the
+ * launch's error word and the call returns TK_ETIMEOUT, as a solve does when
+ * one of its pipeline waits gives up.  Nothing else is in flight, so the
+ * context stays usable.  TK_OK would mean the wait did not give up.
+ *   work: device, at least 16 bytes.  Synchronizes `stream`. */
+TK_API tk_status tk_wait_selftest(int64_t budget_us, void* work, size_t work_bytes, void* stream);
+
 /* ---- phase profiler (tracing) ----
  * When enabled, each instrumented launch is bracketed by CUDA events on its
- * stream and tagged with its algorithmic flops and bytes (the counts of the
- * operation itself, not of the implementation).  tk_profile_collect() waits
+ * stream and tagged with its algorithmic flops and bytes: the counts of the
+ * operation itself, not of the implementation -- one read of each operand and
+ * one write of each result, A counted once per pass in the caller's dtype (8
+ * or 4 bytes per element) whatever copy or digit planes the kernel reads.
+ * impl_bytes is what the implementation moves (e.g. 8 bytes per element of A
+ * for the 4 BF16 digit planes of an LSQR product, 16 for the 8 planes of a
+ * float64-accurate pass, 4 for the float32 copy of a float64 A).  tk_profile_collect() waits
  * for the recorded events, fills out[TK_PHASE_COUNT] with per-phase totals
  * and clears the records.  Not for use inside CUDA graph capture. */
 enum {
@@ -334,6 +385,7 @@ typedef struct {
   double flops;   /* summed algorithmic flops */
   double bytes;   /* summed algorithmic bytes (one read of each operand, one write of each result) */
   int launches;
+  double impl_bytes; /* summed bytes the implementation moves (digit planes, copies) */
 } tk_phase_stats;
 TK_API const char* tk_phase_name(int phase);
 /* Number of kernel launches the library has issued in this process so far. */

@@ -89,6 +89,7 @@ tk_status make_plan(const tk_problem* p, int N, const tk_opts* o, Plan& P) {
   P.mixed = o->precision == TK_PREC_MIXED;
   P.lowrank = o->precond == TK_PRECOND_LOWRANK;
   if (P.under && P.mixed) return einval("the mixed-precision form is built for m >= n");
+  if (P.under && o->x0) return einval("the warm start x0 is supported for m >= n (Algorithms 1 and 3)");
   int64_t s = o->s;
   if (s == 0) s = P.lowrank ? P.c : std::min<int64_t>(4 * P.c, P.L);
   if (o->sketch == TK_SKETCH_SRHT && s > next_pow2(P.L)) return einval("SRHT sketch size exceeds the padded length");
@@ -227,6 +228,11 @@ void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
     B.Roz = a.take<char>(oz_slices_bytes(N, P.m));
     B.ER = a.take<int>(N);
   }
+  if (!P.mixed && P.o.x0 && !P.prep_only) {  // warm start: [b - A x0; -sqrt(l) x0] per lambda
+    B.Xa = a.take<double>((size_t)N * P.n);
+    B.G = a.take<double>((size_t)N * P.n);
+    B.Rres = a.take<double>((size_t)N * P.m);
+  }
   if (P.mixed && !P.prep_only) {
     B.splits = splitk_count(N, P.n, P.m);
     // the emulated A^T r wants the most splits when the fewest lambdas remain
@@ -327,6 +333,15 @@ __global__ void k_refine_update(double* __restrict__ X, const double* __restrict
     nrm[3 * k + 1] = sqrt(dd);
     nrm[3 * k + 2] = sqrt(xx);
   }
+}
+// G_k = -lambda_l x0_l for the k-th listed lambda l (the lower block of the
+// warm start's right-hand side, scaled as Lsqr::run expects: bbot / sqrt(l))
+__global__ void k_neg_lam_rows(const double* __restrict__ Xa, int64_t n, const int* __restrict__ ids,
+                               const double* __restrict__ lam, double* __restrict__ G) {
+  const int k = blockIdx.y;
+  const double lv = lam[ids[k]];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    G[(int64_t)k * n + j] = -lv * Xa[(int64_t)k * n + j];
 }
 __global__ void k_f64_to_f32_flat(const double* __restrict__ s, float* __restrict__ d, int64_t total) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
@@ -500,7 +515,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       return TK_ETIMEOUT;
     }
     for (int i = 0; i < N; ++i) {
-      if (hinfo[i] != 0) inf[i].status = TK_ENOTSPD;
+      if (hinfo[i] != 0) inf[i].status = hinfo[i] < 0 ? TK_ENUMERIC : TK_ENOTSPD;  // negative: NaN pivot
       else ok_ids.push_back(i);
     }
     if (P.mixed) {
@@ -526,7 +541,10 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
                    P.mixed ? B.lrV32 : nullptr, P.mixed ? B.lrS32 : nullptr};
     TK_TRY(lowrank_finish(L, inf.data(), ok_ids, st));
   }
-  TK_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)N * P.n, st));
+  if (P.o.x0)  // warm start (problem (1.2) from x0): rows of lambdas without a preconditioner keep x0
+    TK_CUDA(cudaMemcpyAsync(X, P.o.x0, sizeof(double) * (size_t)N * P.n, cudaMemcpyDeviceToDevice, st));
+  else
+    TK_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)N * P.n, st));
   if (gp) {
     gp->m = P.m;
     gp->n = P.n;
@@ -569,13 +587,31 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
   if (!P.mixed) {
     Lsqr<double>& e = B.e64;
     e.A = A64; e.lda = lda64; e.st = st; e.atol = e.btol = P.o.tol; e.maxiter = P.o.maxiter;
+    e.a_es = P.dt == TK_F64 ? 8.0 : 4.0;
     if (!P.lowrank) {
       e.prec_kind = TK_PRECOND_CHOL; e.R = B.R; e.ldr = P.np; e.rstride = P.np * P.np;
       if (P.inv64) { e.Mi = B.Minv64; e.Mti = B.Mtinv64; e.ldm = P.np; e.mstride = P.np * P.np; }
     } else {
       e.prec_kind = TK_PRECOND_LOWRANK; e.lrV = B.lrV; e.lrS = B.lrS;
     }
-    if (P.o.schedule == TK_SCHED_BATCHED) {
+    if (P.o.x0 && nok > 0) {
+      // x = x0 + d with d = argmin ||B d - [b - A x0; -sqrt(l) x0]|| (B = [A; sqrt(l) I]): the same
+      // minimiser of problem (1.2); LSQR adds d onto X, which holds x0
+      k_gather_x<<<rgrid(P.n, nok), 256, 0, st>>>(X, P.n, B.ids, B.Xa);
+      k_bcast<<<rgrid(P.m, nok), 256, 0, st>>>(p->b, P.m, B.Rres, nok);
+      TK_LAUNCH_CHECK();
+      TK_TRY((gemm<double, double, double>(false, true, nok, P.m, P.n, B.Xa, P.n, A64, lda64, B.Rres, P.m, -1.0,
+                                           B.ones, B.Rres, P.m, st)));
+      k_neg_lam_rows<<<rgrid(P.n, nok), 256, 0, st>>>(B.Xa, P.n, B.ids, B.lam, B.G);
+      TK_LAUNCH_CHECK();
+      if (P.o.schedule == TK_SCHED_BATCHED) {
+        TK_TRY(e.run(B.Rres, P.m, B.G, P.n, B.ids, B.lam, nok, X, P.n, true, res));
+      } else {
+        for (int k = 0; k < nok; ++k)
+          TK_TRY(e.run(B.Rres + (int64_t)k * P.m, 0, B.G + (int64_t)k * P.n, 0, B.ids + k, B.lam, 1, X, P.n, true,
+                       res));
+      }
+    } else if (P.o.schedule == TK_SCHED_BATCHED) {
       TK_TRY(e.run(p->b, 0, nullptr, 0, B.ids, B.lam, nok, X, P.n, false, res));
     } else {
       for (int k = 0; k < nok; ++k) TK_TRY(e.run(p->b, 0, nullptr, 0, B.ids + k, B.lam, 1, X, P.n, false, res));
@@ -595,6 +631,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     //      correction d solves min ||B d - [0; g/sqrt(l)]||, x <- x + d.
     Lsqr<float>& e = B.e32;
     e.A = A32; e.lda = lda32; e.st = st; e.atol = e.btol = P.o.inner_tol; e.maxiter = P.o.maxiter;
+    e.a_es = P.dt == TK_F64 ? 8.0 : 4.0;
     if (P.lsqr_tc && ((uintptr_t)A32 % 16) == 0) {
       TK_TRY(transpose(A32, TK_F32, P.m, P.n, lda32, B.AT32, st));  // float32 A^T for the A^T U product
       e.AT = B.AT32;
@@ -623,7 +660,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       const int cnt = (int)act.size();
       TK_CUDA(cudaMemcpyAsync(B.ids, act.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, st));
       res.clear();
-      if (round == 0) {
+      if (round == 0 && !P.o.x0) {  // from x = 0 the first correction is the solution of [b; 0]
         if (P.o.schedule == TK_SCHED_BATCHED) TK_TRY(e.run(p->b, 0, nullptr, 0, B.ids, B.lam, cnt, B.D, P.n, false, res));
         else
           for (int k = 0; k < cnt; ++k) TK_TRY(e.run(p->b, 0, nullptr, 0, B.ids + k, B.lam, 1, B.D, P.n, false, res));
@@ -645,7 +682,8 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
           TK_TRY((gemm<double, float, double>(false, true, cnt, P.m, P.n, B.Xa, P.n, A32, lda32, B.Rres, P.m, -1.0,
                                               B.ones, B.Rres, P.m, st)));
         }
-        prof_end(tok, st, fl, (P.o.emulate_fp64 ? 16.0 : ea) * P.m * P.n + 8.0 * (2.0 * cnt * P.m + cnt * P.n));
+        prof_end(tok, st, fl, ea * P.m * P.n + 8.0 * (2.0 * cnt * P.m + cnt * P.n),
+                 (P.o.emulate_fp64 ? 16.0 : ea) * P.m * P.n + 8.0 * (2.0 * cnt * P.m + cnt * P.n));
         tok = prof_begin(TK_PHASE_NE64, st);
         int sp;
         if (P.o.emulate_fp64) {
@@ -659,7 +697,8 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
           else
             TK_TRY((gemm_splitk<double, float>(false, false, cnt, P.n, P.m, B.Rres, P.m, A32, lda32, B.part, sp, st)));
         }
-        prof_end(tok, st, fl, (P.o.emulate_fp64 ? 16.0 : ea) * P.m * P.n + 8.0 * (cnt * P.m + (double)sp * cnt * P.n));
+        prof_end(tok, st, fl, ea * P.m * P.n + 8.0 * (cnt * P.m + (double)sp * cnt * P.n),
+                 (P.o.emulate_fp64 ? 16.0 : ea) * P.m * P.n + 8.0 * (cnt * P.m + (double)sp * cnt * P.n));
         k_ne_finish<<<cnt, 256, 0, st>>>(B.part, sp, cnt, P.n, B.ids, B.lam, B.Xa, B.G, B.nrm);
         TK_LAUNCH_CHECK();
         // correction: min ||B d - [0; g/sqrt(l)]||, whose normal equations are
@@ -675,7 +714,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       TK_LAUNCH_CHECK();
       TK_CUDA(cudaMemcpyAsync(hn.data(), B.nrm, sizeof(double) * 3 * cnt, cudaMemcpyDeviceToHost, st));
       int oz_err = 0;
-      if (P.o.emulate_fp64 && (round > 0 || P.lsqr_oz))
+      if (P.o.emulate_fp64 && (round > 0 || P.o.x0 || P.lsqr_oz))
         TK_CUDA(cudaMemcpyAsync(&oz_err, B.oz_err, sizeof(int), cudaMemcpyDeviceToHost, st));
       TK_CUDA(cudaStreamSynchronize(st));
       if (oz_err) {
@@ -694,8 +733,11 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
       for (int k = 0; k < cnt; ++k) {
         tk_info& q = inf[act[k]];
         q.refine_steps += 1;
-        if (round > 0) q.ne_norm = hn[3 * k];
+        const bool checked = round > 0 || P.o.x0;  // this round formed g = A^T (b - A x) - l x
+        if (checked) q.ne_norm = hn[3 * k];
         const double dn = hn[3 * k + 1], xn = hn[3 * k + 2];
+        if (!std::isfinite(dn) || !std::isfinite(xn) || (checked && !std::isfinite(hn[3 * k])))
+          q.status = worse(q.status, TK_ENUMERIC);  // refine_done stops on it; the status says why
         const bool done = refine_done(round, dn, prev_dn[act[k]], xn, P.o.refine_tol);
         prev_dn[act[k]] = dn;
         if (!done) next.push_back(act[k]);
@@ -799,13 +841,14 @@ struct BatchLayout {
 tk_status batch_layout(const tk_problem* ps, int P, int N, const tk_opts* o, int n_opts, BatchLayout& L) {
   L = BatchLayout{};
   L.lanes = batched_lanes(P);
+  if (n_opts == 1 && P > 1 && o->x0) return einval("a warm start x0 belongs to one problem: pass one tk_opts per problem");
   std::vector<Plan> pl(P);
   bool grouped = P >= 2 && N >= 1 && N <= kGroupMaxLambda && (int64_t)P * N <= 65535;  // slot lists index grid.y
   for (int i = 0; i < P; ++i) {
     TK_TRY(make_plan(&ps[i], N, opts_of(o, n_opts, i), pl[i]));
     const Plan& q = pl[i];
     grouped = grouped && q.mixed && !q.under && q.o.schedule == TK_SCHED_BATCHED && !q.lsqr_tc &&
-              q.n <= kGroupMaxN && q.o.group != 0;
+              q.n <= kGroupMaxN && q.o.group != 0 && !q.o.x0;  // warm starts run on the lanes
   }
   L.grouped = grouped;
   if (!grouped) {
@@ -1307,7 +1350,7 @@ tk_status cholesky_common(const double* C, int64_t n, const double* lambdas, int
   tk_status worst = TK_OK;
   for (int i = 0; i < N; ++i) {
     if (breakdown) breakdown[i] = h[i];
-    if (h[i]) worst = TK_ENOTSPD;
+    if (h[i]) worst = worse(worst, h[i] < 0 ? TK_ENUMERIC : TK_ENOTSPD);
   }
   return worst;
 }

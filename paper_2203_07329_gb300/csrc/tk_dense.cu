@@ -204,7 +204,9 @@ __global__ void k_chol_init(const double* __restrict__ Cm, int64_t n, int64_t np
 
 // Factor the diagonal tile (kb, kb) of every lambda in shared memory
 // (right-looking within the tile).  A non-positive pivot records the global
-// row + 1 in info[l] (first one only) and continues with pivot 1.
+// row + 1 in info[l] (first one only; its negative when the pivot is NaN, i.e.
+// non-finite input rather than a matrix that is not positive definite) and
+// continues with pivot 1.
 __global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ R, int64_t ldr, int64_t rstride, int kb,
                                                    int* __restrict__ info) {
   __shared__ double T[CB][CB + 1];
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ R, int64
     if (threadIdx.x == 0) {
       double d = T[j][j];
       if (!(d > 0.0)) {
-        if (info[l] == 0) info[l] = kb * CB + j + 1;
+        if (info[l] == 0) info[l] = (d != d) ? -(kb * CB + j + 1) : kb * CB + j + 1;
         d = 1.0;
       }
       T[j][j] = sqrt(d);

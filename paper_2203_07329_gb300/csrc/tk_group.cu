@@ -714,19 +714,26 @@ tk_status group_solve_mixed(std::vector<GroupProblem>& g, int N, void* work, siz
         f += g[p].lowrank ? 4.0 * hnact[p] * g[p].n * g[p].lr_s : (double)hnact[p] * g[p].n * g[p].n;
       return f;
     };
+    // (flops, algorithmic bytes: A once in its own dtype, implementation bytes: the float32 A read)
+    struct FB {
+      double first, second, impl;
+    };
     auto step_flops = [&]() {
-      double f = 0.0, b = 0.0;
+      FB r{0.0, 0.0, 0.0};
       for (int p = 0; p < P; ++p) {
-        f += 2.0 * hnact[p] * g[p].m * g[p].n;
-        b += 4.0 * ((double)g[p].m * g[p].n + hnact[p] * (double)(g[p].n + 2 * g[p].m));
+        if (hnact[p] == 0) continue;  // retired problems are not in the tile lists
+        const double mn = (double)g[p].m * g[p].n, vec = 4.0 * hnact[p] * (double)(g[p].n + 2 * g[p].m);
+        r.first += 2.0 * hnact[p] * mn;
+        r.second += (g[p].f64 ? 8.0 : 4.0) * mn + vec;
+        r.impl += 4.0 * mn + vec;
       }
-      return std::make_pair(f, b);
+      return r;
     };
     {
       auto fb = step_flops();
       const int tok = prof_begin(TK_PHASE_ATU, st);
       TK_TRY(launch_lm(S, false, st));
-      prof_end(tok, st, fb.first, fb.second);
+      prof_end(tok, st, fb.first, fb.second, fb.impl);
     }
     k_g_over_g<<<chunk_grid(S.maxn, nsl), 256, 0, st>>>(S.dd, S.nact, S.rnd);
     TK_LAUNCH_CHECK();
@@ -814,12 +821,12 @@ tk_status group_solve_mixed(std::vector<GroupProblem>& g, int N, void* work, siz
       prof_end(tok, st, prec_flops(), 0.0);
       tok = prof_begin(TK_PHASE_AW, st);
       TK_TRY(launch_lm(S, true, st));  // Ut = T A^T - (alpha/beta) Ut
-      prof_end(tok, st, fb.first, fb.second);
+      prof_end(tok, st, fb.first, fb.second, fb.impl);
       k_g_beta<<<nsl, kThreads, 0, st>>>(S.dd, S.slots);
       TK_LAUNCH_CHECK();
       tok = prof_begin(TK_PHASE_ATU, st);
       TK_TRY(launch_lm(S, false, st));  // part = Ut A
-      prof_end(tok, st, fb.first, fb.second);
+      prof_end(tok, st, fb.first, fb.second, fb.impl);
       k_g_over_g<<<chunk_grid(S.maxn, nsl), 256, 0, st>>>(S.dd, S.nact, S.slots);
       TK_LAUNCH_CHECK();
       tok = prof_begin(TK_PHASE_PRECOND, st);

@@ -162,7 +162,9 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 // ------------------------------------------------------------ profiler --
 bool prof_enabled();
 int prof_begin(int phase, cudaStream_t st);
-void prof_end(int tok, cudaStream_t st, double flops, double bytes);
+// bytes: the operation's own (each operand once, A in the caller's dtype); impl_bytes: what the
+// implementation moves (digit planes, copies), < 0 = the same
+void prof_end(int tok, cudaStream_t st, double flops, double bytes, double impl_bytes = -1.0);
 
 // --------------------------------------------------------- launchers -----
 // Draws (tk_draw.cu)

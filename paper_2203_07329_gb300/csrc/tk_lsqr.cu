@@ -358,22 +358,24 @@ template <typename T>
 tk_status Lsqr<T>::prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, int count) {
   // C (count x m) = Win (count x n) A^T  [+ beta_row * C]
   const bool digits = use_oz(count);
+  const double es = (double)sizeof(T);
+  const double vec = es * (count * (double)n + 2.0 * count * m);
   int tok = prof_begin(digits ? TK_PHASE_AW_DIGITS : TK_PHASE_AW, st);
   tk_status r;
   if constexpr (std::is_same<T, float>::value) {
     if (digits) {
       r = oz_lsqr_aw(oz_A, oz_EA, m, n, Win, ldw, count, oz_q, oz_e, C, m, beta, oz_err, st);
-      prof_end(tok, st, 2.0 * count * m * n, 8.0 * m * n + 4.0 * count * (double)n + 8.0 * count * m);
+      prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, 8.0 * m * n + vec);
       return r;
     }
     if (tc && beta) {
       r = tc_lmaj_product(true, A, m, n, lda, Win, ldw, count, C, m, beta, nullptr, 1, tc_scratch, st);
-      prof_end(tok, st, 2.0 * count * m * n, (double)sizeof(T) * ((double)m * n + count * (double)n + 2.0 * count * m));
+      prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, es * m * n + vec);
       return r;
     }
   }
   r = gemm<T, T, T>(false, true, count, m, n, Win, ldw, A, lda, C, m, 1.0, beta, beta ? C : nullptr, m, st);
-  prof_end(tok, st, 2.0 * count * m * n, (double)sizeof(T) * ((double)m * n + count * (double)n + 2.0 * count * m));
+  prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, es * m * n + vec);
   return r;
 }
 
@@ -381,27 +383,29 @@ template <typename T>
 tk_status Lsqr<T>::prod_atu(const T* Uin, int count) {
   // part_g (splits x count x n) = Uin (count x m) A
   const bool digits = use_oz(count);
+  const double es = (double)sizeof(T);
   int tok = prof_begin(digits ? TK_PHASE_ATU_DIGITS : TK_PHASE_ATU, st);
   tk_status r;
   if constexpr (std::is_same<T, float>::value) {
     if (digits) {
       cur_splits = std::min(splits, oz_normal_splits(m, n, count));
+      const double vec = es * count * (double)m + 8.0 * cur_splits * count * n;
       r = oz_lsqr_atu(oz_AT, oz_EAT, m, n, Uin, m, count, oz_q, oz_e, part_g, cur_splits, oz_err, st);
-      prof_end(tok, st, 2.0 * count * m * n, 8.0 * m * n + 4.0 * count * (double)m + 8.0 * cur_splits * count * n);
+      prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, 8.0 * m * n + vec);
       return r;
     }
     if (tc && AT) {
       cur_splits = splits;
+      const double vec = es * count * (double)m + 8.0 * splits * count * n;
       r = tc_lmaj_product(false, AT, n, m, m, Uin, m, count, nullptr, 0, nullptr, part_g, splits, tc_scratch, st);
-      prof_end(tok, st, 2.0 * count * m * n,
-               (double)sizeof(T) * ((double)m * n + count * (double)m) + 8.0 * splits * count * n);
+      prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, es * m * n + vec);
       return r;
     }
   }
   cur_splits = splitk_tuned<T, T>(count, n, m, splits);
+  const double vec = es * count * (double)m + 8.0 * cur_splits * count * n;
   r = gemm_splitk<T, T>(false, false, count, n, m, Uin, m, A, lda, part_g, cur_splits, st);
-  prof_end(tok, st, 2.0 * count * m * n,
-           (double)sizeof(T) * ((double)m * n + count * (double)m) + 8.0 * splits * count * n);
+  prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, es * m * n + vec);
   return r;
 }
 

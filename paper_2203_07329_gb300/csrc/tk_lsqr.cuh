@@ -127,6 +127,8 @@ struct Lsqr {
   // problem: A (m x n, row stride lda) in the compute type
   const T* A = nullptr;
   int64_t m = 0, n = 0, lda = 0;
+  // bytes per element of A in the caller's dtype (the profiler's algorithmic bytes of one A pass)
+  double a_es = sizeof(T);
   bool under = false;
   // preconditioner: per-lambda Cholesky factors R + l*rstride, or low rank
   tk_precond prec_kind = TK_PRECOND_CHOL;

@@ -291,6 +291,7 @@ struct OtSmem {
   uint64_t q_empty[2];
   uint64_t acc_full[2];
   uint64_t acc_empty[2];
+  uint64_t mma_drain;  // error path: completes when every MMA the CTA issued is done
   uint32_t tmem_base;
 };
 
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(256, 1)
       mbar_init(&Sm.acc_full[s], 1);
       mbar_init(&Sm.acc_empty[s], 128);
     }
+    mbar_init(&Sm.mma_drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 2) {
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t tmem = Sm.tmem_base;
 
   if (warp == 0 && lane == 0) {
-    int g = 0;
+    int g = 0, gq = 0;  // loads issued into the P ring and the Q ring
     bool live = true;
     for (int kb = 0; kb < nkb && live; ++kb) {
       const int kc = (int)(kbeg + (int64_t)kb * OT_KB);
@@ -357,6 +359,7 @@ __global__ void __launch_bounds__(256, 1)
       if (!mbar_wait(&Sm.q_empty[qs], ((uint32_t)(kb >> 1) & 1u) ^ 1u, err)) break;
       mbar_expect_tx(&Sm.q_full[qs], Q_BYTES);
       for (int p = 0; p < S; ++p) tma_load_3d(&tmQ, &Sm.q_full[qs], Sm.q[qs] + p * OT_QS_BYTES, kc, l0, p);
+      ++gq;
       for (int p = 0; p < S; ++p, ++g) {
         const int ps = g % OT_PST;
         if (!mbar_wait(&Sm.p_empty[ps], ((uint32_t)(g / OT_PST) & 1u) ^ 1u, err)) {
@@ -366,6 +369,10 @@ __global__ void __launch_bounds__(256, 1)
         mbar_expect_tx(&Sm.p_full[ps], OT_P_BYTES);
         tma_load_3d(&tmP, &Sm.p_full[ps], Sm.p[ps], kc, (int)r0, p);
       }
+    }
+    if (*(volatile int*)err) {  // gave up: no bulk copy may still be landing when the CTA exits
+      tma_drain_ring(Sm.p_full, OT_PST, g);
+      tma_drain_ring(Sm.q_full, 2, gq);
     }
   } else if (warp == 1 && lane == 0) {
     int g = 0;
@@ -410,6 +417,10 @@ __global__ void __launch_bounds__(256, 1)
         if (live) tc_commit(&Sm.q_empty[qs]);
       }
       if (live) tc_commit(&Sm.acc_full[bsel]);
+    }
+    if (*(volatile int*)err) {  // gave up: wait for the MMAs issued before tensor memory is freed
+      tc_commit(&Sm.mma_drain);
+      mbar_drain(&Sm.mma_drain, 0u);
     }
   } else if (warp >= 4) {
     const int ew = warp - 4;
@@ -587,6 +598,7 @@ struct CsSmem {
   uint64_t q_empty[2];
   uint64_t acc_full[2];
   uint64_t acc_empty[2];
+  uint64_t mma_drain;  // error path: completes when every MMA the CTA issued is done
   uint32_t tmem_base;
 };
 
@@ -632,6 +644,7 @@ __global__ void __launch_bounds__(256, 1)
       mbar_init(&S.acc_full[s], 1);
       mbar_init(&S.acc_empty[s], 128);
     }
+    mbar_init(&S.mma_drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 2) {
@@ -648,12 +661,18 @@ __global__ void __launch_bounds__(256, 1)
   if (warp == 0 && lane == 0) {
     mbar_expect_tx(&S.p_full, OZ_S * CS_P_BYTES);
     for (int p = 0; p < OZ_S; ++p) tma_load_3d(&tmP, &S.p_full, S.p[p], 0, i0, l * OZ_S + p);
+    int gq = 0;  // tiles issued into the Q ring
     for (int t = 0; t < nt; ++t) {
       const int s = t & 1;
       if (!mbar_wait(&S.q_empty[s], ((uint32_t)(t >> 1) & 1u) ^ 1u, err)) break;
       mbar_expect_tx(&S.q_full[s], OZ_S * CS_Q_BYTES);
       const int j0 = (t_first + t) * CS_N;
       for (int p = 0; p < OZ_S; ++p) tma_load_3d(&tmQ, &S.q_full[s], S.q[s] + p * CS_Q_BYTES, 0, j0, l * OZ_S + p);
+      ++gq;
+    }
+    if (*(volatile int*)err) {  // gave up: no bulk copy may still be landing when the CTA exits
+      mbar_drain(&S.p_full, 0u);
+      tma_drain_ring(S.q_full, 2, gq);
     }
   } else if (warp == 1 && lane == 0) {
     if (mbar_wait(&S.p_full, 0u, err)) {
@@ -675,6 +694,10 @@ __global__ void __launch_bounds__(256, 1)
         tc_commit(&S.q_empty[s]);
         tc_commit(&S.acc_full[s]);
       }
+    }
+    if (*(volatile int*)err) {  // gave up: wait for the MMAs issued before tensor memory is freed
+      tc_commit(&S.mma_drain);
+      mbar_drain(&S.mma_drain, 0u);
     }
   } else if (warp >= 4) {
     const int ew = warp - 4;
@@ -721,8 +744,12 @@ __global__ void __launch_bounds__(256, 1)
         for (int j = 0; j < CS_N; ++j) {
           if (j0 + j < w && j0 + j >= i) {
             const double vhi = (double)hi[j] * 0x1p-35, vlo = (double)lo[j] * 0x1p-63;  // exact
-            const int e = ei + S.ecol[t * CS_N + j];
-            Trow[j0 + j] = tv[j] - (vhi + vlo) * (e >= -1022 && e <= 1023 ? pow2d(e) : ldexp(1.0, e));
+            const int ej = S.ecol[t * CS_N + j];
+            const int e = ei + ej;
+            // a row or column marked non-finite makes the update NaN (its digits are zero)
+            Trow[j0 + j] = (ei >= OZ_EBAD || ej >= OZ_EBAD)
+                               ? __longlong_as_double(0x7ff8000000000000ll)
+                               : tv[j] - (vhi + vlo) * (e >= -1022 && e <= 1023 ? pow2d(e) : ldexp(1.0, e));
           }
         }
       }

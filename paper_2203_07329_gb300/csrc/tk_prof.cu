@@ -14,7 +14,7 @@ namespace {
 struct Rec {
   int phase;
   cudaEvent_t a, b;
-  double flops, bytes;
+  double flops, bytes, impl_bytes;
   bool closed;
 };
 
@@ -49,14 +49,14 @@ bool prof_enabled() {
 int prof_begin(int phase, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on) return -1;
-  Rec r{phase, take_event(), take_event(), 0.0, 0.0, false};
+  Rec r{phase, take_event(), take_event(), 0.0, 0.0, 0.0, false};
   if (!r.a || !r.b) return -1;
   cudaEventRecord(r.a, st);
   g_recs.push_back(r);
   return (int)g_recs.size() - 1;
 }
 
-void prof_end(int tok, cudaStream_t st, double flops, double bytes) {
+void prof_end(int tok, cudaStream_t st, double flops, double bytes, double impl_bytes) {
   if (tok < 0) return;
   std::lock_guard<std::mutex> lk(g_mu);
   if (tok >= (int)g_recs.size()) return;
@@ -64,6 +64,7 @@ void prof_end(int tok, cudaStream_t st, double flops, double bytes) {
   cudaEventRecord(r.b, st);
   r.flops = flops;
   r.bytes = bytes;
+  r.impl_bytes = impl_bytes < 0.0 ? bytes : impl_bytes;
   r.closed = true;
 }
 
@@ -97,7 +98,7 @@ TK_API tk_status tk_profile_collect(tk_phase_stats* out) {
     recs.swap(g_recs);
   }
   if (out)
-    for (int p = 0; p < TK_PHASE_COUNT; ++p) out[p] = tk_phase_stats{0.0, 0.0, 0.0, 0};
+    for (int p = 0; p < TK_PHASE_COUNT; ++p) out[p] = tk_phase_stats{0.0, 0.0, 0.0, 0, 0.0};
   tk_status st = TK_OK;
   for (auto& r : recs) {
     if (r.closed) {
@@ -108,6 +109,7 @@ TK_API tk_status tk_profile_collect(tk_phase_stats* out) {
         out[r.phase].ms += ms;
         out[r.phase].flops += r.flops;
         out[r.phase].bytes += r.bytes;
+        out[r.phase].impl_bytes += r.impl_bytes;
         out[r.phase].launches += 1;
       }
     }

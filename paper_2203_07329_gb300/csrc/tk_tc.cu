@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(128, 1)
 
   if (warp == 0 && lane == 0) {
     // TMA producer
+    int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % TC_STAGES;
       const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
@@ -81,7 +82,9 @@ __global__ void __launch_bounds__(128, 1)
       mbar_expect_tx(&S.full[s], TC_A_BYTES + TC_B_BYTES);
       tma_load_2d(&tmA, &S.full[s], S.a[s], kb * TC_K, m0);
       tma_load_2d(&tmB, &S.full[s], S.b[s], kb * TC_K, n0);
+      ++issued;
     }
+    if (*(volatile int*)err) tma_drain_ring(S.full, TC_STAGES, issued);  // no copy lands after the exit
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
@@ -114,6 +117,7 @@ __global__ void __launch_bounds__(128, 1)
 
   // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
   const bool ok = mbar_wait(&S.accum, 0u, err);
+  if (!ok) mbar_drain(&S.accum, 0u);  // gave up: the issued MMAs finish before tensor memory is freed
   tc_fence_after();
   if (ok) {
     const int64_t row = (int64_t)m0 + warp * 32 + lane;
@@ -269,6 +273,7 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t tmem = S.tmem_base;
 
   if (warp == 0 && lane == 0) {
+    int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % T3_STAGES;
       const uint32_t ph = (uint32_t)(kb / T3_STAGES) & 1u;
@@ -278,7 +283,9 @@ __global__ void __launch_bounds__(256, 1)
       tma_load_2d(&tmX, &S.full[s], S.xh[s], kc, (int)r0);
       tma_load_2d(&tmLh, &S.full[s], S.lh[s], kc, 0);
       tma_load_2d(&tmLl, &S.full[s], S.ll[s], kc, 0);
+      ++issued;
     }
+    if (*(volatile int*)err) tma_drain_ring(S.full, T3_STAGES, issued);  // no copy lands after the exit
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = idesc_tf32(T3_M, NP);
     for (int kb = 0; kb < nk; ++kb) {
@@ -339,6 +346,7 @@ __global__ void __launch_bounds__(256, 1)
 
   // epilogue (warps 0-3: accumulator lanes 32w .. 32w+31 = rows of this tile)
   const bool ok = (warp < 4) ? mbar_wait(&S.accum, 0u, err) : true;
+  if (!ok) mbar_drain(&S.accum, 0u);  // gave up: the issued MMAs finish before tensor memory is freed
   tc_fence_after();
   if (warp < 4 && ok) {
     const int64_t row = r0 + warp * 32 + lane;
@@ -549,3 +557,47 @@ tk_status tc_lmaj_check(void* scratch, int N, int64_t K, cudaStream_t st) {
 }
 
 }  // namespace tk
+
+// ---- the bounded wait on its own ------------------------------------------------
+// One thread waits on a freshly initialized mbarrier that nothing arrives at:
+// its first phase never completes, so the wait must give up after budget_ns
+// and set the error word, exactly as a stuck pipeline stage of the kernels
+// above would.  Nothing is in flight (no copy, no MMA, no tensor memory).
+namespace tk {
+namespace {
+__global__ void k_wait_selftest(uint64_t budget_ns, int* __restrict__ err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) (void)mbar_wait_for(&bar, 0u, err, budget_ns);
+}
+}  // namespace
+}  // namespace tk
+
+extern "C" TK_API tk_status tk_wait_selftest(int64_t budget_us, void* work, size_t work_bytes, void* stream) {
+  using namespace tk;
+  if (budget_us < 1 || budget_us > 2000000) {
+    set_error_msg("tk_wait_selftest: budget_us must be in [1, 2000000]");
+    return TK_EINVAL;
+  }
+  if (!work || work_bytes < 16) {
+    set_error_msg("tk_wait_selftest: work must hold at least 16 bytes");
+    return TK_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = static_cast<int*>(work);
+  TK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  k_wait_selftest<<<1, 32, 0, st>>>((uint64_t)budget_us * 1000ull, err);
+  TK_LAUNCH_CHECK();
+  int h = 0;
+  TK_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    set_error_msg("tk_wait_selftest: the bounded wait gave up as it should");
+    return TK_ETIMEOUT;
+  }
+  return TK_OK;
+}

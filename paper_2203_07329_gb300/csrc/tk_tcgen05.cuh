@@ -27,16 +27,62 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait (about 2^24 polls with back-off: seconds, far beyond any
-// legitimate stage time).  Returns false if it gave up or another role did.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
-  for (uint32_t i = 0; i < (1u << 24); ++i) {
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Budget of one pipeline wait: far beyond any legitimate stage time (micro- to
+// milliseconds), short enough that a stuck pipeline returns an error status
+// while the context stays usable.
+constexpr uint64_t kWaitBudgetNs = 1000000000ull;  // 1 s
+
+// Bounded wait on phase `parity` of mbarrier b: polls with back-off until the
+// phase completes, another role of the launch gave up (*err set), or
+// budget_ns of global time passed (or 2^26 polls, should the timer stall);
+// on giving up it sets *err.  Returns true when the phase completed.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* b, uint32_t parity, int* err, uint64_t budget_ns) {
+  uint64_t t0 = 0;
+  for (uint32_t i = 0; i < (1u << 26); ++i) {
     if (mbar_try_wait(b, parity)) return true;
     if (i >= 64) __nanosleep(128);
-    if ((i & 255u) == 255u && *(volatile int*)err) return false;
+    if ((i & 255u) == 255u) {
+      if (*(volatile int*)err) return false;
+      const uint64_t t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > budget_ns) break;
+    }
   }
   atomicExch(err, 1);
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
+  return mbar_wait_for(b, parity, err, kWaitBudgetNs);
+}
+
+// Error path: wait (bounded, whatever *err says) for phase `parity` of b, so
+// that a CTA whose pipeline gave up does not exit while a bulk copy or an MMA
+// it issued is still writing its shared or tensor memory.
+__device__ __forceinline__ void mbar_drain(uint64_t* b, uint32_t parity) {
+  uint64_t t0 = 0;
+  for (uint32_t i = 0; i < (1u << 26); ++i) {
+    if (mbar_try_wait(b, parity)) return;
+    __nanosleep(256);
+    if ((i & 255u) == 255u) {
+      const uint64_t t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > kWaitBudgetNs) return;
+    }
+  }
+}
+// The last of `issued` TMA loads into each slot of a ring of `slots` full
+// barriers (load j went to slot j % slots, completing phase j / slots).
+__device__ __forceinline__ void tma_drain_ring(uint64_t* full, int slots, int issued) {
+  for (int s = 0; s < slots && s < issued; ++s) {
+    const int j = s + ((issued - 1 - s) / slots) * slots;
+    mbar_drain(&full[s], (uint32_t)(j / slots) & 1u);
+  }
 }
 
 __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1) {

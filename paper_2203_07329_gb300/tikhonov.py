@@ -36,7 +36,8 @@ class tk_opts(C.Structure):
     _fields_ = [("sketch", C.c_int), ("s", C.c_int64), ("precond", C.c_int), ("alpha", C.c_double),
                 ("precision", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int), ("max_refine", C.c_int),
                 ("inner_tol", C.c_double), ("refine_tol", C.c_double), ("seed", C.c_uint64),
-                ("schedule", C.c_int), ("lsqr_tc", C.c_int), ("group", C.c_int), ("emulate_fp64", C.c_int)]
+                ("schedule", C.c_int), ("lsqr_tc", C.c_int), ("group", C.c_int), ("emulate_fp64", C.c_int),
+                ("x0", C.c_void_p)]
 
 
 class tk_info(C.Structure):
@@ -48,7 +49,8 @@ TK_PHASE_COUNT = 14
 
 
 class tk_phase_stats(C.Structure):
-    _fields_ = [("ms", C.c_double), ("flops", C.c_double), ("bytes", C.c_double), ("launches", C.c_int)]
+    _fields_ = [("ms", C.c_double), ("flops", C.c_double), ("bytes", C.c_double), ("launches", C.c_int),
+                ("impl_bytes", C.c_double)]
 
 
 class TikhonovError(RuntimeError):
@@ -101,6 +103,12 @@ def lib() -> C.CDLL:
             "tk_residual_workspace": (SZ, [I64, I64, INT]),
             "tk_residual": (INT, [P, P, INT, I64, INT, P, P, P, SZ, P]),
             "tk_autotune_clear": (None, []),
+            "tk_wait_selftest": (INT, [I64, P, SZ, P]),
+            "tk_create": (INT, [P, P]),
+            "tk_destroy": (INT, [P]),
+            "tk_handle_workspace_bytes": (SZ, [P]),
+            "tk_handle_solve": (INT, [P, P, P, INT, P, P, P]),
+            "tk_handle_solve_batched": (INT, [P, P, INT, P, INT, P, INT, P, P]),
             "tk_autotune_describe": (SZ, [C.c_char_p, SZ]),
         }
         for name, (res, args) in sigs.items():
@@ -183,9 +191,19 @@ def _info_dicts(arr, N):
 
 
 def tk_solve(A: torch.Tensor, b: torch.Tensor, lambdas, opts: tk_opts | None = None, *, work=None, stream=None,
-             X: torch.Tensor | None = None, allow=(TK_OK, TK_ENOCONV, TK_ENOTSPD)) -> SolveResult:
-    """x_{lambda_i} for all lambda_i (problem (1.2)); see tk_solve in include/tikhonov.h."""
+             X: torch.Tensor | None = None, allow=(TK_OK, TK_ENOCONV, TK_ENOTSPD),
+             x0: torch.Tensor | None = None) -> SolveResult:
+    """x_{lambda_i} for all lambda_i (problem (1.2)); see tk_solve in include/tikhonov.h.
+    x0: optional N x n float64 CUDA warm start (sets opts.x0 for this call)."""
     opts = opts or opts_default()
+    if x0 is not None:
+        if not (x0.is_cuda and x0.dtype == torch.float64 and x0.is_contiguous()):
+            raise ValueError("x0 must be a contiguous float64 CUDA tensor (N x n)")
+        if tuple(x0.shape) != (len(lambdas), A.shape[1]):
+            raise ValueError("x0 must be N x n")
+        o2 = tk_opts.from_buffer_copy(opts)
+        o2.x0 = x0.data_ptr()
+        opts = o2
     prob = make_problem(A, b)
     lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
     N = int(lam.shape[0])
@@ -339,7 +357,8 @@ def tk_profile_collect() -> dict:
     arr = (tk_phase_stats * TK_PHASE_COUNT)()
     _check(lib().tk_profile_collect(arr))
     return {lib().tk_phase_name(i).decode(): dict(ms=arr[i].ms, flops=arr[i].flops, bytes=arr[i].bytes,
-                                                   launches=arr[i].launches) for i in range(TK_PHASE_COUNT)}
+                                                   impl_bytes=arr[i].impl_bytes, launches=arr[i].launches)
+            for i in range(TK_PHASE_COUNT)}
 
 
 def tk_launch_count() -> int:
@@ -368,6 +387,12 @@ def tk_autotune_describe() -> str:
     return buf.value.decode()
 
 
+def tk_wait_selftest(budget_us: int, device="cuda", stream=None) -> int:
+    """Status of the bounded-wait self-test (TK_ETIMEOUT when the wait gave up, as it should)."""
+    work = _workspace(16, device)
+    return int(lib().tk_wait_selftest(int(budget_us), _ptr(work), work.numel(), _stream(stream)))
+
+
 def tk_residual(A: torch.Tensor, b: torch.Tensor, X: torch.Tensor, emulate: bool, with_g: bool = False,
                 stream=None):
     """R = b - X A^T (M x m) and, with with_g, G = R A (M x n), float64, for the M rows
@@ -382,3 +407,61 @@ def tk_residual(A: torch.Tensor, b: torch.Tensor, X: torch.Tensor, emulate: bool
     _check(lib().tk_residual(C.byref(prob), _ptr(X), M, X.shape[1], 1 if emulate else 0, _ptr(R), _ptr(G),
                              _ptr(work), work.numel(), _stream(stream)))
     return (R, G) if with_g else R
+
+
+class Handle:
+    """tk_create / tk_destroy: a stream and a library-owned workspace (include/tikhonov.h)."""
+
+    def __init__(self, stream=None):
+        self._h = C.c_void_p(None)
+        _check(lib().tk_create(C.byref(self._h), _stream(stream)))
+
+    def close(self):
+        if self._h:
+            _check(lib().tk_destroy(self._h))
+            self._h = C.c_void_p(None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self) -> int:
+        return int(lib().tk_handle_workspace_bytes(self._h))
+
+    def solve(self, A, b, lambdas, opts=None, X=None, allow=(TK_OK, TK_ENOCONV, TK_ENOTSPD)) -> SolveResult:
+        opts = opts or opts_default()
+        prob = make_problem(A, b)
+        lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+        N = int(lam.shape[0])
+        if X is None:
+            X = torch.empty((N, A.shape[1]), dtype=torch.float64, device=A.device)
+        info = (tk_info * max(N, 1))()
+        st = lib().tk_handle_solve(self._h, C.byref(prob), lam.ctypes.data_as(C.c_void_p), N, C.byref(opts),
+                                   _ptr(X), info)
+        _check(st, allow)
+        return SolveResult(X=X, info=_info_dicts(info, N), status=st)
+
+    def solve_batched(self, problems, lambdas, opts=None, allow=(TK_OK, TK_ENOCONV, TK_ENOTSPD)):
+        P = len(problems)
+        olist = list(opts) if isinstance(opts, (list, tuple)) else [opts or opts_default()]
+        oarr = (tk_opts * len(olist))(*olist)
+        lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+        N = lam.shape[1]
+        probs = (tk_problem * P)(*[make_problem(A, b) for A, b in problems])
+        dev = problems[0][0].device
+        Xs = [torch.empty((N, A.shape[1]), dtype=torch.float64, device=dev) for A, _ in problems]
+        xp = (C.c_void_p * P)(*[x.data_ptr() for x in Xs])
+        info = (tk_info * (P * N))()
+        st = lib().tk_handle_solve_batched(self._h, probs, P, lam.ctypes.data_as(C.c_void_p), N, oarr, len(olist),
+                                           xp, info)
+        _check(st, allow)
+        infos = _info_dicts(info, P * N)
+        return Xs, [infos[p * N:(p + 1) * N] for p in range(P)], st

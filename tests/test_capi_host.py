@@ -140,3 +140,55 @@ def test_emulated_entry_points_validate_on_host(tk):
     assert need_r >= 8 * 2 * (1000 * 128 + 100 * 1024)
     assert L.tk_residual(C.byref(p), fake, 4, 99, 1, fake, None, fake, need_r, None) == tk.TK_EINVAL  # ldx < n
     assert L.tk_residual(C.byref(p), fake, 4, 100, 1, fake, None, fake, need_r - 1, None) == tk.TK_ENOMEM
+
+
+def test_warm_start_arguments_checked_on_host(tk):
+    L = tk.lib()
+    out = C.c_size_t(0)
+    o = tk.opts_default()
+    o.x0 = 0x5000  # a fake device address: validation and sizing never touch it
+    # Algorithm 2 / 4 (m < n) take no warm start
+    assert L.tk_workspace_size(C.byref(_prob(tk, 10, 100)), 2, C.byref(o), C.byref(out)) == tk.TK_EINVAL
+    assert "x0" in tk.last_error()
+    # the float64 form keeps r0 = b - A x0 and -lambda x0 per lambda: a larger workspace
+    cold = tk.opts_default()
+    assert L.tk_workspace_size(C.byref(_prob(tk, 4096, 64)), 4, C.byref(cold), C.byref(out)) == tk.TK_OK
+    w_cold = out.value
+    assert L.tk_workspace_size(C.byref(_prob(tk, 4096, 64)), 4, C.byref(o), C.byref(out)) == tk.TK_OK
+    assert out.value >= w_cold + 8 * 4 * (4096 + 2 * 64)
+    # one warm start cannot serve several problems
+    probs = (tk.tk_problem * 2)(_prob(tk, 500, 20), _prob(tk, 600, 30))
+    assert L.tk_workspace_size_batched(probs, 2, 3, C.byref(o), 1, C.byref(out)) == tk.TK_EINVAL
+
+
+def test_handle_calls_validate_on_host(tk):
+    L = tk.lib()
+    assert L.tk_create(None, None) == tk.TK_EINVAL
+    assert L.tk_destroy(None) == tk.TK_OK
+    assert L.tk_handle_workspace_bytes(None) == 0
+    p = _prob(tk, 100, 10)
+    o = tk.opts_default()
+    lam = np.array([1.0])
+    assert L.tk_handle_solve(None, C.byref(p), lam.ctypes.data_as(C.c_void_p), 1, C.byref(o), C.c_void_p(0x3000),
+                             None) == tk.TK_EINVAL
+    assert L.tk_handle_solve_batched(None, C.byref(p), 1, lam.ctypes.data_as(C.c_void_p), 1, C.byref(o), 1, None,
+                                     None) == tk.TK_EINVAL
+
+
+def test_wait_selftest_validates_on_host(tk):
+    L = tk.lib()
+    fake = C.c_void_p(0x1000)
+    assert L.tk_wait_selftest(0, fake, 16, None) == tk.TK_EINVAL
+    assert L.tk_wait_selftest(3000000, fake, 16, None) == tk.TK_EINVAL
+    assert L.tk_wait_selftest(1000, None, 0, None) == tk.TK_ENOMEM
+    assert L.tk_wait_selftest(1000, fake, 8, None) == tk.TK_ENOMEM
+    assert tk.STATUS_NAMES[tk.TK_ETIMEOUT] == "TK_ETIMEOUT"
+    assert "timed out" in L.tk_status_str(tk.TK_ETIMEOUT).decode()
+
+
+def test_profiler_reports_implementation_bytes_beside_algorithmic(tk):
+    # the stats struct carries both counts; a collect with nothing recorded gives zeros
+    arr = (tk.tk_phase_stats * tk.TK_PHASE_COUNT)()
+    assert tk.lib().tk_profile_collect(arr) == tk.TK_OK
+    assert all(arr[i].bytes == 0.0 and arr[i].impl_bytes == 0.0 for i in range(tk.TK_PHASE_COUNT))
+    assert C.sizeof(tk.tk_phase_stats) == 40
