@@ -146,6 +146,38 @@ def oracle_iteration_sample(A_np, b_np, lam, iters, threads):
     return (time.perf_counter() - t0) / iters
 
 
+def oracle_parallel_sample(A_np, b_np, lams, threads):
+    """Seconds for one oracle LSQR iteration of `threads` lambdas at once, each on its own host
+    thread (the lambda loop is independent, Section 2.1.1; the C oracle releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    n = A_np.shape[1]
+    lam_t = [float(lams[i % len(lams)]) for i in range(threads)]
+    Rs = [np.eye(n) * math.sqrt(1.0 + l) for l in lam_t]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda k: oracle.lsqr_over_chol(A_np, b_np, lam_t[k], Rs[k], 1e-300, 1), range(threads)))
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_baseline(A_np, b_np, lams, ips, reps=2):
+    """The oracle's lambda-solves/s on one host thread and on every core (lambda-parallel).  A lower
+    bound on the oracle's time per lambda-solve: `ips` LSQR iterations, the sketch, Gram matrix and
+    Cholesky factors excluded."""
+    t1 = float(np.mean([oracle_iteration_sample(A_np, b_np, float(lams[0]), 1, 1) for _ in range(reps)]))
+    cores = host_cores()
+    tp = float(np.mean([oracle_parallel_sample(A_np, b_np, lams, cores) for _ in range(reps)]))
+    return {"one_thread": 1.0 / (t1 * ips), "all_cores": cores / (tp * ips), "cores": cores,
+            "s_per_iteration_one_thread": t1, "s_per_iteration_all_cores": tp}
+
+
 def oracle_iters_per_solve():
     """The oracle's own LSQR iteration count at the smallest lambda on a reduced
     problem of the same family (SRHT s = 4n, sigma 1..1e-8, lambda 1e-8)."""
@@ -166,21 +198,21 @@ def run_reference(args):
     import oracle
     from paper_2203_07329_gb300 import datagen
     oracle.build()
-    threads = 1
+    threads = host_cores()
     m, n = (args.m, args.n)
     prob, w = datagen.workload_problem(WORKLOAD, device="cpu", m=m, n=n)
     A_np = prob.A.numpy()
     b_np = prob.b.numpy()
-    lam = float(prob.lambdas[0])
+    lams = prob.lambdas.numpy()
     ips = oracle_iters_per_solve()
-    for _ in range(args.warmup):
-        oracle_iteration_sample(A_np, b_np, lam, 1, threads)
-    times = [oracle_iteration_sample(A_np, b_np, lam, 1, threads) for _ in range(args.steps)]
-    t_iter = float(np.mean(times))
-    value = 1.0 / (t_iter * ips)
-    sample = (f"oracle LSQR iterations (one lambda, full {m}x{n} float64 A, plain C loops, {threads} thread), "
-              f"{args.steps} timed; lambda-solve = {ips} iterations (oracle's own count on the same family); "
-              "sketch, Gram and Cholesky setup excluded")
+    for _ in range(min(args.warmup, 1)):
+        oracle_parallel_sample(A_np, b_np, lams, threads)
+    times = [oracle_parallel_sample(A_np, b_np, lams, threads) for _ in range(args.steps)]
+    t_iter = float(np.mean(times))  # one iteration of `threads` lambdas at once
+    value = threads / (t_iter * ips)
+    sample = (f"oracle LSQR iterations on the full {m}x{n} float64 A (plain C loops), {threads} lambdas at once "
+              f"on {threads} host threads, {args.steps} timed; lambda-solve = {ips} iterations (the oracle's own "
+              "count on the same family); a lower bound on the oracle's time: sketch, Gram and Cholesky excluded")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -280,6 +312,110 @@ def uneven_batch_step(tk, datagen, stream, barrier):
             "phase_ms_summed_over_lanes": {k: v["ms"] for k, v in prof.items() if v["launches"]}}
 
 
+def roofline_of(prof, peaks, peak_src, a_elems):
+    """Roofline line of the phase with the largest event time in `prof` (tk_profile_collect totals over
+    the timed region), judged by that phase's bound; traffic scaled from an ncu capture when one exists."""
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, st = dom
+    bound = PHASE_BOUND.get(name, "fp32")
+    per_launch_ms = st["ms"] / max(st["launches"], 1)
+    secs = st["ms"] / 1e3
+    if bound == "hbm":
+        achieved = st["bytes"] / secs / 1e9 if secs > 0 else 0.0
+        peak, unit = float(peaks["hbm_gbs"]), "GB/s"
+        psrc = f"{peak_src}: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"
+    elif bound == "tensor":
+        achieved = EMULATED_PAIRS * st["flops"] / secs / 1e12 if secs > 0 else 0.0
+        peak, unit = float(peaks["bf16_tflops_sustained"]), "TFLOP/s"
+        psrc = f"{peak_src}: MEASURED_PEAKS.json bf16_tflops_sustained"
+    else:
+        achieved = st["flops"] / secs / 1e12 if secs > 0 else 0.0
+        peak, unit = (PEAK_FP64_TFLOPS if bound == "fp64" else PEAK_FP32_TFLOPS), "TFLOP/s"
+        psrc = "derived from unit counts and max clock (FP64 2 DFMA/clk/SM, FP32 128 FFMA/clk/SM)"
+    # DRAM bytes (read + write) of one launch from an ncu capture of the same kernel on a smaller
+    # case (profiles/), scaled by the elements of A it streams; None for kernels not captured
+    traffic = None
+    if name in MEASURED_TRAFFIC:
+        case_elems, case_bytes = MEASURED_TRAFFIC[name]
+        traffic = case_bytes * a_elems / case_elems
+    roofline = {"bound": bound if bound in ("hbm", "tensor") else "alu", "kernel": name, "achieved": achieved,
+                "peak": peak, "unit": unit, "frac": achieved / peak if peak else None, "traffic": traffic,
+                "algorithmic_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
+                "impl_bytes_per_launch": st["impl_bytes"] / max(st["launches"], 1),
+                "per_launch_ms": per_launch_ms, "launches": st["launches"], "peak_source": psrc}
+    if bound == "hbm" and secs > 0:
+        # what the kernel physically moves (digit planes, copies) beside the method's own bytes
+        roofline["impl_achieved"] = st["impl_bytes"] / secs / 1e9
+        roofline["impl_frac"] = roofline["impl_achieved"] / peak
+    return roofline
+
+
+STREAM_PHASES = ("A_times_W", "At_times_U", "A_times_W_digits", "At_times_U_digits", "refine_residual64",
+                 "refine_normal64")
+
+
+def a_stream_of(prof):
+    """(method GB/s, implementation GB/s) over the phases that stream A (LSQR products, refinement passes)."""
+    ms = sum(prof[k]["ms"] for k in STREAM_PHASES if k in prof)
+    if ms <= 0:
+        return None, None
+    by = sum(prof[k]["bytes"] for k in STREAM_PHASES if k in prof)
+    ib = sum(prof[k]["impl_bytes"] for k in STREAM_PHASES if k in prof)
+    return by / (ms / 1e3) / 1e9, ib / (ms / 1e3) / 1e9
+
+
+def phase_table(prof, steps):
+    return {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] / steps,
+                "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0,
+                "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0,
+                "impl_gbs": (v["impl_bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0}
+            for k, v in prof.items() if v["launches"]}
+
+
+def workload_leg(tk, datagen, stream, barrier, name, make_opts, steps, warmup, peaks, peak_src):
+    """One of the other full-size workloads, timed like the headline: inputs resident in HBM (larger than
+    L2), `warmup` untimed solves, `steps` timed solves with live phase events."""
+    import torch
+    t_gen = time.perf_counter()
+    prob, w = datagen.workload_problem(name, device="cuda")
+    t_gen = time.perf_counter() - t_gen
+    A, b = prob.A, prob.b
+    lams = prob.lambdas.numpy()
+    N = len(lams)
+    o = make_opts(w)
+    work = torch.empty(tk.workspace_size(tk.make_problem(A, b), N, o), dtype=torch.uint8, device="cuda")
+    X = torch.empty((N, A.shape[1]), dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        tk.tk_solve(A, b, lams, o, work=work, X=X, stream=stream)
+    barrier()
+    tk.tk_profile_enable(True)
+    tk.tk_profile_collect()
+    l0 = tk.tk_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        r = tk.tk_solve(A, b, lams, o, work=work, X=X, stream=stream)
+    e1.record(stream)
+    barrier()
+    prof = tk.tk_profile_collect()
+    tk.tk_profile_enable(False)
+    ms = e0.elapsed_time(e1) / steps
+    gbs, igbs = a_stream_of(prof)
+    out = {"value": N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+           "m": int(A.shape[0]), "n": int(A.shape[1]), "N": N, "dtype": str(A.dtype).replace("torch.", ""),
+           "a_bytes": int(A.numel() * A.element_size()), "workspace_bytes": int(work.numel()),
+           "a_stream_gbs": gbs, "a_stream_impl_gbs": igbs,
+           "roofline": roofline_of(prof, peaks, peak_src, A.shape[0] * A.shape[1]),
+           "phases": phase_table(prof, steps), "gpu_launches_per_step": (tk.tk_launch_count() - l0) / steps,
+           "iters_mean": float(np.mean([q["iters"] for q in r.info])),
+           "iters_max": int(max(q["iters"] for q in r.info)),
+           "refine_steps_max": int(max(q["refine_steps"] for q in r.info)),
+           "status_ok": all(q["status"] == 0 for q in r.info), "generate_s": round(t_gen, 1)}
+    del work, X, A, b, prob
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -293,6 +429,8 @@ def main():
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core LSQR comparison step")
     ap.add_argument("--no-uneven", action="store_true", help="skip the 256 uneven problems batch")
     ap.add_argument("--no-small", action="store_true", help="skip the 4096 x 256 workload")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 2048 x 2^18 underdetermined workload")
+    ap.add_argument("--no-c4", action="store_true", help="skip the 2^20 x 4096 float32 precision-form workload")
     ap.add_argument("--no-tune", action="store_true", help="keep the fixed tile rules (no tk_autotune)")
     ap.add_argument("--lsqr-tc", type=int, default=None, choices=[0, 1, 2],
                     help="LSQR products of the timed mixed step: 0 SIMT float32, 1 TF32 x3, 2 4-digit slices "
@@ -425,16 +563,18 @@ def main():
 
     # ---- plain float64 comparisons on the same inputs (one step each)
     if not args.no_fp64:
-        for key, o in (("fp64_batched", o_fp64), ("fp64_one_at_a_time", o_fp64_one)):
-            X64 = torch.empty((N, n), dtype=torch.float64, device="cuda")
+        X64 = torch.empty((N, n), dtype=torch.float64, device="cuda")
+        step(o_fp64, X64)  # warm-up of the float64 kernels (shared by both schedules)
+        for key, o, reps in (("fp64_batched", o_fp64, 2), ("fp64_one_at_a_time", o_fp64_one, 1)):
             barrier()
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-            r64 = step(o, X64)
+            for _ in range(reps):
+                r64 = step(o, X64)
             a1.record(stream)
             barrier()
-            t64 = a0.elapsed_time(a1)
-            extra[key] = {"value": N / (t64 / 1e3), "ms_per_step": t64,
+            t64 = a0.elapsed_time(a1) / reps
+            extra[key] = {"value": N / (t64 / 1e3), "ms_per_step": t64, "timed_steps_after_warmup": reps,
                           "iters_mean": float(np.mean([q["iters"] for q in r64.info]))}
             if key == "fp64_batched":
                 d = (X_mixed - X64).norm(dim=1) / X64.norm(dim=1)
@@ -452,50 +592,9 @@ def main():
 
     # ---- roofline of the dominant phase (live events over the timed region)
     peaks, peak_src = load_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    name, st = dom
-    bound = PHASE_BOUND.get(name, "fp32")
-    per_launch_ms = st["ms"] / max(st["launches"], 1)
-    secs = st["ms"] / 1e3
-    if bound == "hbm":
-        achieved = st["bytes"] / secs / 1e9 if secs > 0 else 0.0
-        peak, unit = float(peaks["hbm_gbs"]), "GB/s"
-        psrc = f"{peak_src}: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"
-    elif bound == "tensor":
-        achieved = EMULATED_PAIRS * st["flops"] / secs / 1e12 if secs > 0 else 0.0
-        peak, unit = float(peaks["bf16_tflops_sustained"]), "TFLOP/s"
-        psrc = f"{peak_src}: MEASURED_PEAKS.json bf16_tflops_sustained"
-    else:
-        achieved = st["flops"] / secs / 1e12 if secs > 0 else 0.0
-        peak, unit = (PEAK_FP64_TFLOPS if bound == "fp64" else PEAK_FP32_TFLOPS), "TFLOP/s"
-        psrc = "derived from unit counts and max clock (FP64 2 DFMA/clk/SM, FP32 128 FFMA/clk/SM)"
-    # DRAM bytes (read + write) of one launch from an ncu capture of the same kernel on a smaller
-    # case (profiles/), scaled by the elements of A it streams; None for kernels not captured
-    traffic = None
-    if name in MEASURED_TRAFFIC:
-        case_elems, case_bytes = MEASURED_TRAFFIC[name]
-        traffic = case_bytes * (m * n) / case_elems
-    roofline = {"bound": bound if bound in ("hbm", "tensor") else "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak if peak else None, "traffic": traffic,
-                "algorithmic_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
-                "impl_bytes_per_launch": st["impl_bytes"] / max(st["launches"], 1),
-                "per_launch_ms": per_launch_ms, "launches": st["launches"], "peak_source": psrc}
-    if bound == "hbm" and secs > 0:
-        # what the kernel physically moves (digit planes, copies) beside the method's own bytes
-        roofline["impl_achieved"] = st["impl_bytes"] / secs / 1e9
-        roofline["impl_frac"] = roofline["impl_achieved"] / peak
-    a_stream_gbs = None
-    streams = ("A_times_W", "At_times_U", "A_times_W_digits", "At_times_U_digits", "refine_residual64",
-               "refine_normal64")
-    lsqr_bytes = sum(prof[k]["bytes"] for k in streams if k in prof)
-    lsqr_ms = sum(prof[k]["ms"] for k in streams if k in prof)
-    if lsqr_ms > 0:
-        a_stream_gbs = lsqr_bytes / (lsqr_ms / 1e3) / 1e9
-    phases = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
-                  "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0,
-                  "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0,
-                  "impl_gbs": (v["impl_bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0}
-              for k, v in prof.items() if v["launches"]}
+    roofline = roofline_of(prof, peaks, peak_src, m * n)
+    a_stream_gbs, a_stream_impl_gbs = a_stream_of(prof)
+    phases = phase_table(prof, args.steps)
 
     # ---- CPU oracle sample (rank 0 only, N = 1 only)
     cpu = None
@@ -506,12 +605,31 @@ def main():
             A_np = A.cpu().numpy()
             b_np = b.cpu().numpy()
             ips = oracle_iters_per_solve()
-            t_it = np.mean([oracle_iteration_sample(A_np, b_np, float(lams[0]), 1, 1) for _ in range(2)])
-            cpu = {"value": 1.0 / (t_it * ips), "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"2 oracle LSQR iterations on the full {m}x{n} float64 A (one lambda, 1 thread); "
-                             f"lambda-solve = {ips} iterations; setup excluded"}
+            ob = oracle_baseline(A_np, b_np, lams, ips)
+            cpu = {"value": ob["all_cores"], "unit": UNIT, "cores": ob["cores"], "kind": "oracle",
+                   "one_thread_value": ob["one_thread"],
+                   "sample": f"oracle LSQR iterations on the full {m}x{n} float64 A (plain C loops): 2 timed "
+                             f"iterations of one lambda on 1 thread, and 2 of {ob['cores']} lambdas at once on "
+                             f"{ob['cores']} host threads; lambda-solve = {ips} iterations (the oracle's own count "
+                             "on the same family); a lower bound on the oracle's time per lambda-solve: sketch, "
+                             "Gram and Cholesky excluded"}
         except Exception as ex:  # the baseline is reported, never the target
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    # ---- the other full-size workloads (the headline's buffers freed first)
+    h2d_bytes = int(A.numel() * A.element_size() + b.numel() * 8)
+    del work, X, A, b
+    torch.cuda.empty_cache()
+    if not args.no_c4:
+        extra["precision_form_1048576x4096_f32"] = workload_leg(
+            tk, datagen, stream, barrier, "ridge_over_1048576x4096_f32",
+            lambda w: tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=w["s"], seed=1, precision=tk.TK_PREC_MIXED),
+            steps=2, warmup=1, peaks=peaks, peak_src=peak_src)
+    if not args.no_c3:
+        extra["under_2048x262144_f64"] = workload_leg(
+            tk, datagen, stream, barrier, "ridge_under_2048x262144_f64",
+            lambda w: tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=w["s"], seed=1, tol=1e-14),
+            steps=2, warmup=1, peaks=peaks, peak_src=peak_src)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -521,10 +639,11 @@ def main():
                            "precision": "mixed (float32 LSQR, float64 refinement, Gram and Cholesky)",
                            "schedule": "batched", "l2": "inputs larger than L2 (A is 4 GiB)",
                            "parallelism": f"{ws} independent replicas" if ws > 1 else "1 GPU"},
-                "roofline": roofline, "a_stream_gbs": a_stream_gbs, "phases": phases,
+                "roofline": roofline, "a_stream_gbs": a_stream_gbs, "a_stream_impl_gbs": a_stream_impl_gbs,
+                "phases": phases,
                 "cpu_baseline": cpu,
                 "e2e": {"value": ws * N / (e2e_ms / 1e3), "unit": UNIT,
-                        "h2d_bytes_per_step": int(A.numel() * A.element_size() + b.numel() * 8),
+                        "h2d_bytes_per_step": h2d_bytes,
                         "d2h_bytes_per_step": int(N * n * 8)},
                 "gpu_launches": int(launches), "clocks": clk,
                 "iters_mean": float(np.mean([q["iters"] for q in info_mixed])),

@@ -76,6 +76,9 @@ def lib():
                 "orc_sd_estimate": (_d, [_p, _i64, _d]),
                 "orc_truncation": (_i64, [_d, _d, _i64]),
                 "orc_lr_diag": (None, [_p, _i64, _d, _p]),
+                "orc_lcurve_norms": (None, [_p, _i64, _i64, _i64, _p, _p, _int, _p, _p]),
+                "orc_lcurve_curvature": (_int, [_p, _p, _p, _int, _p]),
+                "orc_lcurve_refine_grid": (None, [_p, _int, _int, _int, _p]),
                 "orc_alg1": (_int, [_p, _i64, _i64, _i64, _p, _p, _int, _int, _i64, _u64, _d, _int, _p, _p, _p]),
                 "orc_alg2": (_int, [_p, _i64, _i64, _i64, _p, _p, _int, _int, _i64, _u64, _d, _int, _p, _p, _p]),
                 "orc_alg3": (_int, [_p, _i64, _i64, _i64, _p, _p, _int, _int, _i64, _d, _u64, _d, _int, _p, _p, _p,
@@ -433,3 +436,54 @@ def alg4(A, b, lambdas, sketch_kind: int, s: int, alpha: float, seed: int, tol: 
     lib().orc_alg4(_ptr(A), m, n, lda, _ptr(b), _ptr(lam), N, sketch_kind, s, alpha, seed, tol, maxiter, _ptr(X),
                    _ptr(it), _ptr(st), _ptr(si), _ptr(sig))
     return X, it, st, si, sig
+
+
+# ------------------------------------------------------------- L-curve ----
+def lcurve_norms(A, b, X):
+    """(||b - A x_i||, ||x_i||) for the rows x_i of X (Section 4.3)."""
+    A, m, n, lda = _dims(A)
+    b = _f64(b)
+    X = _f64(np.atleast_2d(X))
+    N = X.shape[0]
+    rn, xn = np.zeros(N), np.zeros(N)
+    lib().orc_lcurve_norms(_ptr(A), m, n, lda, _ptr(b), _ptr(X), N, _ptr(rn), _ptr(xn))
+    return rn, xn
+
+
+def lcurve_curvature(lambdas, rn, xn):
+    """Curvature of (ln ||Ax-b||, ln ||x||) in t = ln lambda on an ascending grid, and the corner
+    index (largest interior curvature; Section 4.3 read as Hansen's maximum-curvature corner)."""
+    lam, rn, xn = _f64(lambdas), _f64(rn), _f64(xn)
+    N = lam.shape[0]
+    kap = np.zeros(N)
+    k = lib().orc_lcurve_curvature(_ptr(lam), _ptr(rn), _ptr(xn), N, _ptr(kap))
+    return kap, int(k)
+
+
+def lcurve_refine_grid(lambdas, k, nr):
+    """nr parameters log-spaced strictly between the corner's neighbours."""
+    lam = _f64(lambdas)
+    out = np.zeros(nr)
+    lib().orc_lcurve_refine_grid(_ptr(lam), lam.shape[0], int(k), int(nr), _ptr(out))
+    return out
+
+
+def lcurve(A, b, lambdas, nr, refine=3):
+    """The two-sweep L-curve of Section 4.3 from the dense reference solutions: coarse sweep over the
+    ascending `lambdas`, corner, `nr` parameters between the corner's neighbours, the corner of the
+    merged grid.  Returns (lambdas merged ascending, rn, xn, kappa, corner index, X merged)."""
+    lam = np.sort(_f64(lambdas))
+    X1 = np.stack([ref_ridge_qr(A, b, float(l), refine=refine) for l in lam])
+    rn1, xn1 = lcurve_norms(A, b, X1)
+    _, k = lcurve_curvature(lam, rn1, xn1)
+    lam2 = lcurve_refine_grid(lam, k, nr)
+    X2 = np.stack([ref_ridge_qr(A, b, float(l), refine=refine) for l in lam2])
+    rn2, xn2 = lcurve_norms(A, b, X2)
+    allm = np.concatenate([lam, lam2])
+    order = np.argsort(allm, kind="stable")
+    lamm = allm[order]
+    rnm = np.concatenate([rn1, rn2])[order]
+    xnm = np.concatenate([xn1, xn2])[order]
+    Xm = np.concatenate([X1, X2])[order]
+    kap, km = lcurve_curvature(lamm, rnm, xnm)
+    return lamm, rnm, xnm, kap, km, Xm

@@ -930,3 +930,67 @@ ORC_API void orc_ref_ridge_refine(const double* A, int64_t m, int64_t n, int64_t
   }
   free(g); free(c);
 }
+
+/* ------------------------------------------------------------------------ */
+/* L-curve (Section 4.3, Fig. 4): for each lambda_i the points                */
+/* (||A x_i - b||, ||x_i||) on a log-log plot; the regularization parameter   */
+/* of choice sits at the corner.  The paper does not say how the corner is    */
+/* found; the reading taken here is Hansen's: the point of maximum curvature  */
+/* of the curve P(t) = ln ||A x - b||, Q(t) = ln ||x||, t = ln lambda,        */
+/*   kappa = (P' Q'' - P'' Q') / (P'^2 + Q'^2)^(3/2),                          */
+/* with the derivatives taken as three-point differences on the (possibly     */
+/* non-uniform) grid of sampled t.  The first and last points have no         */
+/* curvature (0) and are never the corner.                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Norms of the residual and of x for each row of X (N x n): rn[i] =
+ * ||b - A x_i||, xn[i] = ||x_i||, plain float64 sums. */
+ORC_API void orc_lcurve_norms(const double* A, int64_t m, int64_t n, int64_t lda, const double* b, const double* X,
+                              int N, double* rn, double* xn) {
+  for (int i = 0; i < N; ++i) {
+    const double* x = X + (int64_t)i * n;
+    double rr = 0.0, xx = 0.0;
+    for (int64_t r = 0; r < m; ++r) {
+      double v = b[r];
+      for (int64_t j = 0; j < n; ++j) v -= A[r * lda + j] * x[j];
+      rr += v * v;
+    }
+    for (int64_t j = 0; j < n; ++j) xx += x[j] * x[j];
+    rn[i] = sqrt(rr);
+    xn[i] = sqrt(xx);
+  }
+}
+
+/* Curvature of the sampled L-curve.  lambdas ascending (N >= 3), rn, xn > 0.
+ * kappa[0] = kappa[N-1] = 0.  Returns the index of the largest kappa over
+ * 1..N-2 (the first one on ties), or -1 if N < 3. */
+ORC_API int orc_lcurve_curvature(const double* lambdas, const double* rn, const double* xn, int N, double* kappa) {
+  for (int i = 0; i < N; ++i) kappa[i] = 0.0;
+  if (N < 3) return -1;
+  int best = 1;
+  for (int k = 1; k < N - 1; ++k) {
+    const double t0 = log(lambdas[k - 1]), t1 = log(lambdas[k]), t2 = log(lambdas[k + 1]);
+    const double h1 = t1 - t0, h2 = t2 - t1;
+    const double P0 = log(rn[k - 1]), P1 = log(rn[k]), P2 = log(rn[k + 1]);
+    const double Q0 = log(xn[k - 1]), Q1 = log(xn[k]), Q2 = log(xn[k + 1]);
+    /* first derivative: weights of the quadratic through the three points */
+    const double a0 = -h2 / (h1 * (h1 + h2)), a1 = (h2 - h1) / (h1 * h2), a2 = h1 / (h2 * (h1 + h2));
+    /* second derivative */
+    const double c0 = 2.0 / (h1 * (h1 + h2)), c1 = -2.0 / (h1 * h2), c2 = 2.0 / (h2 * (h1 + h2));
+    const double dP = a0 * P0 + a1 * P1 + a2 * P2, dQ = a0 * Q0 + a1 * Q1 + a2 * Q2;
+    const double ddP = c0 * P0 + c1 * P1 + c2 * P2, ddQ = c0 * Q0 + c1 * Q1 + c2 * Q2;
+    const double den = pow(dP * dP + dQ * dQ, 1.5);
+    kappa[k] = den > 0.0 ? (dP * ddQ - ddP * dQ) / den : 0.0;
+    if (kappa[k] > kappa[best]) best = k;
+  }
+  return best;
+}
+
+/* The second sweep around a corner at index k of the ascending grid: nr
+ * parameters log-spaced strictly between lambdas[k-1] and lambdas[k+1],
+ *   lambda_j = exp(t_{k-1} + (t_{k+1} - t_{k-1}) j / (nr + 1)),  j = 1..nr. */
+ORC_API void orc_lcurve_refine_grid(const double* lambdas, int N, int k, int nr, double* out) {
+  const int lo = k > 0 ? k - 1 : 0, hi = k < N - 1 ? k + 1 : N - 1;
+  const double a = log(lambdas[lo]), b = log(lambdas[hi]);
+  for (int j = 1; j <= nr; ++j) out[j - 1] = exp(a + (b - a) * (double)j / (double)(nr + 1));
+}
