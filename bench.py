@@ -430,6 +430,7 @@ def main():
     ap.add_argument("--no-uneven", action="store_true", help="skip the 256 uneven problems batch")
     ap.add_argument("--no-small", action="store_true", help="skip the 4096 x 256 workload")
     ap.add_argument("--no-c3", action="store_true", help="skip the 2048 x 2^18 underdetermined workload")
+    ap.add_argument("--no-lcurve", action="store_true", help="skip the L-curve sweep on the headline workload")
     ap.add_argument("--no-c4", action="store_true", help="skip the 2^20 x 4096 float32 precision-form workload")
     ap.add_argument("--no-tune", action="store_true", help="keep the fixed tile rules (no tk_autotune)")
     ap.add_argument("--lsqr-tc", type=int, default=None, choices=[0, 1, 2],
@@ -615,6 +616,32 @@ def main():
                              "Gram and Cholesky excluded"}
         except Exception as ex:  # the baseline is reported, never the target
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    # ---- the L-curve of Section 4.3 on the headline's A: 32 lambda in 1e-10..1, then 16 between the
+    #      corner's neighbours with the sketch, Gram matrix and digit planes reused (one call)
+    if not args.no_lcurve:
+        lam_lc = np.logspace(-10, 0, 32)
+        need = tk.lcurve_workspace_size(A, b, 32, 16, o_mixed)
+        work_lc = torch.empty(need, dtype=torch.uint8, device="cuda")
+        tk.tk_lcurve(A, b, lam_lc, 16, o_mixed, work=work_lc, stream=stream)  # warm-up
+        barrier()
+        tk.tk_profile_enable(True)
+        tk.tk_profile_collect()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        _, pts_lc, k_lc = tk.tk_lcurve(A, b, lam_lc, 16, o_mixed, work=work_lc, stream=stream)
+        c1.record(stream)
+        barrier()
+        prof_lc = tk.tk_profile_collect()
+        tk.tk_profile_enable(False)
+        t_lc = c0.elapsed_time(c1)
+        extra["lcurve_262144x2048_mixed"] = {
+            "value": len(pts_lc) / (t_lc / 1e3), "unit": UNIT, "ms_per_call": t_lc,
+            "lambdas": len(pts_lc), "sweeps": "32 log-spaced in 1e-10..1, then 16 between the corner's neighbours",
+            "corner_lambda": pts_lc[k_lc]["lam"], "corner_curvature": pts_lc[k_lc]["curvature"],
+            "status_ok": all(q["status"] == 0 for q in pts_lc),
+            "phase_ms": {k2: round(v["ms"], 3) for k2, v in prof_lc.items() if v["launches"]}}
+        del work_lc
 
     # ---- the other full-size workloads (the headline's buffers freed first)
     h2d_bytes = int(A.numel() * A.element_size() + b.numel() * 8)

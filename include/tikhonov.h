@@ -161,6 +161,43 @@ TK_API tk_status tk_solve_batched(const tk_problem* ps, int P, const double* lam
                                   tk_info* info);
 
 /*
+ * tk_lcurve -- the L-curve of Section 4.3 (Fig. 4): x_{lambda_i} for every
+ * lambda_i, the points (||A x_i - b||, ||x_i||) of the log-log plot, and the
+ * corner, where the regularization parameter of choice sits.  The paper does
+ * not say how the corner is found; here it is the point of largest curvature
+ * kappa = (P' Q'' - P'' Q') / (P'^2 + Q'^2)^(3/2) of P = ln ||A x - b||,
+ * Q = ln ||x|| as functions of t = ln lambda (Hansen's criterion), with the
+ * derivatives taken as three-point differences on the sampled grid (the end
+ * points have kappa = 0 and are never the corner).
+ *   Sweep 1: the N lambdas (any order; solved ascending).  Sweep 2 (N_refine
+ *   > 0): N_refine parameters log-spaced strictly between the two neighbours
+ *   of sweep 1's corner, solved with the same sketch, Gram matrix (or SVD of
+ *   the sketch), copies and digit planes of A -- only the per-lambda
+ *   factorizations and LSQR run again.  The corner is then taken on the
+ *   merged grid.
+ *   ||A x - b|| is formed from x in float64 (the digit residual of the mixed
+ *   form with emulate_fp64, else the float64 pipe), not from LSQR estimates.
+ *   N >= 3, N + N_refine <= 4096, o->x0 must be NULL.
+ *   X:      device, (N + N_refine) x n float64, rows in the order of points.
+ *   points: host, N + N_refine entries, ascending lambda.
+ *   corner: host, index of the corner in points.
+ *   work:   device, tk_lcurve_workspace_size() bytes.
+ * Returns the worst per-lambda status (as tk_solve).  Synchronizes `stream`.
+ */
+typedef struct {
+  double lambda;
+  double rnorm;      /* ||A x_lambda - b|| */
+  double xnorm;      /* ||x_lambda|| */
+  double curvature;  /* kappa at this point (0 at both ends of the grid) */
+  int iters;         /* LSQR iterations (summed over refinement rounds for MIXED) */
+  tk_status status;
+} tk_lcurve_point;
+TK_API tk_status tk_lcurve_workspace_size(const tk_problem* p, int N, int N_refine, const tk_opts* o, size_t* bytes);
+TK_API tk_status tk_lcurve(const tk_problem* p, const double* lambdas, int N, int N_refine, const tk_opts* o,
+                           void* work, size_t work_bytes, void* stream, double* X, tk_lcurve_point* points,
+                           int* corner);
+
+/*
  * Handle calls -- the same solves for callers that prefer the library to own
  * the workspace (problem (1.2) as in tk_solve; no counterpart in the paper
  * beyond the solve itself).  A handle holds a stream (void* cudaStream_t,

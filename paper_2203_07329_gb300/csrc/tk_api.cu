@@ -2,6 +2,7 @@
 // the steps of Algorithms 1, 2 and 3 (and the mixed-precision refinement
 // around Algorithm 1).  Every numerical step runs in the kernels of the other
 // translation units; this file only sequences them.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -401,14 +402,24 @@ tk_status lowrank_finish(const LowRankParts& L, tk_info* inf, std::vector<int>& 
 }
 
 // ------------------------------------------------------------ solve -------
+// A sweep of several solves over one workspace (the L-curve's second sweep):
+// the workspace is carved for N_plan lambdas whatever this solve's N, and with
+// `reuse` the previous solve's float32 copy of A, sketch, Gram matrix (or SVD
+// of the sketch) and digit planes of A are taken as they are.
+struct SweepCtx {
+  int N_plan = 0;
+  bool reuse = false;
+};
+
 // With gp (grouped batch) only the preconditioner is built: `work` receives
 // what the grouped LSQR reads, `scratch` the build-only buffers, and gp the
 // pointers and the lambdas that have a preconditioner.
 tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk_opts* o, void* work,
                      size_t work_bytes, cudaStream_t st, double* X, tk_info* info, GroupProblem* gp = nullptr,
-                     void* scratch = nullptr, size_t scratch_bytes = 0) {
+                     void* scratch = nullptr, size_t scratch_bytes = 0, const SweepCtx* sw = nullptr) {
   Plan P;
-  TK_TRY(make_plan(p, N, o, P));
+  TK_TRY(make_plan(p, sw ? std::max(N, sw->N_plan) : N, o, P));
+  const bool reuse = sw && sw->reuse;
   P.prep_only = gp != nullptr;
   if (N == 0) return TK_OK;
   if (!lambdas) return einval("lambdas pointer is NULL");
@@ -454,13 +465,17 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
   const float* A32 = (P.dt == TK_F32) ? (const float*)p->A : nullptr;
   int64_t lda64 = P.lda, lda32 = P.lda;
   if (P.mixed && P.dt == TK_F64) {
-    TK_TRY(convert_f64_to_f32((const double*)p->A, B.A32, P.m, P.n, P.lda, P.n, st));
+    if (!reuse) {
+      const int tok = prof_begin(TK_PHASE_SLICE, st);  // a copy of A made once per solve, like the digit planes
+      TK_TRY(convert_f64_to_f32((const double*)p->A, B.A32, P.m, P.n, P.lda, P.n, st));
+      prof_end(tok, st, 0.0, 12.0 * P.m * P.n);
+    }
     A32 = B.A32;
     lda32 = P.n;
   }
   if (!P.mixed && P.dt == TK_F32) {
     // the plain float64 path on float32 data: widen A once (exact)
-    k_widen<<<gsz(P.m * P.n), 256, 0, st>>>((const float*)p->A, P.m, P.n, P.lda, B.A64);
+    if (!reuse) k_widen<<<gsz(P.m * P.n), 256, 0, st>>>((const float*)p->A, P.m, P.n, P.lda, B.A64);
     TK_LAUNCH_CHECK();
     A64 = B.A64;
     lda64 = P.n;
@@ -475,7 +490,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
   }
 
   // ---- step 1-2: draw X and sketch Y = XA (or A X)
-  {
+  if (!reuse) {
     const double es = dt_sk == TK_F64 ? 8.0 : 4.0;
     const double Lp = (double)next_pow2(P.L);
     const double fl = P.o.sketch == TK_SKETCH_SRHT ? Lp * std::log2(Lp) * P.c : 2.0 * P.s * P.L * P.c;
@@ -487,14 +502,17 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
   // ---- steps 3-4 (Cholesky) or 4-7 (low rank)
   std::vector<int> ok_ids;
   if (!P.lowrank) {
-    int tok = prof_begin(TK_PHASE_GRAM, st);
-    if (emulated_gram(P)) {  // the Cholesky reads only j >= i
-      TK_CUDA(cudaMemsetAsync(B.oz_err, 0, sizeof(int), st));
-      TK_TRY(oz_gram(B.Y, P.s, P.c, B.C, B.scratch, B.scratch_bytes, B.oz_err, st));
-    } else {
-      TK_TRY(gram_upper(B.Y, P.s, P.c, B.C, B.scratch, B.scratch_bytes, st));
+    int tok = -1;
+    if (emulated_gram(P)) TK_CUDA(cudaMemsetAsync(B.oz_err, 0, sizeof(int), st));
+    if (!reuse) {
+      tok = prof_begin(TK_PHASE_GRAM, st);
+      if (emulated_gram(P)) {  // the Cholesky reads only j >= i
+        TK_TRY(oz_gram(B.Y, P.s, P.c, B.C, B.scratch, B.scratch_bytes, B.oz_err, st));
+      } else {
+        TK_TRY(gram_upper(B.Y, P.s, P.c, B.C, B.scratch, B.scratch_bytes, st));
+      }
+      prof_end(tok, st, (double)P.s * P.c * (P.c + 1), 8.0 * (P.s * P.c + P.c * (P.c + 1) / 2));
     }
-    prof_end(tok, st, (double)P.s * P.c * (P.c + 1), 8.0 * (P.s * P.c + P.c * (P.c + 1) / 2));
     Arena none;
     OzCholPlan ozp;  // the trailing updates on the tensor cores (the Gram scratch is free again)
     if (emulated_gram(P)) {  // chol_shifted times its float64 and tensor-core parts itself
@@ -534,9 +552,11 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     sa.base = B.svd;
     sa.cap = B.svd_bytes;
     int sweeps = 0;
-    int tok = prof_begin(TK_PHASE_SVD, st);
-    TK_TRY(jacobi_svd(B.Y, P.s, P.c, B.sig, B.lrV, &sweeps, sa, st));
-    prof_end(tok, st, 3.5 * sweeps * (double)P.s * P.s * P.c, 8.0 * P.s * P.c);
+    if (!reuse) {  // sigma and V of the sketch are kept from the previous solve of the sweep
+      int tok = prof_begin(TK_PHASE_SVD, st);
+      TK_TRY(jacobi_svd(B.Y, P.s, P.c, B.sig, B.lrV, &sweeps, sa, st));
+      prof_end(tok, st, 3.5 * sweeps * (double)P.s * P.s * P.c, 8.0 * P.s * P.c);
+    }
     LowRankParts L{P.s, P.c, N, P.o.alpha, B.lam, B.sig, B.sd, B.ranks, B.lrV, B.lrS,
                    P.mixed ? B.lrV32 : nullptr, P.mixed ? B.lrS32 : nullptr};
     TK_TRY(lowrank_finish(L, inf.data(), ok_ids, st));
@@ -647,11 +667,13 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     std::vector<double> hn(3 * std::max(N, 1));
     std::vector<double> prev_dn(std::max(N, 1), INFINITY);
     if (P.o.emulate_fp64 && !act.empty()) {  // A is split once (by rows and by columns); x, r on every pass
-      const int tok = prof_begin(TK_PHASE_SLICE, st);
-      TK_TRY(oz_prepare(p->A, P.dt, P.m, P.n, P.lda, B.Aoz, B.EA, st));
-      TK_TRY(oz_prepare_cols(p->A, P.dt, P.m, P.n, P.lda, B.AozC, B.EC, B.colmax, st));
+      if (!reuse) {
+        const int tok = prof_begin(TK_PHASE_SLICE, st);
+        TK_TRY(oz_prepare(p->A, P.dt, P.m, P.n, P.lda, B.Aoz, B.EA, st));
+        TK_TRY(oz_prepare_cols(p->A, P.dt, P.m, P.n, P.lda, B.AozC, B.EC, B.colmax, st));
+        prof_end(tok, st, 0.0, 2.0 * ((P.dt == TK_F64 ? 16.0 : 8.0) * P.m * P.n + 16.0 * P.m * P.n));
+      }
       TK_CUDA(cudaMemsetAsync(B.oz_err, 0, sizeof(int), st));
-      prof_end(tok, st, 0.0, 2.0 * ((P.dt == TK_F64 ? 16.0 : 8.0) * P.m * P.n + 16.0 * P.m * P.n));
       if (P.lsqr_oz) {  // the LSQR products read the first 4 digits of the same slices
         e.oz_A = B.Aoz; e.oz_EA = B.EA; e.oz_AT = B.AozC; e.oz_EAT = B.EC; e.oz_err = B.oz_err;
       }
@@ -752,6 +774,132 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     for (int i = 0; i < N; ++i) info[i] = inf[i];
   TK_CUDA(cudaStreamSynchronize(st));
   return worst;
+}
+
+// ------------------------------------------------------------ L-curve -----
+// Section 4.3: the points (||A x_i - b||, ||x_i||) of every lambda_i on a
+// log-log plot, the regularization parameter of choice at the corner.  The
+// corner is the point of largest curvature of P(t) = ln ||A x - b||,
+// Q(t) = ln ||x|| in t = ln lambda (Hansen's reading; the paper does not say
+// how the corner is found), with three-point differences on the sampled grid.
+
+// rn[k] = ||R_k|| (row k of R, length m), xn[k] = ||X_k|| (length n); one block per row.
+__global__ void k_lc_norms(const double* __restrict__ R, int64_t m, const double* __restrict__ X, int64_t n,
+                           double* __restrict__ rn, double* __restrict__ xn) {
+  __shared__ double sh[32];
+  const int k = blockIdx.x;
+  double rr = 0.0, xx = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const double v = R[(int64_t)k * m + i];
+    rr = fma(v, v, rr);
+  }
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = X[(int64_t)k * n + j];
+    xx = fma(v, v, xx);
+  }
+  rr = block_sum(rr, sh);
+  xx = block_sum(xx, sh);
+  if (threadIdx.x == 0) {
+    rn[k] = sqrt(rr);
+    xn[k] = sqrt(xx);
+  }
+}
+
+// Curvature on the ascending grid lam[0..N): kappa[0] = kappa[N-1] = 0; the
+// corner is the first largest interior kappa (*corner = -1 if N < 3).  With
+// nr > 0, also the second sweep: nr parameters log-spaced strictly between the
+// corner's neighbours.  One thread: N is a few dozen.
+__global__ void k_lc_curvature(const double* __restrict__ lam, const double* __restrict__ rn,
+                               const double* __restrict__ xn, int N, double* __restrict__ kappa,
+                               int* __restrict__ corner, int nr, double* __restrict__ next) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < N; ++i) kappa[i] = 0.0;
+  if (N < 3) {
+    *corner = -1;
+    return;
+  }
+  int best = 1;
+  for (int k = 1; k < N - 1; ++k) {
+    const double t0 = log(lam[k - 1]), t1 = log(lam[k]), t2 = log(lam[k + 1]);
+    const double h1 = t1 - t0, h2 = t2 - t1;
+    const double p0 = log(rn[k - 1]), p1 = log(rn[k]), p2 = log(rn[k + 1]);
+    const double q0 = log(xn[k - 1]), q1 = log(xn[k]), q2 = log(xn[k + 1]);
+    // derivatives of the quadratic through the three samples, at the middle one
+    const double w0 = -h2 / (h1 * (h1 + h2)), w1 = (h2 - h1) / (h1 * h2), w2 = h1 / (h2 * (h1 + h2));
+    const double v0 = 2.0 / (h1 * (h1 + h2)), v1 = -2.0 / (h1 * h2), v2 = 2.0 / (h2 * (h1 + h2));
+    const double dp = __dmul_rn(w0, p0) + __dmul_rn(w1, p1) + __dmul_rn(w2, p2);
+    const double dq = __dmul_rn(w0, q0) + __dmul_rn(w1, q1) + __dmul_rn(w2, q2);
+    const double ddp = __dmul_rn(v0, p0) + __dmul_rn(v1, p1) + __dmul_rn(v2, p2);
+    const double ddq = __dmul_rn(v0, q0) + __dmul_rn(v1, q1) + __dmul_rn(v2, q2);
+    const double den = pow(__dmul_rn(dp, dp) + __dmul_rn(dq, dq), 1.5);
+    kappa[k] = den > 0.0 ? (__dmul_rn(dp, ddq) - __dmul_rn(ddp, dq)) / den : 0.0;
+    if (kappa[k] > kappa[best]) best = k;
+  }
+  *corner = best;
+  if (nr > 0) {
+    const double a = log(lam[best - 1]), b = log(lam[best + 1]);
+    for (int j = 1; j <= nr; ++j) next[j - 1] = exp(a + (b - a) * (double)j / (double)(nr + 1));
+  }
+}
+
+// out[k] = in[perm[k]] for k < N (doubles), and the rows of X likewise (length n)
+__global__ void k_lc_permute(const int* __restrict__ perm, int N, const double* __restrict__ in,
+                             double* __restrict__ out) {
+  for (int k = threadIdx.x; k < N; k += blockDim.x) out[k] = in[perm[k]];
+}
+
+struct LcBufs {
+  double* R = nullptr;     // N_plan x m residuals
+  double* Xs = nullptr;    // N_plan x n: rows in sweep order, then permuted
+  double* lam = nullptr;   // N_plan (sweep order)
+  double* rn = nullptr;
+  double* xn = nullptr;
+  double* lam_m = nullptr;  // merged, ascending
+  double* rn_m = nullptr;
+  double* xn_m = nullptr;
+  double* kappa = nullptr;
+  double* next = nullptr;   // the second sweep's parameters
+  int* perm = nullptr;
+  int* corner = nullptr;
+};
+void lc_carve(Arena& a, int64_t m, int64_t n, int Np, LcBufs& L) {
+  L.R = a.take<double>((size_t)Np * m);
+  L.Xs = a.take<double>((size_t)Np * n);
+  L.lam = a.take<double>(Np);
+  L.rn = a.take<double>(Np);
+  L.xn = a.take<double>(Np);
+  L.lam_m = a.take<double>(Np);
+  L.rn_m = a.take<double>(Np);
+  L.xn_m = a.take<double>(Np);
+  L.kappa = a.take<double>(Np);
+  L.next = a.take<double>(Np);
+  L.perm = a.take<int>(Np);
+  L.corner = a.take<int>(4);
+}
+
+// rn, xn of the `cnt` solutions X (rows, length n) into rn[off..], xn[off..]:
+// r = b - X A^T in float64 (on the tensor cores from the digit planes of A
+// when the mixed form made them, else on the float64 pipe).
+tk_status lc_norms(const tk_problem* p, const Plan& P, Bufs& B, const LcBufs& L, const double* Xrows, int cnt,
+                   int off, cudaStream_t st) {
+  if (cnt <= 0) return TK_OK;
+  if (P.mixed && P.o.emulate_fp64) {
+    TK_TRY(oz_prepare(Xrows, TK_F64, cnt, P.n, P.n, B.Xoz, B.EX, st));
+    TK_TRY(oz_residual(B.Aoz, B.EA, P.m, P.n, B.Xoz, B.EX, cnt, p->b, L.R, P.m, B.oz_err, st));
+  } else {
+    k_bcast<<<rgrid(P.m, cnt), 256, 0, st>>>(p->b, P.m, L.R, cnt);
+    k_fill<<<1, 256, 0, st>>>(B.ones, cnt, 1.0);
+    TK_LAUNCH_CHECK();
+    if (P.dt == TK_F64)
+      TK_TRY((gemm<double, double, double>(false, true, cnt, P.m, P.n, Xrows, P.n, (const double*)p->A, P.lda, L.R,
+                                           P.m, -1.0, B.ones, L.R, P.m, st)));
+    else
+      TK_TRY((gemm<double, float, double>(false, true, cnt, P.m, P.n, Xrows, P.n, (const float*)p->A, P.lda, L.R,
+                                          P.m, -1.0, B.ones, L.R, P.m, st)));
+  }
+  k_lc_norms<<<cnt, 256, 0, st>>>(L.R, P.m, Xrows, P.n, L.rn + off, L.xn + off);
+  TK_LAUNCH_CHECK();
+  return TK_OK;
 }
 
 }  // namespace
@@ -1414,6 +1562,129 @@ TK_API tk_status tk_lowrank_ranks(const double* sigma, int64_t s, const double* 
   TK_CUDA(cudaMemcpyAsync(ranks, rk, sizeof(int64_t) * N, cudaMemcpyDeviceToHost, st));
   TK_CUDA(cudaStreamSynchronize(st));
   return TK_OK;
+}
+
+// ---- L-curve (Section 4.3) ----------------------------------------------------
+namespace {
+tk_status lcurve_plan(const tk_problem* p, int N, int N_refine, const tk_opts* o, Plan& P, size_t& plan_b,
+                      size_t& total) {
+  if (N < 3) return einval("tk_lcurve: at least 3 lambdas are needed for a curvature");
+  if (N_refine < 0 || N + N_refine > 4096) return einval("tk_lcurve: N_refine must be >= 0 and N + N_refine <= 4096");
+  if (o && o->x0) return einval("tk_lcurve: no warm start (x0) in an L-curve sweep");
+  TK_TRY(make_plan(p, N + N_refine, o, P));
+  plan_b = (plan_bytes(P) + 255) & ~size_t(255);
+  Arena a;
+  LcBufs L;
+  lc_carve(a, P.m, P.n, N + N_refine, L);
+  total = plan_b + a.used + 4096;
+  return TK_OK;
+}
+}  // namespace
+
+TK_API tk_status tk_lcurve_workspace_size(const tk_problem* p, int N, int N_refine, const tk_opts* o,
+                                          size_t* bytes) {
+  if (!bytes) return einval("bytes pointer is NULL");
+  Plan P;
+  size_t pb = 0, tot = 0;
+  TK_TRY(lcurve_plan(p, N, N_refine, o, P, pb, tot));
+  *bytes = tot;
+  return TK_OK;
+}
+
+TK_API tk_status tk_lcurve(const tk_problem* p, const double* lambdas, int N, int N_refine, const tk_opts* o,
+                           void* work, size_t work_bytes, void* stream, double* X, tk_lcurve_point* points,
+                           int* corner) {
+  Plan P;
+  size_t plan_b = 0, total = 0;
+  TK_TRY(lcurve_plan(p, N, N_refine, o, P, plan_b, total));
+  if (!lambdas || !X || !points || !corner) return einval("tk_lcurve: lambdas, X, points and corner must be non-NULL");
+  for (int i = 0; i < N; ++i)
+    if (!(lambdas[i] > 0.0) || !std::isfinite(lambdas[i])) return einval("every lambda must be a positive finite number");
+  if (!p->A || !p->b) return einval("A and b must be non-NULL");
+  if (!work || work_bytes < total) {
+    set_error_msg("workspace smaller than tk_lcurve_workspace_size()");
+    return TK_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int Np = N + N_refine;
+  // the solve's own buffers (the same carve solve_impl makes) and the L-curve's after them
+  Arena a;
+  a.base = (char*)work;
+  a.cap = plan_b;
+  Bufs B;
+  carve(P, a, a, B);
+  Arena la;
+  la.base = (char*)work + plan_b;
+  la.cap = work_bytes - plan_b;
+  LcBufs L;
+  lc_carve(la, P.m, P.n, Np, L);
+  // first sweep: the given lambdas in ascending order
+  std::vector<double> lam(lambdas, lambdas + N);
+  std::sort(lam.begin(), lam.end());
+  std::vector<tk_info> info(Np);
+  SweepCtx sw;
+  sw.N_plan = Np;
+  tk_status s1 = solve_impl(p, lam.data(), N, o, work, plan_b, st, L.Xs, info.data(), nullptr, nullptr, 0, &sw);
+  if (s1 == TK_EINVAL || s1 == TK_ENOMEM || s1 == TK_ECUDA || s1 == TK_ETIMEOUT) return s1;
+  TK_CUDA(cudaMemcpyAsync(L.lam, lam.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
+  TK_TRY(lc_norms(p, P, B, L, L.Xs, N, 0, st));
+  k_lc_curvature<<<1, 32, 0, st>>>(L.lam, L.rn, L.xn, N, L.kappa, L.corner, N_refine, L.next);
+  TK_LAUNCH_CHECK();
+  std::vector<double> next(std::max(N_refine, 1));
+  tk_status s2 = TK_OK;
+  if (N_refine > 0) {
+    // second sweep between the corner's neighbours, reusing the sketch, the Gram matrix (or the
+    // SVD of the sketch) and the copies and digit planes of A
+    TK_CUDA(cudaMemcpyAsync(next.data(), L.next, sizeof(double) * N_refine, cudaMemcpyDeviceToHost, st));
+    TK_CUDA(cudaStreamSynchronize(st));
+    sw.reuse = true;
+    s2 = solve_impl(p, next.data(), N_refine, o, work, plan_b, st, L.Xs + (size_t)N * P.n, info.data() + N,
+                    nullptr, nullptr, 0, &sw);
+    if (s2 == TK_EINVAL || s2 == TK_ENOMEM || s2 == TK_ECUDA || s2 == TK_ETIMEOUT) return s2;
+    TK_CUDA(cudaMemcpyAsync(L.lam + N, next.data(), sizeof(double) * N_refine, cudaMemcpyHostToDevice, st));
+    TK_TRY(lc_norms(p, P, B, L, L.Xs + (size_t)N * P.n, N_refine, N, st));
+  }
+  // both sweeps merged in ascending lambda (two sorted lists), curvature and corner of the merged grid
+  std::vector<double> all(lam);
+  all.insert(all.end(), next.begin(), next.begin() + N_refine);
+  std::vector<int> perm(Np);
+  for (int i = 0; i < Np; ++i) perm[i] = i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return all[x] < all[y]; });
+  TK_CUDA(cudaMemcpyAsync(L.perm, perm.data(), sizeof(int) * Np, cudaMemcpyHostToDevice, st));
+  k_lc_permute<<<1, 256, 0, st>>>(L.perm, Np, L.lam, L.lam_m);
+  k_lc_permute<<<1, 256, 0, st>>>(L.perm, Np, L.rn, L.rn_m);
+  k_lc_permute<<<1, 256, 0, st>>>(L.perm, Np, L.xn, L.xn_m);
+  k_lc_curvature<<<1, 32, 0, st>>>(L.lam_m, L.rn_m, L.xn_m, Np, L.kappa, L.corner, 0, nullptr);
+  // X rows in the merged order
+  TK_LAUNCH_CHECK();
+  k_gather_x<<<rgrid(P.n, Np), 256, 0, st>>>(L.Xs, P.n, L.perm, X);
+  TK_LAUNCH_CHECK();
+  std::vector<double> hl(Np), hr(Np), hx(Np), hk(Np);
+  int hc = -1, herr = 0;
+  TK_CUDA(cudaMemcpyAsync(hl.data(), L.lam_m, sizeof(double) * Np, cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaMemcpyAsync(hr.data(), L.rn_m, sizeof(double) * Np, cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaMemcpyAsync(hx.data(), L.xn_m, sizeof(double) * Np, cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaMemcpyAsync(hk.data(), L.kappa, sizeof(double) * Np, cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaMemcpyAsync(&hc, L.corner, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (P.mixed && P.o.emulate_fp64) TK_CUDA(cudaMemcpyAsync(&herr, B.oz_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error_msg("tk_lcurve: an emulated float64 residual pass timed out");
+    return TK_ETIMEOUT;
+  }
+  tk_status worst = TK_OK;
+  for (int i = 0; i < Np; ++i) {
+    const tk_info& q = info[perm[i]];
+    points[i].lambda = hl[i];
+    points[i].rnorm = hr[i];
+    points[i].xnorm = hx[i];
+    points[i].curvature = hk[i];
+    points[i].iters = q.iters;
+    points[i].status = q.status;
+    worst = worse(worst, q.status);
+  }
+  *corner = hc;
+  return worst;
 }
 
 }  // extern "C"

@@ -278,15 +278,26 @@ constexpr int OT_N = 32;
 constexpr int OT_KB = 64;
 constexpr int OT_CHUNK = 256;
 constexpr int OT_KB_PER_CHUNK = OT_CHUNK / OT_KB;
-constexpr int OT_PST = 8;
 constexpr uint32_t OT_P_BYTES = OT_M * OT_KB * 2;   // 16 KiB
 constexpr uint32_t OT_QS_BYTES = OT_N * OT_KB * 2;  // 4 KiB
 
+// S = 8 (float64-accurate passes): one CTA per SM, an 8-slot ring of P planes
+// and 2 x 8 x 32 tensor-memory columns; S = 4 (the float32 LSQR products):
+// 4 slots and 2 x 4 x 32 columns, so two CTAs share an SM and one streams
+// while the other starts up or flushes its last chunk.
+template <int S>
+struct OtCfg {
+  static constexpr int PST = S == OZ_S ? 8 : 4;
+  static constexpr int CTAS_PER_SM = S == OZ_S ? 1 : 2;
+};
+
+template <int S>
 struct OtSmem {
-  uint8_t p[OT_PST][OT_P_BYTES];
-  uint8_t q[2][OZ_S * OT_QS_BYTES];
-  uint64_t p_full[OT_PST];
-  uint64_t p_empty[OT_PST];
+  static constexpr int PST = OtCfg<S>::PST;
+  uint8_t p[PST][OT_P_BYTES];
+  uint8_t q[2][S * OT_QS_BYTES];
+  uint64_t p_full[PST];
+  uint64_t p_empty[PST];
   uint64_t q_full[2];
   uint64_t q_empty[2];
   uint64_t acc_full[2];
@@ -305,7 +316,7 @@ __device__ __forceinline__ double level_to_double(uint32_t bits, int t) {
 }
 
 template <int S, int MODE>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, OtCfg<S>::CTAS_PER_SM)
     k_oz_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
             const int* __restrict__ EP, const int* __restrict__ EQ, int64_t rows, int M, int64_t K, int64_t kps,
             const double* __restrict__ b, void* __restrict__ out, int64_t ldo, const double* __restrict__ coef,
@@ -314,7 +325,7 @@ __global__ void __launch_bounds__(256, 1)
   constexpr uint32_t TMEM_COLS = 2 * S * OT_N;
   constexpr uint32_t Q_BYTES = S * OT_QS_BYTES;
   extern __shared__ __align__(1024) uint8_t ot_raw[];
-  OtSmem& Sm = *reinterpret_cast<OtSmem*>((reinterpret_cast<uintptr_t>(ot_raw) + 1023) & ~uintptr_t(1023));
+  OtSmem<S>& Sm = *reinterpret_cast<OtSmem<S>*>((reinterpret_cast<uintptr_t>(ot_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r0 = (int64_t)blockIdx.x * OT_M;
   const int l0 = (int)blockIdx.y * OT_N;
@@ -326,7 +337,7 @@ __global__ void __launch_bounds__(256, 1)
   const int nch = (nkb + OT_KB_PER_CHUNK - 1) / OT_KB_PER_CHUNK;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < OT_PST; ++s) {
+    for (int s = 0; s < OtCfg<S>::PST; ++s) {
       mbar_init(&Sm.p_full[s], 1);
       mbar_init(&Sm.p_empty[s], 1);
     }
@@ -361,8 +372,8 @@ __global__ void __launch_bounds__(256, 1)
       for (int p = 0; p < S; ++p) tma_load_3d(&tmQ, &Sm.q_full[qs], Sm.q[qs] + p * OT_QS_BYTES, kc, l0, p);
       ++gq;
       for (int p = 0; p < S; ++p, ++g) {
-        const int ps = g % OT_PST;
-        if (!mbar_wait(&Sm.p_empty[ps], ((uint32_t)(g / OT_PST) & 1u) ^ 1u, err)) {
+        const int ps = g % OtCfg<S>::PST;
+        if (!mbar_wait(&Sm.p_empty[ps], ((uint32_t)(g / OtCfg<S>::PST) & 1u) ^ 1u, err)) {
           live = false;
           break;
         }
@@ -371,7 +382,7 @@ __global__ void __launch_bounds__(256, 1)
       }
     }
     if (*(volatile int*)err) {  // gave up: no bulk copy may still be landing when the CTA exits
-      tma_drain_ring(Sm.p_full, OT_PST, g);
+      tma_drain_ring(Sm.p_full, OtCfg<S>::PST, g);
       tma_drain_ring(Sm.q_full, 2, gq);
     }
   } else if (warp == 1 && lane == 0) {
@@ -393,8 +404,8 @@ __global__ void __launch_bounds__(256, 1)
         tc_fence_after();
         const uint32_t qa = smem_u32(Sm.q[qs]);
         for (int p = 0; p < S; ++p, ++g) {
-          const int ps = g % OT_PST;
-          if (!mbar_wait(&Sm.p_full[ps], (uint32_t)(g / OT_PST) & 1u, err)) {
+          const int ps = g % OtCfg<S>::PST;
+          if (!mbar_wait(&Sm.p_full[ps], (uint32_t)(g / OtCfg<S>::PST) & 1u, err)) {
             live = false;
             break;
           }
@@ -521,7 +532,7 @@ tk_status launch_oz_tc(const void* Ps, const int* EP, int64_t rows, int planesP,
   TK_TRY(make_slice_map(&mQ, Qs, M, kp, OT_N, planesQ));
   const int64_t kps = cdiv(cdiv(K, splits), OT_CHUNK) * OT_CHUNK;  // whole chunks per split
   const int sp = (int)cdiv(K, kps);
-  const size_t smem = sizeof(OtSmem) + 1024;
+  const size_t smem = sizeof(OtSmem<S>) + 1024;
   TK_CUDA(cudaFuncSetAttribute(k_oz_tc<S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const dim3 grid((unsigned)cdiv(rows, OT_M), (unsigned)cdiv(M, OT_N), (unsigned)sp);
   k_oz_tc<S, MODE><<<grid, 256, smem, st>>>(mP, mQ, EP, EQ, rows, M, kp, kps, b, out, ldo, coef, upper_only, err);

@@ -53,6 +53,11 @@ class tk_phase_stats(C.Structure):
                 ("impl_bytes", C.c_double)]
 
 
+class tk_lcurve_point(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("rnorm", C.c_double), ("xnorm", C.c_double), ("curvature", C.c_double),
+                ("iters", C.c_int), ("status", C.c_int)]
+
+
 class TikhonovError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -104,6 +109,8 @@ def lib() -> C.CDLL:
             "tk_residual": (INT, [P, P, INT, I64, INT, P, P, P, SZ, P]),
             "tk_autotune_clear": (None, []),
             "tk_wait_selftest": (INT, [I64, P, SZ, P]),
+            "tk_lcurve_workspace_size": (INT, [P, INT, INT, P, P]),
+            "tk_lcurve": (INT, [P, P, INT, INT, P, P, SZ, P, P, P, P]),
             "tk_create": (INT, [P, P]),
             "tk_destroy": (INT, [P]),
             "tk_handle_workspace_bytes": (SZ, [P]),
@@ -385,6 +392,37 @@ def tk_autotune_describe() -> str:
     buf = C.create_string_buffer(n)
     lib().tk_autotune_describe(buf, n)
     return buf.value.decode()
+
+
+def tk_lcurve(A: torch.Tensor, b: torch.Tensor, lambdas, N_refine: int, opts: tk_opts | None = None, *,
+              work=None, stream=None, allow=(TK_OK, TK_ENOCONV, TK_ENOTSPD)):
+    """The L-curve of Section 4.3 (include/tikhonov.h tk_lcurve): returns (X, points, corner) with X
+    (N + N_refine) x n on the device and points a list of dicts in ascending lambda."""
+    opts = opts or opts_default()
+    prob = make_problem(A, b)
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+    N = int(lam.shape[0])
+    Np = N + int(N_refine)
+    out = C.c_size_t(0)
+    _check(lib().tk_lcurve_workspace_size(C.byref(prob), N, int(N_refine), C.byref(opts), C.byref(out)))
+    if work is None or work.numel() < out.value:
+        work = _workspace(out.value, A.device)
+    X = torch.empty((Np, A.shape[1]), dtype=torch.float64, device=A.device)
+    pts = (tk_lcurve_point * Np)()
+    corner = C.c_int(-1)
+    st = lib().tk_lcurve(C.byref(prob), lam.ctypes.data_as(C.c_void_p), N, int(N_refine), C.byref(opts), _ptr(work),
+                         work.numel(), _stream(stream), _ptr(X), pts, C.byref(corner))
+    _check(st, allow)
+    points = [dict(lam=pts[i].lambda_, rnorm=pts[i].rnorm, xnorm=pts[i].xnorm, curvature=pts[i].curvature,
+                   iters=pts[i].iters, status=pts[i].status) for i in range(Np)]
+    return X, points, corner.value
+
+
+def lcurve_workspace_size(A, b, N: int, N_refine: int, opts: tk_opts) -> int:
+    out = C.c_size_t(0)
+    prob = make_problem(A, b)
+    _check(lib().tk_lcurve_workspace_size(C.byref(prob), N, N_refine, C.byref(opts), C.byref(out)))
+    return int(out.value)
 
 
 def tk_wait_selftest(budget_us: int, device="cuda", stream=None) -> int:

@@ -192,3 +192,30 @@ def test_profiler_reports_implementation_bytes_beside_algorithmic(tk):
     assert tk.lib().tk_profile_collect(arr) == tk.TK_OK
     assert all(arr[i].bytes == 0.0 and arr[i].impl_bytes == 0.0 for i in range(tk.TK_PHASE_COUNT))
     assert C.sizeof(tk.tk_phase_stats) == 40
+
+
+def test_lcurve_validates_on_host(tk):
+    L = tk.lib()
+    out = C.c_size_t(0)
+    o = tk.opts_default()
+    p = _prob(tk, 1000, 20)
+    assert L.tk_lcurve_workspace_size(C.byref(p), 2, 4, C.byref(o), C.byref(out)) == tk.TK_EINVAL  # N < 3
+    assert L.tk_lcurve_workspace_size(C.byref(p), 5, -1, C.byref(o), C.byref(out)) == tk.TK_EINVAL
+    assert L.tk_lcurve_workspace_size(C.byref(p), 5, 4, C.byref(o), C.byref(out)) == tk.TK_OK
+    big = out.value
+    assert L.tk_lcurve_workspace_size(C.byref(p), 5, 0, C.byref(o), C.byref(out)) == tk.TK_OK
+    assert out.value < big  # planned for N + N_refine lambdas
+    ow = tk.opts_default()
+    ow.x0 = 0x5000
+    assert L.tk_lcurve_workspace_size(C.byref(p), 5, 4, C.byref(ow), C.byref(out)) == tk.TK_EINVAL
+    lam = np.array([1e-3, 1e-2, -1.0])
+    pts = (tk.tk_lcurve_point * 3)()
+    k = C.c_int(0)
+    fake = C.c_void_p(0x4000)
+    st = L.tk_lcurve(C.byref(p), lam.ctypes.data_as(C.c_void_p), 3, 0, C.byref(o), fake, 1 << 40, None, fake, pts,
+                     C.byref(k))
+    assert st == tk.TK_EINVAL and "lambda" in tk.last_error()
+    lam = np.array([1e-3, 1e-2, 1e-1])
+    st = L.tk_lcurve(C.byref(p), lam.ctypes.data_as(C.c_void_p), 3, 0, C.byref(o), fake, 16, None, fake, pts,
+                     C.byref(k))
+    assert st == tk.TK_ENOMEM
