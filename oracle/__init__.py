@@ -76,6 +76,9 @@ def lib():
                 "orc_sd_estimate": (_d, [_p, _i64, _d]),
                 "orc_truncation": (_i64, [_d, _d, _i64]),
                 "orc_lr_diag": (None, [_p, _i64, _d, _p]),
+                "orc_draw_sparse": (None, [_u64, _i64, _i64, _p, _p]),
+                "orc_sparse_over": (None, [_p, _i64, _i64, _i64, _u64, _i64, _p]),
+                "orc_sparse_under": (None, [_p, _i64, _i64, _i64, _u64, _i64, _p]),
                 "orc_lcurve_norms": (None, [_p, _i64, _i64, _i64, _p, _p, _int, _p, _p]),
                 "orc_lcurve_curvature": (_int, [_p, _p, _p, _int, _p]),
                 "orc_lcurve_refine_grid": (None, [_p, _int, _int, _int, _p]),
@@ -101,6 +104,7 @@ def lib():
 
 SKETCH_SRHT = 0
 SKETCH_GAUSS = 1
+SKETCH_SPARSE = 2
 
 
 def _f64(a) -> np.ndarray:
@@ -195,11 +199,40 @@ def gauss_under(A, seed: int, s: int) -> np.ndarray:
     return Y
 
 
+def draw_sparse(seed: int, L: int, s: int):
+    """Sparse embedding draws (Section 2.1.1, one nonzero per column): rows h (int32[L]) and signs
+    (int8[L]) of Philox stream 4."""
+    h = np.zeros(L, dtype=np.int32)
+    d = np.zeros(L, dtype=np.int8)
+    lib().orc_draw_sparse(seed, L, s, _ptr(h), _ptr(d))
+    return h, d
+
+
+def sparse_over(A, seed: int, s: int) -> np.ndarray:
+    """Y = X A with the sparse embedding X (s x m): Y[h_i] += sign_i A[i], rows in ascending order."""
+    A, m, n, lda = _dims(A)
+    Y = np.zeros((s, n))
+    lib().orc_sparse_over(_ptr(A), m, n, lda, seed, s, _ptr(Y))
+    return Y
+
+
+def sparse_under(A, seed: int, s: int) -> np.ndarray:
+    """Y = A X^T with the sparse embedding on the columns (m x s)."""
+    A, m, n, lda = _dims(A)
+    Y = np.zeros((m, s))
+    lib().orc_sparse_under(_ptr(A), m, n, lda, seed, s, _ptr(Y))
+    return Y
+
+
 def sketch_over(A, kind: int, seed: int, s: int) -> np.ndarray:
+    if kind == SKETCH_SPARSE:
+        return sparse_over(A, seed, s)
     return srht_over(A, seed, s) if kind == SKETCH_SRHT else gauss_over(A, seed, s)
 
 
 def sketch_under(A, kind: int, seed: int, s: int) -> np.ndarray:
+    if kind == SKETCH_SPARSE:
+        return sparse_under(A, seed, s)
     return srht_under(A, seed, s) if kind == SKETCH_SRHT else gauss_under(A, seed, s)
 
 

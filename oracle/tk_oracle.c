@@ -15,7 +15,7 @@
  *
  * Sections follow the paper:
  *   problem (1.2)-(1.4) ............ ridge LLS, B = [A; sqrt(l) I], D = [A sqrt(l) I]
- *   Section 2.1.1 .................. SRTT X = sqrt(m/s) S F D, Gaussian embedding
+ *   Section 2.1.1 .................. SRTT X = sqrt(m/s) S F D, Gaussian and sparse embeddings
  *   Algorithm 1 .................... Y = XA, C = Y^T Y, R_i = chol(C + l_i I), LSQR, x = R^-1 y
  *   Algorithm 2 .................... Y = AX, C = Y Y^T, min-norm LSQR on R^-T D
  *   Section 3.1, eq. (RinvOver) .... R^-1 = l^{-1/2} (I - V S V^T)
@@ -67,7 +67,8 @@ ORC_API void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uin
 
 /* Draw convention: key = seed (low word, high word); counter =
  * (index low word, index high word, stream, 0).  Stream 0: Rademacher signs,
- * stream 1: row-sampling keys, stream 2: Gaussian entries. */
+ * stream 1: row-sampling keys, stream 2: Gaussian entries, stream 4: the
+ * sparse embedding's rows and signs. */
 static void draw(uint64_t seed, uint64_t index, uint32_t stream, uint32_t w[4]) {
   uint32_t c[4] = {(uint32_t)index, (uint32_t)(index >> 32), stream, 0u};
   uint32_t k[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -231,6 +232,48 @@ ORC_API void orc_gauss_under(const double* A, int64_t m, int64_t n, int64_t lda,
       for (int64_t j = 0; j < n; ++j) acc += A[i * lda + j] * orc_gauss_entry(seed, (uint64_t)(k * n + j), inv);
       Y[i * s + k] = acc;
     }
+}
+
+/* Sparse embedding (Section 2.1.1: one nonzero element in each column; the
+ * sparse subspace embedding of Theorem 3.5).  Column i of the s x L matrix X
+ * holds sign_i in row h_i, both from Philox stream 4 at index i:
+ *   h_i = floor(w0 * s / 2^32)  (multiply-shift: uniform over 0..s-1 to within
+ *         s / 2^32), sign_i = -1 when the low bit of w1 is set, +1 otherwise.
+ * Every column has unit norm, so E[X^T X] = I with no scaling. */
+ORC_API void orc_draw_sparse(uint64_t seed, int64_t L, int64_t s, int32_t* h, int8_t* sign) {
+  for (int64_t i = 0; i < L; ++i) {
+    uint32_t w[4];
+    draw(seed, (uint64_t)i, 4u, w);
+    h[i] = (int32_t)(((uint64_t)w[0] * (uint64_t)s) >> 32);
+    sign[i] = (w[1] & 1u) ? (int8_t)-1 : (int8_t)1;
+  }
+}
+
+/* Sparse sketch, overdetermined: Y = X A (s x n): Y[h_i] += sign_i A[i] for
+ * i = 0..m-1 in ascending order (that order fixes every float64 sum). */
+ORC_API void orc_sparse_over(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, int64_t s,
+                             double* Y) {
+  int32_t* h = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  int8_t* d = (int8_t*)malloc((size_t)(m > 0 ? m : 1));
+  orc_draw_sparse(seed, m, s, h, d);
+  for (int64_t k = 0; k < s * n; ++k) Y[k] = 0.0;
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) Y[(int64_t)h[i] * n + j] += (double)d[i] * A[i * lda + j];
+  free(h); free(d);
+}
+
+/* Sparse sketch, underdetermined (from the right, Algorithm 2): the n x s
+ * embedding X^T acts on the columns, Y = A X^T (m x s):
+ * Y[:, h_j] += sign_j A[:, j] for j = 0..n-1 in ascending order. */
+ORC_API void orc_sparse_under(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, int64_t s,
+                              double* Y) {
+  int32_t* h = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int8_t* d = (int8_t*)malloc((size_t)(n > 0 ? n : 1));
+  orc_draw_sparse(seed, n, s, h, d);
+  for (int64_t k = 0; k < m * s; ++k) Y[k] = 0.0;
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) Y[i * s + h[j]] += (double)d[j] * A[i * lda + j];
+  free(h); free(d);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -659,16 +702,18 @@ ORC_API void orc_lr_diag(const double* sigma, int64_t si, double lambda, double*
 /* ------------------------------------------------------------------------ */
 /* Whole algorithms, one lambda at a time, exactly in the paper's order       */
 /* ------------------------------------------------------------------------ */
-/* sketch kinds: 0 = SRHT, 1 = Gaussian */
+/* sketch kinds: 0 = SRHT, 1 = Gaussian, 2 = sparse (one nonzero per column) */
 static void sketch_over(int kind, const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, int64_t s,
                         double* Y) {
   if (kind == 0) orc_srht_over(A, m, n, lda, seed, s, Y);
-  else orc_gauss_over(A, m, n, lda, seed, s, Y);
+  else if (kind == 1) orc_gauss_over(A, m, n, lda, seed, s, Y);
+  else orc_sparse_over(A, m, n, lda, seed, s, Y);
 }
 static void sketch_under(int kind, const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, int64_t s,
                          double* Y) {
   if (kind == 0) orc_srht_under(A, m, n, lda, seed, s, Y);
-  else orc_gauss_under(A, m, n, lda, seed, s, Y);
+  else if (kind == 1) orc_gauss_under(A, m, n, lda, seed, s, Y);
+  else orc_sparse_under(A, m, n, lda, seed, s, Y);
 }
 
 /* Algorithm 1: X drawn once (step 1), Y = XA (2), C = Y^T Y (3); for each

@@ -478,3 +478,69 @@ def test_iterations_log_one_over_eps_and_flat_in_lambda(orc):
     R2, _ = orc.cholesky_shifted(orc.gram_tn(orc.gauss_over(A2, 3, 480)), lam)
     _, it_pre, _ = orc.lsqr_over_chol(A2, b2, lam, R2, 1e-12, 500)
     assert it_plain > 4 * it_pre, (it_plain, it_pre)
+
+
+# ------------------------------------------------- sparse embedding (f3) --
+def test_sparse_embedding_draws_one_signed_entry_per_column(orc):
+    # Section 2.1.1: one nonzero element in each column; rows uniform, signs balanced
+    L, s = 20000, 64
+    h, d = orc.draw_sparse(5, L, s)
+    assert h.min() >= 0 and h.max() < s
+    assert set(np.unique(d)) <= {-1, 1}
+    assert abs(d.astype(np.float64).mean()) < 5.0 / math.sqrt(L)
+    counts = np.bincount(h, minlength=s).astype(np.float64)
+    expected = L / s
+    chi2 = np.sum((counts - expected) ** 2 / expected)
+    assert chi2 < (s - 1) + 5 * math.sqrt(2 * (s - 1))
+    # the multiply-shift row: floor(w0 s / 2^32) from word 0 of Philox stream 4, the sign from word 1
+    w = orc.philox4x32_10([7, 0, 4, 0], [5, 0])
+    assert h[7] == (int(w[0]) * s) >> 32 and d[7] == (-1 if int(w[1]) & 1 else 1)
+
+
+def _explicit_sparse(orc, seed, L, s):
+    h, d = orc.draw_sparse(seed, L, s)
+    X = np.zeros((s, L))
+    X[h, np.arange(L)] = d
+    return X
+
+
+def test_sparse_sketch_is_the_explicit_embedding(orc):
+    m, n, s = 700, 9, 50
+    A = RNG.standard_normal((m, n))
+    X = _explicit_sparse(orc, 3, m, s)
+    assert np.all(np.count_nonzero(X, axis=0) == 1)
+    np.testing.assert_allclose(orc.sparse_over(A, 3, s), X @ A, rtol=1e-13, atol=1e-13)
+    B = RNG.standard_normal((n, m))  # underdetermined: the embedding on the columns
+    np.testing.assert_allclose(orc.sparse_under(B, 3, s), B @ X.T, rtol=1e-13, atol=1e-13)
+    # integer data: every partial sum is exact, so the result is exactly X A
+    Ai = RNG.integers(-1000, 1000, size=(m, n)).astype(np.float64)
+    assert np.array_equal(orc.sparse_over(Ai, 3, s), X @ Ai)
+
+
+def test_sparse_embedding_is_isotropic_and_embeds_a_subspace(orc):
+    # E[X^T X] = I (unit columns, independent signs); and for s >> k^2 a k-dim subspace is embedded
+    L, s = 40, 16
+    acc = np.zeros((L, L))
+    T = 400
+    for seed in range(T):
+        X = _explicit_sparse(orc, seed, L, s)
+        acc += X.T @ X
+    acc /= T
+    assert np.allclose(np.diag(acc), 1.0)
+    off = acc - np.diag(np.diag(acc))
+    assert np.abs(off).max() < 5.0 * math.sqrt(1.0 / (s * T)) + 1e-12
+    m, k, s2 = 3000, 4, 1500
+    U, _ = np.linalg.qr(RNG.standard_normal((m, k)))
+    Y = orc.sparse_over(U, 9, s2)
+    assert np.linalg.norm(Y.T @ Y - np.eye(k), 2) < 0.5
+
+
+def test_alg1_with_sparse_sketch_reaches_the_reference(orc):
+    # x_lambda does not depend on the embedding; the sparse sketch only changes the iteration count
+    A, b, p = small_problem(1500, 30, sig_lo=1e-3)
+    lams = np.array([1e-6, 1e-3, 1.0])
+    X, it, _, _ = orc.alg1(A, b, lams, orc.SKETCH_SPARSE, 600, 2, 1e-14, 500)
+    for i, lam in enumerate(lams):
+        xr = orc.ref_ridge_qr(A, b, lam, refine=3)
+        assert np.linalg.norm(X[:, i] - xr) / np.linalg.norm(xr) < 1e-10
+    assert np.all(it < 200), it
