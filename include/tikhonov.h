@@ -56,7 +56,13 @@ typedef enum {
 } tk_status;
 
 typedef enum { TK_F64 = 0, TK_F32 = 1 } tk_dtype;
-typedef enum { TK_SKETCH_SRHT = 0, TK_SKETCH_GAUSS = 1 } tk_sketch;
+/* Embeddings of Section 2.1.1: SRHT (signs, Walsh-Hadamard transform, row
+ * sampling), Gaussian (N(0, 1/s) entries), and SPARSE (one nonzero element
+ * in each column: sign_i in row h_i, both from Philox stream 4 at index i,
+ * h_i = floor(w0 s / 2^32), sign_i = -1 when the low bit of w1 is set; applied
+ * in O(nnz(A)) by adding each row of A into its bucket in ascending row order;
+ * s <= 2^22). */
+typedef enum { TK_SKETCH_SRHT = 0, TK_SKETCH_GAUSS = 1, TK_SKETCH_SPARSE = 2 } tk_sketch;
 typedef enum { TK_PRECOND_CHOL = 0, TK_PRECOND_LOWRANK = 1 } tk_precond;
 typedef enum { TK_PREC_FP64 = 0, TK_PREC_MIXED = 1 } tk_precision;
 typedef enum { TK_SCHED_BATCHED = 0, TK_SCHED_ONE_AT_A_TIME = 1 } tk_schedule;
@@ -72,7 +78,8 @@ typedef struct {
 /* Options.  tk_opts_default() fills the defaults given in brackets. */
 typedef struct {
   tk_sketch sketch;       /* [SRHT] embedding of Section 2.1.1 */
-  int64_t s;              /* sketch size; 0 = 4 * min(m, n) for Cholesky, see alpha for low rank [0] */
+  int64_t s;              /* sketch size; 0 = 4 * min(m, n) for Cholesky (16 * min(m, n) for SPARSE), capped at
+                             max(m, n); min(m, n) for low rank [0] */
   tk_precond precond;     /* [CHOL] Algorithm 1/2, or LOWRANK = Algorithm 3 (m >= n) / 4 (m < n, FP64) */
   double alpha;           /* [2] oversampling of Algorithms 3/4: s_i = alpha * ceil(sd_i) */
   tk_precision precision; /* [FP64] or MIXED (FP32 LSQR + FP64 refinement) */
@@ -260,10 +267,25 @@ TK_API tk_status tk_sketch_draw_static(uint64_t seed, int64_t mp, int64_t s, int
                                        void* stream);
 
 /*
+ * tk_sketch_draw_sparse -- the integer draws of the SPARSE embedding
+ * (Section 2.1.1, one nonzero element per column) and the bucket lists the
+ * sketch uses: h (row of column i, int32[L]), sign (int8[L]), order (the
+ * column indices sorted by h, ascending within a bucket: a stable sort,
+ * int32[L]) and start (int32[s + 1]: bucket k is order[start[k] ..
+ * start[k+1]-1]).  Any output may be NULL.  1 <= s <= 2^22, 1 <= L < 2^31.
+ *   work: device, tk_sketch_draw_sparse_workspace(L, s) bytes.  Synchronizes `stream`.
+ */
+TK_API size_t tk_sketch_draw_sparse_workspace(int64_t L, int64_t s);
+TK_API tk_status tk_sketch_draw_sparse(uint64_t seed, int64_t L, int64_t s, int32_t* h, int8_t* sign, int32_t* order,
+                                       int32_t* start, void* work, size_t work_bytes, void* stream);
+
+/*
  * tk_sketch_apply -- Y = X A (m >= n: Y is s x n, Algorithm 1 step 2) or
  * Y = A X (m < n: Y is m x s, Algorithm 2 step 2), float64 device output.
  * SRHT: X = sqrt(mp/s) S (H/sqrt(mp)) D with mp the next power of two of the
  * long dimension.  Gaussian: X has N(0, 1/s) entries from Philox stream 2.
+ * SPARSE: one signed entry per column (see tk_sketch); Y's float64 sums run
+ * over each bucket's rows in ascending order.
  * With precision MIXED (Gaussian, m >= n only) the sketch is the one the
  * mixed form uses: X and A rounded to BF16, products on the tensor cores
  * with FP32 accumulation.

@@ -53,7 +53,8 @@ constexpr int64_t kMaxLong = (int64_t(1) << 30);
 
 tk_status check_opts(const tk_opts* o) {
   if (!o) return einval("options pointer is NULL");
-  if (o->sketch != TK_SKETCH_SRHT && o->sketch != TK_SKETCH_GAUSS) return einval("unknown sketch kind");
+  if (o->sketch != TK_SKETCH_SRHT && o->sketch != TK_SKETCH_GAUSS && o->sketch != TK_SKETCH_SPARSE)
+    return einval("unknown sketch kind");
   if (o->precond != TK_PRECOND_CHOL && o->precond != TK_PRECOND_LOWRANK) return einval("unknown preconditioner");
   if (o->precision != TK_PREC_FP64 && o->precision != TK_PREC_MIXED) return einval("unknown precision");
   if (o->schedule != TK_SCHED_BATCHED && o->schedule != TK_SCHED_ONE_AT_A_TIME) return einval("unknown schedule");
@@ -92,8 +93,10 @@ tk_status make_plan(const tk_problem* p, int N, const tk_opts* o, Plan& P) {
   if (P.under && P.mixed) return einval("the mixed-precision form is built for m >= n");
   if (P.under && o->x0) return einval("the warm start x0 is supported for m >= n (Algorithms 1 and 3)");
   int64_t s = o->s;
-  if (s == 0) s = P.lowrank ? P.c : std::min<int64_t>(4 * P.c, P.L);
+  // the sparse embedding needs more rows for the same distortion (Theorem 3.5: s grows with sd^2)
+  if (s == 0) s = P.lowrank ? P.c : std::min<int64_t>((o->sketch == TK_SKETCH_SPARSE ? 16 : 4) * P.c, P.L);
   if (o->sketch == TK_SKETCH_SRHT && s > next_pow2(P.L)) return einval("SRHT sketch size exceeds the padded length");
+  if (o->sketch == TK_SKETCH_SPARSE && s > kSparseMaxS) return einval("sparse sketch size above 2^22");
   if (P.lowrank && s > P.c) s = P.c;  // alpha * sd <= n (Algorithm 3); a full-size sketch is still exact
   P.s = s;
   P.np = cdiv(P.c, 64) * 64;
@@ -171,6 +174,7 @@ size_t sketch_scratch(const Plan& P) {
   tk_dtype dt = P.mixed ? TK_F32 : P.dt;
   if (tc_sketch(P)) return tc_sketch_workspace(P.L, P.c, P.s);
   if (P.o.sketch == TK_SKETCH_SRHT) return srht_rows_workspace(P.L, P.c, dt, P.s);
+  if (P.o.sketch == TK_SKETCH_SPARSE) return sparse_rows_workspace(P.L, P.c, P.s);
   return gauss_rows_workspace(P.L, P.c, dt, P.s);
 }
 
@@ -375,6 +379,7 @@ tk_status do_sketch(const Plan& P, const void* A_sk, tk_dtype dt_sk, int64_t ld_
   sa.cap = B.scratch_bytes;
   if (tc_sketch(P)) return tc_gauss_sketch(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
   if (P.o.sketch == TK_SKETCH_SRHT) return srht_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
+  if (P.o.sketch == TK_SKETCH_SPARSE) return sparse_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
   return gauss_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
 }
 
@@ -493,7 +498,9 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
   if (!reuse) {
     const double es = dt_sk == TK_F64 ? 8.0 : 4.0;
     const double Lp = (double)next_pow2(P.L);
-    const double fl = P.o.sketch == TK_SKETCH_SRHT ? Lp * std::log2(Lp) * P.c : 2.0 * P.s * P.L * P.c;
+    const double fl = P.o.sketch == TK_SKETCH_SRHT    ? Lp * std::log2(Lp) * P.c
+                      : P.o.sketch == TK_SKETCH_SPARSE ? (double)P.L * P.c
+                                                       : 2.0 * P.s * P.L * P.c;
     int tok = prof_begin(TK_PHASE_SKETCH, st);
     TK_TRY(do_sketch(P, A_sk, dt_sk, ld_sk, B, st));
     prof_end(tok, st, fl, es * P.L * P.c + 8.0 * P.s * P.c);
@@ -1341,6 +1348,27 @@ TK_API tk_status tk_sketch_draw(uint64_t seed, int64_t mp, int64_t s, int8_t* si
   a.cap = work_bytes;
   cudaStream_t st = (cudaStream_t)stream;
   TK_TRY(draw_signs_rows(seed, mp, s, signs, rows, nullptr, a, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  return TK_OK;
+}
+
+TK_API size_t tk_sketch_draw_sparse_workspace(int64_t L, int64_t s) {
+  if (L < 1 || s < 1) return 0;
+  return sparse_rows_workspace(L, 1, s) + 1024;
+}
+
+TK_API tk_status tk_sketch_draw_sparse(uint64_t seed, int64_t L, int64_t s, int32_t* h, int8_t* sign, int32_t* order,
+                                       int32_t* start, void* work, size_t work_bytes, void* stream) {
+  if (L < 1 || L > INT32_MAX || s < 1 || s > kSparseMaxS) return einval("need 1 <= L < 2^31 and 1 <= s <= 2^22");
+  if (!work || work_bytes < tk_sketch_draw_sparse_workspace(L, s)) {
+    set_error_msg("workspace smaller than tk_sketch_draw_sparse_workspace()");
+    return TK_ENOMEM;
+  }
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  cudaStream_t st = (cudaStream_t)stream;
+  TK_TRY(sparse_draw_sorted(seed, L, s, h, sign, order, start, a, st));
   TK_CUDA(cudaStreamSynchronize(st));
   return TK_OK;
 }

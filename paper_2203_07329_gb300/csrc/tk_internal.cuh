@@ -116,7 +116,7 @@ __device__ __forceinline__ uint4 philox(uint64_t index, uint32_t stream, uint64_
   return make_uint4(x0, x1, x2, x3);
 }
 
-enum : uint32_t { STREAM_SIGNS = 0, STREAM_KEYS = 1, STREAM_GAUSS = 2 };
+enum : uint32_t { STREAM_SIGNS = 0, STREAM_KEYS = 1, STREAM_GAUSS = 2, STREAM_SPARSE = 4 };
 
 // Gaussian entry k of an embedding with N(0, 1/s) entries: Philox call k/4 of
 // stream 2, Box-Muller on word pairs (w0, w1) and (w2, w3).
@@ -181,6 +181,14 @@ size_t srht_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s);
 tk_status gauss_rows(const void* A, tk_dtype dt, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s,
                      double* Y, Arena& ar, cudaStream_t st);
 size_t gauss_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s);
+// Sparse embedding (tk_sparse.cu): one signed entry per column of X (s x L).
+constexpr int64_t kSparseMaxS = int64_t(1) << 22;
+tk_status sparse_rows(const void* A, tk_dtype dt, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s,
+                      double* Y, Arena& ar, cudaStream_t st);
+size_t sparse_rows_workspace(int64_t L, int64_t cols, int64_t s);
+// the draws and the rows sorted by bucket (ascending row within a bucket) on their own, for parity tests
+tk_status sparse_draw_sorted(uint64_t seed, int64_t L, int64_t s, int32_t* h, int8_t* sign, int32_t* order,
+                             int32_t* start, Arena& ar, cudaStream_t st);
 tk_status transpose(const void* A, tk_dtype dt, int64_t rows, int64_t cols, int64_t lda, void* AT,
                     cudaStream_t st);
 tk_status convert_f64_to_f32(const double* src, float* dst, int64_t rows, int64_t cols, int64_t lds, int64_t ldd,

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libtikhonov.so")
 
 TK_OK, TK_EINVAL, TK_ENOMEM, TK_ENOTSPD, TK_ENOCONV, TK_ENUMERIC, TK_ETIMEOUT, TK_ECUDA = range(8)
 TK_F64, TK_F32 = 0, 1
-TK_SKETCH_SRHT, TK_SKETCH_GAUSS = 0, 1
+TK_SKETCH_SRHT, TK_SKETCH_GAUSS, TK_SKETCH_SPARSE = 0, 1, 2
 TK_PRECOND_CHOL, TK_PRECOND_LOWRANK = 0, 1
 TK_PREC_FP64, TK_PREC_MIXED = 0, 1
 TK_SCHED_BATCHED, TK_SCHED_ONE_AT_A_TIME = 0, 1
@@ -97,6 +97,8 @@ def lib() -> C.CDLL:
             "tk_lowrank_ranks_workspace": (SZ, [INT]),
             "tk_lowrank_ranks": (INT, [P, I64, P, INT, D, P, P, P, SZ, P]),
             "tk_sketch_draw_static": (INT, [U64, I64, I64, P, P, P]),
+            "tk_sketch_draw_sparse_workspace": (SZ, [I64, I64]),
+            "tk_sketch_draw_sparse": (INT, [U64, I64, I64, P, P, P, P, P, SZ, P]),
             "tk_phase_name": (C.c_char_p, [INT]),
             "tk_launch_count": (C.c_ulonglong, []),
             "tk_profile_enable": (INT, [INT]),
@@ -281,6 +283,18 @@ def tk_sketch_draw_static(seed: int, mp: int, s: int, device="cuda", stream=None
     return signs, rows[:s]
 
 
+def tk_sketch_draw_sparse(seed: int, L: int, s: int, device="cuda", stream=None):
+    """Sparse embedding draws: (h int32[L], sign int8[L], order int32[L], start int32[s+1]) on the device."""
+    h = torch.empty(L, dtype=torch.int32, device=device)
+    sign = torch.empty(L, dtype=torch.int8, device=device)
+    order = torch.empty(L, dtype=torch.int32, device=device)
+    start = torch.empty(s + 1, dtype=torch.int32, device=device)
+    work = _workspace(int(lib().tk_sketch_draw_sparse_workspace(L, s)), device)
+    _check(lib().tk_sketch_draw_sparse(seed, L, s, _ptr(h), _ptr(sign), _ptr(order), _ptr(start), _ptr(work),
+                                       work.numel(), _stream(stream)))
+    return h, sign, order, start
+
+
 def tk_sketch_apply(A: torch.Tensor, opts: tk_opts, stream=None) -> torch.Tensor:
     """Y = X A (m >= n, s x n) or Y = A X (m < n, m x s), float64."""
     b = torch.zeros(A.shape[0], dtype=torch.float64, device=A.device)
@@ -288,7 +302,7 @@ def tk_sketch_apply(A: torch.Tensor, opts: tk_opts, stream=None) -> torch.Tensor
     out = C.c_size_t(0)
     _check(lib().tk_sketch_apply_workspace(C.byref(prob), C.byref(opts), C.byref(out)))
     m, n = A.shape
-    s = opts.s if opts.s > 0 else min(4 * min(m, n), max(m, n))
+    s = opts.s if opts.s > 0 else min((16 if opts.sketch == TK_SKETCH_SPARSE else 4) * min(m, n), max(m, n))
     Y = torch.empty((s, n) if m >= n else (m, s), dtype=torch.float64, device=A.device)
     work = _workspace(out.value, A.device)
     _check(lib().tk_sketch_apply(C.byref(prob), C.byref(opts), _ptr(Y), _ptr(work), work.numel(), _stream(stream)))

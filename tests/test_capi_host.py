@@ -219,3 +219,21 @@ def test_lcurve_validates_on_host(tk):
     st = L.tk_lcurve(C.byref(p), lam.ctypes.data_as(C.c_void_p), 3, 0, C.byref(o), fake, 16, None, fake, pts,
                      C.byref(k))
     assert st == tk.TK_ENOMEM
+
+
+def test_sparse_sketch_arguments_checked_on_host(tk):
+    L = tk.lib()
+    fake = C.c_void_p(0x1000)
+    assert L.tk_sketch_draw_sparse(1, 0, 4, None, None, None, None, fake, 1 << 20, None) == tk.TK_EINVAL
+    assert L.tk_sketch_draw_sparse(1, 100, 0, None, None, None, None, fake, 1 << 20, None) == tk.TK_EINVAL
+    assert L.tk_sketch_draw_sparse(1, 100, (1 << 22) + 1, None, None, None, None, fake, 1 << 30, None) == tk.TK_EINVAL
+    need = L.tk_sketch_draw_sparse_workspace(100000, 5000)
+    assert need >= 17 * 100000  # keys and indices twice, the signs
+    assert L.tk_sketch_draw_sparse(1, 100000, 5000, None, None, None, None, fake, need - 1, None) == tk.TK_ENOMEM
+    out = C.c_size_t(0)
+    o = tk.opts_default(sketch=tk.TK_SKETCH_SPARSE)
+    assert L.tk_workspace_size(C.byref(_prob(tk, 5000, 50)), 2, C.byref(o), C.byref(out)) == tk.TK_OK
+    o.s = (1 << 22) + 1
+    assert L.tk_workspace_size(C.byref(_prob(tk, 1 << 23, 50)), 2, C.byref(o), C.byref(out)) == tk.TK_EINVAL
+    o.sketch = 7
+    assert L.tk_workspace_size(C.byref(_prob(tk, 5000, 50)), 2, C.byref(o), C.byref(out)) == tk.TK_EINVAL
