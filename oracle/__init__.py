@@ -79,6 +79,7 @@ def lib():
                 "orc_draw_sparse": (None, [_u64, _i64, _i64, _p, _p]),
                 "orc_sparse_over": (None, [_p, _i64, _i64, _i64, _u64, _i64, _p]),
                 "orc_sparse_under": (None, [_p, _i64, _i64, _i64, _u64, _i64, _p]),
+                "orc_bp2_r": (_int, [_p, _i64, _i64, _d, _p]),
                 "orc_lcurve_norms": (None, [_p, _i64, _i64, _i64, _p, _p, _int, _p, _p]),
                 "orc_lcurve_curvature": (_int, [_p, _p, _p, _int, _p]),
                 "orc_lcurve_refine_grid": (None, [_p, _int, _int, _int, _p]),
@@ -520,3 +521,30 @@ def lcurve(A, b, lambdas, nr, refine=3):
     Xm = np.concatenate([X1, X2])[order]
     kap, km = lcurve_curvature(lamm, rnm, xnm)
     return lamm, rnm, xnm, kap, km, Xm
+
+
+# ------------------------------------------------------------------ BP2 ----
+def bp2_r(Y, lam: float) -> np.ndarray:
+    """R_BP2 from a Householder QR of [Y; sqrt(lambda) I] (Section 4.1), diag(R) > 0."""
+    Y = _f64(Y)
+    s, n = Y.shape
+    R = np.zeros((n, n))
+    rc = lib().orc_bp2_r(_ptr(Y), s, n, float(lam), _ptr(R))
+    if rc:
+        raise ValueError("zero column in the BP2 factorization")
+    return R
+
+
+def alg1_bp2(A, b, lambdas, sketch_kind: int, s: int, seed: int, tol: float, maxiter: int):
+    """Algorithm 1 with the BP2 preconditioner (Section 4.1): the same sketch Y = XA, then for each
+    lambda R from a QR of [Y; sqrt(l) I] in place of chol(Y^T Y + l I), LSQR, x = R^-1 y.
+    Returns (X n x N, iterations, istop)."""
+    A = _f64(A)
+    Y = sketch_over(A, sketch_kind, seed, s)
+    N = len(lambdas)
+    X = np.zeros((A.shape[1], N))
+    its, ist = np.zeros(N, dtype=int), np.zeros(N, dtype=int)
+    for i, lam in enumerate(lambdas):
+        R = bp2_r(Y, float(lam))
+        X[:, i], its[i], ist[i] = lsqr_over_chol(A, b, float(lam), R, tol, maxiter)
+    return X, its, ist

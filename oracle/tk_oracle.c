@@ -1039,3 +1039,47 @@ ORC_API void orc_lcurve_refine_grid(const double* lambdas, int N, int k, int nr,
   const double a = log(lambdas[lo]), b = log(lambdas[hi]);
   for (int j = 1; j <= nr; ++j) out[j - 1] = exp(a + (b - a) * (double)j / (double)(nr + 1));
 }
+
+/* ------------------------------------------------------------------------ */
+/* BP2 (Section 4.1): the preconditioner of Algorithm 1 obtained by a QR      */
+/* decomposition instead of a Cholesky factorization,                         */
+/*   Q R_BP2 = [X A; sqrt(lambda) I_n]   ((s + n) x n),                        */
+/* equal to chol(Y^T Y + lambda I) up to the signs of its rows in exact       */
+/* arithmetic.  Plain Householder QR, columns left to right; the rows of R are */
+/* then scaled by the sign of their diagonal so that diag(R) > 0.             */
+/* Returns 0, or -1 when a column is exactly zero (cannot happen for          */
+/* lambda > 0).                                                                */
+/* ------------------------------------------------------------------------ */
+ORC_API int orc_bp2_r(const double* Y, int64_t s, int64_t n, double lambda, double* R) {
+  const int64_t M = s + n;
+  double* Bm = (double*)calloc((size_t)(M * n), sizeof(double));
+  double* v = (double*)malloc(sizeof(double) * (size_t)M);
+  const double sl = sqrt(lambda);
+  for (int64_t i = 0; i < s; ++i)
+    for (int64_t j = 0; j < n; ++j) Bm[i * n + j] = Y[i * n + j];
+  for (int64_t j = 0; j < n; ++j) Bm[(s + j) * n + j] = sl;
+  int rc = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    double nrm = 0.0;
+    for (int64_t i = k; i < M; ++i) nrm += Bm[i * n + k] * Bm[i * n + k];
+    nrm = sqrt(nrm);
+    if (nrm == 0.0) { rc = -1; break; }
+    const double alpha = Bm[k * n + k] > 0.0 ? -nrm : nrm;  /* reflect onto -sign(b_kk) ||b_k|| e_k */
+    for (int64_t i = k; i < M; ++i) v[i] = Bm[i * n + k];
+    v[k] -= alpha;
+    double vv = 0.0;
+    for (int64_t i = k; i < M; ++i) vv += v[i] * v[i];
+    for (int64_t j = k; j < n; ++j) {
+      double d = 0.0;
+      for (int64_t i = k; i < M; ++i) d += v[i] * Bm[i * n + j];
+      d = 2.0 * d / vv;
+      for (int64_t i = k; i < M; ++i) Bm[i * n + j] -= d * v[i];
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    const double sg = Bm[i * n + i] < 0.0 ? -1.0 : 1.0;
+    for (int64_t j = 0; j < n; ++j) R[i * n + j] = j >= i ? sg * Bm[i * n + j] : 0.0;
+  }
+  free(Bm); free(v);
+  return rc;
+}

@@ -544,3 +544,33 @@ def test_alg1_with_sparse_sketch_reaches_the_reference(orc):
         xr = orc.ref_ridge_qr(A, b, lam, refine=3)
         assert np.linalg.norm(X[:, i] - xr) / np.linalg.norm(xr) < 1e-10
     assert np.all(it < 200), it
+
+
+# ------------------------------------------------------------- BP2 (f4) --
+def test_bp2_r_is_the_qr_factor_of_the_augmented_sketch(orc):
+    # Section 4.1: Q R_BP2 = [XA; sqrt(l) I]; R^T R = Y^T Y + l I, R upper triangular with diag > 0,
+    # equal to the Cholesky factor of Algorithm 1 and to LAPACK's QR factor (signs fixed)
+    A = RNG.standard_normal((300, 9))
+    Y = orc.srht_over(A, 4, 64)
+    for lam in (1e-6, 0.3):
+        R = orc.bp2_r(Y, lam)
+        assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) > 0)
+        G = Y.T @ Y + lam * np.eye(9)
+        np.testing.assert_allclose(R.T @ R, G, rtol=1e-12, atol=1e-12 * np.abs(G).max())
+        Rc, _ = orc.cholesky_shifted(orc.gram_tn(Y), lam)
+        np.testing.assert_allclose(R, Rc, rtol=1e-10, atol=1e-12)
+        Rq = np.linalg.qr(np.vstack([Y, math.sqrt(lam) * np.eye(9)]), mode="r")
+        Rq = np.sign(np.diag(Rq))[:, None] * Rq
+        np.testing.assert_allclose(R, Rq, rtol=1e-11, atol=1e-13)
+
+
+def test_alg1_with_bp2_reaches_the_reference(orc):
+    A, b, p = small_problem(1200, 25, sig_lo=1e-4)
+    lams = np.array([1e-7, 1e-3, 1.0])
+    X, it, _ = orc.alg1_bp2(A, b, lams, orc.SKETCH_GAUSS, 100, 3, 1e-14, 500)
+    Xc, itc, _, _ = orc.alg1(A, b, lams, orc.SKETCH_GAUSS, 100, 3, 1e-14, 500)
+    for i, lam in enumerate(lams):
+        xr = orc.ref_ridge_qr(A, b, lam, refine=3)
+        assert np.linalg.norm(X[:, i] - xr) / np.linalg.norm(xr) < 1e-10
+    # the same preconditioner in exact arithmetic: the same iteration counts to within rounding
+    assert np.all(np.abs(it - itc) <= 2), (it, itc)
