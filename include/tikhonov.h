@@ -63,7 +63,11 @@ typedef enum { TK_F64 = 0, TK_F32 = 1 } tk_dtype;
  * in O(nnz(A)) by adding each row of A into its bucket in ascending row order;
  * s <= 2^22). */
 typedef enum { TK_SKETCH_SRHT = 0, TK_SKETCH_GAUSS = 1, TK_SKETCH_SPARSE = 2 } tk_sketch;
-typedef enum { TK_PRECOND_CHOL = 0, TK_PRECOND_LOWRANK = 1 } tk_precond;
+/* Preconditioners: CHOL = Algorithm 1 / 2 (R_i = chol(C + lambda_i I)); LOWRANK = Algorithms 3 / 4
+ * (Sections 3.1 / 3.2); QR = BP2 of Section 4.1 (m >= n): R_i from a Householder QR of the
+ * (s + n) x n partly exact sketch [X A; sqrt(lambda_i) I], the same factor as CHOL in exact
+ * arithmetic, without forming Y^T Y, at the cost of a QR per lambda. */
+typedef enum { TK_PRECOND_CHOL = 0, TK_PRECOND_LOWRANK = 1, TK_PRECOND_QR = 2 } tk_precond;
 typedef enum { TK_PREC_FP64 = 0, TK_PREC_MIXED = 1 } tk_precision;
 typedef enum { TK_SCHED_BATCHED = 0, TK_SCHED_ONE_AT_A_TIME = 1 } tk_schedule;
 
@@ -80,7 +84,7 @@ typedef struct {
   tk_sketch sketch;       /* [SRHT] embedding of Section 2.1.1 */
   int64_t s;              /* sketch size; 0 = 4 * min(m, n) for Cholesky (16 * min(m, n) for SPARSE), capped at
                              max(m, n); min(m, n) for low rank [0] */
-  tk_precond precond;     /* [CHOL] Algorithm 1/2, or LOWRANK = Algorithm 3 (m >= n) / 4 (m < n, FP64) */
+  tk_precond precond;     /* [CHOL] Algorithm 1/2, LOWRANK = Algorithm 3 (m >= n) / 4 (m < n, FP64), QR = BP2 */
   double alpha;           /* [2] oversampling of Algorithms 3/4: s_i = alpha * ceil(sd_i) */
   tk_precision precision; /* [FP64] or MIXED (FP32 LSQR + FP64 refinement) */
   double tol;             /* [1e-14] LSQR stopping tolerance (Paige-Saunders atol = btol) */
@@ -339,6 +343,19 @@ TK_API tk_status tk_cholesky_shifted(const double* C, int64_t n, const double* l
 TK_API size_t tk_cholesky_emulated_workspace(int64_t n, int N);
 TK_API tk_status tk_cholesky_shifted_emulated(const double* C, int64_t n, const double* lambdas, int N, double* R,
                                               int* breakdown, void* work, size_t work_bytes, void* stream);
+
+/*
+ * tk_bp2_factor -- the BP2 preconditioner of Section 4.1: R_i from a
+ * Householder QR of [Y; sqrt(lambda_i) I_n] for i = 0..N-1 (Y device s x n
+ * float64, row-major), upper triangular with a positive diagonal; in exact
+ * arithmetic the factor tk_cholesky_shifted returns for C = Y^T Y.
+ *   lambdas: host N.   R: device N x n x n (zeros below the diagonal).
+ *   breakdown: host N (may be NULL): 0, k+1 for a zero column k, -(k+1) for NaN.
+ *   work: device, tk_bp2_factor_workspace(s, n, N) bytes (N (s + n) n doubles).
+ */
+TK_API size_t tk_bp2_factor_workspace(int64_t s, int64_t n, int N);
+TK_API tk_status tk_bp2_factor(const double* Y, int64_t s, int64_t n, const double* lambdas, int N, double* R,
+                               int* breakdown, void* work, size_t work_bytes, void* stream);
 
 /*
  * tk_sketch_svd -- [~, Sigma, V] = svd(Y, 'econ') of Algorithm 3 step 4 by

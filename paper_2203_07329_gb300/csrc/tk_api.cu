@@ -42,6 +42,7 @@ struct Plan {
   int N = 0, N_cap = 0;
   tk_opts o{};
   bool mixed = false, lowrank = false;
+  bool qr = false;        // BP2: R from a QR of [Y; sqrt(l) I] instead of chol(Y^T Y + l I)
   bool lsqr_tc = false;  // tensor-core float32 LSQR products (3-term TF32)
   bool lsqr_oz = false;  // float32 LSQR products from the 4-digit slices of A
   bool prep_only = false;  // grouped batch: build the preconditioner only
@@ -55,7 +56,8 @@ tk_status check_opts(const tk_opts* o) {
   if (!o) return einval("options pointer is NULL");
   if (o->sketch != TK_SKETCH_SRHT && o->sketch != TK_SKETCH_GAUSS && o->sketch != TK_SKETCH_SPARSE)
     return einval("unknown sketch kind");
-  if (o->precond != TK_PRECOND_CHOL && o->precond != TK_PRECOND_LOWRANK) return einval("unknown preconditioner");
+  if (o->precond != TK_PRECOND_CHOL && o->precond != TK_PRECOND_LOWRANK && o->precond != TK_PRECOND_QR)
+    return einval("unknown preconditioner");
   if (o->precision != TK_PREC_FP64 && o->precision != TK_PREC_MIXED) return einval("unknown precision");
   if (o->schedule != TK_SCHED_BATCHED && o->schedule != TK_SCHED_ONE_AT_A_TIME) return einval("unknown schedule");
   if (!(o->tol > 0.0) || !std::isfinite(o->tol)) return einval("tol must be a positive finite number");
@@ -90,7 +92,9 @@ tk_status make_plan(const tk_problem* p, int N, const tk_opts* o, Plan& P) {
   P.N = N;
   P.mixed = o->precision == TK_PREC_MIXED;
   P.lowrank = o->precond == TK_PRECOND_LOWRANK;
+  P.qr = o->precond == TK_PRECOND_QR;
   if (P.under && P.mixed) return einval("the mixed-precision form is built for m >= n");
+  if (P.under && P.qr) return einval("the BP2 (QR) preconditioner is built for m >= n");
   if (P.under && o->x0) return einval("the warm start x0 is supported for m >= n (Algorithms 1 and 3)");
   int64_t s = o->s;
   // the sparse embedding needs more rows for the same distortion (Theorem 3.5: s grows with sd^2)
@@ -168,7 +172,7 @@ bool tc_sketch(const Plan& P) { return P.mixed && P.o.sketch == TK_SKETCH_GAUSS 
 
 // The mixed form with emulate_fp64 forms its Gram matrix from exact slices on
 // the tensor cores (float64 accuracy).
-bool emulated_gram(const Plan& P) { return P.mixed && P.o.emulate_fp64 && !P.lowrank; }
+bool emulated_gram(const Plan& P) { return P.mixed && P.o.emulate_fp64 && !P.lowrank && !P.qr; }
 
 size_t sketch_scratch(const Plan& P) {
   tk_dtype dt = P.mixed ? TK_F32 : P.dt;
@@ -249,8 +253,9 @@ void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
     B.part = a.take<double>((size_t)B.splits * N * P.n);
     B.nrm = a.take<double>((size_t)3 * N);
   }
-  // the sketch's scratch is free again when the Gram matrix is formed
+  // the sketch's scratch is free again when the Gram matrix (or the BP2 factorization) is formed
   size_t sc = std::max(sketch_scratch(P), P.lowrank ? size_t(0) : gram_scratch_bytes(P.s, P.c));
+  if (P.qr) sc = std::max(sc, bp2_workspace(P.s, P.c, N));
   if (emulated_gram(P)) sc = std::max({sc, oz_gram_workspace(P.s, P.c), oz_chol_workspace(P.np, N)});
   B.scratch_bytes = sc;
   B.scratch = t.take<char>(sc);
@@ -511,7 +516,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
   if (!P.lowrank) {
     int tok = -1;
     if (emulated_gram(P)) TK_CUDA(cudaMemsetAsync(B.oz_err, 0, sizeof(int), st));
-    if (!reuse) {
+    if (!reuse && !P.qr) {
       tok = prof_begin(TK_PHASE_GRAM, st);
       if (emulated_gram(P)) {  // the Cholesky reads only j >= i
         TK_TRY(oz_gram(B.Y, P.s, P.c, B.C, B.scratch, B.scratch_bytes, B.oz_err, st));
@@ -522,7 +527,14 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     }
     Arena none;
     OzCholPlan ozp;  // the trailing updates on the tensor cores (the Gram scratch is free again)
-    if (emulated_gram(P)) {  // chol_shifted times its float64 and tensor-core parts itself
+    if (P.qr) {  // BP2 (Section 4.1): a QR of the (s + n) x n partly exact sketch per lambda
+      tok = prof_begin(TK_PHASE_CHOLESKY, st);
+      TK_TRY(bp2_factor(B.Y, P.s, P.c, B.lam, N, B.R, P.np, P.np, P.np * P.np, B.info, B.scratch, B.scratch_bytes,
+                        st));
+      const double M = (double)(P.s + P.c);
+      prof_end(tok, st, (double)N * (2.0 * M * P.c * P.c - 2.0 * P.c * P.c * (double)P.c / 3.0),
+               8.0 * N * (M * P.c + P.c * P.c / 2.0));
+    } else if (emulated_gram(P)) {  // chol_shifted times its float64 and tensor-core parts itself
       TK_TRY(oz_chol_begin(B.R, P.np, P.np * P.np, N, P.np, B.scratch, B.scratch_bytes, B.oz_err, &ozp, st));
       TK_TRY(chol_shifted(B.C, P.c, B.lam, N, B.R, P.np, P.np * P.np, B.info, none, st, &ozp));
     } else {
@@ -1540,6 +1552,52 @@ TK_API tk_status tk_cholesky_shifted(const double* C, int64_t n, const double* l
 TK_API tk_status tk_cholesky_shifted_emulated(const double* C, int64_t n, const double* lambdas, int N, double* R,
                                               int* breakdown, void* work, size_t work_bytes, void* stream) {
   return cholesky_common(C, n, lambdas, N, R, breakdown, work, work_bytes, stream, true);
+}
+
+TK_API size_t tk_bp2_factor_workspace(int64_t s, int64_t n, int N) {
+  if (s < 0 || n < 1 || N < 1) return 0;
+  const int64_t np = cdiv(n, 64) * 64;
+  Arena a;
+  a.take<double>(N);
+  a.take<int>(N);
+  a.take<double>((size_t)N * np * np);
+  return a.used + bp2_workspace(s, n, N) + 1024;
+}
+
+TK_API tk_status tk_bp2_factor(const double* Y, int64_t s, int64_t n, const double* lambdas, int N, double* R,
+                               int* breakdown, void* work, size_t work_bytes, void* stream) {
+  if (!Y || !R || !lambdas || s < 0 || n < 1 || n > kMaxShort || N < 1) return einval("bad BP2 arguments");
+  for (int i = 0; i < N; ++i)
+    if (!(lambdas[i] > 0.0) || !std::isfinite(lambdas[i])) return einval("every lambda must be a positive finite number");
+  if (!work || work_bytes < tk_bp2_factor_workspace(s, n, N)) {
+    set_error_msg("workspace smaller than tk_bp2_factor_workspace()");
+    return TK_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t np = cdiv(n, 64) * 64;
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  double* lam = a.take<double>(N);
+  int* info = a.take<int>(N);
+  double* Rp = a.take<double>((size_t)N * np * np);
+  const size_t qb = bp2_workspace(s, n, N);
+  void* qw = a.take<char>(qb);
+  if (!a.ok()) return TK_ENOMEM;
+  TK_CUDA(cudaMemcpyAsync(lam, lambdas, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+  TK_TRY(bp2_factor(Y, s, n, lam, N, Rp, np, np, np * np, info, qw, qb, st));
+  for (int i = 0; i < N; ++i)
+    TK_CUDA(cudaMemcpy2DAsync(R + (size_t)i * n * n, sizeof(double) * n, Rp + (size_t)i * np * np,
+                              sizeof(double) * np, sizeof(double) * n, n, cudaMemcpyDeviceToDevice, st));
+  std::vector<int> h(N);
+  TK_CUDA(cudaMemcpyAsync(h.data(), info, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  tk_status worst = TK_OK;
+  for (int i = 0; i < N; ++i) {
+    if (breakdown) breakdown[i] = h[i];
+    if (h[i]) worst = worse(worst, h[i] < 0 ? TK_ENUMERIC : TK_ENOTSPD);
+  }
+  return worst;
 }
 
 TK_API size_t tk_sketch_svd_workspace(int64_t s, int64_t n) { return svd_workspace(s, n) + 1024; }

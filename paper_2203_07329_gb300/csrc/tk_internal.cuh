@@ -310,6 +310,11 @@ tk_status gram_upper(const double* Y, int64_t r, int64_t c, double* C, void* scr
                      cudaStream_t st);
 
 size_t chol_workspace(int64_t n, int N);
+// BP2 (tk_qr.cu, Section 4.1): R_l from a Householder QR of [Y; sqrt(l) I] for every lambda (diag > 0, identity
+// padding up to np); info as chol_shifted (NaN: negative).
+size_t bp2_workspace(int64_t s, int64_t n, int N);
+tk_status bp2_factor(const double* Y, int64_t s, int64_t n, const double* lam_dev, int N, double* R, int64_t np,
+                     int64_t ldr, int64_t rstride, int* info_dev, void* work, size_t bytes, cudaStream_t st);
 tk_status chol_shifted(const double* C, int64_t n, const double* lambdas_dev, int N, double* R, int64_t ldr,
                        int64_t rstride, int* info_dev, Arena& ar, cudaStream_t st, const OzCholPlan* oz = nullptr);
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libtikhonov.so")
 TK_OK, TK_EINVAL, TK_ENOMEM, TK_ENOTSPD, TK_ENOCONV, TK_ENUMERIC, TK_ETIMEOUT, TK_ECUDA = range(8)
 TK_F64, TK_F32 = 0, 1
 TK_SKETCH_SRHT, TK_SKETCH_GAUSS, TK_SKETCH_SPARSE = 0, 1, 2
-TK_PRECOND_CHOL, TK_PRECOND_LOWRANK = 0, 1
+TK_PRECOND_CHOL, TK_PRECOND_LOWRANK, TK_PRECOND_QR = 0, 1, 2
 TK_PREC_FP64, TK_PREC_MIXED = 0, 1
 TK_SCHED_BATCHED, TK_SCHED_ONE_AT_A_TIME = 0, 1
 
@@ -92,6 +92,8 @@ def lib() -> C.CDLL:
             "tk_cholesky_shifted": (INT, [P, I64, P, INT, P, P, P, SZ, P]),
             "tk_cholesky_emulated_workspace": (SZ, [I64, INT]),
             "tk_cholesky_shifted_emulated": (INT, [P, I64, P, INT, P, P, P, SZ, P]),
+            "tk_bp2_factor_workspace": (SZ, [I64, I64, INT]),
+            "tk_bp2_factor": (INT, [P, I64, I64, P, INT, P, P, P, SZ, P]),
             "tk_sketch_svd_workspace": (SZ, [I64, I64]),
             "tk_sketch_svd": (INT, [P, I64, I64, P, P, P, P, SZ, P]),
             "tk_lowrank_ranks_workspace": (SZ, [INT]),
@@ -341,6 +343,20 @@ def tk_cholesky_shifted(Cm: torch.Tensor, lambdas, stream=None, emulate: bool = 
         fn = lib().tk_cholesky_shifted
     st = fn(_ptr(Cm.contiguous()), n, lam.ctypes.data_as(C.c_void_p), N, _ptr(R), brk, _ptr(work), work.numel(),
             _stream(stream))
+    _check(st, (TK_OK, TK_ENOTSPD))
+    return R, list(brk)
+
+
+def tk_bp2_factor(Y: torch.Tensor, lambdas, stream=None):
+    """BP2 factors R_i from a QR of [Y; sqrt(l_i) I] (Section 4.1): (R N x n x n, breakdown list)."""
+    s, n = Y.shape
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+    N = lam.shape[0]
+    R = torch.empty((N, n, n), dtype=torch.float64, device=Y.device)
+    brk = (C.c_int * N)()
+    work = _workspace(lib().tk_bp2_factor_workspace(s, n, N), Y.device)
+    st = lib().tk_bp2_factor(_ptr(Y.contiguous()), s, n, lam.ctypes.data_as(C.c_void_p), N, _ptr(R), brk, _ptr(work),
+                             work.numel(), _stream(stream))
     _check(st, (TK_OK, TK_ENOTSPD))
     return R, list(brk)
 

@@ -237,3 +237,25 @@ def test_sparse_sketch_arguments_checked_on_host(tk):
     assert L.tk_workspace_size(C.byref(_prob(tk, 1 << 23, 50)), 2, C.byref(o), C.byref(out)) == tk.TK_EINVAL
     o.sketch = 7
     assert L.tk_workspace_size(C.byref(_prob(tk, 5000, 50)), 2, C.byref(o), C.byref(out)) == tk.TK_EINVAL
+
+
+def test_bp2_arguments_checked_on_host(tk):
+    L = tk.lib()
+    fake = C.c_void_p(0x1000)
+    lam = np.array([1e-3, 1.0])
+    brk = (C.c_int * 2)()
+    need = L.tk_bp2_factor_workspace(300, 70, 2)
+    assert need >= 8 * 2 * 370 * 70  # the two (s + n) x n stacks
+    assert L.tk_bp2_factor(fake, 300, 70, lam.ctypes.data_as(C.c_void_p), 2, fake, brk, fake, need - 1,
+                           None) == tk.TK_ENOMEM
+    bad = np.array([1e-3, 0.0])
+    assert L.tk_bp2_factor(fake, 300, 70, bad.ctypes.data_as(C.c_void_p), 2, fake, brk, fake, need,
+                           None) == tk.TK_EINVAL
+    out = C.c_size_t(0)
+    o = tk.opts_default(precond=tk.TK_PRECOND_QR)
+    assert L.tk_workspace_size(C.byref(_prob(tk, 10, 100)), 2, C.byref(o), C.byref(out)) == tk.TK_EINVAL  # m < n
+    assert L.tk_workspace_size(C.byref(_prob(tk, 1000, 50)), 3, C.byref(o), C.byref(out)) == tk.TK_OK
+    cho = tk.opts_default()
+    out2 = C.c_size_t(0)
+    assert L.tk_workspace_size(C.byref(_prob(tk, 1000, 50)), 3, C.byref(cho), C.byref(out2)) == tk.TK_OK
+    assert out.value >= out2.value + 8 * 3 * 50 * (200 + 50) - 4096  # the QR stacks (s = 4n = 200)
