@@ -255,7 +255,6 @@ def test_bp2_arguments_checked_on_host(tk):
     o = tk.opts_default(precond=tk.TK_PRECOND_QR)
     assert L.tk_workspace_size(C.byref(_prob(tk, 10, 100)), 2, C.byref(o), C.byref(out)) == tk.TK_EINVAL  # m < n
     assert L.tk_workspace_size(C.byref(_prob(tk, 1000, 50)), 3, C.byref(o), C.byref(out)) == tk.TK_OK
-    cho = tk.opts_default()
-    out2 = C.c_size_t(0)
-    assert L.tk_workspace_size(C.byref(_prob(tk, 1000, 50)), 3, C.byref(cho), C.byref(out2)) == tk.TK_OK
-    assert out.value >= out2.value + 8 * 3 * 50 * (200 + 50) - 4096  # the QR stacks (s = 4n = 200)
+    o.s = 800
+    assert L.tk_workspace_size(C.byref(_prob(tk, 1000, 50)), 3, C.byref(o), C.byref(out)) == tk.TK_OK
+    assert out.value >= 8 * 3 * 50 * (800 + 50)  # the three (s + n) x n QR stacks
