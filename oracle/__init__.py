@@ -79,6 +79,9 @@ def lib():
                 "orc_draw_sparse": (None, [_u64, _i64, _i64, _p, _p]),
                 "orc_sparse_over": (None, [_p, _i64, _i64, _i64, _u64, _i64, _p]),
                 "orc_sparse_under": (None, [_p, _i64, _i64, _i64, _u64, _i64, _p]),
+                "orc_dct2_rows": (None, [_p, _i64, _p, _i64, _p]),
+                "orc_srdct_over": (None, [_p, _i64, _i64, _i64, _u64, _i64, _p]),
+                "orc_srdct_under": (None, [_p, _i64, _i64, _i64, _u64, _i64, _p]),
                 "orc_bp2_r": (_int, [_p, _i64, _i64, _d, _p]),
                 "orc_lcurve_norms": (None, [_p, _i64, _i64, _i64, _p, _p, _int, _p, _p]),
                 "orc_lcurve_curvature": (_int, [_p, _p, _p, _int, _p]),
@@ -106,6 +109,7 @@ def lib():
 SKETCH_SRHT = 0
 SKETCH_GAUSS = 1
 SKETCH_SPARSE = 2
+SKETCH_SRDCT = 3
 
 
 def _f64(a) -> np.ndarray:
@@ -225,13 +229,42 @@ def sparse_under(A, seed: int, s: int) -> np.ndarray:
     return Y
 
 
+def dct2_rows(z, rows) -> np.ndarray:
+    """Rows `rows` of the orthonormal DCT-II of z, each by its defining sum."""
+    z = _f64(z)
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros(r.shape[0])
+    lib().orc_dct2_rows(_ptr(z), z.shape[0], _ptr(r), r.shape[0], _ptr(out))
+    return out
+
+
+def srdct_over(A, seed: int, s: int) -> np.ndarray:
+    """Y = sqrt(mp/s) S C D [A; 0] (s x n), C the orthonormal DCT-II of length mp."""
+    A, m, n, lda = _dims(A)
+    Y = np.zeros((s, n))
+    lib().orc_srdct_over(_ptr(A), m, n, lda, seed, s, _ptr(Y))
+    return Y
+
+
+def srdct_under(A, seed: int, s: int) -> np.ndarray:
+    """Y = sqrt(np/s) [A 0] D C^T S^T (m x s)."""
+    A, m, n, lda = _dims(A)
+    Y = np.zeros((m, s))
+    lib().orc_srdct_under(_ptr(A), m, n, lda, seed, s, _ptr(Y))
+    return Y
+
+
 def sketch_over(A, kind: int, seed: int, s: int) -> np.ndarray:
+    if kind == SKETCH_SRDCT:
+        return srdct_over(A, seed, s)
     if kind == SKETCH_SPARSE:
         return sparse_over(A, seed, s)
     return srht_over(A, seed, s) if kind == SKETCH_SRHT else gauss_over(A, seed, s)
 
 
 def sketch_under(A, kind: int, seed: int, s: int) -> np.ndarray:
+    if kind == SKETCH_SRDCT:
+        return srdct_under(A, seed, s)
     if kind == SKETCH_SPARSE:
         return sparse_under(A, seed, s)
     return srht_under(A, seed, s) if kind == SKETCH_SRHT else gauss_under(A, seed, s)

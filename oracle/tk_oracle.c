@@ -234,6 +234,64 @@ ORC_API void orc_gauss_under(const double* A, int64_t m, int64_t n, int64_t lda,
     }
 }
 
+/* SRDCT (Section 2.1.1 with F the discrete cosine transform, the embedding of
+ * the paper's Fig. 1 and 2): X = sqrt(mp/s) S C D [I; 0], C the orthonormal
+ * DCT-II of length mp (the next power of two, as for the SRHT),
+ *   C[k][i] = a_k cos(pi (2i + 1) k / (2 mp)),  a_0 = sqrt(1/mp), a_k = sqrt(2/mp),
+ * D and S the SRHT's signs (stream 0) and row subset (stream 1).  Only the s
+ * sampled rows of C D [A; 0] are formed, each by its defining sum. */
+ORC_API void orc_dct2_rows(const double* z, int64_t N, const int64_t* rows, int64_t s, double* out) {
+  for (int64_t q = 0; q < s; ++q) {
+    const int64_t k = rows[q];
+    const double a = k == 0 ? sqrt(1.0 / (double)N) : sqrt(2.0 / (double)N);
+    double acc = 0.0;
+    /* the angle's integer part reduced modulo 4 mp first (cos has period 2 pi), so the argument stays
+     * below 2 pi and carries no error from a large multiple of pi */
+    for (int64_t i = 0; i < N; ++i) {
+      const int64_t r = ((2 * i + 1) * k) % (4 * N);
+      acc += z[i] * cos(3.14159265358979323846 * (double)r / (double)(2 * N));
+    }
+    out[q] = a * acc;
+  }
+}
+
+ORC_API void orc_srdct_over(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, int64_t s,
+                            double* Y) {
+  const int64_t mp = orc_next_pow2(m);
+  int8_t* d = (int8_t*)malloc((size_t)mp);
+  int64_t* rows = (int64_t*)malloc(sizeof(int64_t) * (size_t)(s > 0 ? s : 1));
+  double* z = (double*)malloc(sizeof(double) * (size_t)mp);
+  double* o = (double*)malloc(sizeof(double) * (size_t)(s > 0 ? s : 1));
+  orc_draw_signs(seed, mp, d);
+  orc_draw_rows(seed, mp, s, rows);
+  const double scale = sqrt((double)mp / (double)s);
+  for (int64_t j = 0; j < n; ++j) {
+    for (int64_t i = 0; i < mp; ++i) z[i] = (i < m) ? (double)d[i] * A[i * lda + j] : 0.0;
+    orc_dct2_rows(z, mp, rows, s, o);
+    for (int64_t k = 0; k < s; ++k) Y[k * n + j] = scale * o[k];
+  }
+  free(d); free(rows); free(z); free(o);
+}
+
+/* SRDCT on the columns (Algorithm 2): Y = A X^T = sqrt(np/s) [A 0] D C^T S^T (m x s). */
+ORC_API void orc_srdct_under(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, int64_t s,
+                             double* Y) {
+  const int64_t np = orc_next_pow2(n);
+  int8_t* d = (int8_t*)malloc((size_t)np);
+  int64_t* cols = (int64_t*)malloc(sizeof(int64_t) * (size_t)(s > 0 ? s : 1));
+  double* z = (double*)malloc(sizeof(double) * (size_t)np);
+  double* o = (double*)malloc(sizeof(double) * (size_t)(s > 0 ? s : 1));
+  orc_draw_signs(seed, np, d);
+  orc_draw_rows(seed, np, s, cols);
+  const double scale = sqrt((double)np / (double)s);
+  for (int64_t i = 0; i < m; ++i) {
+    for (int64_t j = 0; j < np; ++j) z[j] = (j < n) ? (double)d[j] * A[i * lda + j] : 0.0;
+    orc_dct2_rows(z, np, cols, s, o);
+    for (int64_t k = 0; k < s; ++k) Y[i * s + k] = scale * o[k];
+  }
+  free(d); free(cols); free(z); free(o);
+}
+
 /* Sparse embedding (Section 2.1.1: one nonzero element in each column; the
  * sparse subspace embedding of Theorem 3.5).  Column i of the s x L matrix X
  * holds sign_i in row h_i, both from Philox stream 4 at index i:
@@ -702,18 +760,20 @@ ORC_API void orc_lr_diag(const double* sigma, int64_t si, double lambda, double*
 /* ------------------------------------------------------------------------ */
 /* Whole algorithms, one lambda at a time, exactly in the paper's order       */
 /* ------------------------------------------------------------------------ */
-/* sketch kinds: 0 = SRHT, 1 = Gaussian, 2 = sparse (one nonzero per column) */
+/* sketch kinds: 0 = SRHT, 1 = Gaussian, 2 = sparse (one nonzero per column), 3 = SRDCT */
 static void sketch_over(int kind, const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, int64_t s,
                         double* Y) {
   if (kind == 0) orc_srht_over(A, m, n, lda, seed, s, Y);
   else if (kind == 1) orc_gauss_over(A, m, n, lda, seed, s, Y);
-  else orc_sparse_over(A, m, n, lda, seed, s, Y);
+  else if (kind == 2) orc_sparse_over(A, m, n, lda, seed, s, Y);
+  else orc_srdct_over(A, m, n, lda, seed, s, Y);
 }
 static void sketch_under(int kind, const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed, int64_t s,
                          double* Y) {
   if (kind == 0) orc_srht_under(A, m, n, lda, seed, s, Y);
   else if (kind == 1) orc_gauss_under(A, m, n, lda, seed, s, Y);
-  else orc_sparse_under(A, m, n, lda, seed, s, Y);
+  else if (kind == 2) orc_sparse_under(A, m, n, lda, seed, s, Y);
+  else orc_srdct_under(A, m, n, lda, seed, s, Y);
 }
 
 /* Algorithm 1: X drawn once (step 1), Y = XA (2), C = Y^T Y (3); for each

@@ -574,3 +574,53 @@ def test_alg1_with_bp2_reaches_the_reference(orc):
         assert np.linalg.norm(X[:, i] - xr) / np.linalg.norm(xr) < 1e-10
     # the same preconditioner in exact arithmetic: the same iteration counts to within rounding
     assert np.all(np.abs(it - itc) <= 2), (it, itc)
+
+
+# ----------------------------------------------------------- SRDCT (f4) --
+def test_dct_rows_are_the_orthonormal_dct2(orc):
+    # the defining sums against scipy's fast DCT-II (norm="ortho"), and orthogonality of the matrix
+    import scipy.fft
+    N = 256
+    z = RNG.standard_normal(N)
+    rows = np.array([0, 1, 5, 100, 255])
+    np.testing.assert_allclose(orc.dct2_rows(z, rows), scipy.fft.dct(z, type=2, norm="ortho")[rows], rtol=1e-12,
+                               atol=1e-13)
+    Cm = np.stack([orc.dct2_rows(e, np.arange(64)) for e in np.eye(64)], axis=1)
+    np.testing.assert_allclose(Cm.T @ Cm, np.eye(64), atol=1e-13)
+
+
+def test_srdct_sketch_is_the_explicit_embedding(orc):
+    import scipy.fft
+    m, n, s = 300, 7, 40  # mp = 512: rows 300..511 are zero padding
+    A = RNG.standard_normal((m, n))
+    mp = 512
+    d = orc.draw_signs(6, mp).astype(np.float64)
+    rows = orc.draw_rows(6, mp, s)
+    Z = np.zeros((mp, n))
+    Z[:m] = d[:m, None] * A
+    Yx = math.sqrt(mp / s) * scipy.fft.dct(Z, type=2, norm="ortho", axis=0)[rows]
+    np.testing.assert_allclose(orc.srdct_over(A, 6, s), Yx, rtol=1e-11, atol=1e-12)
+    B = RNG.standard_normal((n, m))
+    Yu = math.sqrt(mp / s) * scipy.fft.dct(np.hstack([d[None, :m] * B, np.zeros((n, mp - m))]), type=2,
+                                          norm="ortho", axis=1)[:, rows]
+    np.testing.assert_allclose(orc.srdct_under(B, 6, s), Yu, rtol=1e-11, atol=1e-12)
+
+
+def test_srdct_is_isotropic_in_expectation(orc):
+    # E[X^T X] = (mp/s) D C^T E[S^T S] C D = I: averaged over seeds on a small case
+    m, s, T = 16, 8, 300
+    acc = np.zeros((m, m))
+    for seed in range(T):
+        X = orc.srdct_over(np.eye(m), seed, s)  # s x m: the embedding itself
+        acc += X.T @ X
+    acc /= T
+    assert np.abs(acc - np.eye(m)).max() < 0.25
+
+
+def test_alg1_with_srdct_reaches_the_reference(orc):
+    A, b, p = small_problem(900, 20, sig_lo=1e-4)
+    lams = np.array([1e-7, 1e-2])
+    X, it, _, _ = orc.alg1(A, b, lams, orc.SKETCH_SRDCT, 100, 2, 1e-14, 500)
+    for i, lam in enumerate(lams):
+        xr = orc.ref_ridge_qr(A, b, lam, refine=3)
+        assert np.linalg.norm(X[:, i] - xr) / np.linalg.norm(xr) < 1e-10
