@@ -61,8 +61,10 @@ typedef enum { TK_F64 = 0, TK_F32 = 1 } tk_dtype;
  * in each column: sign_i in row h_i, both from Philox stream 4 at index i,
  * h_i = floor(w0 s / 2^32), sign_i = -1 when the low bit of w1 is set; applied
  * in O(nnz(A)) by adding each row of A into its bucket in ascending row order;
- * s <= 2^22). */
-typedef enum { TK_SKETCH_SRHT = 0, TK_SKETCH_GAUSS = 1, TK_SKETCH_SPARSE = 2 } tk_sketch;
+ * s <= 2^22), and SRDCT (the SRHT with the orthonormal DCT-II in place of the Hadamard transform,
+ * the embedding of the paper's Fig. 1-2: X = sqrt(mp/s) S C D, same signs and rows as the SRHT,
+ * computed through one complex FFT of length mp per column). */
+typedef enum { TK_SKETCH_SRHT = 0, TK_SKETCH_GAUSS = 1, TK_SKETCH_SPARSE = 2, TK_SKETCH_SRDCT = 3 } tk_sketch;
 /* Preconditioners: CHOL = Algorithm 1 / 2 (R_i = chol(C + lambda_i I)); LOWRANK = Algorithms 3 / 4
  * (Sections 3.1 / 3.2); QR = BP2 of Section 4.1 (m >= n): R_i from a Householder QR of the
  * (s + n) x n partly exact sketch [X A; sqrt(lambda_i) I], the same factor as CHOL in exact

@@ -54,7 +54,8 @@ constexpr int64_t kMaxLong = (int64_t(1) << 30);
 
 tk_status check_opts(const tk_opts* o) {
   if (!o) return einval("options pointer is NULL");
-  if (o->sketch != TK_SKETCH_SRHT && o->sketch != TK_SKETCH_GAUSS && o->sketch != TK_SKETCH_SPARSE)
+  if (o->sketch != TK_SKETCH_SRHT && o->sketch != TK_SKETCH_GAUSS && o->sketch != TK_SKETCH_SPARSE &&
+      o->sketch != TK_SKETCH_SRDCT)
     return einval("unknown sketch kind");
   if (o->precond != TK_PRECOND_CHOL && o->precond != TK_PRECOND_LOWRANK && o->precond != TK_PRECOND_QR)
     return einval("unknown preconditioner");
@@ -99,7 +100,8 @@ tk_status make_plan(const tk_problem* p, int N, const tk_opts* o, Plan& P) {
   int64_t s = o->s;
   // the sparse embedding needs more rows for the same distortion (Theorem 3.5: s grows with sd^2)
   if (s == 0) s = P.lowrank ? P.c : std::min<int64_t>((o->sketch == TK_SKETCH_SPARSE ? 16 : 4) * P.c, P.L);
-  if (o->sketch == TK_SKETCH_SRHT && s > next_pow2(P.L)) return einval("SRHT sketch size exceeds the padded length");
+  if ((o->sketch == TK_SKETCH_SRHT || o->sketch == TK_SKETCH_SRDCT) && s > next_pow2(P.L))
+    return einval("SRHT / SRDCT sketch size exceeds the padded length");
   if (o->sketch == TK_SKETCH_SPARSE && s > kSparseMaxS) return einval("sparse sketch size above 2^22");
   if (P.lowrank && s > P.c) s = P.c;  // alpha * sd <= n (Algorithm 3); a full-size sketch is still exact
   P.s = s;
@@ -179,6 +181,7 @@ size_t sketch_scratch(const Plan& P) {
   if (tc_sketch(P)) return tc_sketch_workspace(P.L, P.c, P.s);
   if (P.o.sketch == TK_SKETCH_SRHT) return srht_rows_workspace(P.L, P.c, dt, P.s);
   if (P.o.sketch == TK_SKETCH_SPARSE) return sparse_rows_workspace(P.L, P.c, P.s);
+  if (P.o.sketch == TK_SKETCH_SRDCT) return srdct_rows_workspace(P.L, P.c, dt, P.s);
   return gauss_rows_workspace(P.L, P.c, dt, P.s);
 }
 
@@ -385,6 +388,7 @@ tk_status do_sketch(const Plan& P, const void* A_sk, tk_dtype dt_sk, int64_t ld_
   if (tc_sketch(P)) return tc_gauss_sketch(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
   if (P.o.sketch == TK_SKETCH_SRHT) return srht_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
   if (P.o.sketch == TK_SKETCH_SPARSE) return sparse_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
+  if (P.o.sketch == TK_SKETCH_SRDCT) return srdct_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
   return gauss_rows(src, dt_sk, P.L, P.c, ld, P.o.seed, P.s, B.Y, sa, st);
 }
 
@@ -504,6 +508,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     const double es = dt_sk == TK_F64 ? 8.0 : 4.0;
     const double Lp = (double)next_pow2(P.L);
     const double fl = P.o.sketch == TK_SKETCH_SRHT    ? Lp * std::log2(Lp) * P.c
+                      : P.o.sketch == TK_SKETCH_SRDCT ? 5.0 * Lp * std::log2(Lp) * P.c
                       : P.o.sketch == TK_SKETCH_SPARSE ? (double)P.L * P.c
                                                        : 2.0 * P.s * P.L * P.c;
     int tok = prof_begin(TK_PHASE_SKETCH, st);

@@ -181,6 +181,10 @@ size_t srht_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s);
 tk_status gauss_rows(const void* A, tk_dtype dt, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s,
                      double* Y, Arena& ar, cudaStream_t st);
 size_t gauss_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s);
+// SRDCT (tk_sketch.cu): X = sqrt(Lp/s) S C D [I; 0], C the orthonormal DCT-II of length Lp.
+tk_status srdct_rows(const void* A, tk_dtype dt, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s,
+                     double* Y, Arena& ar, cudaStream_t st);
+size_t srdct_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s);
 // Sparse embedding (tk_sparse.cu): one signed entry per column of X (s x L).
 constexpr int64_t kSparseMaxS = int64_t(1) << 22;
 tk_status sparse_rows(const void* A, tk_dtype dt, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s,

@@ -119,6 +119,151 @@ tk_status run_fwht_pass(bool first, bool last, const TIn* srcA, const TC* srcZ, 
   return TK_OK;
 }
 
+// ---- SRDCT ---------------------------------------------------------------------
+// X = sqrt(Lp/s) S C D [A; 0] with C the orthonormal DCT-II of length Lp (a
+// power of two), D and S the SRHT's draws.  The DCT of each column comes from
+// one complex FFT of the same length (Makhoul): with v_i = x_2i and
+// v_(Lp-1-i) = x_(2i+1) (i < Lp/2) and V = FFT(v),
+//   DCT-II(x)_k = Re(exp(-i pi k / (2 Lp)) V_k),  times a_k = sqrt((1 + [k > 0]) / Lp).
+// The FFT is radix-2 decimation in frequency: stage j (from the top bit down)
+// pairs rows i and i + 2^j and multiplies the difference by
+// exp(-2 pi i (i mod 2^j) / 2^(j+1)) = T[(i mod 2^j) 2^(a-1-j)], T a table of
+// exp(-2 pi i q / Lp).  Passes run up to 8 stages on a tile of 2^t rows x one
+// 128-byte column block (real and imaginary parts in shared memory); the
+// first pass loads the reordered, sign-flipped rows of A, the last one leaves
+// V_k in row bitrev(k) and evaluates only the sampled k.
+constexpr int kFftMaxBits = 8;
+
+template <typename TC>
+__global__ void k_fft_twiddles(int64_t Lp, TC* __restrict__ tre, TC* __restrict__ tim) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Lp / 2; q += (int64_t)gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (double)q / (double)Lp, &sn, &cs);
+    tre[q] = (TC)cs;
+    tim[q] = (TC)(-sn);
+  }
+}
+
+template <typename TIn, typename TC, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(kFwhtThreads)
+    k_fft_pass(const TIn* __restrict__ src, int64_t ld_src, TC* __restrict__ zre, TC* __restrict__ zim,
+               double* __restrict__ Y, const int8_t* __restrict__ signs, const int32_t* __restrict__ rowmap,
+               const TC* __restrict__ tre, const TC* __restrict__ tim, int64_t L, int a, int64_t cols, int b0, int t,
+               int64_t ncb, double scale) {
+  constexpr int CB = fwht_cb<TC>(), LCB = fwht_lcb<TC>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* sre = reinterpret_cast<TC*>(smem_raw);
+  TC* sim = sre + (CB << t);
+  const int64_t Lp = int64_t(1) << a;
+  const int64_t g = blockIdx.x / ncb;
+  const int64_t cb = blockIdx.x - g * ncb;
+  const int64_t lo = g & ((int64_t(1) << b0) - 1);
+  const int64_t hi = g >> b0;
+  const int rows_t = 1 << t;
+  const int64_t c0 = cb * CB;
+  const int tile_elems = rows_t << LCB;
+  for (int idx = threadIdx.x; idx < tile_elems; idx += blockDim.x) {
+    const int mid = idx >> LCB, c = idx & (CB - 1);
+    const int64_t r = (hi << (b0 + t)) | ((int64_t)mid << b0) | lo;
+    const int64_t col = c0 + c;
+    TC vr = TC(0), vi = TC(0);
+    if (col < cols) {
+      if (FIRST) {
+        const int64_t sr = Lp == 1 ? 0 : (r < Lp / 2 ? 2 * r : 2 * (Lp - 1 - r) + 1);  // Makhoul's reordering
+        if (sr < L) vr = (TC)src[sr * ld_src + col] * (TC)signs[sr];
+      } else {
+        vr = zre[r * cols + col];
+        vi = zim[r * cols + col];
+      }
+    }
+    sre[idx] = vr;
+    sim[idx] = vi;
+  }
+  __syncthreads();
+  const int pairs = (rows_t >> 1) << LCB;
+  for (int lv = t - 1; lv >= 0; --lv) {  // global bit j = b0 + lv, top bit first
+    const int h = 1 << lv;
+    const int j = b0 + lv;
+    for (int p = threadIdx.x; p < pairs; p += blockDim.x) {
+      const int q = p >> LCB, c = p & (CB - 1);
+      const int i = ((q >> lv) << (lv + 1)) | (q & (h - 1));
+      const int ia = (i << LCB) + c, ib = ia + (h << LCB);
+      const TC ar = sre[ia], ai = sim[ia], br = sre[ib], bi = sim[ib];
+      const int64_t tw = ((((int64_t)(i & (h - 1))) << b0) | lo) << (a - 1 - j);
+      const TC wr = tre[tw], wi = tim[tw];
+      const TC dr = ar - br, di = ai - bi;
+      sre[ia] = ar + br;
+      sim[ia] = ai + bi;
+      sre[ib] = dr * wr - di * wi;
+      sim[ib] = dr * wi + di * wr;
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < tile_elems; idx += blockDim.x) {
+    const int mid = idx >> LCB, c = idx & (CB - 1);
+    const int64_t r = (hi << (b0 + t)) | ((int64_t)mid << b0) | lo;
+    const int64_t col = c0 + c;
+    if (col >= cols) continue;
+    if (LAST) {
+      const int64_t k = a == 0 ? 0 : (int64_t)(__brevll((unsigned long long)r) >> (64 - a));  // V_k in row bitrev(k)
+      const int32_t q = rowmap[k];
+      if (q >= 0) {
+        double sn, cs;
+        sincospi((double)k / (double)(2 * Lp), &sn, &cs);
+        const double ak = k == 0 ? sqrt(1.0 / (double)Lp) : sqrt(2.0 / (double)Lp);
+        Y[(int64_t)q * cols + col] = scale * ak * (cs * (double)sre[idx] + sn * (double)sim[idx]);
+      }
+    } else {
+      zre[r * cols + col] = sre[idx];
+      zim[r * cols + col] = sim[idx];
+    }
+  }
+}
+
+template <typename TIn, typename TC>
+tk_status srdct_impl(const TIn* A, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s, double* Y,
+                     Arena& ar, cudaStream_t st) {
+  const int64_t Lp = next_pow2(L);
+  const int a = ilog2(Lp);
+  int8_t* signs = ar.take<int8_t>((size_t)Lp);
+  int32_t* rowmap = ar.take<int32_t>((size_t)Lp);
+  TC* zre = (a > kFftMaxBits) ? ar.take<TC>((size_t)Lp * (size_t)cols) : nullptr;
+  TC* zim = (a > kFftMaxBits) ? ar.take<TC>((size_t)Lp * (size_t)cols) : nullptr;
+  TC* tre = ar.take<TC>((size_t)std::max<int64_t>(Lp / 2, 1));
+  TC* tim = ar.take<TC>((size_t)std::max<int64_t>(Lp / 2, 1));
+  if (!ar.ok()) return TK_ENOMEM;
+  if (a > 62) return TK_EINVAL;
+  TK_TRY(draw_signs_rows(seed, Lp, s, signs, nullptr, rowmap, ar, st));
+  if (s == 0 || cols == 0) return TK_OK;
+  if (Lp >= 2) {
+    k_fft_twiddles<TC><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(Lp / 2, 256), 152 * 32)), 256, 0, st>>>(
+        Lp, tre, tim);
+    TK_LAUNCH_CHECK();
+  }
+  const double scale = sqrt((double)Lp / (double)s);
+  const int CB = fwht_cb<TC>();
+  const int64_t ncb = cdiv(cols, CB);
+  int top = a;
+  bool first = true;
+  do {
+    const int b0 = std::max(top - kFftMaxBits, 0);
+    const int t = top - b0;
+    const bool last = b0 == 0;
+    const int64_t blocks = (Lp >> t) * ncb;
+    const size_t smem = 2 * sizeof(TC) * (size_t)(1 << t) * CB;
+#define TK_FFT_LAUNCH(F, LST)                                                                                   do {                                                                                                            auto kern = k_fft_pass<TIn, TC, F, LST>;                                                                      TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));                  kern<<<(unsigned)blocks, kFwhtThreads, smem, st>>>(A, ld, zre, zim, Y, signs, rowmap, tre, tim, L, a, cols,                                                        b0, t, ncb, scale);                                      } while (0)
+    if (first && last) TK_FFT_LAUNCH(true, true);
+    else if (first) TK_FFT_LAUNCH(true, false);
+    else if (last) TK_FFT_LAUNCH(false, true);
+    else TK_FFT_LAUNCH(false, false);
+#undef TK_FFT_LAUNCH
+    TK_LAUNCH_CHECK();
+    first = false;
+    top = b0;
+  } while (top > 0);
+  return TK_OK;
+}
+
 template <typename TC>
 __global__ void k_gauss_fill(uint64_t seed, int64_t s, int64_t L, double inv_sqrt_s, TC* __restrict__ G) {
   int64_t total = s * L;
@@ -239,6 +384,28 @@ size_t srht_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s) {
   a.take<int32_t>((size_t)Lp);
   if (ilog2(Lp) > kFwhtMaxBits) a.take<char>((size_t)Lp * (size_t)cols * (dt == TK_F64 ? 8 : 4));
   return a.used + draw_workspace(Lp) + 512;
+}
+
+size_t srdct_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s) {
+  (void)s;
+  const int64_t Lp = next_pow2(L);
+  const size_t es = dt == TK_F64 ? 8 : 4;
+  Arena a;
+  a.take<int8_t>((size_t)Lp);
+  a.take<int32_t>((size_t)Lp);
+  if (ilog2(Lp) > kFftMaxBits) {
+    a.take<char>((size_t)Lp * (size_t)cols * es);
+    a.take<char>((size_t)Lp * (size_t)cols * es);
+  }
+  a.take<char>((size_t)std::max<int64_t>(Lp / 2, 1) * es);
+  a.take<char>((size_t)std::max<int64_t>(Lp / 2, 1) * es);
+  return a.used + draw_workspace(Lp) + 512;
+}
+
+tk_status srdct_rows(const void* A, tk_dtype dt, int64_t L, int64_t cols, int64_t ld, uint64_t seed, int64_t s,
+                     double* Y, Arena& ar, cudaStream_t st) {
+  if (dt == TK_F64) return srdct_impl<double, double>((const double*)A, L, cols, ld, seed, s, Y, ar, st);
+  return srdct_impl<float, float>((const float*)A, L, cols, ld, seed, s, Y, ar, st);
 }
 
 size_t gauss_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s) {

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libtikhonov.so")
 
 TK_OK, TK_EINVAL, TK_ENOMEM, TK_ENOTSPD, TK_ENOCONV, TK_ENUMERIC, TK_ETIMEOUT, TK_ECUDA = range(8)
 TK_F64, TK_F32 = 0, 1
-TK_SKETCH_SRHT, TK_SKETCH_GAUSS, TK_SKETCH_SPARSE = 0, 1, 2
+TK_SKETCH_SRHT, TK_SKETCH_GAUSS, TK_SKETCH_SPARSE, TK_SKETCH_SRDCT = 0, 1, 2, 3
 TK_PRECOND_CHOL, TK_PRECOND_LOWRANK, TK_PRECOND_QR = 0, 1, 2
 TK_PREC_FP64, TK_PREC_MIXED = 0, 1
 TK_SCHED_BATCHED, TK_SCHED_ONE_AT_A_TIME = 0, 1
