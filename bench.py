@@ -312,12 +312,15 @@ def uneven_batch_step(tk, datagen, stream, barrier):
             "phase_ms_summed_over_lanes": {k: v["ms"] for k, v in prof.items() if v["launches"]}}
 
 
-def roofline_of(prof, peaks, peak_src, a_elems):
+def roofline_of(prof, peaks, peak_src, a_elems, fp64=False):
     """Roofline line of the phase with the largest event time in `prof` (tk_profile_collect totals over
-    the timed region), judged by that phase's bound; traffic scaled from an ncu capture when one exists."""
+    the timed region), judged by that phase's bound; traffic scaled from an ncu capture when one exists.
+    fp64: the plain float64 form, whose products and inverse run on the float64 pipe."""
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     name, st = dom
     bound = PHASE_BOUND.get(name, "fp32")
+    if fp64 and name in ("A_times_W", "At_times_U", "precond_inverse"):
+        bound = "fp64"
     per_launch_ms = st["ms"] / max(st["launches"], 1)
     secs = st["ms"] / 1e3
     if bound == "hbm":
@@ -372,7 +375,7 @@ def phase_table(prof, steps):
             for k, v in prof.items() if v["launches"]}
 
 
-def workload_leg(tk, datagen, stream, barrier, name, make_opts, steps, warmup, peaks, peak_src):
+def workload_leg(tk, datagen, stream, barrier, name, make_opts, steps, warmup, peaks, peak_src, fp64=False):
     """One of the other full-size workloads, timed like the headline: inputs resident in HBM (larger than
     L2), `warmup` untimed solves, `steps` timed solves with live phase events."""
     import torch
@@ -405,7 +408,7 @@ def workload_leg(tk, datagen, stream, barrier, name, make_opts, steps, warmup, p
            "m": int(A.shape[0]), "n": int(A.shape[1]), "N": N, "dtype": str(A.dtype).replace("torch.", ""),
            "a_bytes": int(A.numel() * A.element_size()), "workspace_bytes": int(work.numel()),
            "a_stream_gbs": gbs, "a_stream_impl_gbs": igbs,
-           "roofline": roofline_of(prof, peaks, peak_src, A.shape[0] * A.shape[1]),
+           "roofline": roofline_of(prof, peaks, peak_src, A.shape[0] * A.shape[1], fp64=fp64),
            "phases": phase_table(prof, steps), "gpu_launches_per_step": (tk.tk_launch_count() - l0) / steps,
            "iters_mean": float(np.mean([q["iters"] for q in r.info])),
            "iters_max": int(max(q["iters"] for q in r.info)),
@@ -656,7 +659,7 @@ def main():
         extra["under_2048x262144_f64"] = workload_leg(
             tk, datagen, stream, barrier, "ridge_under_2048x262144_f64",
             lambda w: tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=w["s"], seed=1, tol=1e-14),
-            steps=2, warmup=1, peaks=peaks, peak_src=peak_src)
+            steps=2, warmup=1, peaks=peaks, peak_src=peak_src, fp64=True)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -251,7 +251,7 @@ tk_status oz_residual(const void* Aslices, const int* EA, int64_t m, int64_t n, 
 // The normal-equation pass: partial[z][l][j] (z < splits; unused planes zero)
 // of sum_i A[i][j] R[l][i], from the column slices of A (oz_prepare_cols) and
 // R (M x m, row stride ldr); Rslices: oz_slices_bytes(M, m), EX: M ints.
-int oz_normal_splits(int64_t m, int64_t n, int64_t M);
+int oz_normal_splits(int64_t m, int64_t n, int64_t M, int S = 8);  // S: digits of the product (4 or 8)
 // Cholesky of C + lambda I (chol_shifted) with the trailing updates on the
 // tensor cores: oz_chol_begin prepares the slice buffers and tensor maps
 // (work: oz_chol_workspace(np, N) bytes), oz_chol_step(kb) replaces the

@@ -120,6 +120,16 @@ __global__ void k_over_beta(const double* __restrict__ part, int chunks, const T
   }
 }
 
+// C[k] = sum_z partial[z][k] (the split-K planes of a product, in order)
+template <typename T>
+__global__ void k_sum_planes_to(const double* __restrict__ part, int splits, int64_t total, T* __restrict__ C) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < splits; ++z) acc += part[(int64_t)z * total + k];
+    C[k] = (T)acc;
+  }
+}
+
 // G = (sum_z partial_z + sqrt(l) Ub) / beta
 template <typename T>
 __global__ void k_over_g(const double* __restrict__ part, int splits, int count, const T* __restrict__ Ub, int64_t n,
@@ -354,6 +364,8 @@ tk_status Lsqr<T>::apply_prec(bool transposed, const T* in, T* out, int count, i
   return r;
 }
 
+inline double total_count(int count, int64_t m) { return (double)count * (double)m; }
+
 template <typename T>
 tk_status Lsqr<T>::prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, int count) {
   // C (count x m) = Win (count x n) A^T  [+ beta_row * C]
@@ -374,6 +386,24 @@ tk_status Lsqr<T>::prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, 
       return r;
     }
   }
+  if (under && !beta) {
+    // the underdetermined product: a short output (count x m, m < n) against a long K = n; split K
+    // over the GPU and add the planes (part_g holds splits x N_cap x n >= sp x count x m values)
+    const int64_t cap = ((int64_t)splits * N_cap * n) / std::max<int64_t>((int64_t)count * m, 1);
+    const int sp = (int)std::min<int64_t>(splitk_count(count, m, n), cap);
+    if (sp > 1) {
+      r = gemm_splitk<T, T>(false, true, count, m, n, Win, ldw, A, lda, part_g, sp, st);
+      if (r == TK_OK) {
+        const int64_t total = (int64_t)count * m;
+        k_sum_planes_to<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 152 * 8)), 256, 0,
+                             st>>>(part_g, sp, total, C);
+        TK_LAUNCH_CHECK();
+      }
+      prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec + 16.0 * sp * total_count(count, m),
+               es * m * n + vec + 16.0 * sp * total_count(count, m));
+      return r;
+    }
+  }
   r = gemm<T, T, T>(false, true, count, m, n, Win, ldw, A, lda, C, m, 1.0, beta, beta ? C : nullptr, m, st);
   prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, es * m * n + vec);
   return r;
@@ -388,7 +418,7 @@ tk_status Lsqr<T>::prod_atu(const T* Uin, int count) {
   tk_status r;
   if constexpr (std::is_same<T, float>::value) {
     if (digits) {
-      cur_splits = std::min(splits, oz_normal_splits(m, n, count));
+      cur_splits = std::min(splits, oz_normal_splits(m, n, count, OZ_LSQR_DIGITS));
       const double vec = es * count * (double)m + 8.0 * cur_splits * count * n;
       r = oz_lsqr_atu(oz_AT, oz_EAT, m, n, Uin, m, count, oz_q, oz_e, part_g, cur_splits, oz_err, st);
       prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, 8.0 * m * n + vec);

@@ -279,23 +279,26 @@ constexpr int OT_KB = 64;
 constexpr int OT_CHUNK = 256;
 constexpr int OT_KB_PER_CHUNK = OT_CHUNK / OT_KB;
 constexpr uint32_t OT_P_BYTES = OT_M * OT_KB * 2;   // 16 KiB
-constexpr uint32_t OT_QS_BYTES = OT_N * OT_KB * 2;  // 4 KiB
 
-// S = 8 (float64-accurate passes): one CTA per SM, an 8-slot ring of P planes
-// and 2 x 8 x 32 tensor-memory columns; S = 4 (the float32 LSQR products):
-// 4 slots and 2 x 4 x 32 columns, so two CTAs share an SM and one streams
-// while the other starts up or flushes its last chunk.
-template <int S>
+// CTA shapes (tensor memory: 2 buffers x S levels x NT columns <= 512):
+//   S = 8, NT = 32 (float64-accurate passes): one CTA per SM, an 8-slot ring of P planes;
+//   S = 4, NT = 32 (float32 LSQR products, <= 32 lambda): 4 slots and 256 columns, so two
+//     CTAs share an SM and one streams while the other starts up or flushes its last chunk;
+//   S = 4, NT = 64 (more than 32 lambda): one CTA per SM over 64 lambda, so the digit planes
+//     of the big operand are read once for 64 lambda instead of once per 32.
+template <int S, int NT>
 struct OtCfg {
-  static constexpr int PST = S == OZ_S ? 8 : 4;
-  static constexpr int CTAS_PER_SM = S == OZ_S ? 1 : 2;
+  static constexpr bool WIDE = S == OZ_S || NT == 64;
+  static constexpr int PST = WIDE ? 8 : 4;
+  static constexpr int CTAS_PER_SM = WIDE ? 1 : 2;
+  static constexpr uint32_t QS_BYTES = NT * OT_KB * 2;  // one digit plane of the small operand
 };
 
-template <int S>
+template <int S, int NT>
 struct OtSmem {
-  static constexpr int PST = OtCfg<S>::PST;
+  static constexpr int PST = OtCfg<S, NT>::PST;
   uint8_t p[PST][OT_P_BYTES];
-  uint8_t q[2][S * OT_QS_BYTES];
+  uint8_t q[2][S * OtCfg<S, NT>::QS_BYTES];
   uint64_t p_full[PST];
   uint64_t p_empty[PST];
   uint64_t q_full[2];
@@ -315,20 +318,21 @@ __device__ __forceinline__ double level_to_double(uint32_t bits, int t) {
   return __hiloint2double((int)(mag | (bits & 0x80000000u)), (int)(bits << 29));
 }
 
-template <int S, int MODE>
-__global__ void __launch_bounds__(256, OtCfg<S>::CTAS_PER_SM)
+template <int S, int MODE, int NT>
+__global__ void __launch_bounds__(256, OtCfg<S, NT>::CTAS_PER_SM)
     k_oz_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
             const int* __restrict__ EP, const int* __restrict__ EQ, int64_t rows, int M, int64_t K, int64_t kps,
             const double* __restrict__ b, void* __restrict__ out, int64_t ldo, const double* __restrict__ coef,
             int upper_only, int* __restrict__ err) {
   using Acc = typename std::conditional<S == OZ_S, double, float>::type;
-  constexpr uint32_t TMEM_COLS = 2 * S * OT_N;
-  constexpr uint32_t Q_BYTES = S * OT_QS_BYTES;
+  constexpr uint32_t TMEM_COLS = 2 * S * NT;
+  constexpr uint32_t QS_BYTES = OtCfg<S, NT>::QS_BYTES;
+  constexpr uint32_t Q_BYTES = S * QS_BYTES;
   extern __shared__ __align__(1024) uint8_t ot_raw[];
-  OtSmem<S>& Sm = *reinterpret_cast<OtSmem<S>*>((reinterpret_cast<uintptr_t>(ot_raw) + 1023) & ~uintptr_t(1023));
+  OtSmem<S, NT>& Sm = *reinterpret_cast<OtSmem<S, NT>*>((reinterpret_cast<uintptr_t>(ot_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t r0 = (int64_t)blockIdx.x * OT_M;
-  const int l0 = (int)blockIdx.y * OT_N;
+  const int l0 = (int)blockIdx.y * NT;
   // a symmetric product (P = Q) needs out[l][r] for l <= r only
   if (upper_only && l0 > r0 + OT_M - 1) return;
   const int64_t kbeg = (int64_t)blockIdx.z * kps;
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(256, OtCfg<S>::CTAS_PER_SM)
   const int nch = (nkb + OT_KB_PER_CHUNK - 1) / OT_KB_PER_CHUNK;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < OtCfg<S>::PST; ++s) {
+    for (int s = 0; s < OtCfg<S, NT>::PST; ++s) {
       mbar_init(&Sm.p_full[s], 1);
       mbar_init(&Sm.p_empty[s], 1);
     }
@@ -369,11 +373,11 @@ __global__ void __launch_bounds__(256, OtCfg<S>::CTAS_PER_SM)
       const int qs = kb & 1;
       if (!mbar_wait(&Sm.q_empty[qs], ((uint32_t)(kb >> 1) & 1u) ^ 1u, err)) break;
       mbar_expect_tx(&Sm.q_full[qs], Q_BYTES);
-      for (int p = 0; p < S; ++p) tma_load_3d(&tmQ, &Sm.q_full[qs], Sm.q[qs] + p * OT_QS_BYTES, kc, l0, p);
+      for (int p = 0; p < S; ++p) tma_load_3d(&tmQ, &Sm.q_full[qs], Sm.q[qs] + p * QS_BYTES, kc, l0, p);
       ++gq;
       for (int p = 0; p < S; ++p, ++g) {
-        const int ps = g % OtCfg<S>::PST;
-        if (!mbar_wait(&Sm.p_empty[ps], ((uint32_t)(g / OtCfg<S>::PST) & 1u) ^ 1u, err)) {
+        const int ps = g % OtCfg<S, NT>::PST;
+        if (!mbar_wait(&Sm.p_empty[ps], ((uint32_t)(g / OtCfg<S, NT>::PST) & 1u) ^ 1u, err)) {
           live = false;
           break;
         }
@@ -382,7 +386,7 @@ __global__ void __launch_bounds__(256, OtCfg<S>::CTAS_PER_SM)
       }
     }
     if (*(volatile int*)err) {  // gave up: no bulk copy may still be landing when the CTA exits
-      tma_drain_ring(Sm.p_full, OtCfg<S>::PST, g);
+      tma_drain_ring(Sm.p_full, OtCfg<S, NT>::PST, g);
       tma_drain_ring(Sm.q_full, 2, gq);
     }
   } else if (warp == 1 && lane == 0) {
@@ -392,7 +396,7 @@ __global__ void __launch_bounds__(256, OtCfg<S>::CTAS_PER_SM)
       const int bsel = c & 1, use = c >> 1;
       if (use > 0 && !mbar_wait(&Sm.acc_empty[bsel], (uint32_t)(use - 1) & 1u, err)) break;
       tc_fence_after();
-      const uint32_t dbase = tmem + (uint32_t)(bsel * S * OT_N);
+      const uint32_t dbase = tmem + (uint32_t)(bsel * S * NT);
       const int kb0 = OT_KB_PER_CHUNK * c;
       const int kb_end = nkb < kb0 + OT_KB_PER_CHUNK ? nkb : kb0 + OT_KB_PER_CHUNK;
       for (int kb = kb0; kb < kb_end && live; ++kb) {
@@ -404,19 +408,19 @@ __global__ void __launch_bounds__(256, OtCfg<S>::CTAS_PER_SM)
         tc_fence_after();
         const uint32_t qa = smem_u32(Sm.q[qs]);
         for (int p = 0; p < S; ++p, ++g) {
-          const int ps = g % OtCfg<S>::PST;
-          if (!mbar_wait(&Sm.p_full[ps], (uint32_t)(g / OtCfg<S>::PST) & 1u, err)) {
+          const int ps = g % OtCfg<S, NT>::PST;
+          if (!mbar_wait(&Sm.p_full[ps], (uint32_t)(g / OtCfg<S, NT>::PST) & 1u, err)) {
             live = false;
             break;
           }
           tc_fence_after();
-          // the planes Q_0 .. Q_(S-1-p) lie one after another (32 rows each), and the levels
-          // p .. S-1 are consecutive 32-column blocks of the buffer: all pairs (p, q) are one
-          // MMA with N = 32 (S - p) whose column block q lands on level p + q
+          // the planes Q_0 .. Q_(S-1-p) lie one after another (NT rows each), and the levels
+          // p .. S-1 are consecutive NT-column blocks of the buffer: all pairs (p, q) are one
+          // MMA with N = NT (S - p) whose column block q lands on level p + q
           const uint64_t pd = sdesc_sw128(smem_u32(Sm.p[ps]));
           const uint64_t qd = sdesc_sw128(qa);
-          const uint32_t idesc = idesc_bf16(OT_M, OT_N * (S - p));
-          const uint32_t d = dbase + (uint32_t)(p * OT_N);
+          const uint32_t idesc = idesc_bf16(OT_M, NT * (S - p));
+          const uint32_t d = dbase + (uint32_t)(p * NT);
 #pragma unroll
           for (int k = 0; k < OT_KB / 16; ++k) {
             // the first MMA of a chunk (p = 0) overwrites every level of the buffer
@@ -435,9 +439,9 @@ __global__ void __launch_bounds__(256, OtCfg<S>::CTAS_PER_SM)
     }
   } else if (warp >= 4) {
     const int ew = warp - 4;
-    Acc acc[OT_N];
+    Acc acc[NT];
 #pragma unroll
-    for (int j = 0; j < OT_N; ++j) acc[j] = Acc(0);
+    for (int j = 0; j < NT; ++j) acc[j] = Acc(0);
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
       const int bsel = c & 1, use = c >> 1;
@@ -446,19 +450,22 @@ __global__ void __launch_bounds__(256, OtCfg<S>::CTAS_PER_SM)
         break;
       }
       tc_fence_after();
-      const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(bsel * S * OT_N);
+      const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(bsel * S * NT);
 #pragma unroll 1
       for (int t = S - 1; t >= 0; --t) {  // smallest level first
-        uint32_t v[32];
-        tmem_ld32_nowait(base + (uint32_t)(t * OT_N), v);
-        tmem_wait_ld();
-        if constexpr (S == OZ_S) {
 #pragma unroll
-          for (int j = 0; j < OT_N; ++j) acc[j] += level_to_double(v[j], t);
-        } else {
-          const float sc = __int_as_float((127 - 7 * (t + 2)) << 23);  // 2^(-7(t+2)), exact
+        for (int h = 0; h < NT / 32; ++h) {
+          uint32_t v[32];
+          tmem_ld32_nowait(base + (uint32_t)(t * NT + 32 * h), v);
+          tmem_wait_ld();
+          if constexpr (S == OZ_S) {
 #pragma unroll
-          for (int j = 0; j < OT_N; ++j) acc[j] = fmaf(__uint_as_float(v[j]), sc, acc[j]);
+            for (int j = 0; j < 32; ++j) acc[32 * h + j] += level_to_double(v[j], t);
+          } else {
+            const float sc = __int_as_float((127 - 7 * (t + 2)) << 23);  // 2^(-7(t+2)), exact
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[32 * h + j] = fmaf(__uint_as_float(v[j]), sc, acc[32 * h + j]);
+          }
         }
       }
       tc_fence_before();
@@ -469,7 +476,7 @@ __global__ void __launch_bounds__(256, OtCfg<S>::CTAS_PER_SM)
       const int er = EP[r];
       const double br = MODE == 0 ? b[r] : 0.0;
 #pragma unroll
-      for (int j = 0; j < OT_N; ++j) {
+      for (int j = 0; j < NT; ++j) {
         const int l = l0 + j;
         if (l < M) {
           const int eq = EQ[l];
@@ -518,6 +525,24 @@ tk_status make_slice_map(CUtensorMap* map, const void* base, int64_t rows, int64
 
 // P: planesP digit planes of rows x K, Q: planesQ planes of M x K (both K
 // rounded up to 64); S digits of each are used.
+// The lambda-tile width of a product with M rows of the small operand: 64 for the
+// LSQR products (S = 4) over more than 32 lambda, else 32.
+constexpr int oz_tile_n(int S, int64_t M) { return (S != OZ_S && M > 32) ? 64 : 32; }
+
+template <int S, int MODE, int NT>
+tk_status launch_oz_tc_nt(const CUtensorMap& mP, const void* Qs, const int* EP, int64_t rows, const int* EQ, int M,
+                          int planesQ, int64_t kp, int64_t kps, int sp, const double* b, void* out, int64_t ldo,
+                          const double* coef, int* err, cudaStream_t st, int upper_only) {
+  CUtensorMap mQ;
+  TK_TRY(make_slice_map(&mQ, Qs, M, kp, NT, planesQ));
+  const size_t smem = sizeof(OtSmem<S, NT>) + 1024;
+  TK_CUDA(cudaFuncSetAttribute(k_oz_tc<S, MODE, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const dim3 grid((unsigned)cdiv(rows, OT_M), (unsigned)cdiv(M, NT), (unsigned)sp);
+  k_oz_tc<S, MODE, NT><<<grid, 256, smem, st>>>(mP, mQ, EP, EQ, rows, M, kp, kps, b, out, ldo, coef, upper_only, err);
+  TK_LAUNCH_CHECK();
+  return TK_OK;
+}
+
 template <int S, int MODE>
 tk_status launch_oz_tc(const void* Ps, const int* EP, int64_t rows, int planesP, const void* Qs, const int* EQ, int M,
                        int planesQ, int64_t K, int splits, const double* b, void* out, int64_t ldo,
@@ -527,16 +552,18 @@ tk_status launch_oz_tc(const void* Ps, const int* EP, int64_t rows, int planesP,
     set_error_msg("emulated product: dimensions exceed the 32-bit TMA coordinates");
     return TK_EINVAL;
   }
-  CUtensorMap mP, mQ;
+  CUtensorMap mP;
   TK_TRY(make_slice_map(&mP, Ps, rows, kp, OT_M, planesP));
-  TK_TRY(make_slice_map(&mQ, Qs, M, kp, OT_N, planesQ));
   const int64_t kps = cdiv(cdiv(K, splits), OT_CHUNK) * OT_CHUNK;  // whole chunks per split
   const int sp = (int)cdiv(K, kps);
-  const size_t smem = sizeof(OtSmem<S>) + 1024;
-  TK_CUDA(cudaFuncSetAttribute(k_oz_tc<S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const dim3 grid((unsigned)cdiv(rows, OT_M), (unsigned)cdiv(M, OT_N), (unsigned)sp);
-  k_oz_tc<S, MODE><<<grid, 256, smem, st>>>(mP, mQ, EP, EQ, rows, M, kp, kps, b, out, ldo, coef, upper_only, err);
-  TK_LAUNCH_CHECK();
+  if (oz_tile_n(S, M) == 64) {
+    if constexpr (S != OZ_S)
+      TK_TRY((launch_oz_tc_nt<S, MODE, 64>(mP, Qs, EP, rows, EQ, M, planesQ, kp, kps, sp, b, out, ldo, coef, err, st,
+                                           upper_only)));
+  } else {
+    TK_TRY((launch_oz_tc_nt<S, MODE, 32>(mP, Qs, EP, rows, EQ, M, planesQ, kp, kps, sp, b, out, ldo, coef, err, st,
+                                         upper_only)));
+  }
   if (MODE == 1 && sp < splits) {  // the caller sums `splits` planes: the unused ones are zero
     double* o = static_cast<double*>(out);
     TK_CUDA(cudaMemsetAsync(o + (int64_t)sp * M * ldo, 0, sizeof(double) * (size_t)(splits - sp) * M * ldo, st));
@@ -851,11 +878,29 @@ tk_status oz_residual(const void* Aslices, const int* EA, int64_t m, int64_t n, 
   return launch_oz_tc<OZ_S, 0>(Aslices, EA, m, OZ_S, Xslices, EX, (int)M, OZ_S, n, 1, b, R, ldr, nullptr, err, st);
 }
 
-int oz_normal_splits(int64_t m, int64_t n, int64_t M) {
-  const int64_t tiles = cdiv(n, OT_M) * cdiv(M, OT_N);
-  const int64_t want = cdiv(2 * 152, std::max<int64_t>(tiles, 1));  // one CTA per SM: two full waves
+// Split count of a split-K digit product with `tiles` output tiles: the fewest
+// waves (1..8) whose last wave is at least 97 % full, so that no SM idles
+// through a ragged last wave (e.g. 64 tiles x 5 splits on 304 slots ran 1.05
+// waves); at least 256 values of K per split.
+int oz_normal_splits(int64_t m, int64_t n, int64_t M, int S) {
+  const int nt = oz_tile_n(S, M);
+  const int ctas_per_sm = (S == OZ_S || nt == 64) ? 1 : 2;
+  const int64_t tiles = std::max<int64_t>(1, cdiv(n, OT_M) * cdiv(M, nt));
+  const int64_t slots = 152 * (int64_t)ctas_per_sm;
   const int64_t maxs = std::max<int64_t>(1, cdiv(m, OT_CHUNK));
-  return (int)std::max<int64_t>(1, std::min<int64_t>(want, maxs));
+  int64_t best = 1;
+  double best_eff = -1.0;
+  for (int64_t w = 1; w <= 8; ++w) {
+    const int64_t sp = std::min<int64_t>(cdiv(w * slots, tiles), maxs);
+    const int64_t ctas = tiles * sp;
+    const double eff = (double)ctas / (double)(cdiv(ctas, slots) * slots);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = sp;
+    }
+    if (eff >= 0.97 || sp == maxs) break;
+  }
+  return (int)std::max<int64_t>(1, best);
 }
 
 tk_status oz_normal(const void* AslicesT, const int* EC, int64_t m, int64_t n, const double* R, int64_t ldr,
