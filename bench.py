@@ -419,6 +419,42 @@ def workload_leg(tk, datagen, stream, barrier, name, make_opts, steps, warmup, p
     return out
 
 
+def bp2_vs_cholesky(tk, datagen, stream, barrier):
+    """Fig. 2 of the paper on this GPU: the same 15 lambda solved with the Cholesky preconditioner of
+    Algorithm 1 and with BP2 (a QR of [XA; sqrt(l) I] per lambda), SRDCT sketch, float64, for sketch
+    sizes s = 2n .. 20n; A 65536 x 512 with sigma log-spaced 1e5 .. 1e-5 (the figure's spectrum, the
+    rows scaled down from 5e5)."""
+    import torch
+    m, n = 65536, 512
+    sig = datagen.spectrum("log", n, hi=1e5, lo=1e-5)
+    p = datagen.make_ridge_problem(m, n, sig, datagen.log_lambdas(15, 1e-6, 1e2), seed=20220321, device="cuda")
+    lams = p.lambdas.numpy()
+    out = {}
+    for over in (2, 5, 10, 20):
+        row = {}
+        for name, pc in (("cholesky", tk.TK_PRECOND_CHOL), ("bp2_qr", tk.TK_PRECOND_QR)):
+            o = tk.opts_default(sketch=tk.TK_SKETCH_SRDCT, s=over * n, seed=1, precond=pc)
+            work = torch.empty(tk.workspace_size(tk.make_problem(p.A, p.b), len(lams), o), dtype=torch.uint8,
+                               device="cuda")
+            tk.tk_solve(p.A, p.b, lams, o, work=work, stream=stream)  # warm-up
+            barrier()
+            tk.tk_profile_enable(True)
+            tk.tk_profile_collect()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = tk.tk_solve(p.A, p.b, lams, o, work=work, stream=stream)
+            e1.record(stream)
+            barrier()
+            prof = tk.tk_profile_collect()
+            tk.tk_profile_enable(False)
+            row[name] = {"ms_15_lambda": e0.elapsed_time(e1), "factor_ms": prof["cholesky"]["ms"],
+                         "gram_ms": prof["gram"]["ms"], "iters_mean": float(np.mean([q["iters"] for q in r.info])),
+                         "status_ok": all(q["status"] == 0 for q in r.info)}
+            del work
+        out[f"s={over}n"] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,6 +470,9 @@ def main():
     ap.add_argument("--no-small", action="store_true", help="skip the 4096 x 256 workload")
     ap.add_argument("--no-c3", action="store_true", help="skip the 2048 x 2^18 underdetermined workload")
     ap.add_argument("--no-lcurve", action="store_true", help="skip the L-curve sweep on the headline workload")
+    ap.add_argument("--no-bp2", action="store_true", help="skip the BP2-versus-Cholesky comparison (Fig. 2)")
+    ap.add_argument("--sketch", default="srht", choices=["srht", "gauss", "sparse", "srdct"],
+                    help="embedding of the headline solve (the workload's own is the SRHT)")
     ap.add_argument("--no-c4", action="store_true", help="skip the 2^20 x 4096 float32 precision-form workload")
     ap.add_argument("--no-tune", action="store_true", help="keep the fixed tile rules (no tk_autotune)")
     ap.add_argument("--lsqr-tc", type=int, default=None, choices=[0, 1, 2],
@@ -470,9 +509,13 @@ def main():
     N = len(lams)
     s = w["s"]
     extra_opts = {} if args.lsqr_tc is None else {"lsqr_tc": args.lsqr_tc}
-    o_mixed = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, precision=tk.TK_PREC_MIXED, **extra_opts)
-    o_fp64 = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, tol=1e-14)
-    o_fp64_one = tk.opts_default(sketch=tk.TK_SKETCH_SRHT, s=s, seed=1, tol=1e-14,
+    sk = {"srht": tk.TK_SKETCH_SRHT, "gauss": tk.TK_SKETCH_GAUSS, "sparse": tk.TK_SKETCH_SPARSE,
+          "srdct": tk.TK_SKETCH_SRDCT}[args.sketch]
+    if args.sketch == "sparse":
+        s = 4 * s  # the sparse embedding needs more rows for the same distortion (Theorem 3.5)
+    o_mixed = tk.opts_default(sketch=sk, s=s, seed=1, precision=tk.TK_PREC_MIXED, **extra_opts)
+    o_fp64 = tk.opts_default(sketch=sk, s=s, seed=1, tol=1e-14)
+    o_fp64_one = tk.opts_default(sketch=sk, s=s, seed=1, tol=1e-14,
                                  schedule=tk.TK_SCHED_ONE_AT_A_TIME)
     stream = torch.cuda.current_stream()
     work = torch.empty(max(tk.workspace_size(tk.make_problem(A, b), N, o) for o in (o_mixed, o_fp64, o_fp64_one)),
@@ -655,6 +698,8 @@ def main():
             tk, datagen, stream, barrier, "ridge_over_1048576x4096_f32",
             lambda w: tk.opts_default(sketch=tk.TK_SKETCH_GAUSS, s=w["s"], seed=1, precision=tk.TK_PREC_MIXED),
             steps=2, warmup=1, peaks=peaks, peak_src=peak_src)
+    if not args.no_bp2:
+        extra["bp2_vs_cholesky_65536x512_srdct"] = bp2_vs_cholesky(tk, datagen, stream, barrier)
     if not args.no_c3:
         extra["under_2048x262144_f64"] = workload_leg(
             tk, datagen, stream, barrier, "ridge_under_2048x262144_f64",
@@ -665,7 +710,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "m": m, "n": n, "N": N, "sketch": "srht", "s": s,
+                "config": {"workload": WORKLOAD, "m": m, "n": n, "N": N, "sketch": args.sketch, "s": s,
                            "precision": "mixed (float32 LSQR, float64 refinement, Gram and Cholesky)",
                            "schedule": "batched", "l2": "inputs larger than L2 (A is 4 GiB)",
                            "parallelism": f"{ws} independent replicas" if ws > 1 else "1 GPU"},

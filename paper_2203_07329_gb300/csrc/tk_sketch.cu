@@ -93,10 +93,120 @@ __global__ void __launch_bounds__(kFwhtThreads)
   }
 }
 
+// The same pass with the butterflies in registers.  A tile is 2^t rows x 32
+// columns (t = R1 + 3); warp w, lane c own column c.  Phase 1: thread (w, c)
+// loads rows (w << R1) | b, b < 2^R1, straight from global memory (each load
+// instruction is one 32-column row segment of the warp) and runs the R1 low
+// levels in registers.  One exchange through shared memory regroups the rows
+// as (k << R1) | j (k < 8, 2^(R1-3) values of j per warp), the 3 top levels run
+// in registers, and the rows go straight back to global memory.  Shared
+// memory is written and read once per tile instead of once per level.
+template <typename TIn, typename TC, bool FIRST, bool LAST, int R1>
+__global__ void __launch_bounds__(256)
+    k_fwht_reg(const TIn* src, int64_t ld_src, TC* dst, double* __restrict__ Y, const int8_t* __restrict__ signs,
+               const int32_t* __restrict__ rowmap, int64_t L, int64_t cols, int b0, int64_t ncb, double scale) {
+  constexpr int T = R1 + 3, NR = 1 << R1, NJ = NR >> 3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* tile = reinterpret_cast<TC*>(smem_raw);  // [2^T rows][33] (padded: conflict-free transposed reads)
+  const int64_t g = blockIdx.x / ncb;
+  const int64_t cb = blockIdx.x - g * ncb;
+  const int64_t lo = g & ((int64_t(1) << b0) - 1);
+  const int64_t hi = g >> b0;
+  const int w = threadIdx.x >> 5, c = threadIdx.x & 31;
+  const int64_t col = cb * 32 + c;
+  const bool cok = col < cols;
+  auto grow = [&](int mid) -> int64_t { return (hi << (b0 + T)) | ((int64_t)mid << b0) | lo; };
+  TC v[NR];
+#pragma unroll
+  for (int b = 0; b < NR; ++b) {
+    const int64_t r = grow((w << R1) | b);
+    TC x = TC(0);
+    if (cok) {
+      if (FIRST) {
+        if (r < L) x = (TC)src[r * ld_src + col] * (TC)signs[r];
+      } else {
+        x = (TC)src[r * ld_src + col];
+      }
+    }
+    v[b] = x;
+  }
+#pragma unroll
+  for (int h = 1; h < NR; h <<= 1)
+#pragma unroll
+    for (int b = 0; b < NR; ++b)
+      if (!(b & h)) {
+        const TC x = v[b], y = v[b + h];
+        v[b] = x + y;
+        v[b + h] = x - y;
+      }
+#pragma unroll
+  for (int b = 0; b < NR; ++b) tile[((w << R1) | b) * 33 + c] = v[b];
+  __syncthreads();
+  // phase 2: rows (k << R1) | j for j = w NJ + i
+#pragma unroll
+  for (int i = 0; i < NJ; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[i * 8 + k] = tile[((k << R1) | (w * NJ + i)) * 33 + c];
+#pragma unroll
+  for (int i = 0; i < NJ; ++i)
+#pragma unroll
+    for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (!(k & h)) {
+          const TC x = v[i * 8 + k], y = v[i * 8 + k + h];
+          v[i * 8 + k] = x + y;
+          v[i * 8 + k + h] = x - y;
+        }
+  if (!cok) return;
+#pragma unroll
+  for (int i = 0; i < NJ; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t r = grow((k << R1) | (w * NJ + i));
+      if (LAST) {
+        const int32_t q = rowmap[r];
+        if (q >= 0) Y[(int64_t)q * cols + col] = scale * (double)v[i * 8 + k];
+      } else {
+        dst[r * cols + col] = v[i * 8 + k];
+      }
+    }
+}
+
 template <typename TIn, typename TC>
 tk_status run_fwht_pass(bool first, bool last, const TIn* srcA, const TC* srcZ, int64_t ld_src, TC* Z, double* Y,
                         const int8_t* signs, const int32_t* rowmap, int64_t L, int64_t Lp, int64_t cols, int b0,
                         int t, double scale, cudaStream_t st) {
+  if (t >= 6 && t <= (sizeof(TC) == 4 ? 9 : 8)) {
+    const int64_t ncb32 = cdiv(cols, 32);
+    const int64_t blocks32 = (Lp >> t) * ncb32;
+    const size_t smem32 = sizeof(TC) * (size_t)(1 << t) * 33;
+#define TK_FWHT_REG(R, F, LST, SRC)                                                                         \
+  do {                                                                                                      \
+    auto kern = k_fwht_reg<TIn, TC, F, LST, R>;                                                             \
+    TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 * 1024));            \
+    kern<<<(unsigned)blocks32, 256, smem32, st>>>(SRC, ld_src, Z, Y, signs, rowmap, L, cols, b0, ncb32, scale); \
+  } while (0)
+#define TK_FWHT_REG_T(R)                                                                   \
+  do {                                                                                     \
+    if (first && last) TK_FWHT_REG(R, true, true, srcA);                                   \
+    else if (first) TK_FWHT_REG(R, true, false, srcA);                                     \
+    else if (last) TK_FWHT_REG(R, false, true, reinterpret_cast<const TIn*>(srcZ));        \
+    else TK_FWHT_REG(R, false, false, reinterpret_cast<const TIn*>(srcZ));                 \
+  } while (0)
+    switch (t) {
+      case 6: TK_FWHT_REG_T(3); break;
+      case 7: TK_FWHT_REG_T(4); break;
+      case 8: TK_FWHT_REG_T(5); break;
+      default:
+        if constexpr (sizeof(TC) == 4) TK_FWHT_REG_T(6);
+        break;
+    }
+#undef TK_FWHT_REG_T
+#undef TK_FWHT_REG
+    TK_LAUNCH_CHECK();
+    return TK_OK;
+  }
   const int CB = fwht_cb<TC>();
   const int64_t ncb = cdiv(cols, CB);
   const int64_t groups = Lp >> t;
@@ -311,16 +421,19 @@ tk_status srht_impl(const TIn* A, int64_t L, int64_t cols, int64_t ld, uint64_t 
   const int a = ilog2(Lp);
   int8_t* signs = ar.take<int8_t>((size_t)Lp);
   int32_t* rowmap = ar.take<int32_t>((size_t)Lp);
-  TC* Z = (a > kFwhtMaxBits) ? ar.take<TC>((size_t)Lp * (size_t)cols) : nullptr;
+  TC* Z = (a > (sizeof(TC) == 4 ? kFwhtMaxBits : 8)) ? ar.take<TC>((size_t)Lp * (size_t)cols) : nullptr;  // > 1 pass
   if (!ar.ok()) return TK_ENOMEM;
   TK_TRY(draw_signs_rows(seed, Lp, s, signs, nullptr, rowmap, ar, st));
   if (s == 0 || cols == 0) return TK_OK;
   const double scale = 1.0 / sqrt((double)s);
-  int npass = (a + kFwhtMaxBits - 1) / kFwhtMaxBits;
+  // bits per pass: up to 9 (float) or 8 (double, whose register pass holds 32 values); passes of
+  // equal size where possible, so that every pass can run in registers (>= 6 bits)
+  const int maxb = sizeof(TC) == 4 ? kFwhtMaxBits : 8;
+  int npass = (a + maxb - 1) / maxb;
   if (npass == 0) npass = 1;
   int b0 = 0;
   for (int p = 0; p < npass; ++p) {
-    int t = std::min(kFwhtMaxBits, a - b0);
+    int t = (a - b0 + (npass - p) - 1) / (npass - p);  // split the remaining bits evenly
     if (t < 0) t = 0;
     bool first = (p == 0), last = (p == npass - 1);
     TK_TRY((run_fwht_pass<TIn, TC>(first, last, A, Z, first ? ld : cols, Z, Y, signs, rowmap, L, Lp, cols, b0, t,
@@ -382,7 +495,7 @@ size_t srht_rows_workspace(int64_t L, int64_t cols, tk_dtype dt, int64_t s) {
   Arena a;
   a.take<int8_t>((size_t)Lp);
   a.take<int32_t>((size_t)Lp);
-  if (ilog2(Lp) > kFwhtMaxBits) a.take<char>((size_t)Lp * (size_t)cols * (dt == TK_F64 ? 8 : 4));
+  if (ilog2(Lp) > (dt == TK_F64 ? 8 : kFwhtMaxBits)) a.take<char>((size_t)Lp * (size_t)cols * (dt == TK_F64 ? 8 : 4));
   return a.used + draw_workspace(Lp) + 512;
 }
 
