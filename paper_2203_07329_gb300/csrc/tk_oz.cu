@@ -650,6 +650,24 @@ __device__ __forceinline__ int level_int(uint32_t bits) {
 // 2^e as a double (e within the normal range).
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
+// v 2^s as a double, built from the integer's bits with integer instructions
+// only (GB300's float64 pipe is the bottleneck of the update's epilogue):
+// exact for |v| < 2^53.  *ok = false when the result would not be a normal
+// double (the caller then takes the float64 route).
+__device__ __forceinline__ double i53_scaled(long long v, int s, bool* ok) {
+  if (v == 0) return 0.0;
+  const unsigned long long sg = v < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int p = 63 - __clzll((long long)a);  // a in [2^p, 2^(p+1)), p <= 52
+  const int ex = p + s + 1023;
+  if (ex < 1 || ex > 2046) {
+    *ok = false;
+    return 0.0;
+  }
+  const unsigned long long mant = (a << (52 - p)) & ((1ull << 52) - 1);
+  return __longlong_as_double((long long)(sg | ((unsigned long long)ex << 52) | mant));
+}
+
 // Grid: (row slabs of 128, chunks of 8 column tiles of 32, lambda) over the
 // w x w trailing block.  Slab i0 needs the tiles j0 >= i0 (j >= i); a CTA
 // whose chunk holds none exits at once.  The slab's digit planes are loaded
@@ -781,13 +799,23 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
         for (int j = 0; j < CS_N; ++j) {
           if (j0 + j < w && j0 + j >= i) {
-            const double vhi = (double)hi[j] * 0x1p-35, vlo = (double)lo[j] * 0x1p-63;  // exact
             const int ej = S.ecol[t * CS_N + j];
             const int e = ei + ej;
-            // a row or column marked non-finite makes the update NaN (its digits are zero)
-            Trow[j0 + j] = (ei >= OZ_EBAD || ej >= OZ_EBAD)
-                               ? __longlong_as_double(0x7ff8000000000000ll)
-                               : tv[j] - (vhi + vlo) * (e >= -1022 && e <= 1023 ? pow2d(e) : ldexp(1.0, e));
+            if (ei >= OZ_EBAD || ej >= OZ_EBAD) {  // a row or column marked non-finite: NaN (its digits are zero)
+              Trow[j0 + j] = __longlong_as_double(0x7ff8000000000000ll);
+              continue;
+            }
+            // (hi 2^-35 + lo 2^-63) 2^e with the two scaled terms built exactly from the integers'
+            // bits; the sum and the subtraction are the only float64 operations (the same rounding
+            // as scaling the rounded sum, since a power of two scales exactly)
+            bool ok = true;
+            const double shi = i53_scaled(hi[j], e - 35, &ok), slo = i53_scaled(lo[j], e - 63, &ok);
+            if (ok) {
+              Trow[j0 + j] = tv[j] - (shi + slo);
+            } else {  // a scaled term outside the normal range: through the float64 pipe
+              const double vhi = (double)hi[j] * 0x1p-35, vlo = (double)lo[j] * 0x1p-63;  // exact
+              Trow[j0 + j] = tv[j] - (vhi + vlo) * (e >= -1022 && e <= 1023 ? pow2d(e) : ldexp(1.0, e));
+            }
           }
         }
       }
