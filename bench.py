@@ -45,8 +45,9 @@ PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # launch streams every element of A once, so the figure scales with m n; kernels changed since
 # their capture are left out (traffic null).
 MEASURED_TRAFFIC = {
-    # k_oz_tc<4, 2>: profiles/k_oz_tc_digits_aw_65536x2048.md (1084611840 read + 10654208 written)
-    "A_times_W_digits": (65536 * 2048, 1084611840 + 10654208),
+    # profiles/k_oz_tc_lsqr_digits_65536x2048.md: k_oz_tc<4, 2, 32> and k_oz_tc<4, 1, 32> (32 lambda)
+    "A_times_W_digits": (65536 * 2048, 1083622912 + 5114880),
+    "At_times_U_digits": (65536 * 2048, 1091296512 + 1207296),
 }
 
 # How each phase is bounded: "hbm" phases are compared as algorithmic bytes / time with the
