@@ -76,10 +76,12 @@ def test_over_262144x2048_srht(tk, precision):
     its = [q["iters"] for q in res.info]
     cap = 75 if precision == "fp64" else 4 * 40
     assert max(its) <= cap, its
-    # flat in lambda (Section 2.1.1, Lemma 2.1: the same bound for every lambda): iterations per LSQR run
-    # (the mixed form restarts LSQR once per refinement round) vary by at most a factor 2 plus a few
-    per_run = [q["iters"] / max(q["refine_steps"], 1) for q in res.info]
-    assert max(per_run) <= 2 * min(per_run) + 10, per_run
+    # bounded uniformly in lambda (Lemma 2.1: kappa(B R^-1) <= kappa(X U_A) for every lambda): no lambda
+    # needs far more iterations per LSQR run (the mixed form restarts LSQR once per refinement round)
+    # than the median one -- unpreconditioned LSQR would grow like kappa_B ~ 1/sqrt(lambda) as lambda -> 0.
+    # Large lambda converge faster (better conditioned), so the check is one-sided.
+    per_run = np.array([q["iters"] / max(q["refine_steps"], 1) for q in res.info])
+    assert per_run.max() <= 1.5 * np.median(per_run) + 5, per_run
 
 
 def test_under_2048x262144_srht(tk):
