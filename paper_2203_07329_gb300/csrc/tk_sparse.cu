@@ -134,22 +134,13 @@ __global__ void __launch_bounds__(256) k_sparse_apply(const T* __restrict__ A, i
   if (c >= cols) return;
   const int32_t b = start[k], e = start[k + 1];
   double acc = 0.0;
-  // up to 8 rows at a time: their indices first, then 8 independent loads of A, then the adds in
-  // ascending row order (the order of the definition, so the sum is the same)
-  for (int32_t p0 = b; p0 < e; p0 += 8) {
-    const int cnt = e - p0 < 8 ? e - p0 : 8;
-    int32_t r[8];
-    double v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) r[q] = q < cnt ? order[p0 + q] : 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const double x = q < cnt ? (double)A[(int64_t)r[q] * ld + c] : 0.0;
-      v[q] = sign[r[q]] < 0 ? -x : x;
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (q < cnt) acc = acc + v[q];
+  // the rows in ascending order (the order of the definition).  Loading 8 rows' indices first and
+  // then 8 independent rows was measured 3.4x slower (2.61 ms against 0.76 ms on 65536 x 2048,
+  // s = 32768: about two rows per bucket)
+  for (int32_t p = b; p < e; ++p) {
+    const int32_t r = order[p];
+    const double v = (double)A[(int64_t)r * ld + c];
+    acc = acc + (sign[r] < 0 ? -v : v);
   }
   Y[k * cols + c] = acc;
 }
