@@ -55,7 +55,7 @@ MEASURED_TRAFFIC = {
 # The digit products read 8 bytes per element of A (4 BF16 digit planes); the emulated float64
 # passes 16 (8 planes) and flush at most 8 float64 adds per output and 256 values of K.
 PHASE_BOUND = {
-    "A_times_W_digits": "hbm", "At_times_U_digits": "hbm", "refine_residual64": "hbm",
+    "A_times_W_digits": "hbm", "At_times_U_digits": "hbm", "lsqr_step_fused": "hbm", "refine_residual64": "hbm",
     "refine_normal64": "hbm", "slice_A": "hbm", "sketch": "hbm", "precond_apply": "hbm",
     "A_times_W": "fp32", "At_times_U": "fp32", "precond_inverse": "fp32",
     "cholesky": "fp64", "svd": "fp64",
@@ -354,8 +354,8 @@ def roofline_of(prof, peaks, peak_src, a_elems, fp64=False):
     return roofline
 
 
-STREAM_PHASES = ("A_times_W", "At_times_U", "A_times_W_digits", "At_times_U_digits", "refine_residual64",
-                 "refine_normal64")
+STREAM_PHASES = ("A_times_W", "At_times_U", "A_times_W_digits", "At_times_U_digits", "lsqr_step_fused",
+                 "refine_residual64", "refine_normal64")
 
 
 def a_stream_of(prof):
@@ -476,7 +476,7 @@ def main():
                     help="embedding of the headline solve (the workload's own is the SRHT)")
     ap.add_argument("--no-c4", action="store_true", help="skip the 2^20 x 4096 float32 precision-form workload")
     ap.add_argument("--no-tune", action="store_true", help="keep the fixed tile rules (no tk_autotune)")
-    ap.add_argument("--lsqr-tc", type=int, default=None, choices=[0, 1, 2],
+    ap.add_argument("--lsqr-tc", type=int, default=None, choices=[0, 1, 2, 3],
                     help="LSQR products of the timed mixed step: 0 SIMT float32, 1 TF32 x3, 2 4-digit slices "
                          "(default: the library's)")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],

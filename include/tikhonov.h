@@ -102,7 +102,9 @@ typedef struct {
                              exact digits of the slices that emulate_fp64 makes (A rounded to 28 bits,
                              exact level sums; needs emulate_fp64 and m >= n; used when m n > 2^24 and
                              more than 16 lambda are active, SIMT float32 otherwise; the grouped batch
-                             keeps its own products); 0 = SIMT float32 */
+                             keeps its own products); 3 = as 2, with the two products of a step fused into
+                             one kernel over one read of the digits when n <= 2048 and at most 32 lambda
+                             are active; 0 = SIMT float32 */
   int group;              /* [1] tk_solve_batched: when every problem is MIXED, m >= n, BATCHED, n <= 4096,
                              N <= 64 and lsqr_tc != 1, the problems advance together in one grouped LSQR and
                              refinement (one launch per phase for all problems); 0 in any problem's options =
@@ -399,6 +401,25 @@ TK_API size_t tk_residual_workspace(int64_t m, int64_t n, int M);
 TK_API tk_status tk_residual(const tk_problem* p, const double* X, int M, int64_t ldx, int emulate, double* R,
                              double* G, void* work, size_t work_bytes, void* stream);
 
+/* tk_lsqr_step_products -- the two products with A of one LSQR step of the
+ * mixed form (Algorithm 1 step 5 inside LSQR: A R^-1 v and A^T u), on their
+ * own for parity tests of each form of them (no counterpart in the paper
+ * beyond the products themselves): U <- W A^T + coef .* U (coef NULL: U <-
+ * W A^T), then G = U A with the new U.  mode 0: both from the 4-digit slices
+ * of A on the tensor cores, as the solve runs them while more than 16 lambda
+ * are active; mode 1: the same two in one kernel over one read of A's digit
+ * planes (clusters of CTAs sharing a band of rows; n <= 2048); mode 2: the
+ * float32 products of at most 16 lambda from a float32 copy of A (made here
+ * when A is float64), as the solve runs them for its last lambda.
+ *   p: A (device, m x n, float64 or float32); W: device count x n float32;
+ *   U: device count x m float32 (read when coef is not NULL, written);
+ *   coef: device count float64 or NULL; G: device count x n float64, written.
+ *   1 <= count <= 32.  work: tk_lsqr_step_products_workspace(m, n, count) bytes.
+ *   Synchronizes `stream`; TK_ETIMEOUT if a pipeline wait gave up. */
+TK_API size_t tk_lsqr_step_products_workspace(int64_t m, int64_t n, int count);
+TK_API tk_status tk_lsqr_step_products(const tk_problem* p, const float* W, int count, float* U, const double* coef,
+                                       double* G, int mode, void* work, size_t work_bytes, void* stream);
+
 /* tk_autotune -- measured tile shapes for the products of the LSQR and
  * refinement passes (no counterpart in the paper: a tuning step of this
  * library).  For the problem's shape and options it runs, on the workspace
@@ -456,7 +477,9 @@ enum {
   TK_PHASE_SLICE = 12,        /* MIXED, emulate_fp64: the digit planes of A (rows and columns), once per solve */
   TK_PHASE_CHOL_UPDATE = 13,  /* MIXED, emulate_fp64: the Cholesky trailing updates on the tensor cores
                                  (TK_PHASE_CHOLESKY then holds the diagonal blocks and panel solves) */
-  TK_PHASE_COUNT = 14
+  TK_PHASE_LSQR_FUSED = 14,   /* MIXED, lsqr_tc = 3: TK_PHASE_AW_DIGITS and TK_PHASE_ATU_DIGITS of a step in one
+                                 kernel over one read of the digits of A */
+  TK_PHASE_COUNT = 15
 };
 typedef struct {
   double ms;      /* summed event time */

@@ -45,6 +45,7 @@ struct Plan {
   bool qr = false;        // BP2: R from a QR of [Y; sqrt(l) I] instead of chol(Y^T Y + l I)
   bool lsqr_tc = false;  // tensor-core float32 LSQR products (3-term TF32)
   bool lsqr_oz = false;  // float32 LSQR products from the 4-digit slices of A
+  bool lsqr_fused = false;  // ... both products of a step in one kernel
   bool prep_only = false;  // grouped batch: build the preconditioner only
   bool inv64 = false;      // float64 form: explicit float64 R^-1 (small factors)
 };
@@ -61,6 +62,7 @@ tk_status check_opts(const tk_opts* o) {
     return einval("unknown preconditioner");
   if (o->precision != TK_PREC_FP64 && o->precision != TK_PREC_MIXED) return einval("unknown precision");
   if (o->schedule != TK_SCHED_BATCHED && o->schedule != TK_SCHED_ONE_AT_A_TIME) return einval("unknown schedule");
+  if (o->lsqr_tc < 0 || o->lsqr_tc > 3) return einval("lsqr_tc must be 0, 1, 2 or 3");
   if (!(o->tol > 0.0) || !std::isfinite(o->tol)) return einval("tol must be a positive finite number");
   if (o->maxiter < 1) return einval("maxiter must be >= 1");
   if (o->s < 0) return einval("sketch size s must be >= 0");
@@ -115,7 +117,8 @@ tk_status make_plan(const tk_problem* p, int N, const tk_opts* o, Plan& P) {
   P.inv64 = !P.mixed && !P.lowrank && !P.under && P.c <= 512;
   P.lsqr_tc = P.mixed && o->lsqr_tc == 1 && P.N_cap <= 64 && !P.under && P.m % 4 == 0 && P.n % 4 == 0 &&
               (P.dt == TK_F64 || P.lda % 4 == 0);
-  P.lsqr_oz = P.mixed && o->lsqr_tc == 2 && o->emulate_fp64 && !P.under;
+  P.lsqr_oz = P.mixed && (o->lsqr_tc == 2 || o->lsqr_tc == 3) && o->emulate_fp64 && !P.under;
+  P.lsqr_fused = P.lsqr_oz && o->lsqr_tc == 3;
   return TK_OK;
 }
 
@@ -268,6 +271,7 @@ void carve(const Plan& P, Arena& a, Arena& t, Bufs& B) {
     B.e32.m = P.m; B.e32.n = P.n; B.e32.N_cap = P.N_cap; B.e32.under = false; B.e32.lr_s = lr_s;
     B.e32.tc = P.lsqr_tc;
     B.e32.oz = P.lsqr_oz;
+    B.e32.oz_fused = P.lsqr_fused;
     B.e32.carve(a);
   } else {
     B.e64.m = P.m; B.e64.n = P.n; B.e64.N_cap = P.N_cap; B.e64.under = P.under; B.e64.lr_s = lr_s;
@@ -1776,6 +1780,116 @@ TK_API tk_status tk_lcurve(const tk_problem* p, const double* lambdas, int N, in
   }
   *corner = hc;
   return worst;
+}
+
+// ---- the products of one LSQR step on their own (parity of the fused form) ----------
+namespace {
+struct StepBufs {
+  void *Aoz, *AozC, *colmax, *Wq, *Uq;
+  int *EA, *EC, *EW, *EU, *err;
+  double* part;
+  float* A32;
+  int planes;
+};
+void step_carve(Arena& a, int64_t m, int64_t n, int count, StepBufs& w) {
+  w.planes = std::max({oz_normal_splits(m, n, count, OZ_LSQR_DIGITS), 152, lm_small_atu_splits(m, n)});
+  w.A32 = a.take<float>((size_t)m * n);
+  w.Aoz = a.take<char>(oz_slices_bytes(m, n));
+  w.EA = a.take<int>(m);
+  w.AozC = a.take<char>(oz_slices_bytes(n, m));
+  w.EC = a.take<int>(n);
+  w.colmax = a.take<char>(oz_colmax_bytes(n));
+  w.Wq = a.take<char>(oz_slices_bytes(count, n, OZ_LSQR_DIGITS));
+  w.EW = a.take<int>(count);
+  w.Uq = a.take<char>(oz_slices_bytes(count, m, OZ_LSQR_DIGITS));
+  w.EU = a.take<int>(count);
+  w.part = a.take<double>((size_t)w.planes * count * n);
+  w.err = a.take<int>(4);
+}
+}  // namespace
+namespace tk {
+__global__ void k_step_to_f32(const double* __restrict__ s, int64_t rows, int64_t cols, int64_t lds,
+                              float* __restrict__ d) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < rows * cols; k += (int64_t)gridDim.x * blockDim.x)
+    d[k] = (float)s[(k / cols) * lds + k % cols];
+}
+__global__ void k_step_sum_planes(const double* __restrict__ part, int planes, int64_t total, double* __restrict__ G) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < planes; ++z) acc += part[(int64_t)z * total + k];
+    G[k] = acc;
+  }
+}
+}  // namespace tk
+
+TK_API size_t tk_lsqr_step_products_workspace(int64_t m, int64_t n, int count) {
+  if (m < 1 || n < 1 || count < 1) return 0;
+  Arena a;
+  StepBufs w;
+  step_carve(a, m, n, count, w);
+  return a.used + 1024;
+}
+
+TK_API tk_status tk_lsqr_step_products(const tk_problem* p, const float* W, int count, float* U, const double* coef,
+                                       double* G, int mode, void* work, size_t work_bytes, void* stream) {
+  if (!p || !p->A || !W || !U || !G || count < 1 || count > 32 || p->m < 1 || p->n < 1 || p->lda < p->n)
+    return einval("bad step-product arguments (1 <= count <= 32)");
+  if (p->dtype != TK_F64 && p->dtype != TK_F32) return einval("unknown dtype");
+  if (mode < 0 || mode > 2) return einval("mode must be 0, 1 or 2");
+  const bool fused = mode == 1;
+  if (fused && !oz_fused_supported(p->m, p->n, count)) return einval("the fused step needs n <= 2048");
+  if (mode == 2 && !(count <= 16 && lm_small_aw_supported(p->n, count)))
+    return einval("the float32 products need count <= 16 and W within shared memory");
+  if (!work || work_bytes < tk_lsqr_step_products_workspace(p->m, p->n, count)) {
+    set_error_msg("workspace smaller than tk_lsqr_step_products_workspace()");
+    return TK_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena a;
+  a.base = (char*)work;
+  a.cap = work_bytes;
+  StepBufs w;
+  step_carve(a, p->m, p->n, count, w);
+  const int64_t m = p->m, n = p->n;
+  TK_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  int planes = 0;
+  if (mode == 2) {  // the float32 products of the tail (<= 16 lambda) from a float32 copy of A
+    const float* A32 = static_cast<const float*>(p->A);
+    int64_t lda32 = p->lda;
+    if (p->dtype == TK_F64) {
+      k_step_to_f32<<<(unsigned)std::min<int64_t>(cdiv(m * n, 256), 152 * 32), 256, 0, st>>>(
+          static_cast<const double*>(p->A), m, n, p->lda, w.A32);
+      TK_LAUNCH_CHECK();
+      A32 = w.A32;
+      lda32 = n;
+    }
+    TK_TRY(lm_small_aw(A32, lda32, m, n, W, n, count, U, m, coef, st));
+    planes = std::min(w.planes, lm_small_atu_splits(m, n));
+    TK_TRY(lm_small_atu(A32, lda32, m, n, U, m, count, w.part, planes, st));
+  } else {
+  TK_TRY(oz_prepare(p->A, p->dtype, m, n, p->lda, w.Aoz, w.EA, st));
+  if (fused) {
+    TK_TRY(oz_lsqr_fused(w.Aoz, w.EA, m, n, W, n, count, w.Wq, w.EW, U, m, coef, w.part, w.planes, &planes, w.err,
+                         st));
+  } else {
+    TK_TRY(oz_prepare_cols(p->A, p->dtype, m, n, p->lda, w.AozC, w.EC, w.colmax, st));
+    TK_TRY(oz_lsqr_aw(w.Aoz, w.EA, m, n, W, n, count, w.Wq, w.EW, U, m, coef, w.err, st));
+    planes = std::min(w.planes, oz_normal_splits(m, n, count, OZ_LSQR_DIGITS));
+    TK_TRY(oz_lsqr_atu(w.AozC, w.EC, m, n, U, m, count, w.Uq, w.EU, w.part, planes, w.err, st));
+  }
+  }
+  const int64_t total = (int64_t)count * n;
+  k_step_sum_planes<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 152 * 8)), 256, 0, st>>>(
+      w.part, planes, total, G);
+  TK_LAUNCH_CHECK();
+  int herr = 0;
+  TK_CUDA(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TK_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error_msg("LSQR step products: a pipeline wait timed out");
+    return TK_ETIMEOUT;
+  }
+  return TK_OK;
 }
 
 }  // extern "C"

@@ -277,8 +277,25 @@ tk_status oz_chol_step(const OzCholPlan& plan, int kb, cudaStream_t st);
 //   atu: partial[z][l][j] = sum_{i in split z} U[l][i] A[i][j].
 tk_status oz_lsqr_aw(const void* Aslices, const int* EA, int64_t m, int64_t n, const float* W, int64_t ldw, int count,
                      void* Wslices, int* EW, float* U, int64_t ldu, const double* coef, int* err, cudaStream_t st);
+// The two products of one LSQR step fused over one read of A's row-exponent digit planes (count <= 32,
+// n <= 2048): U <- W A^T + coef .* U in place, and partial[z] (z < *planes <= max_planes; count x n
+// float64 planes) whose sum is U A for the new U.  Wslices / EW as oz_lsqr_aw.
+bool oz_fused_supported(int64_t m, int64_t n, int count);
+tk_status oz_lsqr_fused(const void* Aslices, const int* EA, int64_t m, int64_t n, const float* W, int64_t ldw,
+                        int count, void* Wslices, int* EW, float* U, int64_t ldu, const double* coef, double* partial,
+                        int max_planes, int* planes, int* err, cudaStream_t st);
 tk_status oz_lsqr_atu(const void* AslicesT, const int* EC, int64_t m, int64_t n, const float* U, int64_t ldu,
                       int count, void* Uslices, int* EU, double* partial, int splits, int* err, cudaStream_t st);
+// Float32 LSQR products for at most 16 lambda from the float32 A (m x n, row
+// stride lda): aw: C[l][i] = sum_k W[l][k] A[i][k] (+ beta[l] C[l][i]; beta may
+// be null), W (count x n) held in shared memory (lm_small_aw_supported);
+// atu: partial[z][l][j] (z < splits, count x n planes) whose sum is U A.
+bool lm_small_aw_supported(int64_t n, int count);
+tk_status lm_small_aw(const float* A, int64_t lda, int64_t m, int64_t n, const float* W, int64_t ldw, int count,
+                      float* C, int64_t ldc, const double* beta, cudaStream_t st);
+int lm_small_atu_splits(int64_t m, int64_t n);
+tk_status lm_small_atu(const float* A, int64_t lda, int64_t m, int64_t n, const float* U, int64_t ldu, int count,
+                       double* partial, int splits, cudaStream_t st);
 // C = Y^T Y (Y: r x c float64, row stride c), the upper triangle (j >= i) of
 // C (c x c) written, float64-accurate; work: oz_gram_workspace(r, c) bytes.
 size_t oz_gram_workspace(int64_t r, int64_t c);

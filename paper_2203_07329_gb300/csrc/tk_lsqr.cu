@@ -316,6 +316,8 @@ void Lsqr<T>::carve(Arena& a) {
   const int64_t nu = m;  // length of the GEMM-facing u rows
   const int64_t gcols = n;
   splits = splitk_count(N_cap, gcols, m);
+  if (std::is_same<T, float>::value) splits = std::max(splits, lm_small_atu_splits(m, n));  // <= 16 lambda
+  if (oz && oz_fused) splits = std::max(splits, 152);  // one partial plane per cluster of the fused step
   V = a.take<T>((size_t)N_cap * nv);
   W = a.take<T>((size_t)N_cap * nv);
   Y = a.take<T>((size_t)N_cap * nv);
@@ -385,6 +387,11 @@ tk_status Lsqr<T>::prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, 
       prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, es * m * n + vec);
       return r;
     }
+    if (!under && lm_small_aw_supported(n, count)) {  // <= 16 lambda: W on chip, one pass over A's rows
+      r = lm_small_aw(A, lda, m, n, Win, ldw, count, C, m, beta, st);
+      prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, es * m * n + vec);
+      return r;
+    }
   }
   if (under && !beta) {
     // the underdetermined product: a short output (count x m, m < n) against a long K = n; split K
@@ -431,11 +438,33 @@ tk_status Lsqr<T>::prod_atu(const T* Uin, int count) {
       prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, es * m * n + vec);
       return r;
     }
+    if (count <= 16) {  // <= 16 lambda: NL x 4 accumulators per thread, U staged on chip
+      cur_splits = std::min(splits, lm_small_atu_splits(m, n));
+      const double vec = es * count * (double)m + 8.0 * cur_splits * count * n;
+      r = lm_small_atu(A, lda, m, n, Uin, m, count, part_g, cur_splits, st);
+      prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, es * m * n + vec);
+      return r;
+    }
   }
   cur_splits = splitk_tuned<T, T>(count, n, m, splits);
   const double vec = es * count * (double)m + 8.0 * cur_splits * count * n;
   r = gemm_splitk<T, T>(false, false, count, n, m, Uin, m, A, lda, part_g, cur_splits, st);
   prof_end(tok, st, 2.0 * count * m * n, a_es * m * n + vec, es * m * n + vec);
+  return r;
+}
+
+template <typename T>
+tk_status Lsqr<T>::prod_fused(const T* Win, T* C, const double* beta, int count) {
+  // C (count x m) = Win A^T + beta .* C, then part_g (cur_splits x count x n) = C A
+  const double es = (double)sizeof(T);
+  int tok = prof_begin(TK_PHASE_LSQR_FUSED, st);
+  tk_status r = TK_EINVAL;
+  if constexpr (std::is_same<T, float>::value)
+    r = oz_lsqr_fused(oz_A, oz_EA, m, n, Win, n, count, oz_q, oz_e, C, m, beta, part_g, splits, &cur_splits, oz_err,
+                      st);
+  // A once from memory (its second read, a few microseconds later, comes from L2)
+  const double vec = es * (count * (double)n + 2.0 * count * m) + 8.0 * cur_splits * count * n;
+  prof_end(tok, st, 4.0 * count * m * n, a_es * m * n + vec, 8.0 * m * n + vec);
   return r;
 }
 
@@ -568,12 +597,20 @@ tk_status Lsqr<T>::step(int nact) {
   if (!under) {
     TK_TRY(apply_prec(false, V, Tt, nact, n));  // T = R^-1 v
     TK_TRY(gather_coef(nact));
-    TK_TRY(prod_aw(Tt, n, Ut, coef_buf, nact));
-    k_sumsq_rows<T><<<dim3(kSumChunks, nact), 256, 0, st>>>(Ut, m, m, kSumChunks, part_u);
-    TK_LAUNCH_CHECK();
-    k_over_beta<T><<<nact, kVecThreads, 0, st>>>(part_u, kSumChunks, Tt, Ub, n, sc);
-    TK_LAUNCH_CHECK();
-    TK_TRY(prod_atu(Ut, nact));
+    if (use_fused(nact)) {  // u' = A R^-1 v - alpha u and A^T u' over one read of A's digits
+      TK_TRY(prod_fused(Tt, Ut, coef_buf, nact));
+      k_sumsq_rows<T><<<dim3(kSumChunks, nact), 256, 0, st>>>(Ut, m, m, kSumChunks, part_u);
+      TK_LAUNCH_CHECK();
+      k_over_beta<T><<<nact, kVecThreads, 0, st>>>(part_u, kSumChunks, Tt, Ub, n, sc);
+      TK_LAUNCH_CHECK();
+    } else {
+      TK_TRY(prod_aw(Tt, n, Ut, coef_buf, nact));
+      k_sumsq_rows<T><<<dim3(kSumChunks, nact), 256, 0, st>>>(Ut, m, m, kSumChunks, part_u);
+      TK_LAUNCH_CHECK();
+      k_over_beta<T><<<nact, kVecThreads, 0, st>>>(part_u, kSumChunks, Tt, Ub, n, sc);
+      TK_LAUNCH_CHECK();
+      TK_TRY(prod_atu(Ut, nact));
+    }
     k_over_g<T><<<rows_grid(n, nact), 256, 0, st>>>(part_g, cur_splits, nact, Ub, n, sc, Tt);
     TK_LAUNCH_CHECK();
     TK_TRY(apply_prec(true, Tt, Vraw, nact, n));  // R^-T g

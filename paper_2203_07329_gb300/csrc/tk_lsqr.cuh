@@ -177,6 +177,10 @@ struct Lsqr {
   // lambdas, the float32 SIMT products 4 bytes but with work proportional to
   // it: the digits pay off for large A and more than 16 active lambdas
   bool use_oz(int count) const { return oz && oz_A && oz_AT && (int64_t)m * n > (int64_t(1) << 24) && count > 16; }
+  // both products of an overdetermined step in one kernel over one read of
+  // the digits (n <= 2048, at most 32 lambda per launch)
+  bool oz_fused = false;
+  bool use_fused(int count) const { return oz_fused && !under && use_oz(count) && oz_fused_supported(m, n, count); }
 
   static size_t workspace(int64_t m, int64_t n, int N_cap, bool under, int64_t lr_s);
   void carve(Arena& a);
@@ -190,6 +194,7 @@ struct Lsqr {
   tk_status apply_prec(bool transposed, const T* in, T* out, int count, int64_t len);
   tk_status prod_aw(const T* Win, int64_t ldw, T* C, const double* beta, int count);
   tk_status prod_atu(const T* Uin, int count);
+  tk_status prod_fused(const T* Win, T* C, const double* beta, int count);
   tk_status gather_coef(int count);
   // one LSQR step for slots 0..nact-1; `count` of them (see steps())
   tk_status step(int nact);

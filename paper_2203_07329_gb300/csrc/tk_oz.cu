@@ -28,6 +28,7 @@
 // level accumulators in tensor memory, double-buffered so that four epilogue
 // warps flush one 256-value chunk of K while the MMAs of the next chunk run.
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 #include <cuda_bf16.h>
 
@@ -830,6 +831,521 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
+
+// ---- the two products of an LSQR step, fused over one read of A -----------------
+// One LSQR step of the mixed form needs U' = W A^T + c .* U (m values per lambda)
+// and then G = U' A (n values per lambda).  The second product of a band of rows
+// needs the first product over the band's whole rows, so a band must be held
+// between the two.  Here a cluster of CL CTAs (CL a power of two <= 8) owns one
+// band of 128 rows at a time, CTA q the columns [q cpc, (q + 1) cpc) of it (cpc <=
+// 256, so the CTA's slab of the 4 digit planes is at most 256 KiB):
+//   P1  the CTA's part of W A^T for the band (K = its columns) on tcgen05 into one
+//       of two tensor-memory buffers; W's digits stay in shared memory throughout;
+//   X1  the CL partials are added through distributed shared memory: CTA q adds
+//       the rows [q 128/CL, (q + 1) 128/CL) in rank order, forms U' = v + c U for
+//       them (written to U), and stores u' = U' 2^(E_r - E_max) (the row scale of
+//       A's digits moved onto U') into every CTA's copy of the band's u';
+//   X2  every CTA digitizes the band's u' (4 digits, one exponent per lambda) into
+//       the B operand of
+//   P2  G_q += A_slab^T u' on tcgen05, the A operand read MN-major from the same
+//       digit planes, read again (from L2: a few microseconds after P1's read).
+// The producer issues the next band's P1 loads before this band's P2 loads, so A
+// streams from memory while the epilogue exchanges and digitizes.  Each CTA keeps
+// its columns' G in registers across all the bands its cluster processes, and
+// writes one partial plane per cluster at the end.  The exchange uses mbarriers in
+// distributed shared memory with bounded waits; every CTA reaches the cluster
+// barrier before exit, so no CTA leaves while another may still read or write its
+// shared memory.
+constexpr int FU_M = 128;   // band rows
+constexpr int FU_NT = 32;   // lambda
+constexpr int FU_RS = 3;    // ring slots of one 128-column chunk of one digit plane (2 TMA boxes)
+constexpr int FU_S = 4;     // digits (the float32 LSQR products)
+constexpr uint32_t FU_SLOT = 2 * OT_P_BYTES;                 // 32 KiB
+constexpr uint32_t FU_QBOX = FU_NT * 64 * 2;                 // 4 KiB: 32 rows x 64 values of one plane
+constexpr uint32_t FU_QCH = 2 * FU_S * FU_QBOX;              // 32 KiB: 128 K x 4 planes
+constexpr uint32_t FU_TMEM_COLS = 512;                       // P1: 2 x 128, P2: 2 x 128
+
+struct FuSmem {
+  uint8_t ring[FU_RS][FU_SLOT];
+  uint8_t wq[2][FU_QCH];      // W digits of chunk c (resident): [64-K box][plane][32 rows][128 B]
+  uint8_t q2[FU_QCH];         // u' digits: [64-row chunk][plane][32 lambda][128 B]
+  float pbuf[FU_NT * FU_M];   // P1 partial, [lambda][row]
+  float ub[FU_NT * FU_M];     // u' of the band, [lambda][row]
+  uint32_t umax[4][FU_NT];    // per warp: max |u'| bits per lambda
+  int ea[FU_M];
+  int eu[FU_NT];
+  int ew[FU_NT];
+  float psc[FU_NT];           // 2^(E_max + E_u) of the band, per lambda (the P2 scale)
+  int emax4[4];
+  uint64_t ring_full[FU_RS], ring_empty[FU_RS], w_full;
+  uint64_t p1_full[2], p1_empty[2], q2_full, q2_empty, p2_full[2], p2_empty[2];
+  uint64_t pb_full, pb_empty, ub_full, ub_empty;
+  uint64_t mma_drain;
+  uint32_t tmem_base;
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t nclusters_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of `p` (a shared variable of this CTA) in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t dsmem_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void dsmem_arrive(uint32_t bar_cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster_addr) : "memory");
+}
+// generic pointer to `p` (a shared array of this CTA) in CTA `rank` of the cluster: plain loads and
+// stores through it, which the compiler may batch (ordered after the acquiring waits, which clobber memory)
+template <typename T>
+__device__ __forceinline__ T* peer_ptr(T* p, uint32_t rank) {
+  return static_cast<T*>(__cluster_map_shared_rank(static_cast<void*>(p), rank));
+}
+// bounded wait with cluster-scope acquire (data written by other CTAs before their arrive is visible)
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* b, uint32_t parity, int* err) {
+  uint64_t t0 = 0;
+  for (uint32_t i = 0; i < (1u << 26); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (i >= 256) __nanosleep(32);
+    if ((i & 255u) == 255u) {
+      if (*(volatile int*)err) return false;
+      const uint64_t t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > kWaitBudgetNs) break;
+    }
+  }
+  atomicExch(err, 1);
+  return false;
+}
+// true on every one of the 128 epilogue threads iff v is true on all of them (named barrier 1): the
+// epilogue takes every exit together, so no thread is left waiting at a named barrier
+__device__ __forceinline__ bool epi_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// K-major operand, 128-byte swizzle: byte offset of element (row, k) in a box of 64 values per row
+__device__ __forceinline__ uint32_t sw128_off(int row, int k) {
+  return (uint32_t)(row * 128 + ((((k >> 3) ^ (row & 7)) & 7) << 4) + ((k & 7) << 1));
+}
+// MN-major 128-byte-swizzled operand: LBO = distance between 64-element blocks along M, SBO = between
+// 8-row blocks along K
+__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t saddr, uint32_t lbo_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// 2^e as a float (0 below the normal range, inf above)
+__device__ __forceinline__ float pow2f(int e) {
+  return e < -126 ? 0.f : (e > 127 ? __int_as_float(0x7f800000) : __int_as_float((127 + e) << 23));
+}
+
+// The 4 balanced base-128 digits of x 2^-E rounded to 28 bits (|x| < 2^E): the value
+// v = round(x 2^(28 - E)) (exact scaling in float64, one rounding) written as
+// d0 2^21 + d1 2^14 + d2 2^7 + d3 with d1..d3 in [-64, 63].
+__device__ __forceinline__ void oz_split4(float x, int E, unsigned short (&bits)[4]) {
+  int v = (int)__double2ll_rn((double)x * pow2d(28 - E));
+#pragma unroll
+  for (int p = 3; p >= 1; --p) {
+    const int d = ((v + 64) & 127) - 64;
+    bits[p] = oz_bf16_bits(d);
+    v = (v - d) >> 7;
+  }
+  bits[0] = oz_bf16_bits(v);
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_oz_fused(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
+               const int* __restrict__ EA, const int* __restrict__ EW, int64_t m, int64_t n, int count, int cpc,
+               float* __restrict__ U, int64_t ldu, const double* __restrict__ coef, double* __restrict__ partial,
+               int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t fu_raw[];
+  FuSmem& S = *reinterpret_cast<FuSmem*>((reinterpret_cast<uintptr_t>(fu_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t q = cluster_rank();
+  int cl_size;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(cl_size));
+  const int64_t bands = (m + FU_M - 1) / FU_M;
+  const int64_t zc = cluster_id_x(), ncl = nclusters_x();
+  const int nb = zc < bands ? (int)((bands - 1 - zc) / ncl + 1) : 0;  // bands of this cluster
+  const int nch = cpc / 128;       // 128-column chunks of this CTA (1 or 2)
+  const int col0 = (int)q * cpc;   // this CTA's first column
+  const int row_lo = (int)q * (FU_M / cl_size), nrows = FU_M / cl_size;  // this CTA's rows in X1
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < FU_RS; ++s) {
+      mbar_init(&S.ring_full[s], 1);
+      mbar_init(&S.ring_empty[s], 1);
+    }
+    mbar_init(&S.w_full, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&S.p1_full[s], 1);
+      mbar_init(&S.p1_empty[s], 128);
+      mbar_init(&S.p2_full[s], 1);
+      mbar_init(&S.p2_empty[s], 128);
+    }
+    mbar_init(&S.q2_full, 1);
+    mbar_init(&S.q2_empty, 1);
+    mbar_init(&S.pb_full, cl_size);
+    mbar_init(&S.pb_empty, cl_size);
+    mbar_init(&S.ub_full, cl_size);
+    mbar_init(&S.ub_empty, cl_size);
+    mbar_init(&S.mma_drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < FU_NT) S.ew[threadIdx.x] = threadIdx.x < count ? EW[threadIdx.x] : 0;
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "r"(FU_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  cluster_sync_all();  // every CTA's barriers are initialized before any remote arrive
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: W once; then P1(band 0), and per band i: P1(band i + 1), P2(band i) -- the
+    // same 4 planes x nch chunks of A each time
+    int g = 0;
+    mbar_expect_tx(&S.w_full, (uint32_t)nch * FU_QCH);
+    for (int c = 0; c < nch; ++c)
+      for (int kb = 0; kb < 2; ++kb)
+        for (int p = 0; p < FU_S; ++p)
+          tma_load_3d(&tmW, &S.w_full, S.wq[c] + (kb * FU_S + p) * FU_QBOX, col0 + 128 * c + 64 * kb, 0, p);
+    auto load_band = [&](int j) -> bool {
+      const int r0 = (int)((zc + (int64_t)j * ncl) * FU_M);
+      for (int c = 0; c < nch; ++c) {
+        const int k0 = col0 + 128 * c;
+        for (int p = 0; p < FU_S; ++p, ++g) {
+          const int s = g % FU_RS;
+          if (!mbar_wait(&S.ring_empty[s], ((uint32_t)(g / FU_RS) & 1u) ^ 1u, err)) return false;
+          mbar_expect_tx(&S.ring_full[s], FU_SLOT);
+          tma_load_3d(&tmA, &S.ring_full[s], S.ring[s], k0, r0, p);
+          tma_load_3d(&tmA, &S.ring_full[s], S.ring[s] + OT_P_BYTES, k0 + 64, r0, p);
+        }
+      }
+      return true;
+    };
+    bool live = nb == 0 || load_band(0);
+    for (int i = 0; i < nb && live; ++i) {
+      if (i + 1 < nb) live = load_band(i + 1);
+      if (live) live = load_band(i);
+    }
+    if (*(volatile int*)err) {
+      tma_drain_ring(S.ring_full, FU_RS, g);
+      mbar_drain(&S.w_full, 0u);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    int g = 0, T = 0;
+    bool live = mbar_wait(&S.w_full, 0u, err);
+    tc_fence_after();
+    // P1 of the cluster's j-th band into tensor-memory buffer j & 1
+    auto p1 = [&](int j) -> bool {
+      const int buf = j & 1;
+      if (j >= 2 && !mbar_wait(&S.p1_empty[buf], (uint32_t)(((j - 2) >> 1) & 1), err)) return false;
+      tc_fence_after();
+      for (int c = 0; c < nch; ++c) {
+        for (int p = 0; p < FU_S; ++p, ++g) {
+          const int s = g % FU_RS;
+          if (!mbar_wait(&S.ring_full[s], (uint32_t)(g / FU_RS) & 1u, err)) return false;
+          tc_fence_after();
+          const uint32_t idesc = idesc_bf16(FU_M, FU_NT * (FU_S - p));
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks) {  // K = 128 columns: 4 steps in each 64-column box
+            const uint32_t box = (uint32_t)(ks >> 2), kk = (uint32_t)(ks & 3);
+            const uint64_t ad = sdesc_sw128(smem_u32(S.ring[s]) + box * OT_P_BYTES) + 2ull * kk;
+            const uint64_t bd = sdesc_sw128(smem_u32(S.wq[c]) + box * FU_S * FU_QBOX) + 2ull * kk;
+            const uint32_t acc = (c == 0 && p == 0 && ks == 0) ? 0u : 1u;
+            tc_mma_bf16(tmem + 128u * (uint32_t)buf + (uint32_t)(p * FU_NT), ad, bd, idesc, acc);
+          }
+          tc_commit(&S.ring_empty[s]);
+        }
+      }
+      tc_commit(&S.p1_full[buf]);
+      return true;
+    };
+    if (live && nb > 0) live = p1(0);
+    for (int i = 0; i < nb && live; ++i) {
+      if (i + 1 < nb && !p1(i + 1)) break;
+      // P2: wait for the band's u' digits
+      if (!mbar_wait(&S.q2_full, (uint32_t)(i & 1), err)) break;
+      tc_fence_after();
+      for (int c = 0; c < nch && live; ++c, ++T) {
+        const int bsel = T & 1, use = T >> 1;
+        if (use > 0 && !mbar_wait(&S.p2_empty[bsel], (uint32_t)((use - 1) & 1), err)) {
+          live = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dbase = tmem + 256u + 128u * (uint32_t)bsel;
+        for (int p = 0; p < FU_S; ++p, ++g) {
+          const int s = g % FU_RS;
+          if (!mbar_wait(&S.ring_full[s], (uint32_t)(g / FU_RS) & 1u, err)) {
+            live = false;
+            break;
+          }
+          tc_fence_after();
+          // A operand = the slab's columns (M) x the band's rows (K), MN-major; transpose bit 15
+          const uint32_t idesc = idesc_bf16(FU_M, FU_NT * (FU_S - p)) | (1u << 15);
+#pragma unroll
+          for (int ks = 0; ks < 8; ++ks) {  // K = 128 band rows: 16 rows (2 KiB) per step
+            const uint64_t ad = sdesc_mn_sw128(smem_u32(S.ring[s]) + (uint32_t)ks * 2048u, OT_P_BYTES);
+            const uint64_t bd =
+                sdesc_sw128(smem_u32(S.q2) + (uint32_t)(ks >> 2) * FU_S * FU_QBOX) + 2ull * (uint32_t)(ks & 3);
+            tc_mma_bf16(dbase + (uint32_t)(p * FU_NT), ad, bd, idesc, (p == 0 && ks == 0) ? 0u : 1u);
+          }
+          tc_commit(&S.ring_empty[s]);
+        }
+        if (live) tc_commit(&S.p2_full[bsel]);
+      }
+      if (live) tc_commit(&S.q2_empty);  // the band's u' digits are no longer read
+    }
+    if (*(volatile int*)err) {
+      tc_commit(&S.mma_drain);
+      mbar_drain(&S.mma_drain, 0u);
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue warps (thread e = TMEM lane e: a band row in P1, X2; a column in P2)
+    const int e = (int)threadIdx.x - 128, ew = warp - 4;
+    float gacc[2][FU_NT];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int l = 0; l < FU_NT; ++l) gacc[c][l] = 0.f;
+    bool ok = true;
+    int T = 0;
+    // P2 of the previous band: G of this CTA's columns += A_slab^T u', the levels weighted by
+    // 2^(-7 (t + 2)), the sum by 2^(E_max + E_u) (S.psc, still the previous band's)
+    auto p2_read = [&]() -> bool {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {  // nch <= 2, unrolled so that gacc stays in registers
+        if (c >= nch) break;
+        const int bsel = T & 1, use = T >> 1;
+        ++T;
+        if (!epi_all(mbar_wait(&S.p2_full[bsel], (uint32_t)(use & 1), err))) return false;
+        tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + 256u + 128u * (uint32_t)bsel;
+        float lev[FU_NT];
+#pragma unroll
+        for (int l = 0; l < FU_NT; ++l) lev[l] = 0.f;
+#pragma unroll 1
+        for (int t = FU_S - 1; t >= 0; --t) {
+          uint32_t v[32];
+          tmem_ld32_nowait(base + (uint32_t)(t * FU_NT), v);
+          tmem_wait_ld();
+          const float lw = __int_as_float((127 - 7 * (t + 2)) << 23);  // the level weight 2^(-7 (t + 2))
+#pragma unroll
+          for (int l = 0; l < FU_NT; ++l) lev[l] = fmaf(__uint_as_float(v[l]), lw, lev[l]);
+        }
+        tc_fence_before();
+        mbar_arrive(&S.p2_empty[bsel]);
+#pragma unroll
+        for (int l = 0; l < FU_NT; ++l) gacc[c][l] = fmaf(lev[l], S.psc[l], gacc[c][l]);
+      }
+      return true;
+    };
+    int ea_next = nb > 0 && zc * FU_M + e < m ? EA[zc * FU_M + e] : 0;
+    for (int i = 0; i < nb && ok; ++i) {
+      const int64_t r0 = (zc + (int64_t)i * ncl) * FU_M;
+      // the band's row exponents and their maximum over the finite rows (the next band's loaded ahead)
+      const int ea_e = ea_next;
+      {
+        const int64_t rn = r0 + ncl * FU_M + e;
+        ea_next = i + 1 < nb && rn < m ? EA[rn] : 0;
+      }
+      S.ea[e] = ea_e;
+      const int wm = __reduce_max_sync(0xffffffffu, (r0 + e < m && ea_e < OZ_EBAD) ? ea_e : INT_MIN);
+      if (lane == 0) S.emax4[ew] = wm;
+      epi_sync();
+      int eamax = max(max(S.emax4[0], S.emax4[1]), max(S.emax4[2], S.emax4[3]));
+      if (eamax == INT_MIN) eamax = 0;
+      // P1 partial of this CTA's columns, row e of the band
+      const int buf = i & 1;
+      if (!epi_all(mbar_wait(&S.p1_full[buf], (uint32_t)((i >> 1) & 1), err))) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      float acc[FU_NT];
+#pragma unroll
+      for (int l = 0; l < FU_NT; ++l) acc[l] = 0.f;
+      const uint32_t lb = tmem + ((uint32_t)(ew * 32) << 16) + 128u * (uint32_t)buf;
+#pragma unroll 1
+      for (int t = FU_S - 1; t >= 0; --t) {
+        uint32_t v[32];
+        tmem_ld32_nowait(lb + (uint32_t)(t * FU_NT), v);
+        tmem_wait_ld();
+        const float sc = __int_as_float((127 - 7 * (t + 2)) << 23);
+#pragma unroll
+        for (int l = 0; l < FU_NT; ++l) acc[l] = fmaf(__uint_as_float(v[l]), sc, acc[l]);
+      }
+      tc_fence_before();
+      mbar_arrive(&S.p1_empty[buf]);
+      // my partial may be overwritten once every CTA has read the previous band's
+      if (!epi_all(i == 0 || mbar_wait_cluster(&S.pb_empty, (uint32_t)((i - 1) & 1), err))) {
+        ok = false;
+        break;
+      }
+#pragma unroll
+      for (int l = 0; l < FU_NT; ++l) S.pbuf[l * FU_M + e] = acc[l];
+      epi_sync();
+      if (e == 0) {
+        asm volatile("fence.acq_rel.cluster;" ::: "memory");
+        for (int r = 0; r < cl_size; ++r) dsmem_arrive(dsmem_addr(&S.pb_full, (uint32_t)r));
+      }
+      // the previous band's P2 while the peers' partials arrive
+      if (i > 0 && !p2_read()) {
+        ok = false;
+        break;
+      }
+      // X1: my rows of the band (4 at a time), summed over the cluster in rank order; U' = v + c U;
+      // u' into every CTA
+      if (!epi_all(mbar_wait_cluster(&S.pb_full, (uint32_t)(i & 1), err) &&
+                   (i == 0 || mbar_wait_cluster(&S.ub_empty, (uint32_t)((i - 1) & 1), err)))) {
+        ok = false;
+        break;
+      }
+      const int nq = nrows / 4;
+      for (int v = e; v < FU_NT * nq; v += 128) {
+        const int l = v / nq, row = row_lo + 4 * (v % nq);
+        float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int r = 0; r < cl_size; ++r) {
+          const float4 t4 = *reinterpret_cast<const float4*>(peer_ptr(S.pbuf, (uint32_t)r) + l * FU_M + row);
+          s4.x += t4.x;
+          s4.y += t4.y;
+          s4.z += t4.z;
+          s4.w += t4.w;
+        }
+        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+        float up[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int64_t grow = r0 + row + k;
+          up[k] = 0.f;
+          if (grow < m && l < count) {
+            const int er = S.ea[row + k], eq = S.ew[l];
+            const int es = er + eq;
+            const double val = (er >= OZ_EBAD || eq >= OZ_EBAD) ? __longlong_as_double(0x7ff8000000000000ll)
+                               : (es >= -1022 && es <= 1023) ? (double)sv[k] * pow2d(es)
+                                                             : ldexp((double)sv[k], es);
+            float* u = U + (int64_t)l * ldu + grow;
+            const float un = coef ? (float)(val + coef[l] * (double)*u) : (float)val;
+            *u = un;
+            up[k] = er >= OZ_EBAD ? un : un * pow2f(er - eamax);
+          }
+        }
+        const float4 u4 = make_float4(up[0], up[1], up[2], up[3]);
+        for (int r = 0; r < cl_size; ++r)
+          *reinterpret_cast<float4*>(peer_ptr(S.ub, (uint32_t)r) + l * FU_M + row) = u4;
+      }
+      epi_sync();
+      if (e == 0) {
+        asm volatile("fence.acq_rel.cluster;" ::: "memory");
+        for (int r = 0; r < cl_size; ++r) {
+          dsmem_arrive(dsmem_addr(&S.pb_empty, (uint32_t)r));
+          dsmem_arrive(dsmem_addr(&S.ub_full, (uint32_t)r));
+        }
+      }
+      // X2: the band's u' digits (4, one exponent per lambda) into the B operand of P2; thread e = row
+      if (!epi_all(mbar_wait_cluster(&S.ub_full, (uint32_t)(i & 1), err) &&
+                   (i == 0 || mbar_wait(&S.q2_empty, (uint32_t)((i - 1) & 1), err)))) {
+        ok = false;
+        break;
+      }
+#pragma unroll 4
+      for (int l = 0; l < FU_NT; ++l) {
+        const uint32_t b = __float_as_uint(fabsf(S.ub[l * FU_M + e]));  // non-finite: >= 0x7f800000
+        const uint32_t mx = __reduce_max_sync(0xffffffffu, b);
+        if (lane == 0) S.umax[ew][l] = mx;
+      }
+      epi_sync();
+      if (e < FU_NT) {
+        const uint32_t mx = max(max(S.umax[0][e], S.umax[1][e]), max(S.umax[2][e], S.umax[3][e]));
+        const int eu = mx >= 0x7f800000u ? OZ_EBAD : oz_exponent((double)__uint_as_float(mx));
+        S.eu[e] = eu;
+        S.psc[e] = eu >= OZ_EBAD ? __int_as_float(0x7fc00000) : pow2f(eamax + eu);
+      }
+      epi_sync();
+      {
+        uint8_t* base = S.q2 + (e >> 6) * FU_S * FU_QBOX;
+#pragma unroll 4
+        for (int l = 0; l < FU_NT; ++l) {
+          const int eu = S.eu[l];
+          unsigned short bits[FU_S];
+          oz_split4(eu >= OZ_EBAD ? 0.f : S.ub[l * FU_M + e], eu >= OZ_EBAD ? 0 : eu, bits);
+#pragma unroll
+          for (int p = 0; p < FU_S; ++p)
+            *reinterpret_cast<unsigned short*>(base + p * FU_QBOX + sw128_off(l, e & 63)) = bits[p];
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core reads
+      epi_sync();
+      if (e == 0) {
+        mbar_arrive(&S.q2_full);
+        asm volatile("fence.acq_rel.cluster;" ::: "memory");
+        for (int r = 0; r < cl_size; ++r) dsmem_arrive(dsmem_addr(&S.ub_empty, (uint32_t)r));
+      }
+    }
+    // the last band's P2
+    if (ok && nb > 0) ok = p2_read();
+    // this cluster's partial plane of G: partial[z][l][col]
+    if (ok) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (c >= nch) break;
+        const int64_t col = col0 + 128 * c + e;
+        if (col < n) {
+#pragma unroll
+          for (int l = 0; l < FU_NT; ++l)
+            if (l < count) partial[((int64_t)zc * count + l) * n + col] = (double)gacc[c][l];
+        }
+      }
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  cluster_sync_all();  // no CTA leaves while a peer may still use its shared memory
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FU_TMEM_COLS) : "memory");
+  }
+}
+
 }  // namespace
 
 size_t oz_slices_bytes(int64_t rows, int64_t cols, int planes) {
@@ -953,6 +1469,70 @@ tk_status oz_lsqr_atu(const void* AslicesT, const int* EC, int64_t m, int64_t n,
   TK_TRY(oz_prepare(U, TK_F32, count, m, ldu, Uslices, EU, st, OZ_LSQR_DIGITS));
   return launch_oz_tc<OZ_LSQR_DIGITS, 1>(AslicesT, EC, n, OZ_S, Uslices, EU, count, OZ_LSQR_DIGITS, m, splits,
                                          nullptr, partial, n, nullptr, err, st);
+}
+
+// Cluster shape of the fused step for n columns: CL CTAs (a power of two, at most 8, so that each
+// CTA's share of a band's 128 rows is a multiple of 4) of cpc columns (a multiple of 128, at most
+// 256); CL = 0 when n is beyond 8 x 256.
+static void fused_shape(int64_t n, int* CL, int* cpc) {
+  const int64_t n64 = cdiv(n, OZ_KPAD) * OZ_KPAD;
+  const int64_t need = std::max<int64_t>(1, cdiv(n64, 256));
+  int cl = 1;
+  while (cl < need && cl < 8) cl *= 2;
+  const int c = (int)(cdiv(n64, (int64_t)cl * 128) * 128);
+  *CL = c <= 256 ? cl : 0;
+  *cpc = c;
+}
+
+bool oz_fused_supported(int64_t m, int64_t n, int count) {
+  int cl = 0, cpc = 0;
+  fused_shape(n, &cl, &cpc);
+  return cl > 0 && count >= 1 && count <= FU_NT && m >= 1 && m <= INT32_MAX;
+}
+
+tk_status oz_lsqr_fused(const void* Aslices, const int* EA, int64_t m, int64_t n, const float* W, int64_t ldw,
+                        int count, void* Wslices, int* EW, float* U, int64_t ldu, const double* coef, double* partial,
+                        int max_planes, int* planes, int* err, cudaStream_t st) {
+  int CL = 0, cpc = 0;
+  fused_shape(n, &CL, &cpc);
+  if (!oz_fused_supported(m, n, count) || max_planes < 1) {
+    set_error_msg("fused LSQR step: unsupported shape");
+    return TK_EINVAL;
+  }
+  const int64_t n64 = cdiv(n, OZ_KPAD) * OZ_KPAD;
+  TK_TRY(oz_prepare(W, TK_F32, count, n, ldw, Wslices, EW, st, OZ_LSQR_DIGITS));
+  CUtensorMap mA, mW;
+  TK_TRY(make_slice_map(&mA, Aslices, m, n64, OT_M, OZ_S));
+  TK_TRY(make_slice_map(&mW, Wslices, count, n64, FU_NT, OZ_LSQR_DIGITS));
+  const size_t smem = sizeof(FuSmem) + 1024;
+  TK_CUDA(cudaFuncSetAttribute(k_oz_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // one wave of resident clusters, each looping over its bands (no second wave)
+  static int cached[9] = {0};
+  if (!cached[CL]) {
+    cfg.gridDim = dim3((unsigned)((152 / CL) * CL), 1, 1);
+    int nc = 0;
+    TK_CUDA(cudaOccupancyMaxActiveClusters(&nc, k_oz_fused, &cfg));
+    cached[CL] = nc > 0 ? nc : 1;
+  }
+  const int64_t bands = cdiv(m, FU_M);
+  const int ncl = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)cached[CL], bands, (int64_t)max_planes}));
+  cfg.gridDim = dim3((unsigned)(ncl * CL), 1, 1);
+  TK_CUDA(cudaLaunchKernelEx(&cfg, k_oz_fused, mA, mW, EA, (const int*)EW, m, n, count, cpc, U, ldu, coef, partial,
+                             err));
+  TK_LAUNCH_CHECK();
+  *planes = ncl;
+  return TK_OK;
 }
 
 size_t oz_gram_workspace(int64_t r, int64_t c) {

@@ -78,7 +78,8 @@ TK_API const char* tk_phase_name(int phase) {
   static const char* names[TK_PHASE_COUNT] = {"sketch", "gram",        "cholesky",     "svd",
                                               "precond_apply", "A_times_W", "At_times_U", "refine_residual64",
                                               "refine_normal64", "precond_inverse", "A_times_W_digits",
-                                              "At_times_U_digits", "slice_A", "cholesky_update"};
+                                              "At_times_U_digits", "slice_A", "cholesky_update",
+                                              "lsqr_step_fused"};
   if (phase < 0 || phase >= TK_PHASE_COUNT) return "unknown";
   return names[phase];
 }

@@ -45,7 +45,7 @@ class tk_info(C.Structure):
                 ("rnorm", C.c_double), ("arnorm", C.c_double), ("ne_norm", C.c_double), ("status", C.c_int)]
 
 
-TK_PHASE_COUNT = 14
+TK_PHASE_COUNT = 15
 
 
 class tk_phase_stats(C.Structure):
@@ -113,6 +113,8 @@ def lib() -> C.CDLL:
             "tk_residual": (INT, [P, P, INT, I64, INT, P, P, P, SZ, P]),
             "tk_autotune_clear": (None, []),
             "tk_wait_selftest": (INT, [I64, P, SZ, P]),
+            "tk_lsqr_step_products_workspace": (SZ, [I64, I64, INT]),
+            "tk_lsqr_step_products": (INT, [P, P, INT, P, P, P, INT, P, SZ, P]),
             "tk_lcurve_workspace_size": (INT, [P, INT, INT, P, P]),
             "tk_lcurve": (INT, [P, P, INT, INT, P, P, SZ, P, P, P, P]),
             "tk_create": (INT, [P, P]),
@@ -453,6 +455,20 @@ def lcurve_workspace_size(A, b, N: int, N_refine: int, opts: tk_opts) -> int:
     prob = make_problem(A, b)
     _check(lib().tk_lcurve_workspace_size(C.byref(prob), N, N_refine, C.byref(opts), C.byref(out)))
     return int(out.value)
+
+
+def tk_lsqr_step_products(A: torch.Tensor, W: torch.Tensor, U: torch.Tensor, coef: torch.Tensor | None, mode: int,
+                          stream=None) -> torch.Tensor:
+    """U <- W A^T + coef .* U (in place) and G = U A; returns G (count x n).  mode 0: the two digit
+    products; 1: both in one kernel; 2: the float32 products of at most 16 lambda."""
+    b = torch.zeros(A.shape[0], dtype=torch.float64, device=A.device)
+    prob = make_problem(A, b)
+    count = W.shape[0]
+    G = torch.empty((count, A.shape[1]), dtype=torch.float64, device=A.device)
+    work = _workspace(int(lib().tk_lsqr_step_products_workspace(A.shape[0], A.shape[1], count)), A.device)
+    _check(lib().tk_lsqr_step_products(C.byref(prob), _ptr(W.contiguous()), count, _ptr(U), _ptr(coef), _ptr(G),
+                                       int(mode), _ptr(work), work.numel(), _stream(stream)))
+    return G
 
 
 def tk_wait_selftest(budget_us: int, device="cuda", stream=None) -> int:
