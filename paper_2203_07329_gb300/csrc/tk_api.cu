@@ -615,6 +615,7 @@ tk_status solve_impl(const tk_problem* p, const double* lambdas, int N, const tk
     gp->maxiter = P.o.maxiter;
     gp->max_refine = P.o.max_refine;
     gp->refine_tol = P.o.refine_tol;
+    gp->emulate = P.o.emulate_fp64 ? 1 : 0;
     gp->ok_ids = ok_ids;
     if (P.lowrank) {  // the SVD and the ranks follow over all problems at once
       gp->lr_parts = LowRankParts{P.s, P.c, N, P.o.alpha, B.lam, B.sig, B.sd, B.ranks, B.lrV, B.lrS,
@@ -1045,6 +1046,7 @@ tk_status batch_layout(const tk_problem* ps, int P, int N, const tk_opts* o, int
     L.scratch_per = std::max(L.scratch_per, (kb.second + 255) & ~size_t(255));
     gp[i].m = pl[i].m;
     gp[i].n = pl[i].n;
+    gp[i].emulate = pl[i].o.emulate_fp64 ? 1 : 0;  // the digit scratch of the float64 passes
   }
   L.scratch_off = off;
   off += L.scratch_per * (size_t)L.lanes;

@@ -245,9 +245,13 @@ __global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ R, int64
 }
 
 // Row panel: tile (kb, jb), jb > kb, becomes R_kk^-T tile (forward
-// substitution; one column of the tile per thread, held in registers).
+// substitution; one column of the tile per thread, held in registers).  The
+// 64 reciprocals of the diagonal are formed once per tile (thread r forms
+// 1/D[r][r]): GB300's float64 division is slow, and every column would
+// otherwise divide by each of them.
 __global__ void __launch_bounds__(CB) k_chol_trsm(double* __restrict__ R, int64_t ldr, int64_t rstride, int kb) {
   __shared__ double D[CB][CB + 1];
+  __shared__ double Dinv[CB];
   const int l = blockIdx.y;
   const int jb = kb + 1 + blockIdx.x;
   double* Rl = R + (int64_t)l * rstride;
@@ -260,10 +264,11 @@ __global__ void __launch_bounds__(CB) k_chol_trsm(double* __restrict__ R, int64_
     D[i][c] = Dg[(int64_t)i * ldr + c];
     xr[i] = Xg[(int64_t)i * ldr + c];
   }
+  Dinv[c] = 1.0 / Dg[(int64_t)c * ldr + c];
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < CB; ++r) {
-    xr[r] = xr[r] / D[r][r];
+    xr[r] = xr[r] * Dinv[r];
 #pragma unroll
     for (int q = r + 1; q < CB; ++q) xr[q] = fma(-D[r][q], xr[r], xr[q]);
   }

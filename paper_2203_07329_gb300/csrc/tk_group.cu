@@ -61,6 +61,7 @@ struct GDesc {
   const int* ids;
   double *D, *Xa, *G, *Rres, *part64;  // part64: splits64 x cnt x n
   int splits64;
+  int sp64;  // planes of part64 written this round (<= splits64)
   double* nrm;  // 3 x N
 };
 
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(kThreads)
   double acc = 0.0;
   for (int64_t j = threadIdx.x; j < d.n; j += blockDim.x) {
     double g = 0.0;
-    for (int z = 0; z < d.splits64; ++z) g += d.part64[z * plane + (int64_t)q.k * d.n + j];
+    for (int z = 0; z < d.sp64; ++z) g += d.part64[z * plane + (int64_t)q.k * d.n + j];
     g = fma(-lv, d.Xa[(int64_t)q.k * d.n + j], g);
     d.G[(int64_t)q.k * d.n + j] = g;
     acc = fma(g, g, acc);
@@ -443,6 +444,11 @@ struct GState {
   int n_aw = 0, n_atu = 0;
   size_t cap64 = 0;
   double fl_aw = 0.0;  // flops of one step (all slots active): for the profiler
+  // the emulated float64 passes: digit planes of one problem at a time (the largest fits)
+  int64_t oz_m = 0, oz_n = 0;
+  size_t oz_rows_bytes = 0, oz_cols_bytes = 0, oz_vec_bytes = 0;
+  void *oz_rows = nullptr, *oz_cols = nullptr, *oz_colmax = nullptr, *oz_vec = nullptr;
+  int *oz_EA = nullptr, *oz_EC = nullptr, *oz_EV = nullptr, *oz_err = nullptr;
 };
 
 void carve_group(const std::vector<GroupProblem>& g, int N, Arena& a, GState& S) {
@@ -494,7 +500,15 @@ void carve_group(const std::vector<GroupProblem>& g, int N, Arena& a, GState& S)
     d.G = a.take<double>(vn);
     d.Rres = a.take<double>((size_t)N * q.m);
     d.splits64 = z.splits64;
+    d.sp64 = z.splits64;
     d.part64 = a.take<double>((size_t)z.splits64 * vn);
+    if (q.emulate) {
+      S.oz_m = std::max(S.oz_m, q.m);
+      S.oz_n = std::max(S.oz_n, q.n);
+      S.oz_rows_bytes = std::max(S.oz_rows_bytes, oz_slices_bytes(q.m, q.n));
+      S.oz_cols_bytes = std::max(S.oz_cols_bytes, oz_slices_bytes(q.n, q.m));
+      S.oz_vec_bytes = std::max({S.oz_vec_bytes, oz_slices_bytes(N, q.n), oz_slices_bytes(N, q.m)});
+    }
     naw += (size_t)cdiv(q.m, tiles::LM_BN);
     natu += (size_t)cdiv(q.n, tiles::LM_BN) * z.splits;
     n64 += (size_t)cdiv(N, kBM64) * (size_t)std::max(cdiv(q.m, kBN64), cdiv(q.n, kBN64) * z.splits64);
@@ -521,6 +535,18 @@ void carve_group(const std::vector<GroupProblem>& g, int N, Arena& a, GState& S)
     S.hd[p].nrm = S.nrm_all + (size_t)p * 3 * N;
   }
   S.BM = N <= 16 ? 16 : (N <= 32 ? 32 : 64);
+  if (S.oz_rows_bytes > 0) {
+    // the largest problem's digit planes of A's rows and columns, and of the lambda-side vectors
+    // (X: N x n, r: N x m), reused problem by problem
+    S.oz_rows = a.take<char>(S.oz_rows_bytes);
+    S.oz_cols = a.take<char>(S.oz_cols_bytes);
+    S.oz_colmax = a.take<char>(oz_colmax_bytes(S.oz_n));
+    S.oz_vec = a.take<char>(S.oz_vec_bytes);
+    S.oz_EA = a.take<int>((size_t)S.oz_m);
+    S.oz_EC = a.take<int>((size_t)S.oz_n);
+    S.oz_EV = a.take<int>((size_t)N);
+    S.oz_err = a.take<int>(4);
+  }
 }
 
 // ---- launch helpers ----------------------------------------------------------------
@@ -609,8 +635,9 @@ tk_status group_solve_mixed(std::vector<GroupProblem>& g, int N, void* work, siz
     }
     S.n_aw = (int)t_aw.size();
     S.n_atu = (int)t_atu.size();
-    if (S.n_aw) TK_CUDA(cudaMemcpyAsync(S.t_aw, t_aw.data(), sizeof(GTile) * t_aw.size(), cudaMemcpyHostToDevice, st));
-    if (S.n_atu)
+    if (!t_aw.empty())
+      TK_CUDA(cudaMemcpyAsync(S.t_aw, t_aw.data(), sizeof(GTile) * t_aw.size(), cudaMemcpyHostToDevice, st));
+    if (!t_atu.empty())
       TK_CUDA(cudaMemcpyAsync(S.t_atu, t_atu.data(), sizeof(GTile) * t_atu.size(), cudaMemcpyHostToDevice, st));
     return TK_OK;
   };
@@ -650,12 +677,47 @@ tk_status group_solve_mixed(std::vector<GroupProblem>& g, int N, void* work, siz
       // ---- float64 pass: Rres = b - A x, G = A^T Rres - lambda x, for the listed lambda
       k_g_gather_x<<<chunk_grid(S.maxn, nrl), 256, 0, st>>>(S.dd, S.rnd);
       TK_LAUNCH_CHECK();
+      // problems that emulate the float64 products: r = b - Xa A^T and the planes of r A from exact
+      // digits on the tensor cores, one problem at a time through the shared digit scratch
+      bool any_oz = false;
+      for (int p = 0; p < P; ++p) any_oz = any_oz || (hcnt[p] > 0 && g[p].emulate);
+      if (any_oz) {
+        TK_CUDA(cudaMemsetAsync(S.oz_err, 0, sizeof(int), st));
+        for (int mode = 0; mode < 2; ++mode) {
+          double fl = 0.0, by = 0.0, ib = 0.0;
+          const int tok = prof_begin(mode == 0 ? TK_PHASE_RES64 : TK_PHASE_NE64, st);
+          for (int p = 0; p < P; ++p) {
+            if (hcnt[p] == 0 || !g[p].emulate) continue;
+            const GDesc& d = S.hd[p];
+            const tk_dtype dt = g[p].f64 ? TK_F64 : TK_F32;
+            const int M = hcnt[p];
+            if (mode == 0) {
+              TK_TRY(oz_prepare(g[p].Af, dt, g[p].m, g[p].n, g[p].ldaf, S.oz_rows, S.oz_EA, st));
+              TK_TRY(oz_prepare(d.Xa, TK_F64, M, g[p].n, g[p].n, S.oz_vec, S.oz_EV, st));
+              TK_TRY(oz_residual(S.oz_rows, S.oz_EA, g[p].m, g[p].n, S.oz_vec, S.oz_EV, M, g[p].b, d.Rres, g[p].m,
+                                 S.oz_err, st));
+            } else {
+              const int sp = std::min(d.splits64, oz_normal_splits(g[p].m, g[p].n, M));
+              TK_TRY(oz_prepare_cols(g[p].Af, dt, g[p].m, g[p].n, g[p].ldaf, S.oz_cols, S.oz_EC, S.oz_colmax, st));
+              TK_TRY(oz_normal(S.oz_cols, S.oz_EC, g[p].m, g[p].n, d.Rres, g[p].m, M, S.oz_vec, S.oz_EV, d.part64, sp,
+                               S.oz_err, st));
+              S.hd[p].sp64 = sp;
+            }
+            const double es = g[p].f64 ? 8.0 : 4.0;
+            fl += 2.0 * M * g[p].m * g[p].n;
+            by += es * g[p].m * g[p].n + 16.0 * M * g[p].m;
+            ib += (2.0 * es + 32.0) * g[p].m * g[p].n + 16.0 * M * g[p].m;  // A read twice, 8 planes out and in
+          }
+          prof_end(tok, st, fl, by, ib);
+        }
+        TK_CUDA(cudaMemcpyAsync(S.dd, S.hd.data(), sizeof(GDesc) * P, cudaMemcpyHostToDevice, st));
+      }
       for (int mode = 0; mode < 2; ++mode) {
         for (int f = 0; f < 2; ++f) {  // float64 and float32 inputs launch separately
           t64.clear();
           double fl = 0.0, by = 0.0;
           for (int p = 0; p < P; ++p) {
-            if (hcnt[p] == 0 || g[p].f64 != (f == 0)) continue;
+            if (hcnt[p] == 0 || g[p].f64 != (f == 0) || g[p].emulate) continue;
             for (int m0 = 0; m0 < hcnt[p]; m0 += kBM64) {
               if (mode == 0) {
                 for (int64_t n0 = 0; n0 < g[p].m; n0 += kBN64) t64.push_back(GTile{p, 0, m0, 0, n0});
@@ -689,6 +751,15 @@ tk_status group_solve_mixed(std::vector<GroupProblem>& g, int N, void* work, siz
       }
       k_g_ne_finish<<<nrl, kThreads, 0, st>>>(S.dd, S.cnt, S.rnd);
       TK_LAUNCH_CHECK();
+      if (any_oz) {
+        int herr = 0;
+        TK_CUDA(cudaMemcpyAsync(&herr, S.oz_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TK_CUDA(cudaStreamSynchronize(st));
+        if (herr) {
+          set_error_msg("grouped solve: a pipeline wait of the emulated float64 passes timed out");
+          return TK_ETIMEOUT;
+        }
+      }
     }
 
     // ---- float32 LSQR on [b; 0] (round 0) or [0; g / sqrt(l)]: all problems together

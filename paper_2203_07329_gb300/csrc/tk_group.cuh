@@ -51,6 +51,7 @@ struct GroupProblem {
   int maxiter = 500;
   int max_refine = 8;
   double refine_tol = 1e-11;
+  int emulate = 0;  // the float64 refinement passes from exact digits on the tensor cores
   std::vector<int> ok_ids;  // lambdas that have a preconditioner
   tk_info* inf = nullptr;   // host, N entries
   // low rank, before the grouped SVD: the sketch Y (s x n) and its scratch

@@ -39,9 +39,11 @@ def int_inputs(m, n, count, seed, dtype):
 
 
 # counts 1..16 (4-, 8- and 16-lambda kernels), n a multiple of 128, ragged (not a multiple of 4:
-# scalar loads), m ragged against the 4-row groups and the splits
+# scalar loads), m ragged against the 4-row groups and the splits; n beyond one chunk of W in shared
+# memory (3200 columns for 16 lambda: 5000 and 3300 take two chunks, 13000 with 8 lambda two)
 @pytest.mark.parametrize("m,n,count", [(1000, 200, 1), (777, 129, 3), (4097, 2048, 16), (5003, 1000, 8),
-                                       (64, 2048, 5), (3, 30, 9), (2500, 513, 12)])
+                                       (64, 2048, 5), (3, 30, 9), (2500, 513, 12), (1000, 5000, 16),
+                                       (300, 3301, 9), (500, 13000, 7)])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_small_products_exact_on_integers(tk, m, n, count, dtype):
     A, W, U, coef = int_inputs(m, n, count, seed=m * 7 + n + count, dtype=dtype)
