@@ -42,9 +42,9 @@ __global__ void __launch_bounds__(LM_AW_THREADS)
   }
 }
 
-// CW columns per thread (4 for <= 8 lambda, 2 for 16: NL x CW accumulators)
+// CW columns per thread (4 for <= 8 lambda, 2 for 16: NL x CW accumulators); three CTAs per SM
 template <int NL, int CW>
-__global__ void __launch_bounds__(lmb::kAtuThreads, 2)
+__global__ void __launch_bounds__(lmb::kAtuThreads, 3)
     k_lm_atu(const float* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ U, int64_t ldu,
              int count, int64_t rows_per, double* __restrict__ partial, bool vec) {
   __shared__ __align__(16) float us[lmb::kAtuRB][NL];
@@ -91,7 +91,7 @@ tk_status lm_small_aw(const float* A, int64_t lda, int64_t m, int64_t n, const f
 
 int lm_small_atu_splits(int64_t m, int64_t n) {
   const int64_t tiles = cdiv(n, 2 * lmb::kAtuThreads);
-  const int64_t want = cdiv(2 * 152, tiles);                 // two CTAs per SM
+  const int64_t want = cdiv(3 * 152, tiles);                 // three CTAs per SM
   const int64_t maxs = std::max<int64_t>(1, cdiv(m, 64));    // at least 64 rows per split
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, maxs));
 }
