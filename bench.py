@@ -565,15 +565,21 @@ def main():
     X_host = torch.empty((N, n), dtype=torch.float64).pin_memory()
     A_dev = torch.empty_like(A)
     b_dev = torch.empty_like(b)
+
+    def e2e_step():
+        A_dev.copy_(A_host, non_blocking=True)
+        b_dev.copy_(b_host, non_blocking=True)
+        tk.tk_solve(A_dev, b_dev, lams, o_mixed, work=work, X=X, stream=stream)
+        X_host.copy_(X, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):  # untimed, like the device-resident steps (first use of the pinned pages)
+        e2e_step()
     barrier()
     t0 = time.perf_counter()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        A_dev.copy_(A_host, non_blocking=True)
-        b_dev.copy_(b_host, non_blocking=True)
-        tk.tk_solve(A_dev, b_dev, lams, o_mixed, work=work, X=X, stream=stream)
-        X_host.copy_(X, non_blocking=True)
+        e2e_step()
     e1.record(stream)
     barrier()
     e2e_ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
