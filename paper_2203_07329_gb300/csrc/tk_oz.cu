@@ -678,7 +678,7 @@ __device__ __forceinline__ double i53_scaled(long long v, int s, bool* ok) {
 // hi = ((L0 128 + L1) 128 + L2) 128 + L3 and lo likewise from L4..L7 (both
 // below 2^43), and the tile value is hi 2^-35 + lo 2^-63 (exact products of
 // exact integers), scaled by 2^(E_i + E_j).
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(384, 1)
     k_oz_syrk(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
               const int* __restrict__ EC, int64_t np, int kb, double* __restrict__ R, int64_t ldr, int64_t rstride,
               int* __restrict__ err) {
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(256, 1)
       mbar_init(&S.q_full[s], 1);
       mbar_init(&S.q_empty[s], 1);
       mbar_init(&S.acc_full[s], 1);
-      mbar_init(&S.acc_empty[s], 128);
+      mbar_init(&S.acc_empty[s], 256);
     }
     mbar_init(&S.mma_drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -757,65 +757,77 @@ __global__ void __launch_bounds__(256, 1)
       mbar_drain(&S.mma_drain, 0u);
     }
   } else if (warp >= 4) {
-    const int ew = warp - 4;
+    // 8 epilogue warps: warp w reads tensor-memory lanes 32 (w % 4) .. (the rows), and the two warps
+    // of a lane quarter split each tile's 32 columns: warps 4-7 the first 16, warps 8-11 the last 16
+    const int ew = warp & 3, half = (warp - 4) >> 2;
     const int64_t i = i0 + ew * 32 + lane;
     const int* El = EC + (int64_t)l * np;
     const int ei = i < w ? El[i] : 0;
     double* Trow = R + (int64_t)l * rstride + (c0 + i) * ldr + c0;
-    // the exponents of the CTA's columns, once, in shared memory (the four epilogue warps only)
-    for (int c = (int)threadIdx.x - 128; c < CS_TILES * CS_N; c += 128) {
+    // the exponents of the CTA's columns, once, in shared memory (the epilogue warps only)
+    for (int c = (int)threadIdx.x - 128; c < CS_TILES * CS_N; c += 256) {
       const int64_t col = (int64_t)t_first * CS_N + c;
       S.ecol[c] = col < w ? El[col] : 0;
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    // the thread's 16 columns of a tile in 2 groups of 8; per group the 8 levels of the 8 columns are
+    // read from tensor memory and the exact integers hi = L0 2^21 + L1 2^14 + L2 2^7 + L3 and lo (L4 ..
+    // L7 likewise) formed as (L0 128 + L1) 2^14 + (L2 128 + L3) -- the same integers as a Horner
+    // chain, |L0 128 + L1| < 2^30
+    constexpr int G = 8;
     for (int t = 0; t < nt; ++t) {
       const int s = t & 1;
-      const int64_t j0 = (int64_t)(t_first + t) * CS_N;
-      // T of this tile first: its loads do not wait for the products
-      double tv[CS_N];
+      const int64_t j0 = (int64_t)(t_first + t) * CS_N + half * 2 * G;
+      // T of the thread's 16 columns first: their loads do not wait for the products
+      double tv[2][G];
 #pragma unroll
-      for (int j = 0; j < CS_N; ++j) tv[j] = (i < w && j0 + j < w && j0 + j >= i) ? Trow[j0 + j] : 0.0;
+      for (int gi = 0; gi < 2; ++gi)
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const int64_t col = j0 + gi * G + j;
+          tv[gi][j] = (i < w && col < w && col >= i) ? Trow[col] : 0.0;
+        }
       if (!mbar_wait(&S.acc_full[s], (uint32_t)(t >> 1) & 1u, err)) break;
       tc_fence_after();
-      const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(s * OZ_LV * CS_N);
-      long long hi[CS_N], lo[CS_N];
+      const uint32_t base =
+          tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(s * OZ_LV * CS_N) + (uint32_t)(half * 2 * G);
 #pragma unroll
-      for (int j = 0; j < CS_N; ++j) hi[j] = lo[j] = 0;
-#pragma unroll 1
-      for (int lv = 0; lv < OZ_LV; ++lv) {
-        uint32_t v[32];
-        tmem_ld32_nowait(base + (uint32_t)(lv * CS_N), v);
+      for (int gi = 0; gi < 2; ++gi) {
+        const int64_t jg = j0 + gi * G;
+        uint32_t v[OZ_LV][G];
+#pragma unroll
+        for (int lv = 0; lv < OZ_LV; ++lv) tmem_ld8_nowait(base + (uint32_t)(lv * CS_N + gi * G), v[lv]);
         tmem_wait_ld();
-        if (lv < 4) {
-#pragma unroll
-          for (int j = 0; j < CS_N; ++j) hi[j] = hi[j] * 128 + level_int(v[j]);
-        } else {
-#pragma unroll
-          for (int j = 0; j < CS_N; ++j) lo[j] = lo[j] * 128 + level_int(v[j]);
+        if (gi == 1) {
+          tc_fence_before();
+          mbar_arrive(&S.acc_empty[s]);  // every level of the thread's columns is in registers
         }
-      }
-      tc_fence_before();
-      mbar_arrive(&S.acc_empty[s]);  // the levels are in registers: the buffer is free
-      if (i < w) {
+        if (i < w) {
 #pragma unroll
-        for (int j = 0; j < CS_N; ++j) {
-          if (j0 + j < w && j0 + j >= i) {
-            const int ej = S.ecol[t * CS_N + j];
-            const int e = ei + ej;
-            if (ei >= OZ_EBAD || ej >= OZ_EBAD) {  // a row or column marked non-finite: NaN (its digits are zero)
-              Trow[j0 + j] = __longlong_as_double(0x7ff8000000000000ll);
-              continue;
-            }
-            // (hi 2^-35 + lo 2^-63) 2^e with the two scaled terms built exactly from the integers'
-            // bits; the sum and the subtraction are the only float64 operations (the same rounding
-            // as scaling the rounded sum, since a power of two scales exactly)
-            bool ok = true;
-            const double shi = i53_scaled(hi[j], e - 35, &ok), slo = i53_scaled(lo[j], e - 63, &ok);
-            if (ok) {
-              Trow[j0 + j] = tv[j] - (shi + slo);
-            } else {  // a scaled term outside the normal range: through the float64 pipe
-              const double vhi = (double)hi[j] * 0x1p-35, vlo = (double)lo[j] * 0x1p-63;  // exact
-              Trow[j0 + j] = tv[j] - (vhi + vlo) * (e >= -1022 && e <= 1023 ? pow2d(e) : ldexp(1.0, e));
+          for (int j = 0; j < G; ++j) {
+            if (jg + j < w && jg + j >= i) {
+              const int ej = S.ecol[t * CS_N + half * 2 * G + gi * G + j];
+              const int e = ei + ej;
+              if (ei >= OZ_EBAD || ej >= OZ_EBAD) {  // a row or column marked non-finite: NaN (its digits are zero)
+                Trow[jg + j] = __longlong_as_double(0x7ff8000000000000ll);
+                continue;
+              }
+              const int a0 = level_int(v[0][j]) * 128 + level_int(v[1][j]);
+              const int a1 = level_int(v[2][j]) * 128 + level_int(v[3][j]);
+              const int b0 = level_int(v[4][j]) * 128 + level_int(v[5][j]);
+              const int b1 = level_int(v[6][j]) * 128 + level_int(v[7][j]);
+              const long long hi = (long long)a0 * 16384 + a1, lo = (long long)b0 * 16384 + b1;
+              // (hi 2^-35 + lo 2^-63) 2^e with the two scaled terms built exactly from the integers'
+              // bits; the sum and the subtraction are the only float64 operations (the same rounding
+              // as scaling the rounded sum, since a power of two scales exactly)
+              bool ok = true;
+              const double shi = i53_scaled(hi, e - 35, &ok), slo = i53_scaled(lo, e - 63, &ok);
+              if (ok) {
+                Trow[jg + j] = tv[gi][j] - (shi + slo);
+              } else {  // a scaled term outside the normal range: through the float64 pipe
+                const double vhi = (double)hi * 0x1p-35, vlo = (double)lo * 0x1p-63;  // exact
+                Trow[jg + j] = tv[gi][j] - (vhi + vlo) * (e >= -1022 && e <= 1023 ? pow2d(e) : ldexp(1.0, e));
+              }
             }
           }
         }
@@ -1617,7 +1629,7 @@ tk_status oz_chol_step(const OzCholPlan& plan, int kb, cudaStream_t st) {
                                                                                    plan.np, kb, sl, plan.EC);
   TK_LAUNCH_CHECK();
   const dim3 grid((unsigned)cdiv(w, CS_M), (unsigned)cdiv(w / CS_N, CS_TILES), (unsigned)plan.N);
-  k_oz_syrk<<<grid, 256, sizeof(CsSmem) + 1024, st>>>(plan.mP, plan.mQ, plan.EC, plan.np, kb, plan.R, plan.ldr,
+  k_oz_syrk<<<grid, 384, sizeof(CsSmem) + 1024, st>>>(plan.mP, plan.mQ, plan.EC, plan.np, kb, plan.R, plan.ldr,
                                                      plan.rstride, plan.err);
   TK_LAUNCH_CHECK();
   return TK_OK;
