@@ -14,7 +14,9 @@
 // (p, q) with p + q = t share one FP32 accumulator ("level" t), and a level
 // sum of at most 8 pairs over 256 values of K stays below 2^24, so the tensor
 // core's FP32 accumulation is exact.  Every 256 values of K the level sums
-// are scaled by 2^(-7(t+2)) and added into float64 accumulators.  The 28
+// are added, with their weights 2^(-7(t+2)), exactly into two int64
+// accumulators per output (levels 0-3 and 4-7), made one double at the
+// end (with 4 digits: scaled into FP32 accumulators).  The 28
 // pairs with p + q > 7 are dropped: at most 7.1 * 2^-58 of 2^(Ea+Ex), i.e.
 // 2^-51 of max|a| max|x| per product when every digit is +-64 (typical digits
 // give far less).  The result carries errors of a few float64 units relative
@@ -310,15 +312,6 @@ struct OtSmem {
   uint32_t tmem_base;
 };
 
-// An FP32 value holding an integer (|v| < 2^24), times 2^(-7(t+2)), as a
-// double: the float's fields moved into the double's, the power of two added
-// to the exponent (exact; no conversion instruction).
-__device__ __forceinline__ double level_to_double(uint32_t bits, int t) {
-  const uint32_t a = bits & 0x7fffffffu;
-  const uint32_t mag = a ? (a >> 3) + ((uint32_t)(896 - 7 * (t + 2)) << 20) : 0u;
-  return __hiloint2double((int)(mag | (bits & 0x80000000u)), (int)(bits << 29));
-}
-
 template <int S, int MODE, int NT>
 __global__ void __launch_bounds__(256, OtCfg<S, NT>::CTAS_PER_SM)
     k_oz_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ,
@@ -440,9 +433,17 @@ __global__ void __launch_bounds__(256, OtCfg<S, NT>::CTAS_PER_SM)
     }
   } else if (warp >= 4) {
     const int ew = warp - 4;
-    Acc acc[NT];
+    // S = 8 (float64-accurate): the chunk's 8 exact level sums (|L_t| <= (t+1) 2^20, so L0 128 + L1 and
+    // the like fit an int) are added exactly into two int64 accumulators per column, hi += L0 2^21 +
+    // L1 2^14 + L2 2^7 + L3 and lo likewise from L4 .. L7 (value = hi 2^-35 + lo 2^-63; each under 2^44 per
+    // chunk, so exact for K <= 2^27 per split), 8 columns at a time -- integer work, off GB300's slow float64
+    // pipe -- and turned into one double at the end.  S = 4: float32 accumulators.
+    Acc acc[S == OZ_S ? 1 : NT];
+    long long hacc[S == OZ_S ? NT : 1], lacc[S == OZ_S ? NT : 1];
 #pragma unroll
-    for (int j = 0; j < NT; ++j) acc[j] = Acc(0);
+    for (int j = 0; j < (S == OZ_S ? 1 : NT); ++j) acc[j] = Acc(0);
+#pragma unroll
+    for (int j = 0; j < (S == OZ_S ? NT : 1); ++j) hacc[j] = lacc[j] = 0;
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
       const int bsel = c & 1, use = c >> 1;
@@ -452,17 +453,30 @@ __global__ void __launch_bounds__(256, OtCfg<S, NT>::CTAS_PER_SM)
       }
       tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(bsel * S * NT);
-#pragma unroll 1
-      for (int t = S - 1; t >= 0; --t) {  // smallest level first
+      if constexpr (S == OZ_S) {
 #pragma unroll
-        for (int h = 0; h < NT / 32; ++h) {
-          uint32_t v[32];
-          tmem_ld32_nowait(base + (uint32_t)(t * NT + 32 * h), v);
+        for (int g = 0; g < NT / 8; ++g) {
+          uint32_t v[OZ_S][8];
+#pragma unroll
+          for (int t = 0; t < OZ_S; ++t) tmem_ld8_nowait(base + (uint32_t)(t * NT + 8 * g), v[t]);
           tmem_wait_ld();
-          if constexpr (S == OZ_S) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[32 * h + j] += level_to_double(v[j], t);
-          } else {
+          for (int j = 0; j < 8; ++j) {
+            int L[OZ_S];
+#pragma unroll
+            for (int t = 0; t < OZ_S; ++t) L[t] = __float2int_rz(__uint_as_float(v[t][j]));  // exact integers
+            hacc[8 * g + j] += (long long)(L[0] * 128 + L[1]) * 16384 + (L[2] * 128 + L[3]);
+            lacc[8 * g + j] += (long long)(L[4] * 128 + L[5]) * 16384 + (L[6] * 128 + L[7]);
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int t = S - 1; t >= 0; --t) {  // smallest level first
+#pragma unroll
+          for (int h = 0; h < NT / 32; ++h) {
+            uint32_t v[32];
+            tmem_ld32_nowait(base + (uint32_t)(t * NT + 32 * h), v);
+            tmem_wait_ld();
             const float sc = __int_as_float((127 - 7 * (t + 2)) << 23);  // 2^(-7(t+2)), exact
 #pragma unroll
             for (int j = 0; j < 32; ++j) acc[32 * h + j] = fmaf(__uint_as_float(v[j]), sc, acc[32 * h + j]);
@@ -481,8 +495,11 @@ __global__ void __launch_bounds__(256, OtCfg<S, NT>::CTAS_PER_SM)
         const int l = l0 + j;
         if (l < M) {
           const int eq = EQ[l];
+          double d;
+          if constexpr (S == OZ_S) d = fma((double)lacc[j], 0x1p-63, (double)hacc[j] * 0x1p-35);
+          else d = (double)acc[j];
           const double v = (er >= OZ_EBAD || eq >= OZ_EBAD) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                            : ldexp((double)acc[j], er + eq);
+                                                            : ldexp(d, er + eq);
           if (MODE == 0) {
             static_cast<double*>(out)[(int64_t)l * ldo + r] = br - v;
           } else if (MODE == 1) {
@@ -557,6 +574,10 @@ tk_status launch_oz_tc(const void* Ps, const int* EP, int64_t rows, int planesP,
   TK_TRY(make_slice_map(&mP, Ps, rows, kp, OT_M, planesP));
   const int64_t kps = cdiv(cdiv(K, splits), OT_CHUNK) * OT_CHUNK;  // whole chunks per split
   const int sp = (int)cdiv(K, kps);
+  if (S == OZ_S && kps > (int64_t(1) << 27)) {  // the exact int64 level accumulators of a split
+    set_error_msg("emulated product: more than 2^27 values of K in one split");
+    return TK_EINVAL;
+  }
   if (oz_tile_n(S, M) == 64) {
     if constexpr (S != OZ_S)
       TK_TRY((launch_oz_tc_nt<S, MODE, 64>(mP, Qs, EP, rows, EQ, M, planesQ, kp, kps, sp, b, out, ldo, coef, err, st,
