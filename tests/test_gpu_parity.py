@@ -549,6 +549,28 @@ def test_emulated_residual_has_float64_accuracy(tk, dtype):
     assert err_e <= 4 * err_n + 1e-16, (err_e, err_n)
 
 
+# rows sliced in one pass from registers (padded rows of <= 4096 values: 512, 1024, 2048 and 4096
+# values per CTA pass, 16- or 8-byte pair loads, or element loads for an odd leading dimension or an
+# unaligned base) and by the two-pass route above that (4100 columns)
+@pytest.mark.parametrize("m,n,dtype,offset", [(1500, 4096, torch.float64, 0), (700, 4100, torch.float64, 0),
+                                              (900, 1025, torch.float32, 1), (333, 2000, torch.float64, 1),
+                                              (2000, 64, torch.float32, 0), (50, 511, torch.float64, 0)])
+def test_emulated_residual_row_slicing_shapes(tk, m, n, dtype, offset):
+    gen = torch.Generator().manual_seed(m + n)
+    full = torch.randn(m, n + 2 * offset + (1 if offset else 0), generator=gen, dtype=torch.float64)
+    full *= torch.pow(2.0, torch.randint(-30, 31, (m, 1), generator=gen).double())  # row scales 2^-30 .. 2^30
+    full = full.to(dtype).cuda()
+    A = full[:, offset:offset + n]  # a strided view when offset = 1 (leading dimension n + 3)
+    X = torch.randn(4, n, generator=gen, dtype=torch.float64)
+    b = torch.randn(m, generator=gen, dtype=torch.float64)
+    Re = tk.tk_residual(A, b.cuda(), X.cuda(), True).cpu().numpy()
+    Ah = A.cpu().double().numpy()
+    Rref = b.numpy().astype(np.longdouble)[None, :] - X.numpy().astype(np.longdouble) @ Ah.astype(np.longdouble).T
+    scale = np.abs(b.numpy())[None, :] + np.abs(X.numpy()) @ np.abs(Ah).T
+    err = float(np.max(np.abs((Re - Rref).astype(np.float64)) / scale))
+    assert err < 8 * 2.0 ** -53 * math.sqrt(n), err
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_emulated_normal_product_has_float64_accuracy(tk, dtype):
     # G = R A (the rows A^T r_l) on the BF16 tensor cores: every column of G within the
