@@ -549,9 +549,9 @@ def test_emulated_residual_has_float64_accuracy(tk, dtype):
     assert err_e <= 4 * err_n + 1e-16, (err_e, err_n)
 
 
-# rows sliced in one pass from registers (padded rows of <= 4096 values: 512, 1024, 2048 and 4096
-# values per CTA pass, 16- or 8-byte pair loads, or element loads for an odd leading dimension or an
-# unaligned base) and by the two-pass route above that (4100 columns)
+# the row exponents and row slices of A across widths (64 to 4100 columns: one to several 512-value
+# column chunks of the slicing grid, ragged against the 64-value padding), rows of very different
+# scale, and A as a strided view (an odd leading dimension, a base not aligned to a pair)
 @pytest.mark.parametrize("m,n,dtype,offset", [(1500, 4096, torch.float64, 0), (700, 4100, torch.float64, 0),
                                               (900, 1025, torch.float32, 1), (333, 2000, torch.float64, 1),
                                               (2000, 64, torch.float32, 0), (50, 511, torch.float64, 0)])
