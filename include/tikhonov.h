@@ -388,8 +388,11 @@ TK_API tk_status tk_lowrank_ranks(const double* sigma, int64_t s, const double* 
  * tensor cores: every row of A (and of X) is scaled by a power of two and
  * split into 8 signed 7-bit integer slices (exact in BF16, 56 bits), the 36
  * slice products whose weight is at least 2^-56 of the row maxima are
- * accumulated exactly in FP32 over chunks of 128 and added into float64;
- * the error is that of a float64 GEMM.
+ * accumulated exactly in FP32 over chunks of 256 values of K and then
+ * exactly in int64, rounded once to float64 per output; the error is at
+ * most that of a float64 GEMM (emulate = 1 requires n <= 2^27, else
+ * TK_EINVAL: the exactness limit of the int64 accumulators; R A is split
+ * along m so that no split holds more than 2^27 rows).
  *   p:   A (device, m x n, row stride lda, float64 or float32) and b (device, m).
  *   X:   device, M x n float64, row stride ldx >= n.
  *   R:   device, M x m float64 (row l = b - A x_l), written.

@@ -1301,6 +1301,7 @@ TK_API tk_status tk_residual(const tk_problem* p, const double* X, int M, int64_
   if (p->m < 1 || p->n < 1 || p->lda < p->n || M < 0 || (M > 0 && ldx < p->n))
     return einval("bad shapes (m, n >= 1, lda >= n, ldx >= n)");
   if (p->dtype != TK_F64 && p->dtype != TK_F32) return einval("unknown dtype");
+  if (emulate && p->n > (int64_t(1) << 27)) return einval("emulate: n above 2^27 (the exact int64 level sums)");
   if (M == 0) return TK_OK;
   if (!work || work_bytes < tk_residual_workspace(p->m, p->n, M)) {
     set_error_msg("workspace smaller than tk_residual_workspace()");

@@ -258,8 +258,9 @@ __global__ void __launch_bounds__(256) k_oz_slice_t(const T* __restrict__ X, int
 // ---- the product on tcgen05 ---------------------------------------------------
 // D[r][l] = sum_k P[r][k] Q[l][k] from the first S digit planes of P (rows x
 // K, row exponents EP) and of Q (M x K, row exponents EQ), both K-major.
-// S = 8: float64 accuracy (levels flushed into float64); S = 4: the 28-bit
-// rounded operands, float32 accuracy (levels flushed into float32).
+// S = 8: float64 accuracy (levels added exactly into int64 accumulators, one
+// rounding at the end); S = 4: the 28-bit rounded operands, float32 accuracy
+// (levels flushed into float32).
 // CTA: 128 rows of P x 32 rows of Q x one K split (blockIdx.z).
 //   warp 0 (one lane): TMA producer -- per 64 values of K the S planes of Q
 //     (4 KiB each) into a 2-slot ring, then the S planes of P one by one
@@ -281,6 +282,7 @@ constexpr int OT_N = 32;
 constexpr int OT_KB = 64;
 constexpr int OT_CHUNK = 256;
 constexpr int OT_KB_PER_CHUNK = OT_CHUNK / OT_KB;
+constexpr int64_t OT_MAX_KPS = int64_t(1) << 27;  // values of K per split that the int64 level sums hold exactly
 constexpr uint32_t OT_P_BYTES = OT_M * OT_KB * 2;   // 16 KiB
 
 // CTA shapes (tensor memory: 2 buffers x S levels x NT columns <= 512):
@@ -574,7 +576,7 @@ tk_status launch_oz_tc(const void* Ps, const int* EP, int64_t rows, int planesP,
   TK_TRY(make_slice_map(&mP, Ps, rows, kp, OT_M, planesP));
   const int64_t kps = cdiv(cdiv(K, splits), OT_CHUNK) * OT_CHUNK;  // whole chunks per split
   const int sp = (int)cdiv(K, kps);
-  if (S == OZ_S && kps > (int64_t(1) << 27)) {  // the exact int64 level accumulators of a split
+  if (S == OZ_S && kps > OT_MAX_KPS) {  // the exact int64 level accumulators of a split
     set_error_msg("emulated product: more than 2^27 values of K in one split");
     return TK_EINVAL;
   }
@@ -1477,7 +1479,7 @@ int oz_normal_splits(int64_t m, int64_t n, int64_t M, int S) {
     }
     if (eff >= 0.97 || sp == maxs) break;
   }
-  return (int)std::max<int64_t>(1, best);
+  return (int)std::max<int64_t>({int64_t(1), best, cdiv(m, OT_MAX_KPS)});  // at most 2^27 values of K per split
 }
 
 tk_status oz_normal(const void* AslicesT, const int* EC, int64_t m, int64_t n, const double* R, int64_t ldr,

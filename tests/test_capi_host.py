@@ -140,6 +140,12 @@ def test_emulated_entry_points_validate_on_host(tk):
     assert need_r >= 8 * 2 * (1000 * 128 + 100 * 1024)
     assert L.tk_residual(C.byref(p), fake, 4, 99, 1, fake, None, fake, need_r, None) == tk.TK_EINVAL  # ldx < n
     assert L.tk_residual(C.byref(p), fake, 4, 100, 1, fake, None, fake, need_r - 1, None) == tk.TK_ENOMEM
+    # rows of more than 2^27 values: beyond what the int64 level sums of one split hold exactly (the
+    # plain float64 form takes them)
+    wide = (1 << 27) + 1
+    pw = _prob(tk, 2, wide)
+    assert L.tk_residual(C.byref(pw), fake, 1, wide, 1, fake, None, fake, 1 << 40, None) == tk.TK_EINVAL
+    assert "2^27" in tk.last_error()
 
 
 def test_warm_start_arguments_checked_on_host(tk):
